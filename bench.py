@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark: DD / QD GEMM 2mnl/s at n = 4096 on one GB300.
+
+One step = one C := A B through the C ABI (dd_gemm) with the headline
+workload: DD Winograd, n = 4096, operands U[-1, 1) with a random lower limb
+(inputs.uniform, seeds fixed in workloads.py). Inputs are resident in HBM
+before the timed region; three 4096^2 DD matrices are 768 MiB, well above
+the 129 MB L2, so no L2 flush is needed between steps.
+
+Printed: one JSON line (rank 0) with the metric, the end-to-end number
+through host buffers, the roofline of the dominant kernel (the Block base
+case, FP64-issue bound), the CPU oracle timed on a bounded sample, clocks
+sampled during the timed region, and extra measurements (DD Block, QD
+Winograd, QD Block at n = 4096).
+
+--impl reference times the CPU oracle (the plain Simple triple loop) on the
+host cores instead, on a bounded sample of the same workload per step.
+
+Multi-GPU: replicas only (one independent product per rank, no exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1510_08642_gb300 import workloads as WL  # noqa: E402
+
+METRIC = "DD/QD GEMM 2mnl/s at n=4096 & % FP64-op roofline; served-request p50/p99 latency"
+UNIT = "G 2mnl/s"
+SM_COUNT = 152
+FP64_PER_CLK_PER_SM = 2          # measured: DFMA throughput probe (profiles/fp64_int8_peaks.md)
+SM_MAX_MHZ = 2070.0               # profiling recipe / MEASURED_PEAKS.json
+FP64_PEAK = SM_COUNT * FP64_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # FP64 instructions per second
+PINNED_MAC_OPS = {2: 27, 4: 218}  # DD / QD multiply then add of the Simple kernel
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default=WL.DD_WINOGRAD_4096.name)
+    p.add_argument("--cutoff", type=int, default=None)
+    p.add_argument("--extras", choices=["all", "none"], default="all")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def workload_by_name(name):
+    for v in vars(WL).values():
+        if isinstance(v, WL.Workload) and v.name == name:
+            return v
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ------------------------------------------------------------- distributed --
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x, device=None):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks --
+class Clocks:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------- CPU leg ----
+def cpu_oracle_rate(w, seconds, seed_rows=8):
+    """Oracle Simple product on host cores over a row sample; 2mnl/s."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1510_08642_gb300 import inputs as I
+    n, limbs = w.n, w.limbs
+    B = I.uniform(n, n, limbs, seed=w.seed_b)
+    A_all = I.uniform(n, n, limbs, seed=w.seed_a)
+    cores = O.threads()
+    r = seed_rows
+    t0 = time.perf_counter()
+    O.gemm_simple(np.ascontiguousarray(A_all[:, :r]), B, nthreads=cores)
+    t_probe = time.perf_counter() - t0
+    rows = int(max(cores, min(n, r * seconds / max(t_probe, 1e-3))))
+    rows = max(cores, (rows // cores) * cores)
+    t0 = time.perf_counter()
+    O.gemm_simple(np.ascontiguousarray(A_all[:, :rows]), B, nthreads=cores)
+    t = time.perf_counter() - t0
+    macs = rows * n * n
+    return {"value": 2.0 * macs / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{'DD' if limbs == 2 else 'QD'} Simple (Eq. 1 triple loop, pinned op order) "
+                      f"rows 0..{rows - 1} of the n={n} product ({rows}x{n}x{n} multiply-adds), "
+                      f"{t:.1f} s on {cores} threads"}
+
+
+def run_reference(args, w):
+    world, rank, local, dist = dist_init(args.gpus)
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle as O
+    from paper_1510_08642_gb300 import inputs as I
+    n, limbs = w.n, w.limbs
+    B = I.uniform(n, n, limbs, seed=w.seed_b)
+    A = I.uniform(n, n, limbs, seed=w.seed_a)
+    cores = O.threads()
+    # size one step to ~ (a few minutes / (K + W)) of work
+    budget = max(2.0, min(20.0, 150.0 / (args.steps + args.warmup)))
+    t0 = time.perf_counter()
+    O.gemm_simple(np.ascontiguousarray(A[:, :cores]), B, nthreads=cores)
+    t_probe = time.perf_counter() - t0
+    rows = int(max(cores, min(n, cores * budget / max(t_probe, 1e-3))))
+    rows = max(cores, (rows // cores) * cores)
+    Ar = np.ascontiguousarray(A[:, :rows])
+    for _ in range(args.warmup):
+        O.gemm_simple(Ar, B, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.gemm_simple(Ar, B, nthreads=cores)
+    t = (time.perf_counter() - t0) / args.steps
+    v = 2.0 * rows * n * n / t / 1e9
+    sample = (f"{'DD' if limbs == 2 else 'QD'} Simple oracle, rows 0..{rows - 1} of the n={n} "
+              f"product per step ({rows}x{n}x{n} multiply-adds)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n": n, "limbs": limbs, "algo": "simple (CPU oracle)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU leg --
+def roofline_of(prof, limbs):
+    """Dominant kernel (Block base case): FP64 instructions per busy second."""
+    b = prof["block"]
+    if not b["launches"]:
+        return None
+    achieved = b["fp64_ops"] / (b["busy_ms"] * 1e-3)
+    avg_ms = b["sum_ms"] / b["launches"]
+    ops_mac = {2: 12, 4: 113}[limbs]
+    return {"bound": "alu", "kernel": f"block_kernel<{limbs}> (FP64 pipe)",
+            "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "T FP64-instr/s",
+            "frac": achieved / FP64_PEAK, "traffic": None,
+            "peak_source": f"derived: {SM_COUNT} SMs x {FP64_PER_CLK_PER_SM} FP64 instr/clk (measured "
+                           f"by the DFMA probe) x {SM_MAX_MHZ:.0f} MHz; no FP64 figure in MEASURED_PEAKS.json",
+            "fp64_ops_per_mac": ops_mac, "pinned_mac_ops": PINNED_MAC_OPS[limbs],
+            "launches": int(b["launches"]), "avg_launch_ms": avg_ms, "busy_ms": b["busy_ms"],
+            "sum_launch_ms": b["sum_ms"]}
+
+
+def time_gpu(P, torch, w, dA, dB, dC, cutoff, steps, warmup, stream, dist=None, device=None,
+             profile=True):
+    from paper_1510_08642_gb300 import capi
+    kw = dict(algo=w.algo, cutoff=cutoff)
+    for _ in range(warmup):
+        P.gemm(dA, dB, dC, **kw)
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    launches0 = capi.ddg_kernel_launches()
+    if profile:
+        capi.ddg_profile_begin()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        P.gemm(dA, dB, dC, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    prof = capi.ddg_profile_end() if profile else None
+    launches = capi.ddg_kernel_launches() - launches0
+    ms = e0.elapsed_time(e1) / steps
+    ms = max_over_ranks(dist, ms, device)
+    return ms, prof, launches
+
+
+def run_ours(args, w):
+    import numpy as np
+    import torch
+
+    world, rank, local, dist = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import paper_1510_08642_gb300 as P
+    from paper_1510_08642_gb300 import capi, inputs as I
+    capi.load()
+    cutoff = args.cutoff or w.cutoff
+    n, limbs = w.n, w.limbs
+    A = I.uniform(n, n, limbs, seed=w.seed_a)
+    B = I.uniform(n, n, limbs, seed=w.seed_b)
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.empty((limbs, n, n), dtype=torch.float64).pin_memory()
+    dA = hA.to(device)
+    dB = hB.to(device)
+    dC = torch.empty((limbs, n, n), dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    clocks = Clocks(local)
+    # -------- timed region: device-resident inputs
+    for _ in range(args.warmup):
+        P.gemm(dA, dB, dC, algo=w.algo, cutoff=cutoff)
+    torch.cuda.synchronize()
+    clocks.start()
+    ms, prof, launches = time_gpu(P, torch, w, dA, dB, dC, cutoff, args.steps, 0, stream, dist, device)
+    clk = clocks.stop()
+    macs = w.macs
+    value = world * 2.0 * macs / (ms * 1e-3) / 1e9
+
+    # -------- end to end through host buffers (copies inside the timed region)
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dA.copy_(hA, non_blocking=True)
+        dB.copy_(hB, non_blocking=True)
+        P.gemm(dA, dB, dC, algo=w.algo, cutoff=cutoff)
+        hC.copy_(dC, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    ms_e2e = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps, device)
+    e2e = {"value": world * 2.0 * macs / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
+           "d2h_bytes_per_step": int(hC.numel() * 8), "ms_per_step": ms_e2e}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": n, "limbs": limbs, "algo": w.algo, "cutoff": cutoff,
+                       "streams": 7, "distribution": "uniform: hi U[-1,1), lo hi*2^-53*U[-1/2,1/2)",
+                       "l2": "no flush: A, B, C resident are 768 MiB (DD) > 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches)}
+    line["roofline"] = roofline_of(prof, limbs)
+    line["fp64_roofline_2mnl"] = {
+        "value": 2.0 * FP64_PEAK / PINNED_MAC_OPS[limbs] / 1e9,
+        "frac": value / world / (2.0 * FP64_PEAK / PINNED_MAC_OPS[limbs] / 1e9),
+        "note": "2 x FP64 peak / FP64 instructions of the pinned DD multiply-add (27)"}
+    passes = prof["pass"]
+    if passes["launches"]:
+        line["passes"] = {"launches": int(passes["launches"]), "busy_ms": passes["busy_ms"] / args.steps,
+                          "GB_per_s": passes["bytes"] / (passes["busy_ms"] * 1e-3) / 1e9,
+                          "fp64_frac": passes["fp64_ops"] / (passes["busy_ms"] * 1e-3) / FP64_PEAK}
+    del dA, dB, dC, hA, hB, hC
+    torch.cuda.empty_cache()
+
+    # -------- extras (rank 0 of a single-GPU run only; 1 warm-up, 1 timed)
+    if args.extras == "all" and world == 1 and w.name == WL.DD_WINOGRAD_4096.name:
+        extras = {}
+        for xw in (WL.DD_BLOCK_4096, WL.QD_WINOGRAD_4096, WL.QD_BLOCK_4096):
+            XA = torch.from_numpy(I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_a)).to(device)
+            XB = torch.from_numpy(I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_b)).to(device)
+            XC = torch.empty((xw.limbs, xw.n, xw.n), dtype=torch.float64, device=device)
+            xms, xprof, _ = time_gpu(P, torch, xw, XA, XB, XC, xw.cutoff, 1, 1, stream)
+            extras[xw.name] = {"value": 2.0 * xw.macs / (xms * 1e-3) / 1e9, "unit": UNIT, "ms": xms,
+                               "roofline": roofline_of(xprof, xw.limbs), "steps": 1, "warmup": 1}
+            del XA, XB, XC
+            torch.cuda.empty_cache()
+        line["extras"] = extras
+
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_oracle_rate(w, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    w = workload_by_name(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,145 @@
+/*
+ * ddgemm: double-double (DD, 106-bit) and quad-double (QD, 212-bit) dense
+ * matrix products and LU solves on one GB300 GPU (sm_103a).
+ *
+ * The operations are those of T. Kouya, "Performance evaluation of multiple
+ * precision matrix multiplications using parallelized Strassen and Winograd
+ * algorithms" (2015):
+ *   - C := A B of any m x l x n (Section 2, Eq. 1) by the Simple, Block,
+ *     Strassen and Winograd algorithms (Section 2; Section 3 names the
+ *     recursion cutoff n_min, at which the self-recursive call stops);
+ *   - LU decomposition whose trailing update A22 := A22 - L21 U12 is such a
+ *     product (Section 4, steps 1-3), and the solution of A x = b (Eq. 2).
+ *
+ * Conventions for every entry point
+ *   - A DD matrix is two row-major planes of doubles in device memory (hi and
+ *     lo), a QD matrix four (x[0] leading .. x[3]); element (i, j) of plane p
+ *     is p[i * ld + j], with ld >= number of columns (ld >= 1). The value of
+ *     an entry is the exact sum of its limbs; inputs are expected normalised
+ *     (|lo| <= ulp(hi)/2, and likewise between QD limbs); non-finite values
+ *     give undefined results (they are not checked).
+ *   - The caller owns all matrices. The library owns nothing it returns:
+ *     temporary storage for a call is taken from the CUDA stream-ordered
+ *     allocator on the call's stream and released on it before the call's
+ *     work completes.
+ *   - Calls are asynchronous with respect to the host: work is queued on
+ *     `stream` (a cudaStream_t, NULL = the legacy default stream) and may
+ *     fork onto library-owned streams that join back into `stream`. Results
+ *     are ready when `stream` reaches the point after the call.
+ *   - Errors are returned as a status code, never by aborting; a
+ *     human-readable message for the last failing call on the calling host
+ *     thread is available from ddg_last_error(). A status other than DDG_OK
+ *     means that no work, or not all of it, was queued.
+ *   - Sizes of zero are valid and queue nothing (C := A B with l = 0 writes
+ *     zeros for mode DDG_SET). Negative sizes, ld smaller than the column
+ *     count, null planes of a non-empty matrix and C overlapping A or B are
+ *     DDG_EINVAL.
+ */
+#ifndef DDGEMM_H
+#define DDGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DDG_OK = 0,
+  DDG_EINVAL = 1,    /* invalid argument */
+  DDG_ENOMEM = 2,    /* device memory for temporaries could not be had */
+  DDG_ECUDA = 3,     /* a CUDA call failed; see ddg_last_error() */
+  DDG_ESINGULAR = 4, /* LU: an exactly zero pivot */
+  DDG_ETIMEOUT = 5,  /* a bounded device-side wait ran out */
+  DDG_ENOTSUP = 6    /* combination not supported */
+} ddg_status;
+
+/* Section 2: the four algorithms the paper compares. */
+typedef enum {
+  DDG_SIMPLE = 0,   /* Eq. 1, one thread per c_ij, k ascending: bit-exact
+                       reference order (the DD/QD multiply then add of each
+                       term is the pinned sequence documented with the
+                       kernels) */
+  DDG_BLOCK = 1,    /* C_ij = sum_k A_ik B_kj over register/shared tiles */
+  DDG_STRASSEN = 2, /* Strassen 1969: 7 products, 18 quadrant sums per level */
+  DDG_WINOGRAD = 3  /* Winograd's variant: 7 products, 15 quadrant sums */
+} ddg_algo;
+
+/* How C is written: C := A B, C := C + A B or C := C - A B. */
+typedef enum { DDG_SET = 0, DDG_ADD = 1, DDG_SUB = 2 } ddg_mode;
+
+typedef struct {
+  double* hi;
+  double* lo;
+  int64_t ld;
+} dd_mat;
+
+typedef struct {
+  double* x[4];
+  int64_t ld;
+} qd_mat;
+
+typedef struct {
+  int32_t algo;    /* ddg_algo */
+  int32_t cutoff;  /* n_min (Section 3): a Strassen/Winograd level splits the
+                      problem while min(m, l, n) > cutoff; >= 1 */
+  int32_t pad;     /* odd dimensions: 0 = peel the last row/column and fix up
+                      with Block products (default), 1 = zero-pad to a
+                      multiple of 2^depth before recursing */
+  int32_t streams; /* 1 = the 7 sub-products of the top level run in order on
+                      `stream`; 7 (default, also for 0) = on 7 concurrent
+                      streams (the paper's 7 OpenMP sections, Figs. 1-2) */
+  int32_t reserved[4]; /* must be zero */
+} ddg_opts;
+
+/* Fill *opts with the defaults: Winograd, cutoff 512, peeling, 7 streams. */
+void ddg_opts_default(ddg_opts* opts);
+
+/*
+ * dd_gemm: C (mode) A B in double-double, A m x l, B l x n, C m x n.
+ * opts NULL = defaults. Accuracy: DDG_SIMPLE follows the pinned sequence
+ * exactly; DDG_BLOCK stays within |C - C^| <= (l + 4) 2^-106 |A||B|
+ * elementwise; Strassen/Winograd within the normwise bound
+ * 8 l^log2(12) 2^-104 ||A|| ||B||.
+ */
+ddg_status dd_gemm(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, dd_mat C, int32_t mode,
+                   const ddg_opts* opts, void* stream);
+
+/* qd_gemm: as dd_gemm for quad-double (2^-208 in place of 2^-104). */
+ddg_status qd_gemm(int64_t m, int64_t l, int64_t n, qd_mat A, qd_mat B, qd_mat C, int32_t mode,
+                   const ddg_opts* opts, void* stream);
+
+/* FP64 instructions per DD (limbs = 2) or QD (limbs = 4) multiply-add in
+ * the Block kernel's inner loop, counted from its source (for rooflines). */
+int32_t ddg_block_fp64_ops_per_mac(int32_t limbs);
+
+/* Launch profiling. Between ddg_profile_begin() and ddg_profile_end() every
+ * kernel launch of the library is bracketed by CUDA events on its stream.
+ * ddg_profile_end() waits for those events and fills out[k] for kernel
+ * kinds k = 0 (Simple), 1 (Block), 2 (quadrant passes), k < nkinds:
+ * launches, sum of launch durations, busy time (union of the launch
+ * intervals), and algorithmic FP64 instructions and bytes of those launches.
+ * For measurement only: it adds two event records per launch. */
+typedef struct {
+  uint64_t launches;
+  double sum_ms;
+  double busy_ms;
+  double fp64_ops;
+  double bytes;
+} ddg_kernel_prof;
+ddg_status ddg_profile_begin(void);
+ddg_status ddg_profile_end(ddg_kernel_prof* out, int32_t nkinds);
+
+/* Number of CUDA kernels this library has launched in this process, all
+ * threads and devices together (monotonic; for launch accounting). */
+uint64_t ddg_kernel_launches(void);
+
+/* Message describing the last failure on this host thread ("" if none). */
+const char* ddg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDGEMM_H */

@@ -1,0 +1,51 @@
+"""DD / QD matrix products and LU on one GB300 (Kouya 2015, GB300-native).
+
+The compute path is the CUDA library libddgemm.so (C ABI: include/ddgemm.h).
+This package holds its build script (build.py), the ctypes binding
+(capi.py), thin torch helpers below that pass device pointers of torch
+tensors through the C ABI, and the seeded input generator (inputs.py).
+
+A DD matrix is a float64 tensor of shape (2, rows, cols) (planes hi, lo), a
+QD matrix one of shape (4, rows, cols); planes must be row-contiguous.
+"""
+from __future__ import annotations
+
+from . import capi
+
+
+def _mat(T, limbs: int):
+    assert T.dtype.is_floating_point and T.element_size() == 8, "float64 planes expected"
+    assert T.dim() == 3 and T.shape[0] == limbs, f"expected shape ({limbs}, rows, cols)"
+    assert T.is_cuda, "device tensor expected"
+    assert T.stride(2) == 1, "rows must be contiguous"
+    ld = T.stride(1)
+    ps = T.stride(0)
+    base = T.data_ptr()
+    ptrs = [base + q * ps * 8 for q in range(limbs)]
+    if limbs == 2:
+        return capi.dd_mat(ptrs[0], ptrs[1], max(ld, 1))
+    m = capi.qd_mat()
+    for q in range(4):
+        m.x[q] = ptrs[q]
+    m.ld = max(ld, 1)
+    return m
+
+
+def gemm(A, B, C=None, algo: str = "winograd", cutoff: int = 512, mode: str = "set",
+         pad: bool = False, streams: int = 7, stream=None):
+    """C (mode) A B through dd_gemm / qd_gemm on the current CUDA stream.
+
+    A: (limbs, m, l), B: (limbs, l, n), C: (limbs, m, n) or None (allocated).
+    limbs = 2 (DD) or 4 (QD). Returns C.
+    """
+    import torch
+
+    limbs, m, l = A.shape
+    n = B.shape[2]
+    if C is None:
+        C = torch.empty((limbs, m, n), dtype=torch.float64, device=A.device)
+    o = capi.opts(algo, cutoff, pad, streams)
+    s = (stream or torch.cuda.current_stream(A.device)).cuda_stream
+    fn = capi.dd_gemm if limbs == 2 else capi.qd_gemm
+    capi.check(fn(m, l, n, _mat(A, limbs), _mat(B, limbs), _mat(C, limbs), capi.MODES[mode], o, s))
+    return C

@@ -1,0 +1,139 @@
+"""ctypes binding of the C ABI in include/ddgemm.h (argument marshalling only).
+
+Every step of a product runs in the CUDA library libddgemm.so; this module
+only converts Python arguments to the C structures. There is no fallback:
+if the library is missing or fails to load, calls raise.
+
+Names follow the header: dd_gemm, qd_gemm, ddg_opts_default, ddg_last_error,
+ddg_block_fp64_ops_per_mac; the structures dd_mat, qd_mat and ddg_opts.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_i32, c_i64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+
+DDG_OK, DDG_EINVAL, DDG_ENOMEM, DDG_ECUDA, DDG_ESINGULAR, DDG_ETIMEOUT, DDG_ENOTSUP = range(7)
+STATUS_NAMES = ["DDG_OK", "DDG_EINVAL", "DDG_ENOMEM", "DDG_ECUDA", "DDG_ESINGULAR",
+                "DDG_ETIMEOUT", "DDG_ENOTSUP"]
+DDG_SIMPLE, DDG_BLOCK, DDG_STRASSEN, DDG_WINOGRAD = range(4)
+ALGOS = {"simple": DDG_SIMPLE, "block": DDG_BLOCK, "strassen": DDG_STRASSEN,
+         "winograd": DDG_WINOGRAD}
+DDG_SET, DDG_ADD, DDG_SUB = range(3)
+MODES = {"set": DDG_SET, "add": DDG_ADD, "sub": DDG_SUB}
+
+
+class dd_mat(ctypes.Structure):
+    _fields_ = [("hi", c_vp), ("lo", c_vp), ("ld", c_i64)]
+
+
+class qd_mat(ctypes.Structure):
+    _fields_ = [("x", c_vp * 4), ("ld", c_i64)]
+
+
+class ddg_opts(ctypes.Structure):
+    _fields_ = [("algo", c_i32), ("cutoff", c_i32), ("pad", c_i32), ("streams", c_i32),
+                ("reserved", c_i32 * 4)]
+
+
+class ddg_kernel_prof(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("sum_ms", ctypes.c_double),
+                ("busy_ms", ctypes.c_double), ("fp64_ops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+PROF_KINDS = ("simple", "block", "pass")
+
+
+class DDGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+        self.status = status
+
+
+# Every exported symbol and its ctypes signature (restype, argtypes).
+SIGNATURES = {
+    "ddg_opts_default": (None, [ctypes.POINTER(ddg_opts)]),
+    "dd_gemm": (c_i32, [c_i64, c_i64, c_i64, dd_mat, dd_mat, dd_mat, c_i32,
+                        ctypes.POINTER(ddg_opts), c_vp]),
+    "qd_gemm": (c_i32, [c_i64, c_i64, c_i64, qd_mat, qd_mat, qd_mat, c_i32,
+                        ctypes.POINTER(ddg_opts), c_vp]),
+    "ddg_block_fp64_ops_per_mac": (c_i32, [c_i32]),
+    "ddg_last_error": (ctypes.c_char_p, []),
+    "ddg_kernel_launches": (ctypes.c_uint64, []),
+    "ddg_profile_begin": (c_i32, []),
+    "ddg_profile_end": (c_i32, [ctypes.POINTER(ddg_kernel_prof), c_i32]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libddgemm.so (building it first if absent); raises if impossible."""
+    global _lib
+    if _lib is None:
+        p = path or _build.LIB_PATH
+        if not os.path.exists(p):
+            _build.build()
+        L = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return load().ddg_last_error().decode()
+
+
+def check(status: int) -> None:
+    if status != DDG_OK:
+        raise DDGError(status, last_error())
+
+
+def opts(algo="winograd", cutoff: int = 512, pad: bool = False, streams: int = 7) -> ddg_opts:
+    o = ddg_opts()
+    load().ddg_opts_default(ctypes.byref(o))
+    o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    o.cutoff = int(cutoff)
+    o.pad = 1 if pad else 0
+    o.streams = int(streams)
+    return o
+
+
+def dd_gemm(m, l, n, A: dd_mat, B: dd_mat, C: dd_mat, mode: int, o: ddg_opts | None,
+            stream: int = 0) -> int:
+    return load().dd_gemm(m, l, n, A, B, C, mode, ctypes.byref(o) if o is not None else None,
+                          c_vp(stream))
+
+
+def qd_gemm(m, l, n, A: qd_mat, B: qd_mat, C: qd_mat, mode: int, o: ddg_opts | None,
+            stream: int = 0) -> int:
+    return load().qd_gemm(m, l, n, A, B, C, mode, ctypes.byref(o) if o is not None else None,
+                          c_vp(stream))
+
+
+def ddg_block_fp64_ops_per_mac(limbs: int) -> int:
+    return load().ddg_block_fp64_ops_per_mac(limbs)
+
+
+def ddg_kernel_launches() -> int:
+    return load().ddg_kernel_launches()
+
+
+def ddg_profile_begin() -> None:
+    check(load().ddg_profile_begin())
+
+
+def ddg_profile_end() -> dict:
+    """Per kernel kind: launches, sum_ms, busy_ms, fp64_ops, bytes."""
+    arr = (ddg_kernel_prof * len(PROF_KINDS))()
+    check(load().ddg_profile_end(arr, len(PROF_KINDS)))
+    return {k: {f: getattr(arr[i], f) for f, _ in ddg_kernel_prof._fields_}
+            for i, k in enumerate(PROF_KINDS)}

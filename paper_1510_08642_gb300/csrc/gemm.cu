@@ -1,0 +1,371 @@
+// C-ABI entry points dd_gemm / qd_gemm and the Strassen / Winograd recursion
+// (Kouya 2015, Section 2 and Figs. 1-2; Section 3 for n_min).
+//
+// Recursion. A level splits A (m x l), B (l x n) and C into quadrants while
+// min(m, l, n) > cutoff. One fused pass forms the left operands of the seven
+// sub-products, one the right operands, the seven products recurse, and one
+// fused pass combines them into C (passes.cu). The paper runs the seven
+// sub-products of a level in seven OpenMP sections; here the seven products
+// of the top level are forked onto seven CUDA streams (event fork/join on the
+// caller's stream), and each stream runs its sub-tree depth-first, which keeps
+// 7x more thread blocks in flight than one product alone when the recursion
+// reaches small base cases.
+//
+// Odd sizes (the paper measures n = 1023 and 1025 but does not say how they
+// are handled). Default: peel. The even leading part recurses; the last
+// column of A / row of B (odd l) is added by a rank-1 Block product, the last
+// column of C (odd n) and the last row (odd m) are Block products. Option
+// pad = 1: copy A, B (and C) into zero-padded buffers whose sizes are
+// multiples of 2^depth, recurse, copy the result back.
+//
+// Temporaries. Sizes are planned by a dry run of the same recursion, then one
+// block is taken from the stream-ordered allocator. Each fork branch has a
+// stack of its own: nodes below the top level run in stream order, so a
+// node's temporaries are reused by its next sibling. Total for a square n:
+// about 15 (n/2)^2 (1 + 7/3) DD/QD entries.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "ddgemm.h"
+#include "kernels.cuh"
+
+namespace ddg {
+
+std::atomic<uint64_t> g_launches{0};
+static thread_local std::string g_err;
+
+static ddg_status fail(ddg_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define DDG_CUDA(x)                                                                      \
+  do {                                                                                   \
+    cudaError_t e_ = (x);                                                                \
+    if (e_ != cudaSuccess) return fail(DDG_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define DDG_TRY(x)                       \
+  do {                                   \
+    ddg_status s_ = (x);                 \
+    if (s_ != DDG_OK) return s_;         \
+  } while (0)
+
+// ------------------------------------------------------------ stream pool --
+static constexpr int kMaxDev = 64;
+static std::mutex g_pool_mu;
+static bool g_pool_init[kMaxDev];
+static cudaStream_t g_pool[kMaxDev][7];
+
+static ddg_status stream_pool(cudaStream_t** out) {
+  int dev = 0;
+  DDG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) return fail(DDG_ENOTSUP, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool_init[dev]) {
+    for (int i = 0; i < 7; ++i)
+      DDG_CUDA(cudaStreamCreateWithFlags(&g_pool[dev][i], cudaStreamNonBlocking));
+    g_pool_init[dev] = true;
+  }
+  *out = g_pool[dev];
+  return DDG_OK;
+}
+
+// ------------------------------------------------------------- recursion --
+static inline size_t plane_bytes(int64_t rows, int64_t cols) {
+  size_t b = (size_t)rows * (size_t)cols * sizeof(double);
+  return (b + 255) & ~(size_t)255;
+}
+
+struct Ctx {
+  int L = 2;
+  int algo = DDG_WINOGRAD;
+  int cutoff = 512;
+  int nstreams = 7;
+  bool dry = true;
+  char* base = nullptr;
+  size_t region_off[8] = {0};
+  size_t peak[8] = {0};
+  cudaStream_t* pool = nullptr;
+};
+
+static mat alloc_mat(Ctx& c, int region, size_t& sp, int64_t rows, int64_t cols) {
+  mat M{};
+  M.ld = std::max<int64_t>(cols, 1);
+  for (int q = 0; q < c.L; ++q) {
+    if (!c.dry) M.p[q] = reinterpret_cast<double*>(c.base + c.region_off[region] + sp);
+    sp += plane_bytes(rows, cols);
+  }
+  c.peak[region] = std::max(c.peak[region], sp);
+  return M;
+}
+
+static ddg_status zero_mat(const Ctx& c, const mat& M, int64_t rows, int64_t cols, cudaStream_t s) {
+  for (int q = 0; q < c.L; ++q)
+    DDG_CUDA(cudaMemset2DAsync(M.p[q], M.ld * sizeof(double), 0, cols * sizeof(double), rows, s));
+  return DDG_OK;
+}
+
+static ddg_status copy_mat(const Ctx& c, const mat& dst, const mat& src, int64_t rows, int64_t cols,
+                           cudaStream_t s) {
+  for (int q = 0; q < c.L; ++q)
+    DDG_CUDA(cudaMemcpy2DAsync(dst.p[q], dst.ld * sizeof(double), src.p[q], src.ld * sizeof(double),
+                               cols * sizeof(double), rows, cudaMemcpyDeviceToDevice, s));
+  return DDG_OK;
+}
+
+static bool splits(const Ctx& c, int64_t m, int64_t l, int64_t n) {
+  if (c.algo != DDG_STRASSEN && c.algo != DDG_WINOGRAD) return false;
+  const int64_t mn = std::min(m, std::min(l, n));
+  return mn >= 2 && mn > c.cutoff;
+}
+
+static ddg_status rec(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
+                      const mat& C, int mode, cudaStream_t s, int region, size_t sp, int depth);
+
+// One recursion level on even m, l, n.
+static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
+                        const mat& C, int mode, cudaStream_t s, int region, size_t sp, int depth) {
+  const int64_t h = m / 2, k = l / 2, w = n / 2;
+  const mat A11 = view(A, 0, 0), A12 = view(A, 0, k), A21 = view(A, h, 0), A22 = view(A, h, k);
+  const mat B11 = view(B, 0, 0), B12 = view(B, 0, w), B21 = view(B, k, 0), B22 = view(B, k, w);
+  const mat C11 = view(C, 0, 0), C12 = view(C, 0, w), C21 = view(C, h, 0), C22 = view(C, h, w);
+  const bool win = c.algo == DDG_WINOGRAD;
+  const int nl = win ? 4 : 5;  // left / right operand temporaries
+  mat SL[5], SR[5], P[7];
+  for (int i = 0; i < nl; ++i) SL[i] = alloc_mat(c, region, sp, h, k);
+  for (int i = 0; i < nl; ++i) SR[i] = alloc_mat(c, region, sp, k, w);
+  for (int i = 0; i < 7; ++i) P[i] = alloc_mat(c, region, sp, h, w);
+
+  if (!c.dry) {
+    const mat qa[4] = {A11, A12, A21, A22};
+    const mat qb[4] = {B11, B12, B21, B22};
+    DDG_CUDA(launch_pass(c.L, win ? PASS_WINOGRAD_A : PASS_STRASSEN_A, h, k, qa, 4, SL, nl, MODE_SET, s));
+    DDG_CUDA(launch_pass(c.L, win ? PASS_WINOGRAD_B : PASS_STRASSEN_B, k, w, qb, 4, SR, nl, MODE_SET, s));
+  }
+  // the seven sub-products
+  mat lhs[7], rhs[7];
+  if (win) {  // P1 = A11 B11, P2 = A12 B21, P3 = S4 B22, P4 = A22 T4, P5 = S1 T1, P6 = S2 T2, P7 = S3 T3
+    const mat L_[7] = {A11, A12, SL[3], A22, SL[0], SL[1], SL[2]};
+    const mat R_[7] = {B11, B21, B22, SR[3], SR[0], SR[1], SR[2]};
+    for (int i = 0; i < 7; ++i) { lhs[i] = L_[i]; rhs[i] = R_[i]; }
+  } else {  // M1..M7 of Strassen 1969
+    const mat L_[7] = {SL[0], SL[1], A11, A22, SL[2], SL[3], SL[4]};
+    const mat R_[7] = {SR[0], B11, SR[1], SR[2], B22, SR[3], SR[4]};
+    for (int i = 0; i < 7; ++i) { lhs[i] = L_[i]; rhs[i] = R_[i]; }
+  }
+  const bool fork = depth == 0 && c.nstreams == 7;
+  if (fork) {
+    cudaEvent_t ev_fork = nullptr, ev_join[7] = {nullptr};
+    if (!c.dry) {
+      DDG_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+      DDG_CUDA(cudaEventRecord(ev_fork, s));
+    }
+    for (int i = 0; i < 7; ++i) {
+      cudaStream_t cs = c.dry ? s : c.pool[i];
+      if (!c.dry) DDG_CUDA(cudaStreamWaitEvent(cs, ev_fork, 0));
+      DDG_TRY(rec(c, h, k, w, lhs[i], rhs[i], P[i], MODE_SET, cs, 1 + i, 0, depth + 1));
+      if (!c.dry) {
+        DDG_CUDA(cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming));
+        DDG_CUDA(cudaEventRecord(ev_join[i], cs));
+        DDG_CUDA(cudaStreamWaitEvent(s, ev_join[i], 0));
+      }
+    }
+    if (!c.dry) {
+      DDG_CUDA(cudaEventDestroy(ev_fork));
+      for (int i = 0; i < 7; ++i) DDG_CUDA(cudaEventDestroy(ev_join[i]));
+    }
+  } else {
+    for (int i = 0; i < 7; ++i)
+      DDG_TRY(rec(c, h, k, w, lhs[i], rhs[i], P[i], MODE_SET, s, region, sp, depth + 1));
+  }
+  if (!c.dry) {
+    const mat qc[4] = {C11, C12, C21, C22};
+    DDG_CUDA(launch_pass(c.L, win ? PASS_WINOGRAD_C : PASS_STRASSEN_C, h, w, P, 7, qc, 4, mode, s));
+  }
+  return DDG_OK;
+}
+
+static ddg_status rec(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
+                      const mat& C, int mode, cudaStream_t s, int region, size_t sp, int depth) {
+  if (m == 0 || n == 0) return DDG_OK;
+  if (l == 0) return (mode == MODE_SET && !c.dry) ? zero_mat(c, C, m, n, s) : DDG_OK;
+  if (!splits(c, m, l, n)) {
+    if (!c.dry) DDG_CUDA(launch_block(c.L, m, l, n, A, B, C, mode, s));
+    return DDG_OK;
+  }
+  const int64_t m2 = m & ~int64_t(1), l2 = l & ~int64_t(1), n2 = n & ~int64_t(1);
+  DDG_TRY(level(c, m2, l2, n2, A, B, C, mode, s, region, sp, depth));
+  if (!c.dry) {
+    if (l2 != l)  // C[:m2, :n2] (+/-)= A[:m2, l2] B[l2, :n2]
+      DDG_CUDA(launch_block(c.L, m2, 1, n2, view(A, 0, l2), view(B, l2, 0), C,
+                            mode == MODE_SUB ? MODE_SUB : MODE_ADD, s));
+    if (n2 != n)
+      DDG_CUDA(launch_block(c.L, m2, l, 1, A, view(B, 0, n2), view(C, 0, n2), mode, s));
+    if (m2 != m)
+      DDG_CUDA(launch_block(c.L, 1, l, n, view(A, m2, 0), B, view(C, m2, 0), mode, s));
+  }
+  return DDG_OK;
+}
+
+// Top level: optional padding around the recursion.
+static ddg_status top(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
+                      const mat& C, int mode, bool pad, cudaStream_t s) {
+  if (!pad || !splits(c, m, l, n)) return rec(c, m, l, n, A, B, C, mode, s, 0, 0, 0);
+  int depth = 0;
+  for (int64_t t = std::min(m, std::min(l, n)); t >= 2 && t > c.cutoff; t = (t + 1) / 2) ++depth;
+  const int64_t mult = int64_t(1) << depth;
+  auto up = [&](int64_t x) { return (x + mult - 1) / mult * mult; };
+  const int64_t mp = up(m), lp = up(l), np = up(n);
+  if (mp == m && lp == l && np == n) return rec(c, m, l, n, A, B, C, mode, s, 0, 0, 0);
+  size_t sp = 0;
+  mat Ap = alloc_mat(c, 0, sp, mp, lp), Bp = alloc_mat(c, 0, sp, lp, np), Cp = alloc_mat(c, 0, sp, mp, np);
+  if (!c.dry) {
+    DDG_TRY(zero_mat(c, Ap, mp, lp, s));
+    DDG_TRY(zero_mat(c, Bp, lp, np, s));
+    DDG_TRY(copy_mat(c, Ap, A, m, l, s));
+    DDG_TRY(copy_mat(c, Bp, B, l, n, s));
+    if (mode != MODE_SET) DDG_TRY(copy_mat(c, Cp, C, m, n, s));
+  }
+  DDG_TRY(rec(c, mp, lp, np, Ap, Bp, Cp, mode, s, 0, sp, 0));
+  if (!c.dry) DDG_TRY(copy_mat(c, C, Cp, m, n, s));
+  return DDG_OK;
+}
+
+// ----------------------------------------------------------- validation --
+static bool bad_mat(int L, const mat& M, int64_t rows, int64_t cols, const char* name,
+                    std::string& why) {
+  if (rows == 0 || cols == 0) return false;
+  if (M.ld < cols || M.ld < 1) {
+    why = std::string(name) + ": ld smaller than the column count";
+    return true;
+  }
+  for (int q = 0; q < L; ++q)
+    if (!M.p[q]) {
+      why = std::string(name) + ": null limb plane";
+      return true;
+    }
+  return false;
+}
+
+static bool overlaps(int L, const mat& X, int64_t xr, int64_t xc, const mat& Y, int64_t yr, int64_t yc) {
+  if (xr == 0 || xc == 0 || yr == 0 || yc == 0) return false;
+  for (int p = 0; p < L; ++p)
+    for (int q = 0; q < L; ++q) {
+      const char* x0 = reinterpret_cast<const char*>(X.p[p]);
+      const char* x1 = reinterpret_cast<const char*>(X.p[p] + (xr - 1) * X.ld + xc);
+      const char* y0 = reinterpret_cast<const char*>(Y.p[q]);
+      const char* y1 = reinterpret_cast<const char*>(Y.p[q] + (yr - 1) * Y.ld + yc);
+      if (x0 < y1 && y0 < x1) return true;
+    }
+  return false;
+}
+
+static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
+                             const mat& C, int mode, const ddg_opts* opts, void* stream) {
+  g_err.clear();
+  ddg_opts o;
+  ddg_opts_default(&o);
+  if (opts) o = *opts;
+  if (m < 0 || l < 0 || n < 0) return fail(DDG_EINVAL, "negative size");
+  if (mode < DDG_SET || mode > DDG_SUB) return fail(DDG_EINVAL, "mode must be DDG_SET, DDG_ADD or DDG_SUB");
+  if (o.algo < DDG_SIMPLE || o.algo > DDG_WINOGRAD) return fail(DDG_EINVAL, "unknown algo");
+  if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
+  if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
+  if (o.streams != 0 && o.streams != 1 && o.streams != 7) return fail(DDG_EINVAL, "streams must be 0, 1 or 7");
+  for (int i = 0; i < 4; ++i)
+    if (o.reserved[i] != 0) return fail(DDG_EINVAL, "reserved option fields must be zero");
+  std::string why;
+  if (bad_mat(L, A, m, l, "A", why) || bad_mat(L, B, l, n, "B", why) || bad_mat(L, C, m, n, "C", why))
+    return fail(DDG_EINVAL, why);
+  if (overlaps(L, C, m, n, A, m, l) || overlaps(L, C, m, n, B, l, n))
+    return fail(DDG_EINVAL, "C overlaps A or B");
+  if (m > (int64_t)65535 * 8 || n > ((int64_t)1 << 36)) return fail(DDG_EINVAL, "matrix too large");
+  if (m == 0 || n == 0) return DDG_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+  if (o.algo == DDG_SIMPLE) {
+    DDG_CUDA(launch_simple(L, m, l, n, A, B, C, mode, s));
+    return DDG_OK;
+  }
+  Ctx c;
+  c.L = L;
+  c.algo = o.algo;
+  c.cutoff = o.cutoff;
+  c.nstreams = o.streams == 1 ? 1 : 7;
+  if (!splits(c, m, l, n)) {
+    if (l == 0) {
+      if (mode == MODE_SET) return zero_mat(c, C, m, n, s);
+      return DDG_OK;
+    }
+    DDG_CUDA(launch_block(L, m, l, n, A, B, C, mode, s));
+    return DDG_OK;
+  }
+  if (c.nstreams == 7) DDG_TRY(stream_pool(&c.pool));
+  // plan
+  c.dry = true;
+  DDG_TRY(top(c, m, l, n, A, B, C, mode, o.pad == 1, s));
+  size_t total = 0;
+  for (int r = 0; r < 8; ++r) {
+    c.region_off[r] = total;
+    total += (c.peak[r] + 255) & ~(size_t)255;
+  }
+  // run
+  c.dry = false;
+  void* ws = nullptr;
+  if (total) {
+    cudaError_t e = cudaMallocAsync(&ws, total, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DDG_ENOMEM, "cudaMallocAsync of " + std::to_string(total) + " bytes: " + cudaGetErrorString(e));
+    }
+  }
+  c.base = static_cast<char*>(ws);
+  ddg_status st = top(c, m, l, n, A, B, C, mode, o.pad == 1, s);
+  if (ws) {
+    cudaError_t e = cudaFreeAsync(ws, s);
+    if (st == DDG_OK && e != cudaSuccess) return fail(DDG_ECUDA, std::string("cudaFreeAsync: ") + cudaGetErrorString(e));
+  }
+  return st;
+}
+
+}  // namespace ddg
+
+extern "C" {
+
+void ddg_opts_default(ddg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->algo = DDG_WINOGRAD;
+  o->cutoff = 512;
+  o->pad = 0;
+  o->streams = 7;
+}
+
+ddg_status dd_gemm(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, dd_mat C, int32_t mode,
+                   const ddg_opts* opts, void* stream) {
+  ddg::mat a{{A.hi, A.lo, nullptr, nullptr}, A.ld};
+  ddg::mat b{{B.hi, B.lo, nullptr, nullptr}, B.ld};
+  ddg::mat c{{C.hi, C.lo, nullptr, nullptr}, C.ld};
+  return ddg::gemm_entry(2, m, l, n, a, b, c, mode, opts, stream);
+}
+
+ddg_status qd_gemm(int64_t m, int64_t l, int64_t n, qd_mat A, qd_mat B, qd_mat C, int32_t mode,
+                   const ddg_opts* opts, void* stream) {
+  ddg::mat a{{A.x[0], A.x[1], A.x[2], A.x[3]}, A.ld};
+  ddg::mat b{{B.x[0], B.x[1], B.x[2], B.x[3]}, B.ld};
+  ddg::mat c{{C.x[0], C.x[1], C.x[2], C.x[3]}, C.ld};
+  return ddg::gemm_entry(4, m, l, n, a, b, c, mode, opts, stream);
+}
+
+int32_t ddg_block_fp64_ops_per_mac(int32_t limbs) {
+  return (limbs == 2 || limbs == 4) ? ddg::block_fp64_ops_per_mac(limbs) : -1;
+}
+
+const char* ddg_last_error(void) { return ddg::g_err.c_str(); }
+
+uint64_t ddg_kernel_launches(void) { return ddg::g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

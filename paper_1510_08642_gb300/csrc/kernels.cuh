@@ -1,0 +1,65 @@
+// Internal interface between the C-ABI layer and the CUDA kernels.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ddg {
+
+// A matrix of L limb planes (L = 2 for DD, 4 for QD), each row-major with
+// leading dimension ld (in doubles). Unused plane pointers are null.
+struct mat {
+  double* p[4];
+  int64_t ld;
+};
+
+inline mat view(const mat& M, int64_t r0, int64_t c0) {
+  mat v = M;
+  for (int k = 0; k < 4; ++k)
+    if (v.p[k]) v.p[k] += r0 * M.ld + c0;
+  return v;
+}
+
+// Count of kernel launches issued by the library (all kernels, all threads).
+extern std::atomic<uint64_t> g_launches;
+
+// Launch profiling hooks (profile.cu); no-ops unless ddg_profile_begin ran.
+enum ProfKind { PROF_SIMPLE = 0, PROF_BLOCK = 1, PROF_PASS = 2 };
+bool prof_enabled();
+void prof_begin_launch(cudaStream_t s, cudaEvent_t* start);
+void prof_end_launch(cudaStream_t s, cudaEvent_t start, int kind, double fp64_ops, double bytes);
+
+enum Mode { MODE_SET = 0, MODE_ADD = 1, MODE_SUB = 2 };
+
+// Quadrant pass kinds (fused add/sub passes of one recursion level).
+enum PassKind {
+  PASS_WINOGRAD_A = 0,  // S1..S4 from A11, A12, A21, A22
+  PASS_WINOGRAD_B = 1,  // T1..T4 from B11, B12, B21, B22
+  PASS_WINOGRAD_C = 2,  // C11..C22 from P1..P7
+  PASS_STRASSEN_A = 3,  // five left operands of M1..M7
+  PASS_STRASSEN_B = 4,  // five right operands of M1..M7
+  PASS_STRASSEN_C = 5,  // C11..C22 from M1..M7
+  PASS_COMBINE = 6,     // C := C (+/-) X  (used after padding)
+};
+
+// Eq. 1 Simple product, one thread per c_ij, k ascending (pinned sequence).
+cudaError_t launch_simple(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,
+                          int mode, cudaStream_t s);
+
+// Block product C (mode) A B on CTA tiles (the recursion base case).
+cudaError_t launch_block(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,
+                         int mode, cudaStream_t s);
+
+// One fused quadrant pass over a rows x cols quadrant grid.
+cudaError_t launch_pass(int limbs, int kind, int64_t rows, int64_t cols, const mat* in, int nin,
+                        const mat* out, int nout, int mode, cudaStream_t s);
+
+// FP64 instructions of one accurate DD / QD addition as used by the passes.
+int add_fp64_ops(int limbs);
+
+// Number of FP64 instructions of one multiply-accumulate in the Block
+// kernel's inner loop (counted from its source), for the roofline.
+int block_fp64_ops_per_mac(int limbs);
+
+}  // namespace ddg

@@ -1,0 +1,32 @@
+"""Named workloads shared by the benchmark and the full-size parity tests.
+
+Each is a square DD or QD product of the paper's Section 3 benchmark,
+scaled to GB300: operands from inputs.uniform (leading limb U[-1, 1), lower
+limbs 2^-53 U[-1/2, 1/2) below the previous one), seeds fixed here.
+"""
+from dataclasses import dataclass
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    limbs: int
+    n: int
+    algo: str
+    cutoff: int
+    seed_a: int
+    seed_b: int
+
+    @property
+    def macs(self) -> int:
+        return self.n ** 3
+
+
+# The headline: DD Winograd at n = 4096 (Winograd is the paper's fastest
+# algorithm, Table 1), cutoff chosen by the cutoff sweep.
+DD_WINOGRAD_4096 = Workload("dd_winograd_n4096", 2, 4096, "winograd", 512, 101, 102)
+DD_BLOCK_4096 = Workload("dd_block_n4096", 2, 4096, "block", 512, 101, 102)
+QD_WINOGRAD_4096 = Workload("qd_winograd_n4096", 4, 4096, "winograd", 512, 103, 104)
+QD_BLOCK_4096 = Workload("qd_block_n4096", 4, 4096, "block", 512, 103, 104)
+# The small case the oracle finishes in well under a second (Simple, n = 128).
+DD_SIMPLE_128 = Workload("dd_simple_n128", 2, 128, "simple", 512, 0, 1)
