@@ -17,8 +17,9 @@ def _mat(T, limbs: int):
     assert T.dtype.is_floating_point and T.element_size() == 8, "float64 planes expected"
     assert T.dim() == 3 and T.shape[0] == limbs, f"expected shape ({limbs}, rows, cols)"
     assert T.is_cuda, "device tensor expected"
-    assert T.stride(2) == 1, "rows must be contiguous"
-    ld = T.stride(1)
+    empty = T.shape[1] == 0 or T.shape[2] == 0
+    assert empty or T.stride(2) == 1, "rows must be contiguous"
+    ld = max(T.stride(1), T.shape[2]) if not empty else max(T.shape[2], 1)
     ps = T.stride(0)
     base = T.data_ptr()
     ptrs = [base + q * ps * 8 for q in range(limbs)]
