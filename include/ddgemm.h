@@ -110,6 +110,31 @@ ddg_status dd_gemm(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, dd_mat C
 ddg_status qd_gemm(int64_t m, int64_t l, int64_t n, qd_mat A, qd_mat B, qd_mat C, int32_t mode,
                    const ddg_opts* opts, void* stream);
 
+/*
+ * dd_gemm_noalloc: dd_gemm without any device allocation at call time.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot allocate device memory when they multiply: a service whose device
+ * memory is handed out once at start-up and then fixed, a host framework
+ * whose own allocator owns all free device memory, or a latency-bound loop
+ * where an allocation could stall or fail under memory pressure.
+ * Same arguments, modes and results as dd_gemm (Simple, Block, Strassen,
+ * Winograd; peel or pad), except that the seven sub-products always run in
+ * order on `stream` (opts->streams is ignored), so no streams or events are
+ * created either. Recursion temporaries live in one fixed 64 MiB array
+ * compiled into the library: every GPU that loads the library holds those
+ * 64 MiB until the process exits. A product whose temporaries do not fit
+ * (about 80 n^2 bytes for a square Winograd n, so n up to ~900 at any
+ * cutoff) returns DDG_EINVAL with the needed size in ddg_last_error(), and
+ * nothing is queued. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. All calls on a device share the one
+ * array: calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race on it and give wrong results, so order them.
+ * Nothing has to start at zero: every temporary is written before it is read.
+ */
+ddg_status dd_gemm_noalloc(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, dd_mat C,
+                           int32_t mode, const ddg_opts* opts, void* stream);
+
 /* FP64 instructions per DD (limbs = 2) or QD (limbs = 4) multiply-add in
  * the Block kernel's inner loop, counted from its source (for rooflines). */
 int32_t ddg_block_fp64_ops_per_mac(int32_t limbs);

@@ -62,6 +62,8 @@ SIGNATURES = {
                         ctypes.POINTER(ddg_opts), c_vp]),
     "qd_gemm": (c_i32, [c_i64, c_i64, c_i64, qd_mat, qd_mat, qd_mat, c_i32,
                         ctypes.POINTER(ddg_opts), c_vp]),
+    "dd_gemm_noalloc": (c_i32, [c_i64, c_i64, c_i64, dd_mat, dd_mat, dd_mat, c_i32,
+                                ctypes.POINTER(ddg_opts), c_vp]),
     "ddg_block_fp64_ops_per_mac": (c_i32, [c_i32]),
     "ddg_last_error": (ctypes.c_char_p, []),
     "ddg_kernel_launches": (ctypes.c_uint64, []),
@@ -117,6 +119,13 @@ def qd_gemm(m, l, n, A: qd_mat, B: qd_mat, C: qd_mat, mode: int, o: ddg_opts | N
             stream: int = 0) -> int:
     return load().qd_gemm(m, l, n, A, B, C, mode, ctypes.byref(o) if o is not None else None,
                           c_vp(stream))
+
+
+def dd_gemm_noalloc(m, l, n, A: dd_mat, B: dd_mat, C: dd_mat, mode: int, o: ddg_opts | None,
+                    stream: int = 0) -> int:
+    """dd_gemm with its temporaries in the library's fixed 64 MiB array."""
+    return load().dd_gemm_noalloc(m, l, n, A, B, C, mode,
+                                  ctypes.byref(o) if o is not None else None, c_vp(stream))
 
 
 def ddg_block_fp64_ops_per_mac(limbs: int) -> int:

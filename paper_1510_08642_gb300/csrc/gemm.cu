@@ -369,3 +369,102 @@ const char* ddg_last_error(void) { return ddg::g_err.c_str(); }
 uint64_t ddg_kernel_launches(void) { return ddg::g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"
+
+// ------------------------------------------------ allocation-free variant --
+// dd_gemm_noalloc: the same Strassen / Winograd product as dd_gemm, for
+// callers that must not allocate device memory at call time. Its recursion
+// temporaries live in one fixed array compiled into this library, so every
+// GPU that loads the library keeps kNoAllocScratchBytes reserved until the
+// process exits. Host code cannot use the array's name as a device address;
+// the address is looked up once per device with cudaGetSymbolAddress.
+namespace ddg {
+
+static constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kMaxDev];
+
+// Device address of the fixed scratch on the current device (looked up on the
+// first call per device, with that device current).
+static ddg_status noalloc_scratch(void** out) {
+  int dev = 0;
+  DDG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) return fail(DDG_ENOTSUP, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    DDG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return DDG_OK;
+}
+
+static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
+                                     const mat& C, int mode, const ddg_opts* opts, void* stream) {
+  g_err.clear();
+  const int L = 2;
+  ddg_opts o;
+  ddg_opts_default(&o);
+  if (opts) o = *opts;
+  if (m < 0 || l < 0 || n < 0) return fail(DDG_EINVAL, "negative size");
+  if (mode < DDG_SET || mode > DDG_SUB) return fail(DDG_EINVAL, "mode must be DDG_SET, DDG_ADD or DDG_SUB");
+  if (o.algo < DDG_SIMPLE || o.algo > DDG_WINOGRAD) return fail(DDG_EINVAL, "unknown algo");
+  if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
+  if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
+  for (int i = 0; i < 4; ++i)
+    if (o.reserved[i] != 0) return fail(DDG_EINVAL, "reserved option fields must be zero");
+  std::string why;
+  if (bad_mat(L, A, m, l, "A", why) || bad_mat(L, B, l, n, "B", why) || bad_mat(L, C, m, n, "C", why))
+    return fail(DDG_EINVAL, why);
+  if (overlaps(L, C, m, n, A, m, l) || overlaps(L, C, m, n, B, l, n))
+    return fail(DDG_EINVAL, "C overlaps A or B");
+  if (m > (int64_t)65535 * 8 || n > ((int64_t)1 << 36)) return fail(DDG_EINVAL, "matrix too large");
+  if (m == 0 || n == 0) return DDG_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (o.algo == DDG_SIMPLE) {
+    DDG_CUDA(launch_simple(L, m, l, n, A, B, C, mode, s));
+    return DDG_OK;
+  }
+  Ctx c;
+  c.L = L;
+  c.algo = o.algo;
+  c.cutoff = o.cutoff;
+  c.nstreams = 1;  // no forking: no streams or events are created
+  if (!splits(c, m, l, n)) {
+    if (l == 0) return mode == MODE_SET ? zero_mat(c, C, m, n, s) : DDG_OK;
+    DDG_CUDA(launch_block(L, m, l, n, A, B, C, mode, s));
+    return DDG_OK;
+  }
+  c.dry = true;
+  DDG_TRY(top(c, m, l, n, A, B, C, mode, o.pad == 1, s));
+  size_t total = 0;
+  for (int r = 0; r < 8; ++r) {
+    c.region_off[r] = total;
+    total += (c.peak[r] + 255) & ~(size_t)255;
+  }
+  if (total > kNoAllocScratchBytes)
+    return fail(DDG_EINVAL, "dd_gemm_noalloc: this product needs " + std::to_string(total) +
+                                " bytes of scratch; the fixed scratch holds " +
+                                std::to_string(kNoAllocScratchBytes) +
+                                " (use dd_gemm, a larger cutoff, or a smaller problem)");
+  void* base = nullptr;
+  DDG_TRY(noalloc_scratch(&base));
+  c.dry = false;
+  c.base = static_cast<char*>(base);
+  // Every temporary is written in full before it is read (operand passes,
+  // Block products in set mode, memset of padding), so stale contents of the
+  // shared scratch never reach a result.
+  return top(c, m, l, n, A, B, C, mode, o.pad == 1, s);
+}
+
+}  // namespace ddg
+
+extern "C" ddg_status dd_gemm_noalloc(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, dd_mat C,
+                                      int32_t mode, const ddg_opts* opts, void* stream) {
+  ddg::mat a{{A.hi, A.lo, nullptr, nullptr}, A.ld};
+  ddg::mat b{{B.hi, B.lo, nullptr, nullptr}, B.ld};
+  ddg::mat c{{C.hi, C.lo, nullptr, nullptr}, C.ld};
+  return ddg::gemm_noalloc_entry(m, l, n, a, b, c, mode, opts, stream);
+}
