@@ -51,7 +51,9 @@ def parse():
     p.add_argument("--workload", default=WL.DD_WINOGRAD_4096.name)
     p.add_argument("--cutoff", type=int, default=None)
     p.add_argument("--extras", choices=["all", "none"], default="all")
-    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="CPU oracle sample length; 0 skips the CPU baseline")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     return p.parse_args()
 
 
@@ -259,6 +261,27 @@ def time_gpu(P, torch, w, dA, dB, dC, cutoff, steps, warmup, stream, dist=None, 
     return ms, prof, launches
 
 
+def run_e2e(P, torch, w, args, dist, device, stream, hA, hB, hC, dA, dB, dC, cutoff, world):
+    """Same metric through host buffers: H2D of A, B, the product, D2H of C."""
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dA.copy_(hA, non_blocking=True)
+        dB.copy_(hB, non_blocking=True)
+        P.gemm(dA, dB, dC, algo=w.algo, cutoff=cutoff)
+        hC.copy_(dC, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    ms_e2e = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps, device)
+    return {"value": world * 2.0 * w.macs / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
+            "d2h_bytes_per_step": int(hC.numel() * 8), "ms_per_step": ms_e2e}
+
+
 def run_ours(args, w):
     import numpy as np
     import torch
@@ -293,24 +316,9 @@ def run_ours(args, w):
     value = world * 2.0 * macs / (ms * 1e-3) / 1e9
 
     # -------- end to end through host buffers (copies inside the timed region)
-    barrier(dist)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        dA.copy_(hA, non_blocking=True)
-        dB.copy_(hB, non_blocking=True)
-        P.gemm(dA, dB, dC, algo=w.algo, cutoff=cutoff)
-        hC.copy_(dC, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(dist)
-    ms_e2e = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps, device)
-    e2e = {"value": world * 2.0 * macs / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
-           "d2h_bytes_per_step": int(hC.numel() * 8), "ms_per_step": ms_e2e}
-
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(P, torch, w, args, dist, device, stream, hA, hB, hC, dA, dB, dC, cutoff, world)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -346,7 +354,7 @@ def run_ours(args, w):
             torch.cuda.empty_cache()
         line["extras"] = extras
 
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
         line["cpu_baseline"] = cpu_oracle_rate(w, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -30,3 +30,7 @@ QD_WINOGRAD_4096 = Workload("qd_winograd_n4096", 4, 4096, "winograd", 512, 103, 
 QD_BLOCK_4096 = Workload("qd_block_n4096", 4, 4096, "block", 512, 103, 104)
 # The small case the oracle finishes in well under a second (Simple, n = 128).
 DD_SIMPLE_128 = Workload("dd_simple_n128", 2, 128, "simple", 512, 0, 1)
+# Small cases for profiler captures: operands still larger than the L2.
+DD_BLOCK_2560 = Workload("dd_block_n2560", 2, 2560, "block", 512, 105, 106)
+QD_BLOCK_1536 = Workload("qd_block_n1536", 4, 1536, "block", 512, 107, 108)
+DD_WINOGRAD_2560 = Workload("dd_winograd_n2560", 2, 2560, "winograd", 320, 105, 106)
