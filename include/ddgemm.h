@@ -90,16 +90,22 @@ typedef struct {
   int32_t streams; /* 1 = the 7 sub-products of the top level run in order on
                       `stream`; 7 (default, also for 0) = on 7 concurrent
                       streams (the paper's 7 OpenMP sections, Figs. 1-2) */
-  int32_t reserved[4]; /* must be zero */
+  int32_t accum;   /* Block multiply-add: 0 (default) = exact fixed-point
+                      window accumulation of the leading products on the
+                      integer pipe, cross terms by FMA (2 FP64 instructions
+                      per DD multiply-add, 4 per QD); 1 = TwoSum accumulation
+                      on the FP64 pipe (12 per DD, 113 per QD) */
+  int32_t reserved[3]; /* must be zero */
 } ddg_opts;
 
-/* Fill *opts with the defaults: Winograd, cutoff 512, peeling, 7 streams. */
+/* Fill *opts with the defaults: Winograd, cutoff 512, peeling, 7 streams,
+ * fixed-point accumulation. */
 void ddg_opts_default(ddg_opts* opts);
 
 /*
  * dd_gemm: C (mode) A B in double-double, A m x l, B l x n, C m x n.
  * opts NULL = defaults. Accuracy: DDG_SIMPLE follows the pinned sequence
- * exactly; DDG_BLOCK stays within |C - C^| <= (l + 4) 2^-106 |A||B|
+ * exactly; DDG_BLOCK stays within |C - C^| <= (2 l + 4) 2^-106 |A||B|
  * elementwise; Strassen/Winograd within the normwise bound
  * 8 l^log2(12) 2^-104 ||A|| ||B||.
  */
@@ -136,8 +142,9 @@ ddg_status dd_gemm_noalloc(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, 
                            int32_t mode, const ddg_opts* opts, void* stream);
 
 /* FP64 instructions per DD (limbs = 2) or QD (limbs = 4) multiply-add in
- * the Block kernel's inner loop, counted from its source (for rooflines). */
-int32_t ddg_block_fp64_ops_per_mac(int32_t limbs);
+ * the Block kernel's inner loop for accumulation scheme `accum` (0 or 1, as
+ * in ddg_opts), counted from its source (for rooflines); -1 if invalid. */
+int32_t ddg_block_fp64_ops_per_mac(int32_t limbs, int32_t accum);
 
 /* Launch profiling. Between ddg_profile_begin() and ddg_profile_end() every
  * kernel launch of the library is bracketed by CUDA events on its stream.

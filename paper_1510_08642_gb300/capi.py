@@ -36,7 +36,7 @@ class qd_mat(ctypes.Structure):
 
 class ddg_opts(ctypes.Structure):
     _fields_ = [("algo", c_i32), ("cutoff", c_i32), ("pad", c_i32), ("streams", c_i32),
-                ("reserved", c_i32 * 4)]
+                ("accum", c_i32), ("reserved", c_i32 * 3)]
 
 
 class ddg_kernel_prof(ctypes.Structure):
@@ -64,7 +64,7 @@ SIGNATURES = {
                         ctypes.POINTER(ddg_opts), c_vp]),
     "dd_gemm_noalloc": (c_i32, [c_i64, c_i64, c_i64, dd_mat, dd_mat, dd_mat, c_i32,
                                 ctypes.POINTER(ddg_opts), c_vp]),
-    "ddg_block_fp64_ops_per_mac": (c_i32, [c_i32]),
+    "ddg_block_fp64_ops_per_mac": (c_i32, [c_i32, c_i32]),
     "ddg_last_error": (ctypes.c_char_p, []),
     "ddg_kernel_launches": (ctypes.c_uint64, []),
     "ddg_profile_begin": (c_i32, []),
@@ -99,13 +99,18 @@ def check(status: int) -> None:
         raise DDGError(status, last_error())
 
 
-def opts(algo="winograd", cutoff: int = 512, pad: bool = False, streams: int = 7) -> ddg_opts:
+ACCUMS = {"fx": 0, "twosum": 1}
+
+
+def opts(algo="winograd", cutoff: int = 512, pad: bool = False, streams: int = 7,
+         accum="fx") -> ddg_opts:
     o = ddg_opts()
     load().ddg_opts_default(ctypes.byref(o))
     o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
     o.cutoff = int(cutoff)
     o.pad = 1 if pad else 0
     o.streams = int(streams)
+    o.accum = ACCUMS[accum] if isinstance(accum, str) else int(accum)
     return o
 
 
@@ -128,8 +133,8 @@ def dd_gemm_noalloc(m, l, n, A: dd_mat, B: dd_mat, C: dd_mat, mode: int, o: ddg_
                                   ctypes.byref(o) if o is not None else None, c_vp(stream))
 
 
-def ddg_block_fp64_ops_per_mac(limbs: int) -> int:
-    return load().ddg_block_fp64_ops_per_mac(limbs)
+def ddg_block_fp64_ops_per_mac(limbs: int, accum: int = 0) -> int:
+    return load().ddg_block_fp64_ops_per_mac(limbs, accum)
 
 
 def ddg_kernel_launches() -> int:

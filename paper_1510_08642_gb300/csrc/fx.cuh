@@ -1,0 +1,287 @@
+// Fixed-point window accumulation of exact products (the GB300 Block kernel's
+// multiply-add).
+//
+// GB300 retires 2 FP64 instructions per clock per SM but 64 IMAD and 128
+// integer add/logic/shift instructions. The Block kernel therefore forms the
+// exact product of two doubles' significands on the integer pipe
+// (53 x 53 -> 106 bits by four 32x32->64 multiplies) and adds it, shifted
+// by the exponent, into a wide two's-complement fixed-point accumulator
+// (Kulisch-style, but only as wide as the product's range needs). Per output
+// entry c_ij the accumulator's scale is fixed before the k loop from the
+// largest exponent of row i of A and of column j of B, so no product can
+// overflow it and the accumulation is exact; bits below the window (2^-159
+// of the largest product for DD, 2^-255 for QD) are truncated.
+//
+// Word layout: acc[0] is the least significant 32-bit word; the top word
+// carries the sign. A double x is unpacked as |x| = (m1:m0) 2^(e - 1075) with
+// m1 holding the hidden bit (e >= 1; zero and subnormals have e = 1).
+//
+// The helpers are __host__ __device__ so that their bit manipulation can be
+// checked on the host against exact arithmetic.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+
+namespace ddg {
+namespace fx {
+
+struct unpacked {
+  uint32_t m0, m1;  // significand, m1 < 2^21
+  int e;            // biased exponent, >= 1
+  uint32_t s;       // sign bit
+};
+
+__host__ __device__ __forceinline__ uint64_t dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t b;
+  std::memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+
+__host__ __device__ __forceinline__ double bitsd(uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  std::memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+
+__host__ __device__ __forceinline__ unpacked unpack(double x) {
+  const uint64_t b = dbits(x);
+  const uint32_t hi = (uint32_t)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7FF);
+  unpacked u;
+  u.m0 = (uint32_t)b;
+  u.m1 = (hi & 0xFFFFFu) | (e ? 0x100000u : 0u);
+  u.e = e ? e : 1;
+  u.s = hi >> 31;
+  return u;
+}
+
+// Biased exponent field of x (0 for zero / subnormal).
+__host__ __device__ __forceinline__ int expfield(double x) {
+  return (int)((dbits(x) >> 52) & 0x7FF);
+}
+
+// (hi:lo << r) >> 32, r in [0, 31]
+__host__ __device__ __forceinline__ uint32_t shl_funnel(uint32_t lo, uint32_t hi, int r) {
+#ifdef __CUDA_ARCH__
+  return __funnelshift_l(lo, hi, r);
+#else
+  return (uint32_t)(((((uint64_t)hi) << 32) | lo) << r >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ int clz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+  return __clz((int)x);
+#else
+  return x ? __builtin_clz(x) : 32;
+#endif
+}
+
+// Exact 106-bit product of two significands, as four 32-bit words.
+__host__ __device__ __forceinline__ void mant_mul(const unpacked& a, const unpacked& b, uint32_t (&p)[4]) {
+  const uint64_t t00 = (uint64_t)a.m0 * b.m0;
+  const uint64_t t01 = (uint64_t)a.m0 * b.m1;
+  const uint64_t t10 = (uint64_t)a.m1 * b.m0;
+  const uint64_t t11 = (uint64_t)a.m1 * b.m1;
+  const uint64_t mid = t01 + t10;  // < 2^54
+  const uint64_t lo = t00 + (mid << 32);
+  const uint64_t hi = t11 + (mid >> 32) + (lo < t00 ? 1u : 0u);
+  p[0] = (uint32_t)lo;
+  p[1] = (uint32_t)(lo >> 32);
+  p[2] = (uint32_t)hi;
+  p[3] = (uint32_t)(hi >> 32);
+}
+
+// acc += (d XOR mask) + neg, mask = -neg: adds d, or subtracts it when neg = 1.
+template <int NW>
+__host__ __device__ __forceinline__ void acc_add(uint32_t (&A)[NW], const uint32_t (&d)[NW], uint32_t neg) {
+  const uint32_t m = 0u - neg;
+#ifdef __CUDA_ARCH__
+  if constexpr (NW == 6) {
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %6, 0xFFFFFFFF;\n\t"
+        "addc.cc.u32 %0, %0, %7;\n\t"
+        "addc.cc.u32 %1, %1, %8;\n\t"
+        "addc.cc.u32 %2, %2, %9;\n\t"
+        "addc.cc.u32 %3, %3, %10;\n\t"
+        "addc.cc.u32 %4, %4, %11;\n\t"
+        "addc.u32 %5, %5, %12;\n\t}"
+        : "+r"(A[0]), "+r"(A[1]), "+r"(A[2]), "+r"(A[3]), "+r"(A[4]), "+r"(A[5])
+        : "r"(neg), "r"(d[0] ^ m), "r"(d[1] ^ m), "r"(d[2] ^ m), "r"(d[3] ^ m), "r"(d[4] ^ m),
+          "r"(d[5] ^ m));
+  } else if constexpr (NW == 9) {
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %9, 0xFFFFFFFF;\n\t"
+        "addc.cc.u32 %0, %0, %10;\n\t"
+        "addc.cc.u32 %1, %1, %11;\n\t"
+        "addc.cc.u32 %2, %2, %12;\n\t"
+        "addc.cc.u32 %3, %3, %13;\n\t"
+        "addc.cc.u32 %4, %4, %14;\n\t"
+        "addc.cc.u32 %5, %5, %15;\n\t"
+        "addc.cc.u32 %6, %6, %16;\n\t"
+        "addc.cc.u32 %7, %7, %17;\n\t"
+        "addc.u32 %8, %8, %18;\n\t}"
+        : "+r"(A[0]), "+r"(A[1]), "+r"(A[2]), "+r"(A[3]), "+r"(A[4]), "+r"(A[5]), "+r"(A[6]),
+          "+r"(A[7]), "+r"(A[8])
+        : "r"(neg), "r"(d[0] ^ m), "r"(d[1] ^ m), "r"(d[2] ^ m), "r"(d[3] ^ m), "r"(d[4] ^ m),
+          "r"(d[5] ^ m), "r"(d[6] ^ m), "r"(d[7] ^ m), "r"(d[8] ^ m));
+  } else {
+    static_assert(NW == 6 || NW == 9, "accumulator width");
+  }
+#else
+  uint64_t c = neg;
+  for (int t = 0; t < NW; ++t) {
+    const uint64_t v = (uint64_t)A[t] + (uint64_t)(d[t] ^ m) + c;
+    A[t] = (uint32_t)v;
+    c = v >> 32;
+  }
+#endif
+}
+
+// 128-bit right shift of p by s >= 1 bits (bits shifted out are dropped).
+__host__ __device__ __forceinline__ void shr128(uint32_t (&p)[4], int s) {
+  uint64_t lo = ((uint64_t)p[1] << 32) | p[0];
+  uint64_t hi = ((uint64_t)p[3] << 32) | p[2];
+  if (s >= 128) {
+    lo = 0;
+    hi = 0;
+  } else if (s >= 64) {
+    lo = s == 64 ? hi : hi >> (s - 64);
+    hi = 0;
+  } else if (s > 0) {
+    lo = (lo >> s) | (hi << (64 - s));
+    hi >>= s;
+  }
+  p[0] = (uint32_t)lo;
+  p[1] = (uint32_t)(lo >> 32);
+  p[2] = (uint32_t)hi;
+  p[3] = (uint32_t)(hi >> 32);
+}
+
+// Add sign * p * 2^pos (in units of the accumulator's least significant bit)
+// into A. WF is the word index that positions in [32 (WF - 1), 32 WF + 31]
+// fall into on the fast path (two candidate word offsets, one select per
+// word); any other position takes the general path.
+template <int NW, int WF>
+__host__ __device__ __forceinline__ void place(uint32_t (&A)[NW], uint32_t (&p)[4], int pos, uint32_t neg) {
+  uint32_t d[NW];
+  if (pos >= 32 * (WF - 1) && pos < 32 * (WF + 1)) {
+    const int r = pos & 31;
+    const bool hiw = (pos >> 5) == WF;
+    const uint32_t q0 = p[0] << r;
+    const uint32_t q1 = shl_funnel(p[0], p[1], r);
+    const uint32_t q2 = shl_funnel(p[1], p[2], r);
+    const uint32_t q3 = shl_funnel(p[2], p[3], r);
+    const uint32_t q4 = shl_funnel(p[3], 0u, r);
+    const uint32_t q[5] = {q0, q1, q2, q3, q4};
+#pragma unroll
+    for (int t = 0; t < NW; ++t) {
+      const int jl = t - (WF - 1), jh = t - WF;  // piece index for each candidate offset
+      const uint32_t vl = (jl >= 0 && jl < 5) ? q[jl < 0 ? 0 : (jl > 4 ? 4 : jl)] : 0u;
+      const uint32_t vh = (jh >= 0 && jh < 5) ? q[jh < 0 ? 0 : (jh > 4 ? 4 : jh)] : 0u;
+      d[t] = hiw ? vh : vl;
+    }
+  } else {
+    if (pos < 0) {
+      shr128(p, -pos);
+      pos = 0;
+    }
+    const int w = pos >> 5, r = pos & 31;
+    const uint32_t q0 = p[0] << r;
+    const uint32_t q1 = shl_funnel(p[0], p[1], r);
+    const uint32_t q2 = shl_funnel(p[1], p[2], r);
+    const uint32_t q3 = shl_funnel(p[2], p[3], r);
+    const uint32_t q4 = shl_funnel(p[3], 0u, r);
+    const uint32_t q[5] = {q0, q1, q2, q3, q4};
+#pragma unroll
+    for (int t = 0; t < NW; ++t) {
+      uint32_t v = 0u;
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        if (t - c >= 0) v = (w == t - c) ? q[c] : v;
+      d[t] = v;
+    }
+  }
+  acc_add<NW>(A, d, neg);
+}
+
+// Power of two 2^k as a double for k in [-2044, 2046], as the product of
+// two factors that are both normal (the product rounds only if subnormal).
+__host__ __device__ __forceinline__ double pow2_product(double x, int k) {
+  const int k1 = k / 2, k2 = k - k1;
+  const double f1 = bitsd((uint64_t)(k1 + 1023) << 52);
+  const double f2 = bitsd((uint64_t)(k2 + 1023) << 52);
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(__dmul_rn(x, f1), f2);
+#else
+  return (x * f1) * f2;
+#endif
+}
+
+// Magnitude and sign of a two's-complement accumulator.
+template <int NW>
+__host__ __device__ __forceinline__ uint32_t acc_abs(uint32_t (&A)[NW]) {
+  const uint32_t neg = A[NW - 1] >> 31;
+  const uint32_t m = 0u - neg;
+  uint64_t c = neg;
+#pragma unroll
+  for (int t = 0; t < NW; ++t) {
+    const uint64_t v = (uint64_t)(A[t] ^ m) + c;
+    A[t] = (uint32_t)v;
+    c = v >> 32;
+  }
+  return neg;
+}
+
+// Split the magnitude |A| into K chunks of 53 bits from its leading bit down:
+// |A| ~= sum_c chunk[c] * 2^(exp[c]) (in units of the LSB), truncated below.
+// Returns false if A is zero.
+template <int NW, int K>
+__host__ __device__ __forceinline__ bool acc_chunks(const uint32_t (&A)[NW], uint64_t (&chunk)[K], int (&exp)[K]) {
+  int top = -1;
+#pragma unroll
+  for (int t = 0; t < NW; ++t)
+    if (A[t] != 0u) top = t;
+  if (top < 0) return false;
+  // gather the top word and the words below it into a bit string g (MSB first)
+  constexpr int G = (53 * K + 31) / 32 + 2;  // words needed below the leading bit
+  uint32_t g[G];
+#pragma unroll
+  for (int i = 0; i < G; ++i) {
+    const int t = top - i;
+    uint32_t v = 0u;
+#pragma unroll
+    for (int u = 0; u < NW; ++u) v = (u == t) ? A[u] : v;
+    g[i] = v;
+  }
+  const int lz = clz32(g[0]);
+  // left-align: shift the string so that the leading one is bit 31 of g[0]
+#pragma unroll
+  for (int i = 0; i < G; ++i) g[i] = shl_funnel(i + 1 < G ? g[i + 1] : 0u, g[i], lz);
+  const int lead = 32 * top + 31 - lz;  // bit position of the leading one
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    // bits [53 c, 53 c + 53) of the aligned string, counted from the top
+    const int b0 = 53 * c;
+    const int w = b0 >> 5, o = b0 & 31;
+    const uint64_t x = ((uint64_t)g[w] << 32) | g[w + 1];
+    const uint32_t y = g[w + 2];
+    // 96 bits x:y starting at bit offset o; take 53 bits
+    const uint64_t top64 = (o == 0) ? x : ((x << o) | ((uint64_t)y >> (32 - o)));
+    chunk[c] = top64 >> 11;
+    exp[c] = lead - 52 - b0;
+  }
+  return true;
+}
+
+}  // namespace fx
+}  // namespace ddg

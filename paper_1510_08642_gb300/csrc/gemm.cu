@@ -81,6 +81,7 @@ static inline size_t plane_bytes(int64_t rows, int64_t cols) {
 
 struct Ctx {
   int L = 2;
+  int accum = 0;
   int algo = DDG_WINOGRAD;
   int cutoff = 512;
   int nstreams = 7;
@@ -114,6 +115,12 @@ static ddg_status copy_mat(const Ctx& c, const mat& dst, const mat& src, int64_t
     DDG_CUDA(cudaMemcpy2DAsync(dst.p[q], dst.ld * sizeof(double), src.p[q], src.ld * sizeof(double),
                                cols * sizeof(double), rows, cudaMemcpyDeviceToDevice, s));
   return DDG_OK;
+}
+
+static cudaError_t base_case(const Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
+                             const mat& C, int mode, cudaStream_t s) {
+  return c.accum == 0 ? launch_block_fx(c.L, m, l, n, A, B, C, mode, s)
+                      : launch_block(c.L, m, l, n, A, B, C, mode, s);
 }
 
 static bool splits(const Ctx& c, int64_t m, int64_t l, int64_t n) {
@@ -193,19 +200,19 @@ static ddg_status rec(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, con
   if (m == 0 || n == 0) return DDG_OK;
   if (l == 0) return (mode == MODE_SET && !c.dry) ? zero_mat(c, C, m, n, s) : DDG_OK;
   if (!splits(c, m, l, n)) {
-    if (!c.dry) DDG_CUDA(launch_block(c.L, m, l, n, A, B, C, mode, s));
+    if (!c.dry) DDG_CUDA(base_case(c, m, l, n, A, B, C, mode, s));
     return DDG_OK;
   }
   const int64_t m2 = m & ~int64_t(1), l2 = l & ~int64_t(1), n2 = n & ~int64_t(1);
   DDG_TRY(level(c, m2, l2, n2, A, B, C, mode, s, region, sp, depth));
   if (!c.dry) {
     if (l2 != l)  // C[:m2, :n2] (+/-)= A[:m2, l2] B[l2, :n2]
-      DDG_CUDA(launch_block(c.L, m2, 1, n2, view(A, 0, l2), view(B, l2, 0), C,
+      DDG_CUDA(base_case(c, m2, 1, n2, view(A, 0, l2), view(B, l2, 0), C,
                             mode == MODE_SUB ? MODE_SUB : MODE_ADD, s));
     if (n2 != n)
-      DDG_CUDA(launch_block(c.L, m2, l, 1, A, view(B, 0, n2), view(C, 0, n2), mode, s));
+      DDG_CUDA(base_case(c, m2, l, 1, A, view(B, 0, n2), view(C, 0, n2), mode, s));
     if (m2 != m)
-      DDG_CUDA(launch_block(c.L, 1, l, n, view(A, m2, 0), B, view(C, m2, 0), mode, s));
+      DDG_CUDA(base_case(c, 1, l, n, view(A, m2, 0), B, view(C, m2, 0), mode, s));
   }
   return DDG_OK;
 }
@@ -275,7 +282,8 @@ static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& 
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
   if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
   if (o.streams != 0 && o.streams != 1 && o.streams != 7) return fail(DDG_EINVAL, "streams must be 0, 1 or 7");
-  for (int i = 0; i < 4; ++i)
+  if (o.accum != 0 && o.accum != 1) return fail(DDG_EINVAL, "accum must be 0 or 1");
+  for (int i = 0; i < 3; ++i)
     if (o.reserved[i] != 0) return fail(DDG_EINVAL, "reserved option fields must be zero");
   std::string why;
   if (bad_mat(L, A, m, l, "A", why) || bad_mat(L, B, l, n, "B", why) || bad_mat(L, C, m, n, "C", why))
@@ -292,6 +300,7 @@ static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& 
   }
   Ctx c;
   c.L = L;
+  c.accum = o.accum;
   c.algo = o.algo;
   c.cutoff = o.cutoff;
   c.nstreams = o.streams == 1 ? 1 : 7;
@@ -300,7 +309,7 @@ static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& 
       if (mode == MODE_SET) return zero_mat(c, C, m, n, s);
       return DDG_OK;
     }
-    DDG_CUDA(launch_block(L, m, l, n, A, B, C, mode, s));
+    DDG_CUDA(base_case(c, m, l, n, A, B, C, mode, s));
     return DDG_OK;
   }
   if (c.nstreams == 7) DDG_TRY(stream_pool(&c.pool));
@@ -342,6 +351,7 @@ void ddg_opts_default(ddg_opts* o) {
   o->cutoff = 512;
   o->pad = 0;
   o->streams = 7;
+  o->accum = 0;
 }
 
 ddg_status dd_gemm(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, dd_mat C, int32_t mode,
@@ -360,8 +370,9 @@ ddg_status qd_gemm(int64_t m, int64_t l, int64_t n, qd_mat A, qd_mat B, qd_mat C
   return ddg::gemm_entry(4, m, l, n, a, b, c, mode, opts, stream);
 }
 
-int32_t ddg_block_fp64_ops_per_mac(int32_t limbs) {
-  return (limbs == 2 || limbs == 4) ? ddg::block_fp64_ops_per_mac(limbs) : -1;
+int32_t ddg_block_fp64_ops_per_mac(int32_t limbs, int32_t accum) {
+  if ((limbs != 2 && limbs != 4) || (accum != 0 && accum != 1)) return -1;
+  return accum == 0 ? ddg::block_fx_fp64_ops_per_mac(limbs) : ddg::block_fp64_ops_per_mac(limbs);
 }
 
 const char* ddg_last_error(void) { return ddg::g_err.c_str(); }
@@ -413,7 +424,8 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
   if (o.algo < DDG_SIMPLE || o.algo > DDG_WINOGRAD) return fail(DDG_EINVAL, "unknown algo");
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
   if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
-  for (int i = 0; i < 4; ++i)
+  if (o.accum != 0 && o.accum != 1) return fail(DDG_EINVAL, "accum must be 0 or 1");
+  for (int i = 0; i < 3; ++i)
     if (o.reserved[i] != 0) return fail(DDG_EINVAL, "reserved option fields must be zero");
   std::string why;
   if (bad_mat(L, A, m, l, "A", why) || bad_mat(L, B, l, n, "B", why) || bad_mat(L, C, m, n, "C", why))
@@ -429,12 +441,13 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
   }
   Ctx c;
   c.L = L;
+  c.accum = o.accum;
   c.algo = o.algo;
   c.cutoff = o.cutoff;
   c.nstreams = 1;  // no forking: no streams or events are created
   if (!splits(c, m, l, n)) {
     if (l == 0) return mode == MODE_SET ? zero_mat(c, C, m, n, s) : DDG_OK;
-    DDG_CUDA(launch_block(L, m, l, n, A, B, C, mode, s));
+    DDG_CUDA(base_case(c, m, l, n, A, B, C, mode, s));
     return DDG_OK;
   }
   c.dry = true;

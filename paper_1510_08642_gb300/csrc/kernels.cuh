@@ -48,6 +48,12 @@ cudaError_t launch_simple(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat
                           int mode, cudaStream_t s);
 
 // Block product C (mode) A B on CTA tiles (the recursion base case).
+// launch_block: TwoSum accumulation on the FP64 pipe (block.cu);
+// launch_block_fx: exact fixed-point accumulation of the leading products on
+// the integer pipe (block_fx.cu).
+cudaError_t launch_block_fx(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,
+                            int mode, cudaStream_t s);
+int block_fx_fp64_ops_per_mac(int limbs);
 cudaError_t launch_block(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,
                          int mode, cudaStream_t s);
 

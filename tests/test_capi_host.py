@@ -28,14 +28,16 @@ def test_header_symbols_exported():
 
 
 def test_block_ops_per_mac():
-    assert capi.ddg_block_fp64_ops_per_mac(2) == 12
-    assert capi.ddg_block_fp64_ops_per_mac(4) == 113
-    assert capi.ddg_block_fp64_ops_per_mac(3) == -1
+    assert capi.ddg_block_fp64_ops_per_mac(2, 1) == 12
+    assert capi.ddg_block_fp64_ops_per_mac(4, 1) == 113
+    assert capi.ddg_block_fp64_ops_per_mac(2, 0) == 2
+    assert capi.ddg_block_fp64_ops_per_mac(4, 0) == 4
+    assert capi.ddg_block_fp64_ops_per_mac(3, 0) == -1
 
 
 def test_opts_default():
     o = capi.opts()
-    assert (o.algo, o.cutoff, o.pad, o.streams) == (capi.DDG_WINOGRAD, 512, 0, 7)
+    assert (o.algo, o.cutoff, o.pad, o.streams, o.accum) == (capi.DDG_WINOGRAD, 512, 0, 7, 0)
 
 
 FAKE = 1 << 40  # never dereferenced: every call below fails validation or is empty
@@ -73,9 +75,13 @@ def test_validation(case, status):
         assert capi.last_error()
 
 
-def test_reserved_must_be_zero():
+def test_reserved_and_accum_checked():
     o = capi.opts()
     o.reserved[0] = 1
+    st = capi.dd_gemm(4, 4, 4, dd(4), dd(4, FAKE + (1 << 33)), dd(4, FAKE + (1 << 34)), 0, o, 0)
+    assert st == capi.DDG_EINVAL
+    o = capi.opts()
+    o.accum = 2
     st = capi.dd_gemm(4, 4, 4, dd(4), dd(4, FAKE + (1 << 33)), dd(4, FAKE + (1 << 34)), 0, o, 0)
     assert st == capi.DDG_EINVAL
 

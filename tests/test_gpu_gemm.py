@@ -87,18 +87,19 @@ def check_bounds(A, B, C, algo, C0=None, mode="set", elementwise=True):
     if algo == "block" and elementwise:
         u2 = U2 if limbs == 2 else 8 * Q2
         scale = absprod(A, B)
-        bound = (l + 4) * u2 * scale + (np.abs(C0[0]) * u2 * 4 if C0 is not None else 0) + 1e-300
+        bound = (2 * l + 4) * u2 * scale + (np.abs(C0[0]) * u2 * 4 if C0 is not None else 0) + 1e-300
         assert np.all(np.abs(err) <= bound)
     return nw
 
 
+@pytest.mark.parametrize("accum", ["fx", "twosum"])
 @pytest.mark.parametrize("limbs", [2, 4])
 @pytest.mark.parametrize("algo,cutoff,shape", CASES)
-def test_algorithms_within_bound(limbs, algo, cutoff, shape):
+def test_algorithms_within_bound(limbs, algo, cutoff, shape, accum):
     m, l, n = shape
     A = I.uniform(m, l, limbs, seed=7)
     B = I.uniform(l, n, limbs, seed=8)
-    C = run(A, B, algo=algo, cutoff=cutoff)
+    C = run(A, B, algo=algo, cutoff=cutoff, accum=accum)
     nw = check_bounds(A, B, C, algo)
     # far inside the bound in practice: a wrong quadrant formula is O(1)
     assert nw < (1e-28 if limbs == 2 else 1e-60)
@@ -115,13 +116,14 @@ def test_update_modes(limbs, algo, mode):
     check_bounds(A, B, C, algo, C0=C0, mode=mode)
 
 
+@pytest.mark.parametrize("accum", ["fx", "twosum"])
 @pytest.mark.parametrize("algo", ["block", "strassen", "winograd"])
 @pytest.mark.parametrize("limbs", [2, 4])
-def test_integer_exact(algo, limbs):
+def test_integer_exact(algo, limbs, accum):
     m, l, n = 96, 130, 70
     A = I.integer(m, l, limbs, seed=12, bits=20)
     B = I.integer(l, n, limbs, seed=13, bits=20)
-    C = run(A, B, algo=algo, cutoff=16)
+    C = run(A, B, algo=algo, cutoff=16, accum=accum)
     err = O.gemm_error(A, B, C)
     assert not err.any()
 
@@ -145,12 +147,33 @@ def test_streams_do_not_change_bits(algo):
     assert np.array_equal(c7, c1)
 
 
-def test_wide_range_inputs():
-    A = I.wide(160, 200, 2, seed=18)
-    B = I.wide(200, 120, 2, seed=19)
+@pytest.mark.parametrize("limbs", [2, 4])
+@pytest.mark.parametrize("accum", ["fx", "twosum"])
+def test_wide_range_inputs(limbs, accum):
+    A = I.wide(160, 200, limbs, seed=18)
+    B = I.wide(200, 120, limbs, seed=19)
     for algo in ("block", "winograd"):
-        C = run(A, B, algo=algo, cutoff=32)
+        C = run(A, B, algo=algo, cutoff=32, accum=accum)
         check_bounds(A, B, C, algo, elementwise=(algo == "block"))
+
+
+@pytest.mark.parametrize("limbs", [2, 4])
+def test_fx_special_values(limbs):
+    """Zero rows / columns, tiny and huge magnitudes, exact cancellation."""
+    m, l, n = 40, 70, 36
+    A = I.uniform(m, l, limbs, seed=20)
+    B = I.uniform(l, n, limbs, seed=21)
+    A[:, 3, :] = 0.0            # zero row of A
+    B[:, :, 5] = 0.0            # zero column of B
+    A[:, 7, :] *= 2.0 ** -600   # tiny row
+    B[:, :, 9] *= 2.0 ** 500    # huge column
+    A[:, 11, 35:] = A[:, 11, :35]
+    B[:, 35:, 13] = -B[:, :35, 13]  # row 11 x column 13 cancels exactly
+    C = run(A, B, algo="block")
+    err = O.gemm_error(A, B, C)
+    u2 = U2 if limbs == 2 else 8 * Q2
+    assert np.all(np.abs(err) <= (2 * l + 4) * u2 * absprod(A, B) + 1e-300)
+    assert not C[:, 3, :].any() and not C[:, :, 5].any()
 
 
 def test_paper_matrices_table1_shapes():
