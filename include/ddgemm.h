@@ -117,6 +117,40 @@ ddg_status qd_gemm(int64_t m, int64_t l, int64_t n, qd_mat A, qd_mat B, qd_mat C
                    const ddg_opts* opts, void* stream);
 
 /*
+ * dd_getrf: in-place LU decomposition P A = L U of an n x n DD matrix
+ * (Section 4, steps 1-3): right-looking blocked LU with block columns of K
+ * (1 <= K <= 512; the paper takes K = alpha n_min) whose trailing update
+ * A22 := A22 - L21 U12 is the DD product of `opts` (algo, cutoff, ...;
+ * NULL = defaults, Winograd) in mode DDG_SUB. On return A holds L (unit
+ * lower, below the diagonal) and U.
+ *   pivot = 1: partial pivoting, pivot of column j = the first row i >= j
+ *              with the largest |a_ij| compared as DD; pivot = 0: none (the
+ *              paper's setting, Section 4).
+ *   ipiv: device array of n int64: row j was interchanged with row ipiv[j]
+ *         (0-based) at step j (ipiv[j] = j without pivoting).
+ *   info: device pointer to one int64 or NULL. Non-NULL: the call is fully
+ *         asynchronous and *info receives 0, or 1 + the first column with an
+ *         exactly zero pivot (the factorisation continues past it, leaving
+ *         that column's quotients untouched). NULL: the call waits for the
+ *         stream and returns DDG_ESINGULAR for a zero pivot.
+ * Temporary storage (partial arg-maxes, n/32 entries) comes from the
+ * stream-ordered allocator.
+ */
+ddg_status dd_getrf(int64_t n, dd_mat A, int64_t* ipiv, int32_t K, int32_t pivot, const ddg_opts* opts,
+                    int64_t* info, void* stream);
+
+/*
+ * dd_getrs: solve A X = B (Section 4, Eq. 2) with the factors of dd_getrf:
+ * the row interchanges of ipiv applied to B, forward substitution with the
+ * unit lower factor, back substitution with the upper factor (DD quotients
+ * by the diagonal). B (n x nrhs) is overwritten by X. Recursive blocked
+ * triangular solves: 32-row triangles in one kernel, off-diagonal updates by
+ * the Block product. Temporary storage (a copy of B and the permutation)
+ * comes from the stream-ordered allocator. Asynchronous.
+ */
+ddg_status dd_getrs(int64_t n, int64_t nrhs, dd_mat LU, const int64_t* ipiv, dd_mat B, void* stream);
+
+/*
  * dd_gemm_noalloc: dd_gemm without any device allocation at call time.
  * The paper has no counterpart; this entry point exists for callers that
  * cannot allocate device memory when they multiply: a service whose device

@@ -51,3 +51,27 @@ def gemm(A, B, C=None, algo: str = "winograd", cutoff: int = 512, mode: str = "s
     fn = capi.dd_gemm if limbs == 2 else capi.qd_gemm
     capi.check(fn(m, l, n, _mat(A, limbs), _mat(B, limbs), _mat(C, limbs), capi.MODES[mode], o, s))
     return C
+
+
+def getrf(A, K: int = 64, pivot: bool = True, algo: str = "winograd", cutoff: int = 32,
+          accum: str = "fx", info=None, stream=None):
+    """In-place DD LU through dd_getrf; returns the device ipiv (int64, n)."""
+    import torch
+
+    n = A.shape[1]
+    ipiv = torch.empty(n, dtype=torch.int64, device=A.device)
+    o = capi.opts(algo, cutoff, False, 7, accum)
+    s = (stream or torch.cuda.current_stream(A.device)).cuda_stream
+    capi.check(capi.dd_getrf(n, _mat(A, 2), ipiv.data_ptr(), K, 1 if pivot else 0, o,
+                             info.data_ptr() if info is not None else None, s))
+    return ipiv
+
+
+def getrs(LU, ipiv, B, stream=None):
+    """Solve with dd_getrs; B (2, n, nrhs) is overwritten with X and returned."""
+    import torch
+
+    n, nrhs = B.shape[1], B.shape[2]
+    s = (stream or torch.cuda.current_stream(LU.device)).cuda_stream
+    capi.check(capi.dd_getrs(n, nrhs, _mat(LU, 2), ipiv.data_ptr(), _mat(B, 2), s))
+    return B

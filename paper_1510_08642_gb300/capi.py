@@ -65,6 +65,8 @@ SIGNATURES = {
     "dd_gemm_noalloc": (c_i32, [c_i64, c_i64, c_i64, dd_mat, dd_mat, dd_mat, c_i32,
                                 ctypes.POINTER(ddg_opts), c_vp]),
     "ddg_block_fp64_ops_per_mac": (c_i32, [c_i32, c_i32]),
+    "dd_getrf": (c_i32, [c_i64, dd_mat, c_vp, c_i32, c_i32, ctypes.POINTER(ddg_opts), c_vp, c_vp]),
+    "dd_getrs": (c_i32, [c_i64, c_i64, dd_mat, c_vp, dd_mat, c_vp]),
     "ddg_last_error": (ctypes.c_char_p, []),
     "ddg_kernel_launches": (ctypes.c_uint64, []),
     "ddg_profile_begin": (c_i32, []),
@@ -151,3 +153,13 @@ def ddg_profile_end() -> dict:
     check(load().ddg_profile_end(arr, len(PROF_KINDS)))
     return {k: {f: getattr(arr[i], f) for f, _ in ddg_kernel_prof._fields_}
             for i, k in enumerate(PROF_KINDS)}
+
+
+def dd_getrf(n, A: dd_mat, ipiv: int, K: int, pivot: int, o: ddg_opts | None, info: int | None,
+             stream: int = 0) -> int:
+    return load().dd_getrf(n, A, c_vp(ipiv), K, pivot, ctypes.byref(o) if o is not None else None,
+                           c_vp(info) if info else None, c_vp(stream))
+
+
+def dd_getrs(n, nrhs, LU: dd_mat, ipiv: int, B: dd_mat, stream: int = 0) -> int:
+    return load().dd_getrs(n, nrhs, LU, c_vp(ipiv), B, c_vp(stream))

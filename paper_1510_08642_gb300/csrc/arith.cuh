@@ -72,6 +72,28 @@ __device__ __forceinline__ dd_t dd_add(dd_t a, dd_t b) {
 
 __device__ __forceinline__ dd_t dd_neg(dd_t a) { return dd_t{-a.hi, -a.lo}; }
 
+// DD quotient a / b by long division: three double quotient digits, each
+// remainder formed with the DD product and sum above (relative error a few
+// units of 2^-104).
+__device__ __forceinline__ dd_t dd_div(dd_t a, dd_t b) {
+  const double q1 = __ddiv_rn(a.hi, b.hi);
+  dd_t r = dd_add(a, dd_mul(dd_t{-q1, 0.0}, b));
+  const double q2 = __ddiv_rn(r.hi, b.hi);
+  r = dd_add(r, dd_mul(dd_t{-q2, 0.0}, b));
+  const double q3 = __ddiv_rn(r.hi, b.hi);
+  dd_t q;
+  fast_two_sum(q1, q2, q.hi, q.lo);
+  return dd_add(q, dd_t{q3, 0.0});
+}
+
+// |a| > |b| as DD numbers (compares hi, then the lo of the same sign).
+__device__ __forceinline__ bool dd_abs_greater(dd_t a, dd_t b) {
+  const double ah = fabs(a.hi), bh = fabs(b.hi);
+  const double al = a.hi < 0.0 ? -a.lo : a.lo;
+  const double bl = b.hi < 0.0 ? -b.lo : b.lo;
+  return ah > bh || (ah == bh && al > bl);
+}
+
 struct qd_t {
   double x[4];
 };

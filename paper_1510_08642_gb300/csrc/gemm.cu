@@ -24,6 +24,7 @@
 // node's temporaries are reused by its next sibling. Total for a square n:
 // about 15 (n/2)^2 (1 + 7/3) DD/QD entries.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -40,6 +41,9 @@ static ddg_status fail(ddg_status st, const std::string& msg) {
   g_err = msg;
   return st;
 }
+
+void clear_error() { g_err.clear(); }
+ddg_status set_error(ddg_status st, const std::string& msg) { return fail(st, msg); }
 
 #define DDG_CUDA(x)                                                                      \
   do {                                                                                   \
@@ -257,18 +261,41 @@ static bool bad_mat(int L, const mat& M, int64_t rows, int64_t cols, const char*
   return false;
 }
 
+// Do the element sets of two strided regions X (xr x xc) and Y (yr x yc)
+// share an address? Exact when both have the same leading dimension (views
+// into one matrix, e.g. L21, U12 and A22 of an LU step); otherwise the
+// conservative test on the address ranges.
+static bool region_overlap(const double* x, int64_t xr, int64_t xc, int64_t xld, const double* y,
+                           int64_t yr, int64_t yc, int64_t yld) {
+  const char* x0 = reinterpret_cast<const char*>(x);
+  const char* x1 = reinterpret_cast<const char*>(x + (xr - 1) * xld + xc);
+  const char* y0 = reinterpret_cast<const char*>(y);
+  const char* y1 = reinterpret_cast<const char*>(y + (yr - 1) * yld + yc);
+  if (!(x0 < y1 && y0 < x1)) return false;
+  const std::ptrdiff_t db = y0 - x0;
+  if (xld != yld || db % (std::ptrdiff_t)sizeof(double) != 0) return true;
+  int64_t d = db / (std::ptrdiff_t)sizeof(double);
+  int64_t dr = d >= 0 ? d / xld : -((-d + xld - 1) / xld);
+  int64_t dc = d - dr * xld;  // 0 <= dc < ld
+  // Y's element (r, c) is X's (r + dr, c + dc) if c + dc < ld, else (r + dr + 1, c + dc - ld)
+  auto rect = [&](int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
+    return r0 < xr && 0 < r1 && c0 < xc && 0 < c1 && r0 < r1 && c0 < c1;
+  };
+  if (rect(dr, dr + yr, dc, std::min(dc + yc, xld))) return true;
+  if (dc + yc > xld && rect(dr + 1, dr + 1 + yr, 0, dc + yc - xld)) return true;
+  return false;
+}
+
 static bool overlaps(int L, const mat& X, int64_t xr, int64_t xc, const mat& Y, int64_t yr, int64_t yc) {
   if (xr == 0 || xc == 0 || yr == 0 || yc == 0) return false;
   for (int p = 0; p < L; ++p)
-    for (int q = 0; q < L; ++q) {
-      const char* x0 = reinterpret_cast<const char*>(X.p[p]);
-      const char* x1 = reinterpret_cast<const char*>(X.p[p] + (xr - 1) * X.ld + xc);
-      const char* y0 = reinterpret_cast<const char*>(Y.p[q]);
-      const char* y1 = reinterpret_cast<const char*>(Y.p[q] + (yr - 1) * Y.ld + yc);
-      if (x0 < y1 && y0 < x1) return true;
-    }
+    for (int q = 0; q < L; ++q)
+      if (region_overlap(X.p[p], xr, xc, X.ld, Y.p[q], yr, yc, Y.ld)) return true;
   return false;
 }
+
+ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
+                    int mode, const ddg_opts& o, cudaStream_t s);
 
 static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
                              const mat& C, int mode, const ddg_opts* opts, void* stream) {
@@ -291,8 +318,12 @@ static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& 
   if (overlaps(L, C, m, n, A, m, l) || overlaps(L, C, m, n, B, l, n))
     return fail(DDG_EINVAL, "C overlaps A or B");
   if (m > (int64_t)65535 * 8 || n > ((int64_t)1 << 36)) return fail(DDG_EINVAL, "matrix too large");
+  return gemm_run(L, m, l, n, A, B, C, mode, o, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
+                    int mode, const ddg_opts& o, cudaStream_t s) {
   if (m == 0 || n == 0) return DDG_OK;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
   if (o.algo == DDG_SIMPLE) {
     DDG_CUDA(launch_simple(L, m, l, n, A, B, C, mode, s));

@@ -3,6 +3,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace ddg {
@@ -63,6 +64,21 @@ cudaError_t launch_pass(int limbs, int kind, int64_t rows, int64_t cols, const m
 
 // FP64 instructions of one accurate DD / QD addition as used by the passes.
 int add_fp64_ops(int limbs);
+
+}  // namespace ddg
+
+#include "ddgemm.h"
+
+namespace ddg {
+
+// Error text of the calling host thread (ddg_last_error).
+void clear_error();
+ddg_status set_error(ddg_status st, const std::string& msg);
+
+// C (mode) A B with options o (validated by the caller): the body of
+// dd_gemm / qd_gemm, used by the LU routines.
+ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
+                    int mode, const ddg_opts& o, cudaStream_t s);
 
 // Number of FP64 instructions of one multiply-accumulate in the Block
 // kernel's inner loop (counted from its source), for the roofline.
