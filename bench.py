@@ -221,7 +221,7 @@ def roofline_of(prof, limbs):
     b = prof["block"]
     if not b["launches"]:
         return None
-    achieved = b["fp64_ops"] / (b["busy_ms"] * 1e-3)
+    achieved = b["ops"] / (b["busy_ms"] * 1e-3)
     avg_ms = b["sum_ms"] / b["launches"]
     ops_mac = {2: 12, 4: 113}[limbs]
     return {"bound": "alu", "kernel": f"block_kernel<{limbs}> (FP64 pipe)",
@@ -336,7 +336,7 @@ def run_ours(args, w):
     if passes["launches"]:
         line["passes"] = {"launches": int(passes["launches"]), "busy_ms": passes["busy_ms"] / args.steps,
                           "GB_per_s": passes["bytes"] / (passes["busy_ms"] * 1e-3) / 1e9,
-                          "fp64_frac": passes["fp64_ops"] / (passes["busy_ms"] * 1e-3) / FP64_PEAK}
+                          "fp64_frac": passes["ops"] / (passes["busy_ms"] * 1e-3) / FP64_PEAK}
     del dA, dB, dC, hA, hB, hC
     torch.cuda.empty_cache()
 

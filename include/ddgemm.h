@@ -63,7 +63,14 @@ typedef enum {
                        kernels) */
   DDG_BLOCK = 1,    /* C_ij = sum_k A_ik B_kj over register/shared tiles */
   DDG_STRASSEN = 2, /* Strassen 1969: 7 products, 18 quadrant sums per level */
-  DDG_WINOGRAD = 3  /* Winograd's variant: 7 products, 15 quadrant sums */
+  DDG_WINOGRAD = 3, /* Winograd's variant: 7 products, 15 quadrant sums */
+  DDG_OZAKI = 4     /* not in the paper: DD only. A and B split exactly into
+                       `slices` INT8 digit matrices per row / column scale
+                       (balanced base 128), slice products on the INT8 tensor
+                       cores with INT32 accumulation, recombined exactly and
+                       rounded to DD. Error <= l (s + 3) 2^-7s max|a_i.|
+                       max|b_.j| per entry (normwise, not elementwise, DD
+                       accuracy); l * slices <= 2^19 / 1 */
 } ddg_algo;
 
 /* How C is written: C := A B, C := C + A B or C := C - A B. */
@@ -95,7 +102,9 @@ typedef struct {
                       integer pipe, cross terms by FMA (2 FP64 instructions
                       per DD multiply-add, 4 per QD); 1 = TwoSum accumulation
                       on the FP64 pipe (12 per DD, 113 per QD) */
-  int32_t reserved[3]; /* must be zero */
+  int32_t slices;  /* DDG_OZAKI: number of INT8 slices s in [2, 18];
+                      0 = 16 (about 2^-110 of the row/column maxima) */
+  int32_t reserved[2]; /* must be zero */
 } ddg_opts;
 
 /* Fill *opts with the defaults: Winograd, cutoff 512, peeling, 7 streams,
@@ -183,7 +192,8 @@ int32_t ddg_block_fp64_ops_per_mac(int32_t limbs, int32_t accum);
 /* Launch profiling. Between ddg_profile_begin() and ddg_profile_end() every
  * kernel launch of the library is bracketed by CUDA events on its stream.
  * ddg_profile_end() waits for those events and fills out[k] for kernel
- * kinds k = 0 (Simple), 1 (Block), 2 (quadrant passes), k < nkinds:
+ * kinds k = 0 (Simple), 1 (Block), 2 (quadrant passes), 3 (INT8 slice
+ * products), k < nkinds:
  * launches, sum of launch durations, busy time (union of the launch
  * intervals), and algorithmic FP64 instructions and bytes of those launches.
  * For measurement only: it adds two event records per launch. */
@@ -191,7 +201,8 @@ typedef struct {
   uint64_t launches;
   double sum_ms;
   double busy_ms;
-  double fp64_ops;
+  double ops;   /* FP64 instructions (kinds 0-2) or INT8 operations, 2 per
+                   multiply-add (kind 3, the slice products) */
   double bytes;
 } ddg_kernel_prof;
 ddg_status ddg_profile_begin(void);

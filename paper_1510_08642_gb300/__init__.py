@@ -33,7 +33,7 @@ def _mat(T, limbs: int):
 
 
 def gemm(A, B, C=None, algo: str = "winograd", cutoff: int = 512, mode: str = "set",
-         pad: bool = False, streams: int = 7, accum: str = "fx", stream=None):
+         pad: bool = False, streams: int = 7, accum: str = "fx", slices: int = 0, stream=None):
     """C (mode) A B through dd_gemm / qd_gemm on the current CUDA stream.
 
     A: (limbs, m, l), B: (limbs, l, n), C: (limbs, m, n) or None (allocated).
@@ -46,7 +46,7 @@ def gemm(A, B, C=None, algo: str = "winograd", cutoff: int = 512, mode: str = "s
     n = B.shape[2]
     if C is None:
         C = torch.empty((limbs, m, n), dtype=torch.float64, device=A.device)
-    o = capi.opts(algo, cutoff, pad, streams, accum)
+    o = capi.opts(algo, cutoff, pad, streams, accum, slices)
     s = (stream or torch.cuda.current_stream(A.device)).cuda_stream
     fn = capi.dd_gemm if limbs == 2 else capi.qd_gemm
     capi.check(fn(m, l, n, _mat(A, limbs), _mat(B, limbs), _mat(C, limbs), capi.MODES[mode], o, s))

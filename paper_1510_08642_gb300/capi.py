@@ -19,9 +19,9 @@ c_i32, c_i64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
 DDG_OK, DDG_EINVAL, DDG_ENOMEM, DDG_ECUDA, DDG_ESINGULAR, DDG_ETIMEOUT, DDG_ENOTSUP = range(7)
 STATUS_NAMES = ["DDG_OK", "DDG_EINVAL", "DDG_ENOMEM", "DDG_ECUDA", "DDG_ESINGULAR",
                 "DDG_ETIMEOUT", "DDG_ENOTSUP"]
-DDG_SIMPLE, DDG_BLOCK, DDG_STRASSEN, DDG_WINOGRAD = range(4)
+DDG_SIMPLE, DDG_BLOCK, DDG_STRASSEN, DDG_WINOGRAD, DDG_OZAKI = range(5)
 ALGOS = {"simple": DDG_SIMPLE, "block": DDG_BLOCK, "strassen": DDG_STRASSEN,
-         "winograd": DDG_WINOGRAD}
+         "winograd": DDG_WINOGRAD, "ozaki": DDG_OZAKI}
 DDG_SET, DDG_ADD, DDG_SUB = range(3)
 MODES = {"set": DDG_SET, "add": DDG_ADD, "sub": DDG_SUB}
 
@@ -36,16 +36,16 @@ class qd_mat(ctypes.Structure):
 
 class ddg_opts(ctypes.Structure):
     _fields_ = [("algo", c_i32), ("cutoff", c_i32), ("pad", c_i32), ("streams", c_i32),
-                ("accum", c_i32), ("reserved", c_i32 * 3)]
+                ("accum", c_i32), ("slices", c_i32), ("reserved", c_i32 * 2)]
 
 
 class ddg_kernel_prof(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("sum_ms", ctypes.c_double),
-                ("busy_ms", ctypes.c_double), ("fp64_ops", ctypes.c_double),
+                ("busy_ms", ctypes.c_double), ("ops", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
 
 
-PROF_KINDS = ("simple", "block", "pass")
+PROF_KINDS = ("simple", "block", "pass", "ozaki")
 
 
 class DDGError(RuntimeError):
@@ -105,7 +105,7 @@ ACCUMS = {"fx": 0, "twosum": 1}
 
 
 def opts(algo="winograd", cutoff: int = 512, pad: bool = False, streams: int = 7,
-         accum="fx") -> ddg_opts:
+         accum="fx", slices: int = 0) -> ddg_opts:
     o = ddg_opts()
     load().ddg_opts_default(ctypes.byref(o))
     o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
@@ -113,6 +113,7 @@ def opts(algo="winograd", cutoff: int = 512, pad: bool = False, streams: int = 7
     o.pad = 1 if pad else 0
     o.streams = int(streams)
     o.accum = ACCUMS[accum] if isinstance(accum, str) else int(accum)
+    o.slices = int(slices)
     return o
 
 

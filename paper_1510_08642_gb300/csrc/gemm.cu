@@ -305,12 +305,13 @@ static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& 
   if (opts) o = *opts;
   if (m < 0 || l < 0 || n < 0) return fail(DDG_EINVAL, "negative size");
   if (mode < DDG_SET || mode > DDG_SUB) return fail(DDG_EINVAL, "mode must be DDG_SET, DDG_ADD or DDG_SUB");
-  if (o.algo < DDG_SIMPLE || o.algo > DDG_WINOGRAD) return fail(DDG_EINVAL, "unknown algo");
+  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI) return fail(DDG_EINVAL, "unknown algo");
+  if (o.slices != 0 && (o.slices < 2 || o.slices > 18)) return fail(DDG_EINVAL, "slices must be 0 or in [2, 18]");
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
   if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
   if (o.streams != 0 && o.streams != 1 && o.streams != 7) return fail(DDG_EINVAL, "streams must be 0, 1 or 7");
   if (o.accum != 0 && o.accum != 1) return fail(DDG_EINVAL, "accum must be 0 or 1");
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i] != 0) return fail(DDG_EINVAL, "reserved option fields must be zero");
   std::string why;
   if (bad_mat(L, A, m, l, "A", why) || bad_mat(L, B, l, n, "B", why) || bad_mat(L, C, m, n, "C", why))
@@ -328,6 +329,12 @@ ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const 
   if (o.algo == DDG_SIMPLE) {
     DDG_CUDA(launch_simple(L, m, l, n, A, B, C, mode, s));
     return DDG_OK;
+  }
+  if (o.algo == DDG_OZAKI) {
+    if (L != 2) return fail(DDG_ENOTSUP, "DDG_OZAKI is implemented for DD only");
+    if (m > 65535) return fail(DDG_EINVAL, "DDG_OZAKI: m must be <= 65535");
+    if (l == 0) return mode == MODE_SET ? zero_mat(Ctx{}, C, m, n, s) : DDG_OK;
+    return ozaki_dd_gemm(m, l, n, A, B, C, mode, o.slices ? o.slices : 16, s);
   }
   Ctx c;
   c.L = L;
@@ -452,11 +459,12 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
   if (opts) o = *opts;
   if (m < 0 || l < 0 || n < 0) return fail(DDG_EINVAL, "negative size");
   if (mode < DDG_SET || mode > DDG_SUB) return fail(DDG_EINVAL, "mode must be DDG_SET, DDG_ADD or DDG_SUB");
-  if (o.algo < DDG_SIMPLE || o.algo > DDG_WINOGRAD) return fail(DDG_EINVAL, "unknown algo");
+  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI) return fail(DDG_EINVAL, "unknown algo");
+  if (o.slices != 0 && (o.slices < 2 || o.slices > 18)) return fail(DDG_EINVAL, "slices must be 0 or in [2, 18]");
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
   if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
   if (o.accum != 0 && o.accum != 1) return fail(DDG_EINVAL, "accum must be 0 or 1");
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i] != 0) return fail(DDG_EINVAL, "reserved option fields must be zero");
   std::string why;
   if (bad_mat(L, A, m, l, "A", why) || bad_mat(L, B, l, n, "B", why) || bad_mat(L, C, m, n, "C", why))
@@ -464,6 +472,7 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
   if (overlaps(L, C, m, n, A, m, l) || overlaps(L, C, m, n, B, l, n))
     return fail(DDG_EINVAL, "C overlaps A or B");
   if (m > (int64_t)65535 * 8 || n > ((int64_t)1 << 36)) return fail(DDG_EINVAL, "matrix too large");
+  if (o.algo == DDG_OZAKI) return fail(DDG_EINVAL, "dd_gemm_noalloc: DDG_OZAKI needs a workspace; use dd_gemm");
   if (m == 0 || n == 0) return DDG_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (o.algo == DDG_SIMPLE) {

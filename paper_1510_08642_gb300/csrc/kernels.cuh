@@ -26,7 +26,7 @@ inline mat view(const mat& M, int64_t r0, int64_t c0) {
 extern std::atomic<uint64_t> g_launches;
 
 // Launch profiling hooks (profile.cu); no-ops unless ddg_profile_begin ran.
-enum ProfKind { PROF_SIMPLE = 0, PROF_BLOCK = 1, PROF_PASS = 2 };
+enum ProfKind { PROF_SIMPLE = 0, PROF_BLOCK = 1, PROF_PASS = 2, PROF_OZAKI = 3 };
 bool prof_enabled();
 void prof_begin_launch(cudaStream_t s, cudaEvent_t* start);
 void prof_end_launch(cudaStream_t s, cudaEvent_t start, int kind, double fp64_ops, double bytes);
@@ -79,6 +79,10 @@ ddg_status set_error(ddg_status st, const std::string& msg);
 // dd_gemm / qd_gemm, used by the LU routines.
 ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
                     int mode, const ddg_opts& o, cudaStream_t s);
+
+// DD product by INT8 slices (Ozaki scheme), s slices (ozaki.cu).
+ddg_status ozaki_dd_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
+                         int mode, int s, cudaStream_t st);
 
 // Number of FP64 instructions of one multiply-accumulate in the Block
 // kernel's inner loop (counted from its source), for the roofline.

@@ -1,0 +1,348 @@
+// DD product by error-free splitting into INT8 slices (the Ozaki scheme,
+// Ozaki, Ogita, Oishi 2012), as a precision alternative to the FP64-pipe
+// Block kernel for the DD product C := A B of Kouya 2015, Section 2, Eq. 1.
+//
+// Split (integer pipe, no FP64). Row i of A is scaled by 2^-ea_i, where
+// 2^ea_i bounds every |a_ik|, and rounded to the integer
+//   X_ik = round(a_ik 2^(T - ea_i)),   T = 6 + 7 (s - 1),
+// then written in balanced base 128: X = sum_p d_p 128^(s-p), d_p in
+// [-64, 63] for p >= 2 and d_1 in [-64, 64]. The digits of slice p form an
+// int8 matrix alpha^(p); B is split the same way per column j (beta^(q),
+// stored transposed so that both operands are k-contiguous).
+// Products (INT8 tensor cores, mma.sync m16n8k32 with INT32 accumulation;
+// tcgen05 has no INT8 kind on sm_103a). Slice pairs of equal weight
+// 2^(-12 - 7 (p + q - 2)) are summed by concatenating along k: for each
+// diagonal r = p + q = 2 .. s + 1,
+//   D_r = sum_{p + q = r} alpha^(p) beta^(q),
+// exact in INT32 while (r - 1) l 2^12 < 2^31. Pairs with p + q > s + 1 are
+// dropped (their weight is below the slices' own rounding).
+// Recombination (integer pipe): V_ij = sum_r D_r 2^(7 (s + 1 - r)) exactly in
+// a 192-bit fixed-point word, then c_ij = V_ij 2^(ea_i + fb_j - T - 6), rounded
+// to DD (and combined with C for the update modes).
+// Error per entry <= l (s + 3) 2^(-7 s) 2^(ea_i + fb_j) (slice rounding and
+// dropped pairs) plus the final DD rounding.
+#include <algorithm>
+#include <string>
+
+#include "arith.cuh"
+#include "fx.cuh"
+#include "kernels.cuh"
+
+namespace ddg {
+
+namespace {
+
+constexpr int OBM = 128, OBN = 128, OBK = 64, OST = 3, OROW = OBK + 16;
+constexpr int STAGE_BYTES = (OBM + OBN) * OROW;
+constexpr int OZ_SMEM = OST * STAGE_BYTES;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldsm_x4(const void* p, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(s));
+}
+
+__device__ __forceinline__ void mma_s8(int (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+}  // namespace
+
+// Largest exponent field of the leading limb per row (byrow) or per column.
+__global__ void oz_exp_kernel(int64_t rows, int64_t cols, mat X, int byrow, int* ex) {
+  if (byrow) {
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    int f = 1;
+    for (int64_t k = lane; k < cols; k += 32) f = max(f, fx::expfield(X.p[0][r * X.ld + k]));
+    f = __reduce_max_sync(0xffffffffu, f);
+    if (lane == 0) ex[r] = f;
+  } else {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    int f = 1;
+    for (int64_t k = 0; k < rows; ++k) f = max(f, fx::expfield(X.p[0][k * X.ld + c]));
+    ex[c] = f;
+  }
+}
+
+// Balanced base-128 digits of round(x 2^(T - e)) for x = hi + lo, where
+// 2^e bounds |x| (field = biased exponent with |hi| < 2^(field - 1022)).
+__device__ __forceinline__ void oz_digits(double hi, double lo, int field, int s, int8_t* out,
+                                          int64_t stride) {
+  const int T = 6 + 7 * (s - 1);
+  uint32_t acc[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+  // LSB of acc = 2^(e - T - 64); a double M 2^(E - 1075) sits at E - field + T + 11
+  {
+    fx::unpacked u = fx::unpack(hi);
+    uint32_t p[4] = {u.m0, u.m1, 0u, 0u};
+    fx::place<6, 3>(acc, p, u.e - field + T + 11, u.s);
+    fx::unpacked v = fx::unpack(lo);
+    uint32_t q[4] = {v.m0, v.m1, 0u, 0u};
+    fx::place<6, 2>(acc, q, v.e - field + T + 11, v.s);
+  }
+  // X = floor((acc + 2^63) / 2^64): round half up to an integer
+  const uint32_t half[6] = {0u, 0x80000000u, 0u, 0u, 0u, 0u};
+  fx::acc_add<6>(acc, half, 0u);
+  unsigned long long xl = ((unsigned long long)acc[3] << 32) | acc[2];
+  long long xh = (long long)(((unsigned long long)acc[5] << 32) | acc[4]);
+  for (int p = s; p >= 2; --p) {
+    int d = (int)(xl & 127u);
+    d = d >= 64 ? d - 128 : d;
+    // (X - d) >> 7, 128-bit arithmetic
+    const long long dd = d;
+    const unsigned long long nl = xl - (unsigned long long)dd;
+    const long long borrow = (dd > 0 && nl > xl) ? 1 : ((dd < 0 && nl < xl) ? -1 : 0);
+    xh -= borrow;
+    xl = (nl >> 7) | ((unsigned long long)xh << 57);
+    xh >>= 7;
+    out[(int64_t)(p - 1) * stride] = (int8_t)d;
+  }
+  out[0] = (int8_t)(int)(long long)xl;  // remaining top digit in [-64, 64]
+}
+
+// Slices of A (per row) into As[s][mpad][lpad], of B (per column, stored
+// transposed) into Bs[s][npad][lpad]; padding is zero.
+__global__ void oz_split_a_kernel(int64_t m, int64_t l, mat A, const int* ex, int s, int64_t mpad,
+                                  int64_t lpad, int8_t* As) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (k >= lpad) return;
+  const int64_t stride = mpad * lpad;
+  int8_t* out = As + i * lpad + k;
+  if (i < m && k < l) {
+    oz_digits(A.p[0][i * A.ld + k], A.p[1][i * A.ld + k], ex[i], s, out, stride);
+  } else {
+    for (int p = 0; p < s; ++p) out[(int64_t)p * stride] = 0;
+  }
+}
+
+__global__ void oz_split_b_kernel(int64_t l, int64_t n, mat B, const int* ex, int s, int64_t npad,
+                                  int64_t lpad, int8_t* Bs) {
+  // tile: 32 k x 32 j; digits staged in shared memory and written k-contiguous
+  __shared__ int8_t t[18][32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int64_t k0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  for (int kk = ty; kk < 32; kk += 8) {
+    const int64_t k = k0 + kk, j = j0 + tx;
+    int8_t dig[18];
+    if (k < l && j < n) {
+      oz_digits(B.p[0][k * B.ld + j], B.p[1][k * B.ld + j], ex[j], s, dig, 1);
+    } else {
+      for (int p = 0; p < s; ++p) dig[p] = 0;
+    }
+    for (int p = 0; p < s; ++p) t[p][tx][kk] = dig[p];
+  }
+  __syncthreads();
+  const int64_t stride = npad * lpad;
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int64_t j = j0 + jj, k = k0 + tx;
+    if (j < npad && k < lpad)
+      for (int p = 0; p < s; ++p) Bs[(int64_t)p * stride + j * lpad + k] = t[p][jj][tx];
+  }
+}
+
+// D[r - 2] = sum_{p + q = r} alpha^(p) beta^(q) for the diagonal of blockIdx.z
+// (z = 0 is the longest diagonal, r = s + 1, scheduled first).
+__global__ void __launch_bounds__(256) oz_gemm_kernel(int64_t mpad, int64_t npad, int64_t lpad, int s,
+                                                      const int8_t* __restrict__ As,
+                                                      const int8_t* __restrict__ Bs, int32_t* D) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps: 64 x 32 each
+  const int r = s + 1 - (int)blockIdx.z;
+  const int nseg = r - 1;
+  const int64_t m0 = (int64_t)blockIdx.y * OBM, n0 = (int64_t)blockIdx.x * OBN;
+  const int kps = (int)(lpad / OBK);
+  const int total = nseg * kps;
+
+  auto load = [&](int q, int stage) {
+    const int seg = q / kps, kk = q % kps;
+    const int pa = seg + 1, pb = r - pa;
+    const int8_t* ga = As + (int64_t)(pa - 1) * mpad * lpad + m0 * lpad + (int64_t)kk * OBK;
+    const int8_t* gb = Bs + (int64_t)(pb - 1) * npad * lpad + n0 * lpad + (int64_t)kk * OBK;
+    uint8_t* sa = smem + stage * STAGE_BYTES;
+    uint8_t* sb = sa + OBM * OROW;
+#pragma unroll
+    for (int c = tid; c < OBM * OBK / 16; c += 256) {
+      const int row = c >> 2, col = (c & 3) * 16;
+      cp_async16(sa + row * OROW + col, ga + row * lpad + col);
+      cp_async16(sb + row * OROW + col, gb + row * lpad + col);
+    }
+  };
+
+  int acc[4][4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0;
+
+#pragma unroll
+  for (int q = 0; q < OST - 1; ++q) {
+    if (q < total) load(q, q);
+    cp_commit();
+  }
+  for (int q = 0; q < total; ++q) {
+    cp_wait<OST - 2>();
+    __syncthreads();
+    if (q + OST - 1 < total) load(q + OST - 1, (q + OST - 1) % OST);
+    cp_commit();
+    const uint8_t* sa = smem + (q % OST) * STAGE_BYTES;
+    const uint8_t* sb = sa + OBM * OROW;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      uint32_t af[4][4], bf[4][2];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) {
+        const int row = wm * 64 + mi * 16 + (lane & 15);
+        const int col = ks * 32 + (lane >> 4) * 16;
+        ldsm_x4(sa + row * OROW + col, af[mi][0], af[mi][1], af[mi][2], af[mi][3]);
+      }
+#pragma unroll
+      for (int nj = 0; nj < 2; ++nj) {
+        const int row = wn * 32 + nj * 16 + (lane & 7) + ((lane >> 4) << 3);
+        const int col = ks * 32 + ((lane >> 3) & 1) * 16;
+        ldsm_x4(sb + row * OROW + col, bf[2 * nj][0], bf[2 * nj][1], bf[2 * nj + 1][0], bf[2 * nj + 1][1]);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) mma_s8(acc[mi][ni], af[mi], bf[ni][0], bf[ni][1]);
+    }
+  }
+  cp_wait<0>();
+  int32_t* Dr = D + (int64_t)(r - 2) * mpad * npad;
+  const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) {
+      const int64_t row = m0 + wm * 64 + mi * 16 + g;
+      const int64_t col = n0 + wn * 32 + ni * 8 + 2 * tq;
+      *reinterpret_cast<int2*>(Dr + row * npad + col) = make_int2(acc[mi][ni][0], acc[mi][ni][1]);
+      *reinterpret_cast<int2*>(Dr + (row + 8) * npad + col) = make_int2(acc[mi][ni][2], acc[mi][ni][3]);
+    }
+}
+
+// C (mode) sum_r D_r 2^(ea_i + fb_j - 12 - 7 (r - 2)), exact in 192 bits,
+// rounded once to DD.
+__global__ void oz_recombine_kernel(int64_t m, int64_t n, int s, int64_t mpad, int64_t npad,
+                                    const int32_t* D, const int* exa, const int* exb, mat C, int mode) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= n || i >= m) return;
+  uint32_t acc[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+  const int64_t plane = mpad * npad;
+  for (int r = 2; r <= s + 1; ++r) {
+    const int32_t v = D[(int64_t)(r - 2) * plane + i * npad + j];
+    const int sh = 7 * (s + 1 - r);
+    const int w = sh >> 5, b = sh & 31;
+    const long long x = (long long)v * (long long)(1u << b);  // |x| < 2^62
+    const uint32_t lo = (uint32_t)x, hi = (uint32_t)((unsigned long long)x >> 32);
+    const uint32_t ext = x < 0 ? 0xFFFFFFFFu : 0u;
+    uint32_t d[6];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) d[t] = t < w ? 0u : (t == w ? lo : (t == w + 1 ? hi : ext));
+    fx::acc_add<6>(acc, d, 0u);
+  }
+  const int T = 6 + 7 * (s - 1);
+  // a ~ 2^(ea - T) sum_p d_p 128^(s - p), likewise b, so
+  // c = 2^(ea + fb - 2T) sum_r D_r 128^(2s - r) = V 2^(ea + fb - T - 6),
+  // with ea = exa - 1022, fb = exb - 1022.
+  const int lsb = (exa[i] - 1022) + (exb[j] - 1022) - T - 6;
+  const uint32_t neg = fx::acc_abs<6>(acc);
+  uint64_t ch[2];
+  int ex[2];
+  dd_t v{0.0, 0.0};
+  if (fx::acc_chunks<6, 2>(acc, ch, ex)) {
+    auto sc = [&](uint64_t c, int k) {
+      if (c == 0 || k < -2044) return 0.0;
+      double x = fx::pow2_product(__ull2double_rn(c), k > 2046 ? 2046 : k);
+      return neg ? -x : x;
+    };
+    two_sum(sc(ch[0], lsb + ex[0]), sc(ch[1], lsb + ex[1]), v.hi, v.lo);
+  }
+  const int64_t off = i * C.ld + j;
+  if (mode == MODE_ADD) v = dd_add(dd_t{C.p[0][off], C.p[1][off]}, v);
+  else if (mode == MODE_SUB) v = dd_add(dd_t{C.p[0][off], C.p[1][off]}, dd_neg(v));
+  C.p[0][off] = v.hi;
+  C.p[1][off] = v.lo;
+}
+
+// ------------------------------------------------------------------ host --
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+ddg_status ozaki_dd_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
+                         int mode, int s, cudaStream_t st) {
+  if (m == 0 || n == 0) return DDG_OK;
+  // X < 2^T must fit the 128-bit digit loop and the 192-bit split word: T <= 125
+  if (s < 2 || s > 18) return set_error(DDG_EINVAL, "ozaki slices must be in [2, 18]");
+  const int64_t mpad = (m + OBM - 1) / OBM * OBM, npad = (n + OBN - 1) / OBN * OBN;
+  const int64_t lpad = std::max<int64_t>(OBK, (l + OBK - 1) / OBK * OBK);
+  if ((int64_t)s * lpad * 4096 >= ((int64_t)1 << 31))
+    return set_error(DDG_EINVAL, "ozaki: s * l too large for exact INT32 accumulation");
+  const size_t bA = al256((size_t)s * mpad * lpad), bB = al256((size_t)s * npad * lpad);
+  const size_t bD = al256((size_t)s * mpad * npad * 4), bE = al256((size_t)(m + n) * 4);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, bA + bB + bD + bE, st) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(DDG_ENOMEM, "ozaki: workspace allocation failed");
+  }
+  char* base = static_cast<char*>(ws);
+  int8_t* As = reinterpret_cast<int8_t*>(base);
+  int8_t* Bs = reinterpret_cast<int8_t*>(base + bA);
+  int32_t* D = reinterpret_cast<int32_t*>(base + bA + bB);
+  int* exa = reinterpret_cast<int*>(base + bA + bB + bD);
+  int* exb = exa + m;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    attr_done = true;
+  }
+  cudaEvent_t ev = nullptr;
+  auto launched = [&]() { g_launches.fetch_add(1, std::memory_order_relaxed); };
+  oz_exp_kernel<<<(unsigned)((m + 7) / 8), 256, 0, st>>>(m, l, A, 1, exa);
+  launched();
+  oz_exp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(l, n, B, 0, exb);
+  launched();
+  oz_split_a_kernel<<<dim3((unsigned)((lpad + 255) / 256), (unsigned)mpad), 256, 0, st>>>(m, l, A, exa, s, mpad, lpad, As);
+  launched();
+  oz_split_b_kernel<<<dim3((unsigned)(npad / 32), (unsigned)(lpad / 32)), dim3(32, 8), 0, st>>>(l, n, B, exb, s, npad, lpad, Bs);
+  launched();
+  prof_begin_launch(st, &ev);
+  oz_gemm_kernel<<<dim3((unsigned)(npad / OBN), (unsigned)(mpad / OBM), (unsigned)s), 256, OZ_SMEM, st>>>(
+      mpad, npad, lpad, s, As, Bs, D);
+  launched();
+  cudaError_t e = cudaGetLastError();
+  if (ev) {
+    const double pairs = 0.5 * s * (s + 1);
+    prof_end_launch(st, ev, PROF_OZAKI, 2.0 * pairs * (double)mpad * (double)npad * (double)lpad,
+                    (double)s * (mpad + npad) * lpad + 4.0 * s * mpad * npad);
+  }
+  if (e == cudaSuccess) {
+    oz_recombine_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)m), 256, 0, st>>>(m, n, s, mpad, npad, D, exa, exb, C, mode);
+    launched();
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(ws, st);
+  if (e != cudaSuccess) return set_error(DDG_ECUDA, std::string("ozaki: ") + cudaGetErrorString(e));
+  return DDG_OK;
+}
+
+}  // namespace ddg

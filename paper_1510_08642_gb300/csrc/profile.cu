@@ -78,7 +78,7 @@ ddg_status ddg_profile_end(ddg_kernel_prof* out, int32_t nkinds) {
       ddg_kernel_prof& o = out[r.kind];
       o.launches += 1;
       o.sum_ms += d;
-      o.fp64_ops += r.fp64_ops;
+      o.ops += r.fp64_ops;
       o.bytes += r.bytes;
       iv[r.kind].push_back({t0, t1});
     }

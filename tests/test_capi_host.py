@@ -37,7 +37,7 @@ def test_block_ops_per_mac():
 
 def test_opts_default():
     o = capi.opts()
-    assert (o.algo, o.cutoff, o.pad, o.streams, o.accum) == (capi.DDG_WINOGRAD, 512, 0, 7, 0)
+    assert (o.algo, o.cutoff, o.pad, o.streams, o.accum, o.slices) == (capi.DDG_WINOGRAD, 512, 0, 7, 0, 0)
 
 
 FAKE = 1 << 40  # never dereferenced: every call below fails validation or is empty

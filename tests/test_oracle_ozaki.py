@@ -1,0 +1,73 @@
+"""Pins for the INT8-slice oracle (oracle/ozaki.py), against exact arithmetic.
+
+* the integer X is within 1/2 + 2^-63 of a 2^(T - e) (rounding);
+* the balanced digits reconstruct X exactly and lie in [-64, 64];
+* every product of digit slices is exact in INT32 for the sizes used;
+* the whole result is within its error bound of the exact product
+  (Kulisch checker) and exact for integer matrices with enough slices.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.ozaki as OZ
+from paper_1510_08642_gb300 import inputs as I
+
+
+@pytest.mark.parametrize("s", [4, 9, 16])
+def test_split_reconstructs(s):
+    A = I.uniform(5, 9, 2, seed=1)
+    A[:, 2, 3] = 0.0
+    A[:, 4, :] *= 2.0 ** -40
+    T = 6 + 7 * (s - 1)
+    S, f = OZ.split(A, s, by_row=True)
+    assert np.all(np.abs(S) <= 64)
+    assert np.all(np.abs(S[1:]) <= 64) and np.all(S[1:] >= -64) and np.all(S[1:] <= 63)
+    for i in range(5):
+        e = int(f[i]) - 1022
+        for k in range(9):
+            X = sum(int(S[p, i, k]) * 128 ** (s - 1 - p) for p in range(s))
+            exact = (Fraction(float(A[0, i, k])) + Fraction(float(A[1, i, k]))) * Fraction(2) ** (T - e)
+            assert abs(X - exact) <= Fraction(1, 2) + Fraction(1, 1 << 62)
+            assert abs(exact) < Fraction(2) ** T
+
+
+def test_digits_balanced_cases():
+    s = 5
+    for X in [0, 1, -1, 63, 64, -64, 127, 128, -129, 64 * 128 ** 4, -64 * 128 ** 4, 12345678, -987654321]:
+        d = OZ.digits(X, s)
+        assert sum(v * 128 ** (s - 1 - p) for p, v in enumerate(d)) == X
+        assert all(-64 <= v <= 63 for v in d[1:])
+
+
+@pytest.mark.parametrize("s", [8, 12, 16])
+def test_ozaki_within_bound(s):
+    m, l, n = 7, 33, 6
+    A = I.uniform(m, l, 2, seed=2)
+    B = I.uniform(l, n, 2, seed=3)
+    C, (SA, SB, D, fa, fb) = OZ.gemm(A, B, s)
+    assert np.abs(D).max() < 2 ** 31
+    err = O.gemm_error(A, B, C)
+    for i in range(m):
+        for j in range(n):
+            scale = 2.0 ** (int(fa[i]) - 1022 + int(fb[j]) - 1022)
+            assert abs(err[i, j]) <= l * (s + 3) * 2.0 ** (-7 * s) * scale + 2.0 ** -104 * scale
+
+
+def test_ozaki_integer_exact():
+    A = I.integer(6, 20, 2, seed=4, bits=20)
+    B = I.integer(20, 5, 2, seed=5, bits=20)
+    C, _ = OZ.gemm(A, B, 8)
+    assert not O.gemm_error(A, B, C).any()
+
+
+def test_ozaki_modes():
+    A = I.uniform(4, 10, 2, seed=6)
+    B = I.uniform(10, 3, 2, seed=7)
+    C0 = I.uniform(4, 3, 2, seed=8)
+    for mode in ("add", "sub"):
+        C, _ = OZ.gemm(A, B, 16, C0=C0, mode=mode)
+        err = O.gemm_error(A, B, C, C0=C0, mode=mode)
+        assert np.abs(err).max() < 2.0 ** -95
