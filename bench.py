@@ -40,6 +40,7 @@ FP64_PER_CLK_PER_SM = 2          # measured: DFMA throughput probe (profiles/fp6
 SM_MAX_MHZ = 2070.0               # profiling recipe / MEASURED_PEAKS.json
 FP64_PEAK = SM_COUNT * FP64_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # FP64 instructions per second
 PINNED_MAC_OPS = {2: 27, 4: 218}  # DD / QD multiply then add of the Simple kernel
+INT8_MMA_PEAK = 1.50e14           # mma.sync m16n8k32 s8 ops/s, measured by the same probe
 
 
 def parse():
@@ -217,13 +218,25 @@ def run_reference(args, w):
 
 # ----------------------------------------------------------------- GPU leg --
 def roofline_of(prof, limbs):
-    """Dominant kernel (Block base case): FP64 instructions per busy second."""
+    """Dominant kernel: the Block base case (FP64 instructions per busy
+    second) or, for the INT8-slice product, its slice GEMM (INT8 ops)."""
+    oz = prof.get("ozaki")
+    if oz and oz["launches"]:
+        achieved = oz["ops"] / (oz["busy_ms"] * 1e-3)
+        return {"bound": "tensor", "kernel": "oz_gemm_kernel (INT8 mma.sync m16n8k32)",
+                "achieved": achieved / 1e12, "peak": INT8_MMA_PEAK / 1e12, "unit": "T INT8-op/s",
+                "frac": achieved / INT8_MMA_PEAK, "traffic": None,
+                "peak_source": "measured: mma.sync s8 throughput probe (tcgen05 has no INT8 kind on "
+                               "sm_103a; MEASURED_PEAKS.json has no INT8 figure)",
+                "launches": int(oz["launches"]), "avg_launch_ms": oz["sum_ms"] / oz["launches"],
+                "busy_ms": oz["busy_ms"]}
     b = prof["block"]
     if not b["launches"]:
         return None
     achieved = b["ops"] / (b["busy_ms"] * 1e-3)
     avg_ms = b["sum_ms"] / b["launches"]
-    ops_mac = {2: 12, 4: 113}[limbs]
+    from paper_1510_08642_gb300 import capi
+    ops_mac = capi.ddg_block_fp64_ops_per_mac(limbs, 0)
     return {"bound": "alu", "kernel": f"block_kernel<{limbs}> (FP64 pipe)",
             "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "T FP64-instr/s",
             "frac": achieved / FP64_PEAK, "traffic": None,
@@ -237,7 +250,7 @@ def roofline_of(prof, limbs):
 def time_gpu(P, torch, w, dA, dB, dC, cutoff, steps, warmup, stream, dist=None, device=None,
              profile=True):
     from paper_1510_08642_gb300 import capi
-    kw = dict(algo=w.algo, cutoff=cutoff)
+    kw = dict(algo=w.algo, cutoff=cutoff, slices=w.slices)
     for _ in range(warmup):
         P.gemm(dA, dB, dC, **kw)
     torch.cuda.synchronize()
@@ -282,6 +295,34 @@ def run_e2e(P, torch, w, args, dist, device, stream, hA, hB, hC, dA, dB, dC, cut
             "d2h_bytes_per_step": int(hC.numel() * 8), "ms_per_step": ms_e2e}
 
 
+def time_lu(P, torch, w, device, stream, K):
+    """Section 4 solve: dd_getrf (Winograd trailing updates) + dd_getrs, b = A 1."""
+    from paper_1510_08642_gb300 import inputs as I
+    n = w.n
+    A0 = torch.from_numpy(I.uniform(n, n, 2, seed=w.seed_a)).to(device)
+    ones = torch.zeros((2, n, 1), dtype=torch.float64, device=device)
+    ones[0] = 1.0
+    b0 = P.gemm(A0, ones, algo="block")
+    times = []
+    for it in range(2):  # one warm-up, one timed
+        A = A0.clone()
+        b = b0.clone()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ipiv = P.getrf(A, K=K, pivot=True, algo=w.algo, cutoff=w.cutoff)
+        P.getrs(A, ipiv, b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = times[-1]
+    err = float((b[0] - 1.0 + b[1]).abs().max().item())
+    return {"value": (2.0 * n ** 3 / 3.0) / (ms * 1e-3) / 1e9, "unit": "G 2mnl/s (2n^3/3 per solve)",
+            "ms": ms, "K": K, "cutoff": w.cutoff, "pivot": "partial", "steps": 1, "warmup": 1,
+            "max_abs_err_x_minus_1": err}
+
+
 def run_ours(args, w):
     import numpy as np
     import torch
@@ -307,7 +348,7 @@ def run_ours(args, w):
     clocks = Clocks(local)
     # -------- timed region: device-resident inputs
     for _ in range(args.warmup):
-        P.gemm(dA, dB, dC, algo=w.algo, cutoff=cutoff)
+        P.gemm(dA, dB, dC, algo=w.algo, cutoff=cutoff, slices=w.slices)
     torch.cuda.synchronize()
     clocks.start()
     ms, prof, launches = time_gpu(P, torch, w, dA, dB, dC, cutoff, args.steps, 0, stream, dist, device)
@@ -343,7 +384,8 @@ def run_ours(args, w):
     # -------- extras (rank 0 of a single-GPU run only; 1 warm-up, 1 timed)
     if args.extras == "all" and world == 1 and w.name == WL.DD_WINOGRAD_4096.name:
         extras = {}
-        for xw in (WL.DD_BLOCK_4096, WL.QD_WINOGRAD_4096, WL.QD_BLOCK_4096):
+        for xw in (WL.DD_BLOCK_4096, WL.QD_WINOGRAD_4096, WL.QD_BLOCK_4096, WL.DD_OZAKI_4096_S16,
+                   WL.DD_OZAKI_4096_S13, WL.DD_WINOGRAD_8192, WL.DD_OZAKI_8192_S16):
             XA = torch.from_numpy(I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_a)).to(device)
             XB = torch.from_numpy(I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_b)).to(device)
             XC = torch.empty((xw.limbs, xw.n, xw.n), dtype=torch.float64, device=device)
@@ -352,6 +394,7 @@ def run_ours(args, w):
                                "roofline": roofline_of(xprof, xw.limbs), "steps": 1, "warmup": 1}
             del XA, XB, XC
             torch.cuda.empty_cache()
+        extras[WL.DD_LU_4096.name] = time_lu(P, torch, WL.DD_LU_4096, device, stream, K=256)
         line["extras"] = extras
 
     if rank == 0 and world == 1 and args.cpu_seconds > 0:

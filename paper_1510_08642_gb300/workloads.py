@@ -16,6 +16,7 @@ class Workload:
     cutoff: int
     seed_a: int
     seed_b: int
+    slices: int = 0
 
     @property
     def macs(self) -> int:
@@ -34,3 +35,14 @@ DD_SIMPLE_128 = Workload("dd_simple_n128", 2, 128, "simple", 512, 0, 1)
 DD_BLOCK_2560 = Workload("dd_block_n2560", 2, 2560, "block", 512, 105, 106)
 QD_BLOCK_1536 = Workload("qd_block_n1536", 4, 1536, "block", 512, 107, 108)
 DD_WINOGRAD_2560 = Workload("dd_winograd_n2560", 2, 2560, "winograd", 320, 105, 106)
+# The precision study: the INT8-slice DD product against the FP64-pipe DD
+# Winograd product, n = 4096 and 8192.
+DD_OZAKI_4096_S16 = Workload("dd_ozaki_n4096_s16", 2, 4096, "ozaki", 512, 101, 102, 16)
+DD_OZAKI_4096_S13 = Workload("dd_ozaki_n4096_s13", 2, 4096, "ozaki", 512, 101, 102, 13)
+DD_WINOGRAD_8192 = Workload("dd_winograd_n8192", 2, 8192, "winograd", 512, 109, 110)
+DD_OZAKI_8192_S16 = Workload("dd_ozaki_n8192_s16", 2, 8192, "ozaki", 512, 109, 110, 16)
+# Section 4 LU solve (random [-1, 1] matrix), block column K, Winograd update.
+DD_LU_4096 = Workload("dd_lu_n4096", 2, 4096, "winograd", 512, 111, 0)
+# Same 512^3 leaves as the headline at n = 2048 (two levels, 49 leaves):
+# operands 200 MB > L2, small enough for a counter capture.
+DD_WINOGRAD_2048 = Workload("dd_winograd_n2048", 2, 2048, "winograd", 512, 112, 113)
