@@ -184,6 +184,57 @@ ddg_status dd_getrs(int64_t n, int64_t nrhs, dd_mat LU, const int64_t* ipiv, dd_
 ddg_status dd_gemm_noalloc(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, dd_mat C,
                            int32_t mode, const ddg_opts* opts, void* stream);
 
+/*
+ * Batched products (grouped launches). The paper has no batched form; this
+ * runs many independent C (mode) A B problems of uneven shapes, DD and QD
+ * mixed, as a few grouped persistent launches: every problem's Strassen /
+ * Winograd recursion is expanded breadth-first, the fused passes of one
+ * depth share a launch, and every base-case Block product of the batch
+ * shares one launch per limb count (tiles taken from a global counter).
+ * Problems must write disjoint C; A and B may be shared.
+ */
+typedef struct {
+  int32_t limbs;   /* 2 (DD) or 4 (QD) */
+  int32_t mode;    /* ddg_mode */
+  int64_t m, l, n;
+  double* A[4];    /* limb planes (device); unused entries ignored */
+  int64_t lda;
+  double* B[4];
+  int64_t ldb;
+  double* C[4];
+  int64_t ldc;
+  int32_t algo;    /* DDG_BLOCK, DDG_STRASSEN or DDG_WINOGRAD */
+  int32_t cutoff;  /* recursion cutoff n_min, >= 1 */
+} ddg_problem;
+
+typedef struct {
+  int64_t problems;
+  int64_t leaf_tasks;       /* base-case products */
+  int64_t leaf_tiles;       /* CTA tiles over all grouped Block launches */
+  int64_t pass_tasks;       /* fused quadrant passes */
+  int64_t launches_per_run; /* kernels per ddg_batch_run */
+  uint64_t workspace_bytes;
+  double fp64_ops;          /* algorithmic FP64 instructions of the leaves */
+} ddg_batch_stats;
+
+typedef struct ddg_batch_s* ddg_batch;
+
+/* Plan a batch: validates every problem, expands the recursions, allocates
+ * all temporaries and uploads the task lists (cudaMalloc / cudaMemcpy:
+ * synchronous, on the current device). The plan keeps the pointers of the
+ * problems; their matrices must stay valid while the plan is run.
+ * use_graph = 1: ddg_batch_run captures the launches into a CUDA graph on
+ * its first call and replays the graph afterwards. */
+ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* probs, int32_t use_graph);
+/* Queue one execution of the plan on `stream` (allocation-free). Runs of
+ * one plan must not overlap on the GPU (they share the temporaries). */
+ddg_status ddg_batch_run(ddg_batch b, void* stream);
+ddg_status ddg_batch_get_stats(ddg_batch b, ddg_batch_stats* stats);
+/* Free the plan (cudaFree: waits for the device). */
+ddg_status ddg_batch_destroy(ddg_batch b);
+/* One-shot: create, run on `stream`, wait for it, destroy. */
+ddg_status dd_gemm_batched(int32_t count, const ddg_problem* probs, void* stream);
+
 /* FP64 instructions per DD (limbs = 2) or QD (limbs = 4) multiply-add in
  * the Block kernel's inner loop for accumulation scheme `accum` (0 or 1, as
  * in ddg_opts), counted from its source (for rooflines); -1 if invalid. */

@@ -75,3 +75,46 @@ def getrs(LU, ipiv, B, stream=None):
     s = (stream or torch.cuda.current_stream(LU.device)).cuda_stream
     capi.check(capi.dd_getrs(n, nrhs, _mat(LU, 2), ipiv.data_ptr(), _mat(B, 2), s))
     return B
+
+
+def problem(A, B, C, algo: str = "block", cutoff: int = 512, mode: str = "set"):
+    """A ddg_problem for the batched entry points from three device tensors."""
+    limbs = A.shape[0]
+    p = capi.ddg_problem()
+    p.limbs = limbs
+    p.mode = capi.MODES[mode]
+    p.m, p.l, p.n = A.shape[1], A.shape[2], B.shape[2]
+    for name, T in (("A", A), ("B", B), ("C", C)):
+        mt = _mat(T, limbs)
+        ptrs = [mt.hi, mt.lo] if limbs == 2 else list(mt.x)
+        arr = getattr(p, name)
+        for q in range(limbs):
+            arr[q] = ptrs[q]
+        setattr(p, "ld" + name.lower(), mt.ld)
+    p.algo = capi.ALGOS[algo]
+    p.cutoff = cutoff
+    return p
+
+
+class Batch:
+    """A batch plan (ddg_batch): grouped launches, optionally a CUDA graph."""
+
+    def __init__(self, problems, use_graph: bool = False):
+        self.handle = capi.ddg_batch_create(problems, use_graph)
+        self.stats = capi.ddg_batch_get_stats(self.handle)
+
+    def run(self, stream=None):
+        import torch
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        capi.ddg_batch_run(self.handle, s)
+
+    def close(self):
+        if self.handle:
+            capi.ddg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

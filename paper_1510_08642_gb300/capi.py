@@ -48,6 +48,18 @@ class ddg_kernel_prof(ctypes.Structure):
 PROF_KINDS = ("simple", "block", "pass", "ozaki")
 
 
+class ddg_problem(ctypes.Structure):
+    _fields_ = [("limbs", c_i32), ("mode", c_i32), ("m", c_i64), ("l", c_i64), ("n", c_i64),
+                ("A", c_vp * 4), ("lda", c_i64), ("B", c_vp * 4), ("ldb", c_i64),
+                ("C", c_vp * 4), ("ldc", c_i64), ("algo", c_i32), ("cutoff", c_i32)]
+
+
+class ddg_batch_stats(ctypes.Structure):
+    _fields_ = [("problems", c_i64), ("leaf_tasks", c_i64), ("leaf_tiles", c_i64),
+                ("pass_tasks", c_i64), ("launches_per_run", c_i64),
+                ("workspace_bytes", ctypes.c_uint64), ("fp64_ops", ctypes.c_double)]
+
+
 class DDGError(RuntimeError):
     def __init__(self, status: int, msg: str):
         name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
@@ -65,6 +77,11 @@ SIGNATURES = {
     "dd_gemm_noalloc": (c_i32, [c_i64, c_i64, c_i64, dd_mat, dd_mat, dd_mat, c_i32,
                                 ctypes.POINTER(ddg_opts), c_vp]),
     "ddg_block_fp64_ops_per_mac": (c_i32, [c_i32, c_i32]),
+    "ddg_batch_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(ddg_problem), c_i32]),
+    "ddg_batch_run": (c_i32, [c_vp, c_vp]),
+    "ddg_batch_get_stats": (c_i32, [c_vp, ctypes.POINTER(ddg_batch_stats)]),
+    "ddg_batch_destroy": (c_i32, [c_vp]),
+    "dd_gemm_batched": (c_i32, [c_i32, ctypes.POINTER(ddg_problem), c_vp]),
     "dd_getrf": (c_i32, [c_i64, dd_mat, c_vp, c_i32, c_i32, ctypes.POINTER(ddg_opts), c_vp, c_vp]),
     "dd_getrs": (c_i32, [c_i64, c_i64, dd_mat, c_vp, dd_mat, c_vp]),
     "ddg_last_error": (ctypes.c_char_p, []),
@@ -164,3 +181,29 @@ def dd_getrf(n, A: dd_mat, ipiv: int, K: int, pivot: int, o: ddg_opts | None, in
 
 def dd_getrs(n, nrhs, LU: dd_mat, ipiv: int, B: dd_mat, stream: int = 0) -> int:
     return load().dd_getrs(n, nrhs, LU, c_vp(ipiv), B, c_vp(stream))
+
+
+def ddg_batch_create(problems, use_graph: bool = False) -> int:
+    arr = (ddg_problem * max(len(problems), 1))(*problems)
+    h = c_vp()
+    check(load().ddg_batch_create(ctypes.byref(h), len(problems), arr, 1 if use_graph else 0))
+    return h.value
+
+
+def ddg_batch_run(handle: int, stream: int = 0) -> None:
+    check(load().ddg_batch_run(c_vp(handle), c_vp(stream)))
+
+
+def ddg_batch_get_stats(handle: int) -> dict:
+    st = ddg_batch_stats()
+    check(load().ddg_batch_get_stats(c_vp(handle), ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in ddg_batch_stats._fields_}
+
+
+def ddg_batch_destroy(handle: int) -> None:
+    check(load().ddg_batch_destroy(c_vp(handle)))
+
+
+def dd_gemm_batched(problems, stream: int = 0) -> int:
+    arr = (ddg_problem * max(len(problems), 1))(*problems)
+    return load().dd_gemm_batched(len(problems), arr, c_vp(stream))

@@ -20,6 +20,8 @@
 // Error: truncation below the window (2^-159 resp. 2^-255 of the largest
 // product of row i and column j, per term) plus one rounding per FP64 term
 // and the final rounding to DD/QD.
+#include <algorithm>
+
 #include "arith.cuh"
 #include "fx.cuh"
 #include "kernels.cuh"
@@ -49,20 +51,27 @@ __device__ __forceinline__ double scaled(uint64_t chunk, int k, uint32_t neg) {
 }  // namespace
 
 template <int L>
-__global__ void __launch_bounds__(128) block_fx_kernel(int64_t m, int64_t l, int64_t n, mat A,
-                                                       mat B, mat C, int mode) {
+struct fx_smem {
+  double As[L][fxcfg<L>::BK][fxcfg<L>::BM];
+  double Bs[L][fxcfg<L>::BK][fxcfg<L>::BN];
+  int row_f[fxcfg<L>::BM], col_f[fxcfg<L>::BN];
+};
+
+// One BM x BN tile of C at (i0, j0): C (mode) A B restricted to the tile.
+template <int L>
+__device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
+                                        const mat& C, int mode, int64_t i0, int64_t j0, fx_smem<L>& sm) {
   using P = fxcfg<L>;
   constexpr int BM = P::BM, BN = P::BN, BK = P::BK, TM = P::TM, TN = P::TN, NW = P::NW;
   constexpr int NX = BN / TN, NY = BM / TM, NT = NX * NY;
   static_assert(NT == 128, "block kernel assumes 128 threads");
-  __shared__ double As[L][BK][BM];
-  __shared__ double Bs[L][BK][BN];
-  __shared__ int row_f[BM], col_f[BN];
+  auto& As = sm.As;
+  auto& Bs = sm.Bs;
+  auto& row_f = sm.row_f;
+  auto& col_f = sm.col_f;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tx = tid % NX, ty = tid / NX;
-  const int64_t i0 = (int64_t)blockIdx.y * BM;
-  const int64_t j0 = (int64_t)blockIdx.x * BN;
 
   // ---- largest exponent field of the leading limb, per row of A / column of B
   for (int c = tid; c < BN; c += NT) col_f[c] = 1;
@@ -218,6 +227,71 @@ __global__ void __launch_bounds__(128) block_fx_kernel(int64_t m, int64_t l, int
         N::store(C.p, off, v);
       }
     }
+}
+
+template <int L>
+__global__ void __launch_bounds__(128) block_fx_kernel(int64_t m, int64_t l, int64_t n, mat A, mat B,
+                                                       mat C, int mode) {
+  __shared__ fx_smem<L> sm;
+  fx_tile<L>(m, l, n, A, B, C, mode, (int64_t)blockIdx.y * fxcfg<L>::BM,
+             (int64_t)blockIdx.x * fxcfg<L>::BN, sm);
+}
+
+// Grouped persistent launch: every CTA takes the next tile of the task list
+// (tiles numbered task by task, tasks sorted by decreasing l by the planner)
+// from a global counter until none is left. No CTA waits on another.
+template <int L>
+__global__ void __launch_bounds__(128) grouped_fx_kernel(const gtask* __restrict__ tasks, int ntasks,
+                                                         int64_t total, unsigned long long* counter) {
+  __shared__ fx_smem<L> sm;
+  __shared__ int64_t st;
+  for (;;) {
+    if (threadIdx.x == 0) st = (int64_t)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const int64_t t = st;
+    __syncthreads();
+    if (t >= total) break;
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tasks[mid].tile0 <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const gtask g = tasks[lo];
+    const int64_t local = t - g.tile0;
+    const int64_t bi = local / g.tiles_n, bj = local % g.tiles_n;
+    fx_tile<L>(g.m, g.l, g.n, g.A, g.B, g.C, g.mode, bi * fxcfg<L>::BM, bj * fxcfg<L>::BN, sm);
+    __syncthreads();
+  }
+}
+
+void fx_tile_shape(int limbs, int* bm, int* bn) {
+  *bm = limbs == 2 ? fxcfg<2>::BM : fxcfg<4>::BM;
+  *bn = limbs == 2 ? fxcfg<2>::BN : fxcfg<4>::BN;
+}
+
+cudaError_t launch_grouped_fx(int limbs, const gtask* tasks, int ntasks, int64_t total_tiles,
+                              unsigned long long* counter, double ops, cudaStream_t s) {
+  if (ntasks == 0 || total_tiles == 0) return cudaSuccess;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  const int per_sm = limbs == 2 ? 2 : 3;  // resident CTAs per SM (register limited)
+  const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)sms * per_sm);
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaEvent_t ev = nullptr;
+  prof_begin_launch(s, &ev);
+  if (limbs == 2) grouped_fx_kernel<2><<<(unsigned)grid, 128, 0, s>>>(tasks, ntasks, total_tiles, counter);
+  else grouped_fx_kernel<4><<<(unsigned)grid, 128, 0, s>>>(tasks, ntasks, total_tiles, counter);
+  e = cudaGetLastError();
+  if (ev) prof_end_launch(s, ev, PROF_BLOCK, ops, 0.0);
+  return e;
 }
 
 cudaError_t launch_block_fx(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,

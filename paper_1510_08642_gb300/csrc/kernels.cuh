@@ -55,8 +55,38 @@ cudaError_t launch_simple(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat
 cudaError_t launch_block_fx(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,
                             int mode, cudaStream_t s);
 int block_fx_fp64_ops_per_mac(int limbs);
+
+// One product of a grouped launch (device-resident task list). Tiles are
+// numbered consecutively: task t owns tiles [tile0, tile0 + tiles_m tiles_n).
+struct gtask {
+  int64_t m, l, n;
+  mat A, B, C;
+  int mode;
+  int tiles_n;
+  int64_t tile0;
+};
+void fx_tile_shape(int limbs, int* bm, int* bn);
+cudaError_t launch_grouped_fx(int limbs, const gtask* tasks, int ntasks, int64_t total_tiles,
+                              unsigned long long* counter, double ops, cudaStream_t s);
 cudaError_t launch_block(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,
                          int mode, cudaStream_t s);
+
+// Operands of one fused pass: up to 7 input and 5 output quadrants.
+struct pass_args {
+  mat in[7];
+  mat out[5];
+};
+
+// One pass of a grouped launch: tiles of 8 x 32 elements numbered from tile0.
+struct ptask {
+  int64_t rows, cols;
+  pass_args a;
+  int mode;
+  int tiles_x;
+  int64_t tile0;
+};
+cudaError_t launch_grouped_pass(int limbs, int kind, const ptask* tasks, int ntasks, int64_t total_tiles,
+                                cudaStream_t s);
 
 // One fused quadrant pass over a rows x cols quadrant grid.
 cudaError_t launch_pass(int limbs, int kind, int64_t rows, int64_t cols, const mat* in, int nin,

@@ -31,6 +31,8 @@ bool prof_enabled() { return g_on; }
 void prof_begin_launch(cudaStream_t s, cudaEvent_t* start) {
   *start = nullptr;
   if (!g_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   if (cudaEventCreate(start) != cudaSuccess) { *start = nullptr; return; }
   cudaEventRecord(*start, s);
 }
