@@ -323,6 +323,50 @@ def time_lu(P, torch, w, device, stream, K):
             "max_abs_err_x_minus_1": err}
 
 
+def time_batched(P, torch, device, stream, count=1000, reps=3):
+    """The batched workload: `count` products, m, l, n log-uniform in
+    [32, 1024], 70% DD / 30% QD, one batch plan replayed as a CUDA graph.
+    Operands are views into one resident 1024^2 pool per limb count (A and B
+    may be shared between problems; every C is its own)."""
+    from paper_1510_08642_gb300 import autotune, inputs as I
+    dims = I.log_uniform_dims(count, 32, 1024, seed=4)
+    kind = I.uniform01(5, count)
+    off = I.splitmix64(6, 4 * count).reshape(count, 4)
+    pools = {L: torch.from_numpy(I.uniform(1024, 1024, L, seed=200 + L)).to(device) for L in (2, 4)}
+    tuner = autotune.Tuner()
+    probs, keep, work = [], [], 0.0
+    for t in range(count):
+        m, l, n = (int(x) for x in dims[t])
+        L = 4 if kind[t] < 0.3 else 2
+        pool = pools[L]
+        r0, c0 = int(off[t, 0] % (1025 - m)), int(off[t, 1] % (1025 - l))
+        r1, c1 = int(off[t, 2] % (1025 - l)), int(off[t, 3] % (1025 - n))
+        A = pool[:, r0:r0 + m, c0:c0 + l]
+        B = pool[:, r1:r1 + l, c1:c1 + n]
+        C = torch.empty((L, m, n), dtype=torch.float64, device=device)
+        algo, cutoff = tuner.choose(L, m, l, n)
+        probs.append(P.problem(A, B, C, algo, cutoff))
+        keep.append(C)
+        work += 2.0 * m * l * n
+    batch = P.Batch(probs, use_graph=True)
+    batch.run(stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        batch.run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    st = dict(batch.stats)
+    batch.close()
+    return {"value": work / (ms * 1e-3) / 1e9, "unit": UNIT, "ms": ms, "problems": count,
+            "launches_per_run": st["launches_per_run"], "leaf_tiles": st["leaf_tiles"],
+            "workspace_bytes": st["workspace_bytes"], "graph": True, "steps": reps, "warmup": 1,
+            "tuning_table": os.path.exists(tuner.path)}
+
+
 def run_ours(args, w):
     import numpy as np
     import torch
@@ -395,6 +439,7 @@ def run_ours(args, w):
             del XA, XB, XC
             torch.cuda.empty_cache()
         extras[WL.DD_LU_4096.name] = time_lu(P, torch, WL.DD_LU_4096, device, stream, K=256)
+        extras["batched_1000_mixed"] = time_batched(P, torch, device, stream)
         line["extras"] = extras
 
     if rank == 0 and world == 1 and args.cpu_seconds > 0:

@@ -219,20 +219,24 @@ typedef struct {
 
 typedef struct ddg_batch_s* ddg_batch;
 
-/* Plan a batch: validates every problem, expands the recursions, allocates
- * all temporaries and uploads the task lists (cudaMalloc / cudaMemcpy:
- * synchronous, on the current device). The plan keeps the pointers of the
- * problems; their matrices must stay valid while the plan is run.
+/* Plan a batch on the current device: validates every problem, expands the
+ * recursions, takes all temporaries in one block from the stream-ordered
+ * allocator on `stream` and queues the upload of the task lists there (the
+ * host copy is staged before the call returns). The plan keeps the pointers
+ * of the problems; their matrices must stay valid while the plan is run.
+ * Runs on other streams must be ordered after `stream`.
  * use_graph = 1: ddg_batch_run captures the launches into a CUDA graph on
  * its first call and replays the graph afterwards. */
-ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* probs, int32_t use_graph);
+ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* probs, int32_t use_graph,
+                            void* stream);
 /* Queue one execution of the plan on `stream` (allocation-free). Runs of
  * one plan must not overlap on the GPU (they share the temporaries). */
 ddg_status ddg_batch_run(ddg_batch b, void* stream);
 ddg_status ddg_batch_get_stats(ddg_batch b, ddg_batch_stats* stats);
-/* Free the plan (cudaFree: waits for the device). */
-ddg_status ddg_batch_destroy(ddg_batch b);
-/* One-shot: create, run on `stream`, wait for it, destroy. */
+/* Free the plan: its memory is released in order on `stream` (after the
+ * runs queued there); a plan that used a graph first waits for the device. */
+ddg_status ddg_batch_destroy(ddg_batch b, void* stream);
+/* One-shot: create, run and release on `stream` (asynchronous). */
 ddg_status dd_gemm_batched(int32_t count, const ddg_problem* probs, void* stream);
 
 /* FP64 instructions per DD (limbs = 2) or QD (limbs = 4) multiply-add in

@@ -99,18 +99,18 @@ def problem(A, B, C, algo: str = "block", cutoff: int = 512, mode: str = "set"):
 class Batch:
     """A batch plan (ddg_batch): grouped launches, optionally a CUDA graph."""
 
-    def __init__(self, problems, use_graph: bool = False):
-        self.handle = capi.ddg_batch_create(problems, use_graph)
+    def __init__(self, problems, use_graph: bool = False, stream=None):
+        import torch
+        self.stream = stream or torch.cuda.current_stream()
+        self.handle = capi.ddg_batch_create(problems, use_graph, self.stream.cuda_stream)
         self.stats = capi.ddg_batch_get_stats(self.handle)
 
     def run(self, stream=None):
-        import torch
-        s = (stream or torch.cuda.current_stream()).cuda_stream
-        capi.ddg_batch_run(self.handle, s)
+        capi.ddg_batch_run(self.handle, (stream or self.stream).cuda_stream)
 
-    def close(self):
+    def close(self, stream=None):
         if self.handle:
-            capi.ddg_batch_destroy(self.handle)
+            capi.ddg_batch_destroy(self.handle, (stream or self.stream).cuda_stream)
             self.handle = None
 
     def __del__(self):

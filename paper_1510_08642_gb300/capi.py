@@ -77,10 +77,10 @@ SIGNATURES = {
     "dd_gemm_noalloc": (c_i32, [c_i64, c_i64, c_i64, dd_mat, dd_mat, dd_mat, c_i32,
                                 ctypes.POINTER(ddg_opts), c_vp]),
     "ddg_block_fp64_ops_per_mac": (c_i32, [c_i32, c_i32]),
-    "ddg_batch_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(ddg_problem), c_i32]),
+    "ddg_batch_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(ddg_problem), c_i32, c_vp]),
     "ddg_batch_run": (c_i32, [c_vp, c_vp]),
     "ddg_batch_get_stats": (c_i32, [c_vp, ctypes.POINTER(ddg_batch_stats)]),
-    "ddg_batch_destroy": (c_i32, [c_vp]),
+    "ddg_batch_destroy": (c_i32, [c_vp, c_vp]),
     "dd_gemm_batched": (c_i32, [c_i32, ctypes.POINTER(ddg_problem), c_vp]),
     "dd_getrf": (c_i32, [c_i64, dd_mat, c_vp, c_i32, c_i32, ctypes.POINTER(ddg_opts), c_vp, c_vp]),
     "dd_getrs": (c_i32, [c_i64, c_i64, dd_mat, c_vp, dd_mat, c_vp]),
@@ -183,10 +183,11 @@ def dd_getrs(n, nrhs, LU: dd_mat, ipiv: int, B: dd_mat, stream: int = 0) -> int:
     return load().dd_getrs(n, nrhs, LU, c_vp(ipiv), B, c_vp(stream))
 
 
-def ddg_batch_create(problems, use_graph: bool = False) -> int:
+def ddg_batch_create(problems, use_graph: bool = False, stream: int = 0) -> int:
     arr = (ddg_problem * max(len(problems), 1))(*problems)
     h = c_vp()
-    check(load().ddg_batch_create(ctypes.byref(h), len(problems), arr, 1 if use_graph else 0))
+    check(load().ddg_batch_create(ctypes.byref(h), len(problems), arr, 1 if use_graph else 0,
+                                  c_vp(stream)))
     return h.value
 
 
@@ -200,8 +201,8 @@ def ddg_batch_get_stats(handle: int) -> dict:
     return {f: getattr(st, f) for f, _ in ddg_batch_stats._fields_}
 
 
-def ddg_batch_destroy(handle: int) -> None:
-    check(load().ddg_batch_destroy(c_vp(handle)))
+def ddg_batch_destroy(handle: int, stream: int = 0) -> None:
+    check(load().ddg_batch_destroy(c_vp(handle), c_vp(stream)))
 
 
 def dd_gemm_batched(problems, stream: int = 0) -> int:

@@ -150,6 +150,7 @@ struct ddg_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int kernels_per_run = 0;
+  cudaStream_t create_stream = nullptr;
   ddg_batch_stats stats{};
 };
 
@@ -193,7 +194,8 @@ static bool bad_problem(const ddg_problem& p, std::string& why) {
 
 extern "C" {
 
-ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* probs, int32_t use_graph) {
+ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* probs, int32_t use_graph,
+                            void* stream) {
   using namespace ddg;
   clear_error();
   if (!out) return set_error(DDG_EINVAL, "out is null");
@@ -242,7 +244,8 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
     for (int L : {2, 4}) tb += ((dry.leaves[L].size() * sizeof(gtask) + 255) & ~(size_t)255) + 256;
     b->bytes = temps + tb + 4096;
   }
-  if (cudaMalloc(reinterpret_cast<void**>(&b->buf), std::max<size_t>(b->bytes, 256)) != cudaSuccess) {
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMallocAsync(reinterpret_cast<void**>(&b->buf), std::max<size_t>(b->bytes, 256), cs) != cudaSuccess) {
     cudaGetLastError();
     delete b;
     return set_error(DDG_ENOMEM, "ddg_batch_create: workspace of " + std::to_string(b->bytes) + " bytes");
@@ -303,12 +306,14 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
       if (std::get<0>(kv.first) == d) add_g(kv.second, std::get<1>(kv.first));
   }
   if (temps + host.size() > b->bytes) {
-    cudaFree(b->buf);
+    cudaFreeAsync(b->buf, cs);
     delete b;
     return set_error(DDG_ECUDA, "ddg_batch_create: task list larger than planned");
   }
-  if (!host.empty() && cudaMemcpy(b->buf + temps, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaFree(b->buf);
+  // pageable source: the copy is staged before the call returns
+  if (!host.empty() &&
+      cudaMemcpyAsync(b->buf + temps, host.data(), host.size(), cudaMemcpyHostToDevice, cs) != cudaSuccess) {
+    cudaFreeAsync(b->buf, cs);
     delete b;
     return set_error(DDG_ECUDA, "ddg_batch_create: task upload");
   }
@@ -319,10 +324,11 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
   b->stats.workspace_bytes = (uint64_t)b->bytes;
   b->stats.fp64_ops = real.fp64_ops;
   if (use_graph && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaFree(b->buf);
+    cudaFreeAsync(b->buf, cs);
     delete b;
     return set_error(DDG_ECUDA, "ddg_batch_create: capture stream");
   }
+  b->create_stream = cs;
   *out = b;
   return DDG_OK;
 }
@@ -334,6 +340,9 @@ ddg_status ddg_batch_run(ddg_batch b, void* stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!b->use_graph) return enqueue(b, s);
   if (!b->exec) {
+    // the capture stream must see the plan's upload, queued on the create stream
+    if (cudaStreamSynchronize(b->create_stream) != cudaSuccess)
+      return set_error(DDG_ECUDA, "ddg_batch_run: waiting for the plan upload");
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return set_error(DDG_ECUDA, "ddg_batch_run: begin capture");
     ddg_status st = enqueue(b, b->cap);
@@ -361,16 +370,21 @@ ddg_status ddg_batch_get_stats(ddg_batch b, ddg_batch_stats* st) {
   return DDG_OK;
 }
 
-ddg_status ddg_batch_destroy(ddg_batch b) {
+ddg_status ddg_batch_destroy(ddg_batch b, void* stream) {
   if (!b) return DDG_OK;
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(b->dev);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  if (b->cap) cudaStreamDestroy(b->cap);
   ddg_status st = DDG_OK;
-  if (b->buf && cudaFree(b->buf) != cudaSuccess) st = ddg::set_error(DDG_ECUDA, "ddg_batch_destroy: free");
+  if (b->exec || b->cap) {
+    // a graph may still be running: wait for the device before destroying it
+    if (cudaDeviceSynchronize() != cudaSuccess) st = ddg::set_error(DDG_ECUDA, "ddg_batch_destroy: sync");
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+  }
+  if (b->buf && cudaFreeAsync(b->buf, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess && st == DDG_OK)
+    st = ddg::set_error(DDG_ECUDA, "ddg_batch_destroy: free");
   cudaSetDevice(cur);
   delete b;
   return st;
@@ -378,12 +392,10 @@ ddg_status ddg_batch_destroy(ddg_batch b) {
 
 ddg_status dd_gemm_batched(int32_t count, const ddg_problem* probs, void* stream) {
   ddg_batch b = nullptr;
-  ddg_status st = ddg_batch_create(&b, count, probs, 0);
+  ddg_status st = ddg_batch_create(&b, count, probs, 0, stream);
   if (st != DDG_OK) return st;
   st = ddg_batch_run(b, stream);
-  if (st == DDG_OK && cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
-    st = ddg::set_error(DDG_ECUDA, "dd_gemm_batched: synchronize");
-  ddg_status st2 = ddg_batch_destroy(b);
+  ddg_status st2 = ddg_batch_destroy(b, stream);
   return st != DDG_OK ? st : st2;
 }
 

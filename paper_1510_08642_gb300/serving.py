@@ -1,0 +1,279 @@
+"""Continuous-batching request server for DD products and DD linear solves.
+
+The paper's Section 4 application (A x = b by blocked LU whose trailing
+update is the Winograd DD product) and the DD product itself, served to
+requests that arrive over time:
+
+* arrival: requests (GEMM of order n, or an LU solve of order n) arrive at
+  given times (a Poisson process for the rate sweeps);
+* admission: a request is admitted when its HBM footprint (operands,
+  result and the library's temporaries) fits in the memory budget next to
+  the requests in flight and a slot (CUDA stream) is free; its operands
+  are then created on the device and stay there until it completes;
+* batching: all GEMM requests admitted together form one batch plan
+  (grouped persistent launches of the library); each LU solve takes a slot
+  of its own (dd_getrf with Winograd trailing updates, then dd_getrs);
+* continuous: requests that arrive while others run are admitted as slots
+  and memory free up, so their work overlaps on the device;
+* completion: a CUDA event per unit of work; latency = completion time on
+  the device clock (relative to a reference event) minus arrival time.
+
+Every arithmetic step runs in the CUDA library; this module only schedules.
+Operands are generated on the device from a seed per request (uniform
+[-1, 1) leading limbs, lower limbs 2^-53 U[-1/2, 1/2) below), so a request
+gives the same result alone and in any mix.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import Batch, capi, getrf, getrs, problem
+
+
+@dataclass
+class Request:
+    rid: int
+    kind: str            # "gemm" or "lu"
+    n: int
+    arrival: float       # seconds after the start of the run
+    seed: int
+    admitted: float = math.nan
+    done: float = math.nan
+    result: object = None   # device tensor (C, or x for an LU solve)
+    info: int = 0           # LU: 0 or 1 + column of a zero pivot
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+    @property
+    def work(self) -> float:
+        """2 m l n of the product, or 2 n^3 / 3 for the solve."""
+        return 2.0 * self.n ** 3 if self.kind == "gemm" else 2.0 * self.n ** 3 / 3.0
+
+
+def footprint(req: Request) -> int:
+    """Device bytes a request holds while in flight (DD: 16 bytes/entry)."""
+    n2 = req.n * req.n * 16
+    if req.kind == "gemm":
+        return 3 * n2 + 4 * n2          # A, B, C and Winograd temporaries (< 3.5 n^2 entries)
+    return n2 + 2 * req.n * 16 + n2     # A (factored in place), b / x, temporaries of the updates
+
+
+def make_operands(req: Request, device):
+    import torch
+    g = torch.Generator(device=device).manual_seed(req.seed)
+
+    def dd(rows, cols):
+        T = torch.empty((2, rows, cols), dtype=torch.float64, device=device)
+        T[0].uniform_(-1.0, 1.0, generator=g)
+        T[1] = T[0] * (2.0 ** -53) * (torch.rand((rows, cols), generator=g, dtype=torch.float64,
+                                                 device=device) - 0.5)
+        return T
+
+    if req.kind == "gemm":
+        return dd(req.n, req.n), dd(req.n, req.n)
+    A = dd(req.n, req.n)
+    return (A,)
+
+
+def poisson_requests(count: int, rate: float, seed: int, gemm_n=(256, 2048), lu_n=(1024, 2048, 4096)):
+    """The serving workload: Poisson arrivals at `rate` per second, 50% DD
+    GEMMs (n log-uniform in gemm_n), 50% DD LU solves (n uniform from lu_n)."""
+    from . import inputs as I
+    u = I.uniform01(seed, 4 * count).reshape(count, 4)
+    gaps = -np.log1p(-u[:, 0]) / rate if rate > 0 else np.zeros(count)
+    t = np.cumsum(gaps) - gaps[0]
+    reqs = []
+    for i in range(count):
+        if u[i, 1] < 0.5:
+            lo, hi = gemm_n
+            n = int(round(math.exp(math.log(lo) + u[i, 2] * (math.log(hi) - math.log(lo)))))
+            reqs.append(Request(i, "gemm", n, float(t[i]), seed * 100003 + i))
+        else:
+            n = int(lu_n[min(int(u[i, 2] * len(lu_n)), len(lu_n) - 1)])
+            reqs.append(Request(i, "lu", n, float(t[i]), seed * 100003 + i))
+    return reqs
+
+
+@dataclass
+class Unit:
+    kind: str
+    reqs: list
+    slot: int
+    event: object
+    bytes: int
+    keep: list = field(default_factory=list)
+    batch: object = None
+
+
+class Server:
+    def __init__(self, device=None, slots: int = 4, hbm_budget: int = 64 << 30, max_batch: int = 32,
+                 gemm_algo: str = "winograd", gemm_cutoff: int = 256, lu_K: int = 256,
+                 lu_algo: str = "winograd", lu_cutoff: int = 512, keep_results: bool = False):
+        import torch
+        self.torch = torch
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        capi.load()
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.budget = hbm_budget
+        self.max_batch = max_batch
+        self.gemm_algo, self.gemm_cutoff = gemm_algo, gemm_cutoff
+        self.lu_K, self.lu_algo, self.lu_cutoff = lu_K, lu_algo, lu_cutoff
+        self.keep_results = keep_results
+
+    # -- dispatch -----------------------------------------------------------
+    def _start_gemms(self, reqs, slot):
+        torch = self.torch
+        s = self.streams[slot]
+        keep, probs = [], []
+        with torch.cuda.stream(s):
+            for r in reqs:
+                A, B = make_operands(r, self.device)
+                C = torch.empty((2, r.n, r.n), dtype=torch.float64, device=self.device)
+                algo = self.gemm_algo if r.n > self.gemm_cutoff else "block"
+                probs.append(problem(A, B, C, algo, self.gemm_cutoff))
+                keep += [A, B]
+                r.result = C
+            batch = Batch(probs, use_graph=False, stream=s)
+            batch.run(s)
+            batch.close(s)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(s)
+        return Unit("gemm", reqs, slot, ev, sum(footprint(r) for r in reqs), keep)
+
+    def _start_lu(self, r, slot):
+        torch = self.torch
+        s = self.streams[slot]
+        with torch.cuda.stream(s):
+            (A,) = make_operands(r, self.device)
+            ones = torch.zeros((2, r.n, 1), dtype=torch.float64, device=self.device)
+            ones[0] = 1.0
+            from . import gemm
+            b = gemm(A, ones, algo="block", stream=s)
+            info = torch.zeros(1, dtype=torch.int64, device=self.device)
+            ipiv = getrf(A, K=self.lu_K, pivot=True, algo=self.lu_algo, cutoff=self.lu_cutoff,
+                         info=info, stream=s)
+            getrs(A, ipiv, b, stream=s)
+            r.result = b
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(s)
+        return Unit("lu", [r], slot, ev, footprint(r), [A, ipiv, info, ones])
+
+    # -- loop ---------------------------------------------------------------
+    def run(self, requests, poll_s: float = 2e-4):
+        """Serve `requests` (arrival times relative to the start); returns stats."""
+        torch = self.torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        queue, inflight = [], []
+        free_slots = list(range(len(self.streams)))
+        used = 0
+        torch.cuda.synchronize(self.device)
+        ref = torch.cuda.Event(enable_timing=True)
+        ref.record(torch.cuda.current_stream(self.device))
+        torch.cuda.synchronize(self.device)
+        t0 = time.perf_counter()
+        done = 0
+        ip = 0
+        while done < len(requests):
+            now = time.perf_counter() - t0
+            while ip < len(pending) and pending[ip].arrival <= now:
+                queue.append(pending[ip])
+                ip += 1
+            # completions
+            still = []
+            for u in inflight:
+                if u.event.query():
+                    t_dev = ref.elapsed_time(u.event) * 1e-3
+                    for r in u.reqs:
+                        r.done = t_dev
+                        if u.kind == "lu":
+                            r.info = int(u.keep[2].item())
+                        if not self.keep_results:
+                            r.result = None
+                    used -= u.bytes
+                    free_slots.append(u.slot)
+                    done += len(u.reqs)
+                else:
+                    still.append(u)
+            inflight = still
+            # admission: GEMMs in one batch per free slot, LU one per slot
+            progressed = False
+            while queue and free_slots:
+                head = queue[0]
+                if head.kind == "lu":
+                    if used + footprint(head) > self.budget and inflight:
+                        break
+                    queue.pop(0)
+                    head.admitted = time.perf_counter() - t0
+                    slot = free_slots.pop(0)
+                    u = self._start_lu(head, slot)
+                else:
+                    take, b = [], 0
+                    for r in queue:
+                        if r.kind != "gemm" or len(take) >= self.max_batch:
+                            break
+                        if used + b + footprint(r) > self.budget and (inflight or take):
+                            break
+                        take.append(r)
+                        b += footprint(r)
+                    if not take:
+                        break
+                    for r in take:
+                        queue.remove(r)
+                        r.admitted = time.perf_counter() - t0
+                    slot = free_slots.pop(0)
+                    u = self._start_gemms(take, slot)
+                inflight.append(u)
+                used += u.bytes
+                progressed = True
+            if not progressed:
+                nxt = pending[ip].arrival - (time.perf_counter() - t0) if ip < len(pending) else poll_s
+                time.sleep(max(0.0, min(poll_s, nxt)))
+        torch.cuda.synchronize(self.device)
+        return stats(requests)
+
+
+def stats(requests) -> dict:
+    out = {}
+    for kind in ("gemm", "lu", "all"):
+        rs = [r for r in requests if kind == "all" or r.kind == kind]
+        if not rs:
+            continue
+        lat = np.array([r.latency for r in rs]) * 1e3
+        span = max(r.done for r in rs) - min(r.arrival for r in rs)
+        out[kind] = {"count": len(rs), "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                     "throughput_rps": len(rs) / span if span > 0 else float("inf"),
+                     "work_G2mnl_per_s": sum(r.work for r in rs) / span / 1e9 if span > 0 else float("inf")}
+    return out
+
+
+def saturation_rate(server: Server, count: int = 40, seed: int = 1) -> float:
+    """Requests per second when every request is already queued at t = 0."""
+    reqs = poisson_requests(count, 0.0, seed)
+    st = server.run(reqs)
+    return st["all"]["throughput_rps"]
+
+
+def sweep(rates=(0.25, 0.5, 0.75, 0.9, 1.1), count: int = 60, seed: int = 2, server: Server | None = None):
+    """p50 / p99 latency and throughput at fractions of the saturation rate."""
+    server = server or Server()
+    mu = saturation_rate(server)
+    rows = []
+    for i, f in enumerate(rates):
+        reqs = poisson_requests(count, f * mu, seed + i)
+        st = server.run(reqs)
+        rows.append({"rate_fraction": f, "rate_rps": f * mu, **{k: v for k, v in st.items()}})
+    return {"saturation_rps": mu, "points": rows}
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    count = int(sys.argv[1]) if len(sys.argv) > 1 else 60
+    print(json.dumps(sweep(count=count)))
