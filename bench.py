@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="CPU oracle sample length; 0 skips the CPU baseline")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    p.add_argument("--lu-k", type=int, default=256, help="LU block column width K")
     return p.parse_args()
 
 
@@ -451,11 +452,27 @@ def run_ours(args, w):
     return 0
 
 
+def run_lu_only(args, w):
+    """An LU workload as the timed step (for profiling the solve alone)."""
+    import torch
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    import paper_1510_08642_gb300 as P
+    from paper_1510_08642_gb300 import capi
+    capi.load()
+    stream = torch.cuda.current_stream(device)
+    r = time_lu(P, torch, w, device, stream, K=args.lu_k)
+    print(json.dumps({"workload": w.name, **r}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     w = workload_by_name(args.workload)
     if args.impl == "reference":
         return run_reference(args, w)
+    if w.name.startswith("dd_lu"):
+        return run_lu_only(args, w)
     return run_ours(args, w)
 
 

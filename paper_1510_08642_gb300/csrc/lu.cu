@@ -8,16 +8,21 @@
 //   1. panel: for each column j of the block, pivot search (the first row of
 //      largest |a_ij| compared as DD; skipped in the paper's no-pivot mode),
 //      swap of the two whole rows, DD quotients l_ij = a_ij / a_jj and the
-//      rank-1 update of the block's remaining columns. One single-CTA launch
-//      (pivot + swap) and one grid launch (quotients + update + partial
-//      arg-max of the next column) per column.
+//      rank-1 update of the next columns. One single-CTA launch (pivot +
+//      swap) and one grid launch (quotients + update + partial arg-max of
+//      the next column) per column. Wide block columns are factored
+//      recursively in halves (left half, triangular solve and Block update of
+//      the right half, right half), so the rank-1 updates in pinned DD
+//      arithmetic stay within 16 columns.
 //   2. U12 := L11^-1 A12 by a recursive triangular solve whose off-diagonal
-//      updates are Block products (base case: 32-row triangles in one
-//      kernel, one thread per right-hand column).
+//      updates are Block products (base case: 8-row triangles in one kernel,
+//      one thread per right-hand column: a GB300 SM issues FP64 slowly, so
+//      the per-thread chain of DD operations is kept short).
 //   3. A22 := A22 - L21 U12 through the matrix product.
 // The loop runs while columns remain; the last block has min(K, remaining)
 // columns (the paper's garbled loop end, read as "until no columns remain").
 #include <algorithm>
+#include <functional>
 #include <string>
 
 #include "arith.cuh"
@@ -28,8 +33,9 @@ namespace ddg {
 namespace {
 
 constexpr int RB = 32;       // rows per CTA in the column kernels
-constexpr int TB = 32;       // triangle size of the substitution base case
+constexpr int TB = 8;        // triangle size of the substitution base case
 constexpr int KMAX = 512;    // widest block column
+constexpr int PANEL_BASE = 16;  // widest panel factored column by column
 
 struct partial_t {
   double hi, lo;
@@ -344,22 +350,46 @@ ddg_status dd_getrf(int64_t n, dd_mat A, int64_t* ipiv, int32_t K, int32_t pivot
     if (e != cudaSuccess && st == DDG_OK) st = set_error(DDG_ECUDA, std::string("dd_getrf: ") + cudaGetErrorString(e));
   };
   if (cudaMemsetAsync(dinfo, 0, sizeof(int64_t), s) != cudaSuccess) st = set_error(DDG_ECUDA, "memset");
+  // Panel of columns [c0, c0 + w), rows [c0, n): per-column kernels for
+  // narrow panels; wider ones split in halves (left half, its triangular
+  // solve and Block update of the right half, then the right half), so the
+  // rank-1 updates in pinned DD arithmetic stay within PANEL_BASE columns and
+  // the rest of the panel work runs in the Block kernel.
+  std::function<void(int64_t, int64_t)> panel = [&](int64_t c0, int64_t w) {
+    if (st != DDG_OK || w <= 0) return;
+    if (w <= PANEL_BASE) {
+      const int64_t pe = c0 + w;
+      for (int64_t j = c0; j < pe && st == DDG_OK; ++j) {
+        const int64_t nparts = (n - j + RB - 1) / RB;
+        if (pivot && j == c0) {
+          lu_argmax_kernel<<<(unsigned)nparts, 32, 0, s>>>(n, M, j, j, part);
+          cu(cudaGetLastError());
+        }
+        lu_pivot_kernel<<<1, 256, 0, s>>>(n, M, j, nparts, part, ipiv, dinfo, pivot);
+        cu(cudaGetLastError());
+        if (j + 1 < n) {
+          const int64_t blocks = (n - j - 1 + RB - 1) / RB;
+          lu_update_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, M, j, pe, part, (pivot && j + 1 < pe) ? 1 : 0);
+          cu(cudaGetLastError());
+        }
+      }
+      return;
+    }
+    const int64_t w1 = std::max<int64_t>(PANEL_BASE, (w / 2) / PANEL_BASE * PANEL_BASE);
+    panel(c0, w1);
+    if (st != DDG_OK) return;
+    const int64_t w2 = w - w1, c1 = c0 + w1;
+    st = trsm_lower_unit(w1, w2, view(M, c0, c0), view(M, c0, c1), s);
+    if (st != DDG_OK) return;
+    if (n - c1 > 0)
+      st = gemm_run(2, n - c1, w1, w2, view(M, c1, c0), view(M, c0, c1), view(M, c1, c1), MODE_SUB,
+                    block_opts(), s);
+    if (st != DDG_OK) return;
+    panel(c1, w2);
+  };
   for (int64_t j0 = 0; j0 < n && st == DDG_OK; j0 += K) {
     const int64_t pe = std::min<int64_t>(n, j0 + K);
-    for (int64_t j = j0; j < pe && st == DDG_OK; ++j) {
-      const int64_t nparts = (n - j + RB - 1) / RB;
-      if (pivot && j == j0) {
-        lu_argmax_kernel<<<(unsigned)nparts, 32, 0, s>>>(n, M, j, j, part);
-        cu(cudaGetLastError());
-      }
-      lu_pivot_kernel<<<1, 256, 0, s>>>(n, M, j, nparts, part, ipiv, dinfo, pivot);
-      cu(cudaGetLastError());
-      if (j + 1 < n) {
-        const int64_t blocks = (n - j - 1 + RB - 1) / RB;
-        lu_update_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, M, j, pe, part, (pivot && j + 1 < pe) ? 1 : 0);
-        cu(cudaGetLastError());
-      }
-    }
+    panel(j0, pe - j0);
     if (st != DDG_OK || pe >= n) break;
     const int64_t kb = pe - j0, rest = n - pe;
     st = trsm_lower_unit(kb, rest, view(M, j0, j0), view(M, j0, pe), s);

@@ -46,3 +46,4 @@ DD_LU_4096 = Workload("dd_lu_n4096", 2, 4096, "winograd", 512, 111, 0)
 # Same 512^3 leaves as the headline at n = 2048 (two levels, 49 leaves):
 # operands 200 MB > L2, small enough for a counter capture.
 DD_WINOGRAD_2048 = Workload("dd_winograd_n2048", 2, 2048, "winograd", 512, 112, 113)
+DD_LU_1024 = Workload("dd_lu_n1024", 2, 1024, "winograd", 512, 114, 0)
