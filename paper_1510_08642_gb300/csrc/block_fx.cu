@@ -32,12 +32,12 @@ namespace {
 
 template <int L> struct fxcfg;
 template <> struct fxcfg<2> {
-  static constexpr int BM = 32, BN = 64, BK = 16, TM = 4, TN = 4, NW = 6;
+  static constexpr int BM = 16, BN = 32, BK = 16, TM = 2, TN = 2, NW = 6;
   static constexpr int POS0 = 53;     // pos of a product = (ea - fa) + (eb - fb) + POS0
   static constexpr int LSB0 = -2203;  // LSB exponent = fa + fb + LSB0
 };
 template <> struct fxcfg<4> {
-  static constexpr int BM = 16, BN = 32, BK = 8, TM = 2, TN = 2, NW = 9;
+  static constexpr int BM = 8, BN = 32, BK = 8, TM = 1, TN = 2, NW = 9;
   static constexpr int POS0 = 149;
   static constexpr int LSB0 = -2299;
 };
@@ -280,7 +280,7 @@ cudaError_t launch_grouped_fx(int limbs, const gtask* tasks, int ntasks, int64_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 152;
   }
-  const int per_sm = limbs == 2 ? 2 : 3;  // resident CTAs per SM (register limited)
+  const int per_sm = limbs == 2 ? 5 : 3;  // resident CTAs per SM (register limited)
   const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)sms * per_sm);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
