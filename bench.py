@@ -218,6 +218,23 @@ def run_reference(args, w):
 
 
 # ----------------------------------------------------------------- GPU leg --
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json),
+    or None when the kernel's sources changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != rec["sources_sha256"]:
+            return None
+        return rec["bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def roofline_of(prof, limbs):
     """Dominant kernel: the Block base case (FP64 instructions per busy
     second) or, for the INT8-slice product, its slice GEMM (INT8 ops)."""
@@ -238,9 +255,12 @@ def roofline_of(prof, limbs):
     avg_ms = b["sum_ms"] / b["launches"]
     from paper_1510_08642_gb300 import capi
     ops_mac = capi.ddg_block_fp64_ops_per_mac(limbs, 0)
-    return {"bound": "alu", "kernel": f"block_kernel<{limbs}> (FP64 pipe)",
+    return {"bound": "alu", "kernel": f"block_fx_kernel<{limbs}> (FP64 pipe + exact integer accumulation)",
             "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "T FP64-instr/s",
-            "frac": achieved / FP64_PEAK, "traffic": None,
+            "frac": achieved / FP64_PEAK,
+            "traffic": traffic_for("block_fx_kernel<2>") if limbs == 2 else None,
+            "traffic_note": "DRAM bytes per 512^3 leaf launch (ncu, profiles/traffic.json); "
+                            "algorithmic 12.6 MB per leaf",
             "peak_source": f"derived: {SM_COUNT} SMs x {FP64_PER_CLK_PER_SM} FP64 instr/clk (measured "
                            f"by the DFMA probe) x {SM_MAX_MHZ:.0f} MHz; no FP64 figure in MEASURED_PEAKS.json",
             "fp64_ops_per_mac": ops_mac, "pinned_mac_ops": PINNED_MAC_OPS[limbs],
