@@ -7,10 +7,11 @@
 // Steps per block column of width K (the paper's K = alpha n_min):
 //   1. panel: for each column j of the block, pivot search (the first row of
 //      largest |a_ij| compared as DD; skipped in the paper's no-pivot mode),
-//      swap of the two whole rows, DD quotients l_ij = a_ij / a_jj and the
-//      rank-1 update of the next columns. One single-CTA launch (pivot +
-//      swap) and one grid launch (quotients + update + partial arg-max of
-//      the next column) per column. Wide block columns are factored
+//      swap of the two whole rows, DD quotients l_ij = a_ij (1 / a_jj) and
+//      the rank-1 update of the next columns: one grid launch per column
+//      (quotients, update, partial arg-maxes of the next column), whose last
+//      CTA to finish chooses and swaps the next pivot (an atomic counter; no
+//      CTA waits for another). Wide block columns are factored
 //      recursively in halves (left half, triangular solve and Block update of
 //      the right half, right half), so the rank-1 updates in pinned DD
 //      arithmetic stay within 16 columns.
@@ -37,9 +38,19 @@ constexpr int TB = 8;        // triangle size of the substitution base case
 constexpr int KMAX = 512;    // widest block column
 constexpr int PANEL_BASE = 16;  // widest panel factored column by column
 
+// Pivot candidates compare by integer keys of |x| as a DD number (leading
+// magnitude, then the trailing limb with the leading limb's sign): no FP64
+// compare instructions on the pivot search's critical path.
 struct partial_t {
-  double hi, lo;
+  unsigned long long kh, kl;
   int64_t idx;
+};
+
+// Per-call device state of the column steps.
+struct col_state {
+  unsigned int counter;  // CTAs finished in the current launch
+  unsigned int pad;
+  dd_t rinv;             // 1 / pivot of the column being eliminated (0 if zero)
 };
 
 __device__ __forceinline__ dd_t ldA(const mat& A, int64_t i, int64_t j) {
@@ -50,86 +61,68 @@ __device__ __forceinline__ void stA(const mat& A, int64_t i, int64_t j, dd_t v) 
   A.p[1][i * A.ld + j] = v.lo;
 }
 
-// Is candidate (v, i) a better pivot than (w, k): larger |x|, ties to the
-// smaller row index.
-__device__ __forceinline__ bool better(dd_t v, int64_t i, dd_t w, int64_t k) {
-  if (dd_abs_greater(v, w)) return true;
-  if (dd_abs_greater(w, v)) return false;
-  return i < k;
+__device__ __forceinline__ unsigned long long dkey(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);  // order of doubles
 }
 
-__device__ __forceinline__ void warp_argmax(dd_t& v, int64_t& i) {
+__device__ __forceinline__ partial_t cand(dd_t v, int64_t i) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v.hi);
+  const double lo = (b >> 63) ? -v.lo : v.lo;
+  return partial_t{b & 0x7FFFFFFFFFFFFFFFull, dkey(lo), i};
+}
+
+__device__ __forceinline__ partial_t none() { return partial_t{0ull, 0ull, INT64_MAX}; }
+
+// Is a a better pivot than b: larger |x|, ties to the smaller row index.
+__device__ __forceinline__ bool better(const partial_t& a, const partial_t& b) {
+  if (a.kh != b.kh) return a.kh > b.kh;
+  if (a.kl != b.kl) return a.kl > b.kl;
+  return a.idx < b.idx;
+}
+
+__device__ __forceinline__ void warp_best(partial_t& v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    dd_t w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-    int64_t k = __shfl_xor_sync(0xffffffffu, i, o);
-    if (better(w, k, v, i)) {
-      v = w;
-      i = k;
-    }
+    partial_t w{__shfl_xor_sync(0xffffffffu, v.kh, o), __shfl_xor_sync(0xffffffffu, v.kl, o),
+                __shfl_xor_sync(0xffffffffu, v.idx, o)};
+    if (better(w, v)) v = w;
   }
 }
 
-}  // namespace
-
-// Partial arg-max of column j over rows [r0, n): one warp per RB rows.
-__global__ void __launch_bounds__(32) lu_argmax_kernel(int64_t n, mat A, int64_t j, int64_t r0,
-                                                       partial_t* part) {
-  const int64_t i = r0 + (int64_t)blockIdx.x * RB + threadIdx.x;
-  dd_t v{0.0, 0.0};
-  int64_t idx = INT64_MAX;
-  if (i < n) {
-    v = ldA(A, i, j);
-    idx = i;
-  }
-  warp_argmax(v, idx);
-  if (threadIdx.x == 0) part[blockIdx.x] = partial_t{v.hi, v.lo, idx};
+__device__ __forceinline__ bool dd_is_zero(dd_t v) {
+  return ((unsigned long long)__double_as_longlong(v.hi) & 0x7FFFFFFFFFFFFFFFull) == 0ull &&
+         ((unsigned long long)__double_as_longlong(v.lo) & 0x7FFFFFFFFFFFFFFFull) == 0ull;
 }
 
-// Pivot of column j: reduce the partial arg-maxes (or take row j), record
-// it, flag an exactly zero pivot, and swap rows j and p across all columns.
-__global__ void __launch_bounds__(256) lu_pivot_kernel(int64_t n, mat A, int64_t j, int64_t nparts,
-                                                       const partial_t* part, int64_t* ipiv,
-                                                       int64_t* info, int pivot) {
-  __shared__ dd_t sv[8];
-  __shared__ int64_t si[8];
+// Executed by the last CTA of a launch (all its threads): choose the pivot
+// of column j from the partial arg-maxes (or row j without pivoting),
+// record it, flag an exactly zero pivot, swap rows j and p across all
+// columns, and publish 1 / pivot for the quotients of column j.
+__device__ void finish_pivot(int64_t n, const mat& A, int64_t j, int64_t nparts, const partial_t* part,
+                             int64_t* ipiv, int64_t* info, int pivot, col_state* cs) {
+  __shared__ partial_t sbest[8];
   __shared__ int64_t sp;
   const int tid = threadIdx.x;
   if (pivot) {
-    dd_t v{0.0, 0.0};
-    int64_t idx = INT64_MAX;
+    partial_t v = none();
     for (int64_t t = tid; t < nparts; t += blockDim.x) {
       const partial_t q = part[t];
-      const dd_t w{q.hi, q.lo};
-      if (better(w, q.idx, v, idx)) {
-        v = w;
-        idx = q.idx;
-      }
+      if (better(q, v)) v = q;
     }
-    warp_argmax(v, idx);
-    if ((tid & 31) == 0) {
-      sv[tid >> 5] = v;
-      si[tid >> 5] = idx;
-    }
+    warp_best(v);
+    if ((tid & 31) == 0) sbest[tid >> 5] = v;
     __syncthreads();
     if (tid == 0) {
       for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-        if (better(sv[w], si[w], v, idx)) {
-          v = sv[w];
-          idx = si[w];
-        }
-      sp = (idx >= j && idx < n) ? idx : j;
+        if (better(sbest[w], v)) v = sbest[w];
+      sp = (v.idx >= j && v.idx < n) ? v.idx : j;
     }
   } else if (tid == 0) {
     sp = j;
   }
   __syncthreads();
   const int64_t p = sp;
-  if (tid == 0) {
-    ipiv[j] = p;
-    const dd_t d = ldA(A, p, j);
-    if (d.hi == 0.0 && d.lo == 0.0 && *info == 0) *info = j + 1;
-  }
   if (p != j) {
     for (int64_t c = tid; c < n; c += blockDim.x)
 #pragma unroll
@@ -141,24 +134,68 @@ __global__ void __launch_bounds__(256) lu_pivot_kernel(int64_t n, mat A, int64_t
         *rp = t;
       }
   }
+  __syncthreads();
+  if (tid == 0) {
+    ipiv[j] = p;
+    const dd_t piv = ldA(A, j, j);
+    const bool zero = dd_is_zero(piv);
+    if (zero && *info == 0) *info = j + 1;
+    cs->rinv = zero ? dd_t{0.0, 0.0} : dd_div(dd_t{1.0, 0.0}, piv);
+    cs->counter = 0u;
+  }
 }
 
-// Quotients l_ij = a_ij / a_jj for rows below j, rank-1 update of columns
-// (j, pe) of those rows, and (optionally) the partial arg-max of column j+1.
-__global__ void __launch_bounds__(256) lu_update_kernel(int64_t n, mat A, int64_t j, int64_t pe,
-                                                        partial_t* part, int want_argmax) {
+// Am I the last CTA of this launch to get here? (publishes this CTA's
+// global writes first; no CTA waits for another)
+__device__ __forceinline__ bool last_block(col_state* cs) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&cs->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+}  // namespace
+
+// First column j of a narrow panel: partial arg-maxes of column j over rows
+// [j, n) (RB rows per CTA), then the last CTA chooses and swaps the pivot.
+__global__ void __launch_bounds__(256) lu_start_kernel(int64_t n, mat A, int64_t j, partial_t* part,
+                                                       int64_t* ipiv, int64_t* info, int pivot,
+                                                       col_state* cs) {
+  const int tid = threadIdx.x;
+  if (pivot && tid < 32) {
+    const int64_t i = j + (int64_t)blockIdx.x * RB + tid;
+    partial_t v = i < n ? cand(ldA(A, i, j), i) : none();
+    warp_best(v);
+    if (tid == 0) part[blockIdx.x] = v;
+  }
+  if (last_block(cs)) finish_pivot(n, A, j, gridDim.x, part, ipiv, info, pivot, cs);
+}
+
+// Column j (its pivot row already in place, 1 / pivot in cs): quotients
+// l_ij = a_ij (1 / a_jj) for rows below j, rank-1 update of columns (j, pe)
+// of those rows; then, if column j + 1 belongs to the same panel, the
+// partial arg-maxes of the updated column j + 1 and, in the last CTA, its
+// pivot.
+__global__ void __launch_bounds__(256) lu_col_kernel(int64_t n, mat A, int64_t j, int64_t pe,
+                                                     partial_t* part, int64_t* ipiv, int64_t* info,
+                                                     int pivot, col_state* cs) {
   __shared__ dd_t u[KMAX];
   __shared__ dd_t lq[RB];
   const int tid = threadIdx.x;
   const int64_t r0 = j + 1 + (int64_t)blockIdx.x * RB;
   const int rows = (int)(n - r0 < RB ? n - r0 : RB);
   const int cols = (int)(pe - j - 1);
-  const dd_t piv = ldA(A, j, j);
-  const bool zero = piv.hi == 0.0 && piv.lo == 0.0;
+  const dd_t rinv = cs->rinv;
+  const bool zero = dd_is_zero(rinv);
   if (tid < rows) {
     dd_t l{0.0, 0.0};
     if (!zero) {
-      l = dd_div(ldA(A, r0 + tid, j), piv);
+      l = dd_mul(ldA(A, r0 + tid, j), rinv);
       stA(A, r0 + tid, j, l);
     }
     lq[tid] = l;
@@ -170,19 +207,14 @@ __global__ void __launch_bounds__(256) lu_update_kernel(int64_t n, mat A, int64_
     const int64_t i = r0 + r, jc = j + 1 + c;
     stA(A, i, jc, dd_add(ldA(A, i, jc), dd_mul(dd_neg(lq[r]), u[c])));
   }
-  if (want_argmax) {
-    __syncthreads();
-    if (tid < 32) {
-      dd_t v{0.0, 0.0};
-      int64_t idx = INT64_MAX;
-      if (tid < rows) {
-        v = ldA(A, r0 + tid, j + 1);
-        idx = r0 + tid;
-      }
-      warp_argmax(v, idx);
-      if (tid == 0) part[blockIdx.x] = partial_t{v.hi, v.lo, idx};
-    }
+  if (j + 1 >= pe) return;  // the next panel starts with lu_start_kernel
+  __syncthreads();
+  if (pivot && tid < 32) {
+    partial_t v = tid < rows ? cand(ldA(A, r0 + tid, j + 1), r0 + tid) : none();
+    warp_best(v);
+    if (tid == 0) part[blockIdx.x] = v;
   }
+  if (last_block(cs)) finish_pivot(n, A, j + 1, gridDim.x, part, ipiv, info, pivot, cs);
 }
 
 // X := L^-1 X for a unit lower triangle L (m <= TB rows), one thread per
@@ -336,20 +368,23 @@ ddg_status dd_getrf(int64_t n, dd_mat A, int64_t* ipiv, int32_t K, int32_t pivot
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const mat M{{A.hi, A.lo, nullptr, nullptr}, A.ld};
   const int64_t maxparts = (n + RB - 1) / RB;
-  const size_t bytes = sizeof(partial_t) * (size_t)maxparts + 256;
+  const size_t bytes = sizeof(partial_t) * (size_t)maxparts + 512;
   void* ws = nullptr;
   if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
     cudaGetLastError();
     return set_error(DDG_ENOMEM, "dd_getrf: scratch allocation failed");
   }
-  partial_t* part = reinterpret_cast<partial_t*>(static_cast<char*>(ws) + 256);
+  partial_t* part = reinterpret_cast<partial_t*>(static_cast<char*>(ws) + 512);
   int64_t* dinfo = info ? info : reinterpret_cast<int64_t*>(ws);
+  col_state* cs = reinterpret_cast<col_state*>(static_cast<char*>(ws) + 256);
   ddg_status st = DDG_OK;
   auto cu = [&](cudaError_t e) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (e != cudaSuccess && st == DDG_OK) st = set_error(DDG_ECUDA, std::string("dd_getrf: ") + cudaGetErrorString(e));
   };
-  if (cudaMemsetAsync(dinfo, 0, sizeof(int64_t), s) != cudaSuccess) st = set_error(DDG_ECUDA, "memset");
+  if (cudaMemsetAsync(dinfo, 0, sizeof(int64_t), s) != cudaSuccess ||
+      cudaMemsetAsync(cs, 0, sizeof(col_state), s) != cudaSuccess)
+    st = set_error(DDG_ECUDA, "memset");
   // Panel of columns [c0, c0 + w), rows [c0, n): per-column kernels for
   // narrow panels; wider ones split in halves (left half, its triangular
   // solve and Block update of the right half, then the right half), so the
@@ -359,19 +394,13 @@ ddg_status dd_getrf(int64_t n, dd_mat A, int64_t* ipiv, int32_t K, int32_t pivot
     if (st != DDG_OK || w <= 0) return;
     if (w <= PANEL_BASE) {
       const int64_t pe = c0 + w;
-      for (int64_t j = c0; j < pe && st == DDG_OK; ++j) {
-        const int64_t nparts = (n - j + RB - 1) / RB;
-        if (pivot && j == c0) {
-          lu_argmax_kernel<<<(unsigned)nparts, 32, 0, s>>>(n, M, j, j, part);
-          cu(cudaGetLastError());
-        }
-        lu_pivot_kernel<<<1, 256, 0, s>>>(n, M, j, nparts, part, ipiv, dinfo, pivot);
+      const int64_t nstart = pivot ? (n - c0 + RB - 1) / RB : 1;
+      lu_start_kernel<<<(unsigned)nstart, 256, 0, s>>>(n, M, c0, part, ipiv, dinfo, pivot, cs);
+      cu(cudaGetLastError());
+      for (int64_t j = c0; j < pe && j + 1 < n && st == DDG_OK; ++j) {
+        const int64_t blocks = (n - j - 1 + RB - 1) / RB;
+        lu_col_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, M, j, pe, part, ipiv, dinfo, pivot, cs);
         cu(cudaGetLastError());
-        if (j + 1 < n) {
-          const int64_t blocks = (n - j - 1 + RB - 1) / RB;
-          lu_update_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, M, j, pe, part, (pivot && j + 1 < pe) ? 1 : 0);
-          cu(cudaGetLastError());
-        }
       }
       return;
     }
