@@ -16,9 +16,9 @@
 //      the right half, right half), so the rank-1 updates in pinned DD
 //      arithmetic stay within 16 columns.
 //   2. U12 := L11^-1 A12 by a recursive triangular solve whose off-diagonal
-//      updates are Block products (base case: 8-row triangles in one kernel,
-//      one thread per right-hand column: a GB300 SM issues FP64 slowly, so
-//      the per-thread chain of DD operations is kept short).
+//      updates are Block products (base case: 32-row triangles, one warp per
+//      right-hand column: a GB300 SM issues FP64 slowly, so the chain of DD
+//      operations per warp is kept short).
 //   3. A22 := A22 - L21 U12 through the matrix product.
 // The loop runs while columns remain; the last block has min(K, remaining)
 // columns (the paper's garbled loop end, read as "until no columns remain").
@@ -34,7 +34,7 @@ namespace ddg {
 namespace {
 
 constexpr int RB = 32;       // rows per CTA in the column kernels
-constexpr int TB = 8;        // triangle size of the substitution base case
+constexpr int TB = 32;       // triangle size of the substitution base case (one warp)
 constexpr int KMAX = 512;    // widest block column
 constexpr int PANEL_BASE = 16;  // widest panel factored column by column
 
@@ -217,8 +217,12 @@ __global__ void __launch_bounds__(256) lu_col_kernel(int64_t n, mat A, int64_t j
   if (last_block(cs)) finish_pivot(n, A, j + 1, gridDim.x, part, ipiv, info, pivot, cs);
 }
 
-// X := L^-1 X for a unit lower triangle L (m <= TB rows), one thread per
-// column of X; the triangle is staged in shared memory.
+// X := L^-1 X for a unit lower triangle L (m <= TB rows): one warp per
+// column of X, lane i holding row i. At step k lane k's value is final and
+// is broadcast by a shuffle; lanes below it subtract l_ik x_k. A GB300 SM
+// issues one FP64 warp instruction per 16 cycles, so spreading the rows of
+// a column over the lanes (one DD multiply-add per step) keeps the chain
+// short: TB steps instead of TB (TB - 1) / 2 multiply-adds per thread.
 __global__ void __launch_bounds__(128) trsm_lower_unit_base(int64_t m, int64_t r, mat Lm, mat X) {
   __shared__ dd_t T[TB][TB];
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
@@ -226,20 +230,20 @@ __global__ void __launch_bounds__(128) trsm_lower_unit_base(int64_t m, int64_t r
     T[i][k] = (i < m && k < i) ? ldA(Lm, i, k) : dd_t{0.0, 0.0};
   }
   __syncthreads();
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (c >= r) return;
-  dd_t x[TB];
-#pragma unroll
-  for (int i = 0; i < TB; ++i) {
-    dd_t acc = i < m ? ldA(X, i, c) : dd_t{0.0, 0.0};
-#pragma unroll
-    for (int k = 0; k < i; ++k) acc = dd_add(acc, dd_mul(dd_neg(T[i][k]), x[k]));
-    x[i] = acc;
-    if (i < m) stA(X, i, c, acc);
+  dd_t acc = lane < m ? ldA(X, lane, c) : dd_t{0.0, 0.0};
+  for (int k = 0; k < m; ++k) {
+    const dd_t xk{__shfl_sync(0xffffffffu, acc.hi, k), __shfl_sync(0xffffffffu, acc.lo, k)};
+    if (lane > k) acc = dd_add(acc, dd_mul(dd_neg(T[lane][k]), xk));
   }
+  if (lane < m) stA(X, lane, c, acc);
 }
 
-// X := U^-1 X for an upper triangle U with nonzero diagonal (m <= TB rows).
+// X := U^-1 X for an upper triangle U with nonzero diagonal (m <= TB rows),
+// one warp per column as above, from the last row up; each lane first forms
+// the DD reciprocal of its diagonal entry.
 __global__ void __launch_bounds__(128) trsm_upper_base(int64_t m, int64_t r, mat U, mat X) {
   __shared__ dd_t T[TB][TB];
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
@@ -247,17 +251,17 @@ __global__ void __launch_bounds__(128) trsm_upper_base(int64_t m, int64_t r, mat
     T[i][k] = (i < m && k < m && k >= i) ? ldA(U, i, k) : dd_t{i == k ? 1.0 : 0.0, 0.0};
   }
   __syncthreads();
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (c >= r) return;
-  dd_t x[TB];
-#pragma unroll
-  for (int i = TB - 1; i >= 0; --i) {
-    dd_t acc = i < m ? ldA(X, i, c) : dd_t{0.0, 0.0};
-#pragma unroll
-    for (int k = i + 1; k < TB; ++k) acc = dd_add(acc, dd_mul(dd_neg(T[i][k]), x[k]));
-    x[i] = dd_div(acc, T[i][i]);
-    if (i < m) stA(X, i, c, x[i]);
+  const dd_t rinv = dd_div(dd_t{1.0, 0.0}, T[lane][lane]);
+  dd_t acc = lane < m ? ldA(X, lane, c) : dd_t{0.0, 0.0};
+  for (int k = (int)m - 1; k >= 0; --k) {
+    if (lane == k) acc = dd_mul(acc, rinv);
+    const dd_t xk{__shfl_sync(0xffffffffu, acc.hi, k), __shfl_sync(0xffffffffu, acc.lo, k)};
+    if (lane < k) acc = dd_add(acc, dd_mul(dd_neg(T[lane][k]), xk));
   }
+  if (lane < m) stA(X, lane, c, acc);
 }
 
 // Row permutation of the interchanges ipiv[0..n): perm[i] = source row of
@@ -314,7 +318,7 @@ static cudaError_t counted(cudaError_t e) {
 static ddg_status trsm_lower_unit(int64_t m, int64_t r, const mat& Lm, const mat& X, cudaStream_t s) {
   if (m == 0 || r == 0) return DDG_OK;
   if (m <= TB) {
-    trsm_lower_unit_base<<<(unsigned)((r + 127) / 128), 128, 0, s>>>(m, r, Lm, X);
+    trsm_lower_unit_base<<<(unsigned)((r + 3) / 4), 128, 0, s>>>(m, r, Lm, X);
     return counted(cudaGetLastError()) == cudaSuccess ? DDG_OK : set_error(DDG_ECUDA, "trsm launch");
   }
   const int64_t m1 = std::max<int64_t>(TB, (m / 2) / TB * TB);
@@ -329,7 +333,7 @@ static ddg_status trsm_lower_unit(int64_t m, int64_t r, const mat& Lm, const mat
 static ddg_status trsm_upper(int64_t m, int64_t r, const mat& U, const mat& X, cudaStream_t s) {
   if (m == 0 || r == 0) return DDG_OK;
   if (m <= TB) {
-    trsm_upper_base<<<(unsigned)((r + 127) / 128), 128, 0, s>>>(m, r, U, X);
+    trsm_upper_base<<<(unsigned)((r + 3) / 4), 128, 0, s>>>(m, r, U, X);
     return counted(cudaGetLastError()) == cudaSuccess ? DDG_OK : set_error(DDG_ECUDA, "trsm launch");
   }
   const int64_t m1 = std::max<int64_t>(TB, (m / 2) / TB * TB);
