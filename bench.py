@@ -56,10 +56,15 @@ def parse():
                    help="CPU oracle sample length; 0 skips the CPU baseline")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     p.add_argument("--lu-k", type=int, default=256, help="LU block column width K")
+    p.add_argument("--requests", type=int, default=120, help="serving: requests per rate point")
+    p.add_argument("--rates", type=float, nargs="+", default=[0.25, 0.5, 0.75, 0.9, 1.1],
+                   help="serving: arrival rates as fractions of the saturation rate")
     return p.parse_args()
 
 
 def workload_by_name(name):
+    if name == "serving":
+        return WL.Workload("serving", 2, 0, "winograd", 512, 0, 0)
     for v in vars(WL).values():
         if isinstance(v, WL.Workload) and v.name == name:
             return v
@@ -450,7 +455,8 @@ def run_ours(args, w):
     if args.extras == "all" and world == 1 and w.name == WL.DD_WINOGRAD_4096.name:
         extras = {}
         for xw in (WL.DD_BLOCK_4096, WL.QD_WINOGRAD_4096, WL.QD_BLOCK_4096, WL.DD_OZAKI_4096_S16,
-                   WL.DD_OZAKI_4096_S13, WL.DD_WINOGRAD_8192, WL.DD_OZAKI_8192_S16):
+                   WL.DD_OZAKI_4096_S13, WL.DD_WINOGRAD_8192, WL.DD_OZAKI_8192_S16,
+                   WL.QD_OZAKI_4096_S32):
             XA = torch.from_numpy(I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_a)).to(device)
             XB = torch.from_numpy(I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_b)).to(device)
             XC = torch.empty((xw.limbs, xw.n, xw.n), dtype=torch.float64, device=device)
@@ -469,6 +475,21 @@ def run_ours(args, w):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def run_serving(args):
+    """The serving workload: Poisson arrivals of DD GEMMs (n log-uniform in
+    [256, 2048]) and DD LU solves (n in {1024, 2048, 4096}), 50 / 50, at
+    fractions of the measured saturation rate; p50 / p99 latency per type."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1510_08642_gb300 import serving as S
+    srv = S.Server(slots=4, hbm_budget=96 << 30, max_batch=32, gemm_cutoff=512, lu_K=256,
+                   lu_cutoff=512)
+    res = S.sweep(rates=tuple(args.rates), count=args.requests, seed=3, server=srv)
+    print(json.dumps({"workload": "serving_dd_gemm_lu_mix", "requests_per_point": args.requests, **res}),
+          flush=True)
     return 0
 
 
@@ -493,6 +514,8 @@ def main():
         return run_reference(args, w)
     if w.name.startswith("dd_lu"):
         return run_lu_only(args, w)
+    if w.name == "serving":
+        return run_serving(args)
     return run_ours(args, w)
 
 

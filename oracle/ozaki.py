@@ -14,7 +14,8 @@ documents for its DDG_OZAKI algorithm, step by step:
 4. D_r = sum_{p + q = r} alpha^(p) beta^(q) for r = 2 .. s + 1 (int64 GEMMs);
 5. V = sum_r D_r 2^(7 (s + 1 - r)) exactly, c = V 2^(e_i + e_j - T - 6);
    rounded to DD as: hi = leading 53 bits of |V| (truncated), lo = next 53
-   bits (truncated), signs applied, then TwoSum(hi, lo).
+   bits (truncated), signs applied, then TwoSum(hi, lo); to QD as four such
+   53-bit pieces, renormalised (the oracle's VecSum + compaction).
 
 Slow and obviously exact; for small matrices.
 """
@@ -25,7 +26,7 @@ from fractions import Fraction
 
 import numpy as np
 
-from . import dd_add
+from . import dd_add, qd_add, renorm
 
 
 def exp_field(x: float) -> int:
@@ -41,12 +42,12 @@ def row_fields(M0: np.ndarray, axis: int) -> np.ndarray:
     return np.maximum(f.max(axis=axis), 1)
 
 
-def to_integer(hi: float, lo: float, field: int, s: int) -> int:
+def to_integer(limbs, field: int, s: int) -> int:
     T = 6 + 7 * (s - 1)
     e = field - 1022
     acc = 0
-    for limb in (hi, lo):
-        v = Fraction(limb) * Fraction(2) ** (T - e + 64)
+    for limb in limbs:
+        v = Fraction(float(limb)) * Fraction(2) ** (T - e + 64)
         acc += int(v)  # truncation toward zero at 2^-64 units
     return (acc + (1 << 63)) >> 64
 
@@ -72,23 +73,29 @@ def split(M: np.ndarray, s: int, by_row: bool):
     for i in range(rows):
         for k in range(cols):
             fld = int(f[i] if by_row else f[k])
-            X = to_integer(float(M[0, i, k]), float(M[1, i, k]), fld, s)
+            X = to_integer(M[:, i, k], fld, s)
             S[:, i, k] = digits(X, s)
     return S, f
 
 
-def _chunk_dd(V: int, lsb: int):
+def _chunks(V: int, lsb: int, k: int):
+    """The k leading 53-bit pieces of |V| (truncated) as signed doubles."""
     if V == 0:
-        return 0.0, 0.0
+        return [0.0] * k
     neg = V < 0
     a = -V if neg else V
     P = a.bit_length() - 1
-    c0 = a >> (P - 52) if P >= 52 else a << (52 - P)
-    c1 = ((a >> (P - 105)) if P >= 105 else (a << (105 - P))) & ((1 << 53) - 1)
-    hi = math.ldexp(float(c0), lsb + P - 52)
-    lo = math.ldexp(float(c1), lsb + P - 105)
-    if neg:
-        hi, lo = -hi, -lo
+    out = []
+    for c in range(k):
+        sh = P - 52 - 53 * c
+        piece = ((a >> sh) if sh >= 0 else (a << -sh)) & ((1 << 53) - 1)
+        x = math.ldexp(float(piece), lsb + sh)
+        out.append(-x if neg else x)
+    return out
+
+
+def _chunk_dd(V: int, lsb: int):
+    hi, lo = _chunks(V, lsb, 2)
     s_ = hi + lo
     bv = s_ - hi
     av = s_ - bv
@@ -96,8 +103,8 @@ def _chunk_dd(V: int, lsb: int):
 
 
 def gemm(A: np.ndarray, B: np.ndarray, s: int = 16, C0=None, mode: str = "set"):
-    """DD C (mode) A B by the INT8-slice scheme above; returns (2, m, n)."""
-    _, m, l = A.shape
+    """DD / QD C (mode) A B by the INT8-slice scheme above; returns (limbs, m, n)."""
+    limbs, m, l = A.shape
     n = B.shape[2]
     SA, fa = split(A, s, by_row=True)
     SB, fb = split(B, s, by_row=False)
@@ -107,17 +114,22 @@ def gemm(A: np.ndarray, B: np.ndarray, s: int = 16, C0=None, mode: str = "set"):
             q = r - p
             D[r] += SA[p - 1] @ SB[q - 1]
     T = 6 + 7 * (s - 1)
-    C = np.zeros((2, m, n))
+    C = np.zeros((limbs, m, n))
     for i in range(m):
         for j in range(n):
             V = 0
             for r in range(2, s + 2):
                 V += int(D[r, i, j]) << (7 * (s + 1 - r))
             lsb = (int(fa[i]) - 1022) + (int(fb[j]) - 1022) - T - 6
-            hi, lo = _chunk_dd(V, lsb)
+            if limbs == 2:
+                v = np.array(_chunk_dd(V, lsb))
+                add = dd_add
+            else:
+                v = renorm(np.array(_chunks(V, lsb, 4)))
+                add = qd_add
             if mode == "add":
-                hi, lo = dd_add([C0[0, i, j], C0[1, i, j]], [hi, lo])
+                v = add(C0[:, i, j], v)
             elif mode == "sub":
-                hi, lo = dd_add([C0[0, i, j], C0[1, i, j]], [-hi, -lo])
-            C[0, i, j], C[1, i, j] = hi, lo
+                v = add(C0[:, i, j], -v)
+            C[:, i, j] = v
     return C, (SA, SB, D, fa, fb)

@@ -306,7 +306,8 @@ static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& 
   if (m < 0 || l < 0 || n < 0) return fail(DDG_EINVAL, "negative size");
   if (mode < DDG_SET || mode > DDG_SUB) return fail(DDG_EINVAL, "mode must be DDG_SET, DDG_ADD or DDG_SUB");
   if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI) return fail(DDG_EINVAL, "unknown algo");
-  if (o.slices != 0 && (o.slices < 2 || o.slices > 18)) return fail(DDG_EINVAL, "slices must be 0 or in [2, 18]");
+  if (o.slices != 0 && (o.slices < 2 || o.slices > (L == 2 ? 18 : 32)))
+    return fail(DDG_EINVAL, "slices must be 0 or in [2, 18] (DD) / [2, 32] (QD)");
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
   if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
   if (o.streams != 0 && o.streams != 1 && o.streams != 7) return fail(DDG_EINVAL, "streams must be 0, 1 or 7");
@@ -331,10 +332,13 @@ ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const 
     return DDG_OK;
   }
   if (o.algo == DDG_OZAKI) {
-    if (L != 2) return fail(DDG_ENOTSUP, "DDG_OZAKI is implemented for DD only");
     if (m > 65535) return fail(DDG_EINVAL, "DDG_OZAKI: m must be <= 65535");
-    if (l == 0) return mode == MODE_SET ? zero_mat(Ctx{}, C, m, n, s) : DDG_OK;
-    return ozaki_dd_gemm(m, l, n, A, B, C, mode, o.slices ? o.slices : 16, s);
+    if (l == 0) {
+      Ctx z;
+      z.L = L;
+      return mode == MODE_SET ? zero_mat(z, C, m, n, s) : DDG_OK;
+    }
+    return ozaki_gemm(L, m, l, n, A, B, C, mode, o.slices ? o.slices : (L == 2 ? 16 : 32), s);
   }
   Ctx c;
   c.L = L;
@@ -460,7 +464,8 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
   if (m < 0 || l < 0 || n < 0) return fail(DDG_EINVAL, "negative size");
   if (mode < DDG_SET || mode > DDG_SUB) return fail(DDG_EINVAL, "mode must be DDG_SET, DDG_ADD or DDG_SUB");
   if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI) return fail(DDG_EINVAL, "unknown algo");
-  if (o.slices != 0 && (o.slices < 2 || o.slices > 18)) return fail(DDG_EINVAL, "slices must be 0 or in [2, 18]");
+  if (o.slices != 0 && (o.slices < 2 || o.slices > (L == 2 ? 18 : 32)))
+    return fail(DDG_EINVAL, "slices must be 0 or in [2, 18] (DD) / [2, 32] (QD)");
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
   if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
   if (o.accum != 0 && o.accum != 1) return fail(DDG_EINVAL, "accum must be 0 or 1");

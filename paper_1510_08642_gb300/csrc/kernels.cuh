@@ -110,9 +110,9 @@ ddg_status set_error(ddg_status st, const std::string& msg);
 ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
                     int mode, const ddg_opts& o, cudaStream_t s);
 
-// DD product by INT8 slices (Ozaki scheme), s slices (ozaki.cu).
-ddg_status ozaki_dd_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
-                         int mode, int s, cudaStream_t st);
+// DD / QD product by INT8 slices (Ozaki scheme), s slices (ozaki.cu).
+ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
+                      int mode, int s, cudaStream_t st);
 
 // Number of FP64 instructions of one multiply-accumulate in the Block
 // kernel's inner loop (counted from its source), for the roofline.

@@ -35,6 +35,7 @@ namespace {
 constexpr int OBM = 128, OBN = 128, OBK = 64, OST = 3, OROW = OBK + 16;
 constexpr int STAGE_BYTES = (OBM + OBN) * OROW;
 constexpr int OZ_SMEM = OST * STAGE_BYTES;
+constexpr int OZ_MAXS = 32;  // most slices (QD); DD allows 18
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -80,43 +81,69 @@ __global__ void oz_exp_kernel(int64_t rows, int64_t cols, mat X, int byrow, int*
   }
 }
 
-// Balanced base-128 digits of round(x 2^(T - e)) for x = hi + lo, where
-// 2^e bounds |x| (field = biased exponent with |hi| < 2^(field - 1022)).
-__device__ __forceinline__ void oz_digits(double hi, double lo, int field, int s, int8_t* out,
+// Balanced base-128 digits of round(x 2^(T - e)) for x = the sum of the L
+// limbs, where 2^e bounds |x| (field = biased exponent with |x0| <
+// 2^(field - 1022)). The limbs are placed exactly (bits below 2^-64 units
+// truncated toward zero) in a fixed-point word of NW 32-bit words, rounded
+// half up to the integer X, and X is cut into digits from the least
+// significant end: d_p = the balanced residue of X mod 128, X = (X - d_p) / 128.
+template <int L>
+__device__ __forceinline__ void oz_digits(const double (&x)[L], int field, int s, int8_t* out,
                                           int64_t stride) {
+  constexpr int NW = L == 2 ? 6 : 9;   // split word: 192 / 288 bits
+  constexpr int KW = L == 2 ? 2 : 4;   // X in 64-bit words (X < 2^T)
   const int T = 6 + 7 * (s - 1);
-  uint32_t acc[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+  uint32_t acc[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) acc[w] = 0u;
   // LSB of acc = 2^(e - T - 64); a double M 2^(E - 1075) sits at E - field + T + 11
-  {
-    fx::unpacked u = fx::unpack(hi);
+#pragma unroll
+  for (int q = 0; q < L; ++q) {
+    fx::unpacked u = fx::unpack(x[q]);
     uint32_t p[4] = {u.m0, u.m1, 0u, 0u};
-    fx::place<6, 3>(acc, p, u.e - field + T + 11, u.s);
-    fx::unpacked v = fx::unpack(lo);
-    uint32_t q[4] = {v.m0, v.m1, 0u, 0u};
-    fx::place<6, 2>(acc, q, v.e - field + T + 11, v.s);
+    if (q == 0) fx::place<NW, (L == 2 ? 3 : 6)>(acc, p, u.e - field + T + 11, u.s);
+    else fx::place<NW, (L == 2 ? 2 : 4)>(acc, p, u.e - field + T + 11, u.s);
   }
   // X = floor((acc + 2^63) / 2^64): round half up to an integer
-  const uint32_t half[6] = {0u, 0x80000000u, 0u, 0u, 0u, 0u};
-  fx::acc_add<6>(acc, half, 0u);
-  unsigned long long xl = ((unsigned long long)acc[3] << 32) | acc[2];
-  long long xh = (long long)(((unsigned long long)acc[5] << 32) | acc[4]);
+  uint32_t half[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) half[w] = w == 1 ? 0x80000000u : 0u;
+  fx::acc_add<NW>(acc, half, 0u);
+  unsigned long long X[KW];
+#pragma unroll
+  for (int k = 0; k < KW; ++k) {
+    const int w0 = 2 + 2 * k, w1 = 3 + 2 * k;
+    const uint32_t lo = w0 < NW ? acc[w0 < NW ? w0 : 0] : 0u;
+    // sign-extend past the top word
+    const uint32_t sext = (acc[NW - 1] >> 31) ? 0xFFFFFFFFu : 0u;
+    const uint32_t hi = w1 < NW ? acc[w1 < NW ? w1 : 0] : sext;
+    X[k] = ((unsigned long long)hi << 32) | lo;
+  }
   for (int p = s; p >= 2; --p) {
-    int d = (int)(xl & 127u);
+    int d = (int)(X[0] & 127u);
     d = d >= 64 ? d - 128 : d;
-    // (X - d) >> 7, 128-bit arithmetic
-    const long long dd = d;
-    const unsigned long long nl = xl - (unsigned long long)dd;
-    const long long borrow = (dd > 0 && nl > xl) ? 1 : ((dd < 0 && nl < xl) ? -1 : 0);
-    xh -= borrow;
-    xl = (nl >> 7) | ((unsigned long long)xh << 57);
-    xh >>= 7;
+    // X -= d (multiword, two's complement), then X >>= 7 (arithmetic)
+    const unsigned long long dd = (unsigned long long)(long long)d;
+    const unsigned long long ext = d < 0 ? ~0ull : 0ull;
+    unsigned long long carry = 0;
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+      const unsigned long long sub = k == 0 ? dd : ext;
+      const unsigned long long r = X[k] - sub - carry;
+      carry = (X[k] < sub) || (X[k] - sub < carry) ? 1ull : 0ull;
+      X[k] = r;
+    }
+#pragma unroll
+    for (int k = 0; k < KW - 1; ++k) X[k] = (X[k] >> 7) | (X[k + 1] << 57);
+    X[KW - 1] = (unsigned long long)((long long)X[KW - 1] >> 7);
     out[(int64_t)(p - 1) * stride] = (int8_t)d;
   }
-  out[0] = (int8_t)(int)(long long)xl;  // remaining top digit in [-64, 64]
+  out[0] = (int8_t)(int)(long long)X[0];  // remaining top digit in [-64, 64]
 }
 
 // Slices of A (per row) into As[s][mpad][lpad], of B (per column, stored
 // transposed) into Bs[s][npad][lpad]; padding is zero.
+template <int L>
 __global__ void oz_split_a_kernel(int64_t m, int64_t l, mat A, const int* ex, int s, int64_t mpad,
                                   int64_t lpad, int8_t* As) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,23 +152,30 @@ __global__ void oz_split_a_kernel(int64_t m, int64_t l, mat A, const int* ex, in
   const int64_t stride = mpad * lpad;
   int8_t* out = As + i * lpad + k;
   if (i < m && k < l) {
-    oz_digits(A.p[0][i * A.ld + k], A.p[1][i * A.ld + k], ex[i], s, out, stride);
+    double x[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) x[q] = A.p[q][i * A.ld + k];
+    oz_digits<L>(x, ex[i], s, out, stride);
   } else {
     for (int p = 0; p < s; ++p) out[(int64_t)p * stride] = 0;
   }
 }
 
+template <int L>
 __global__ void oz_split_b_kernel(int64_t l, int64_t n, mat B, const int* ex, int s, int64_t npad,
                                   int64_t lpad, int8_t* Bs) {
   // tile: 32 k x 32 j; digits staged in shared memory and written k-contiguous
-  __shared__ int8_t t[18][32][33];
+  __shared__ int8_t t[OZ_MAXS][32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   const int64_t k0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
   for (int kk = ty; kk < 32; kk += 8) {
     const int64_t k = k0 + kk, j = j0 + tx;
-    int8_t dig[18];
+    int8_t dig[OZ_MAXS];
     if (k < l && j < n) {
-      oz_digits(B.p[0][k * B.ld + j], B.p[1][k * B.ld + j], ex[j], s, dig, 1);
+      double x[L];
+#pragma unroll
+      for (int q = 0; q < L; ++q) x[q] = B.p[q][k * B.ld + j];
+      oz_digits<L>(x, ex[j], s, dig, 1);
     } else {
       for (int p = 0; p < s; ++p) dig[p] = 0;
     }
@@ -240,14 +274,21 @@ __global__ void __launch_bounds__(256) oz_gemm_kernel(int64_t mpad, int64_t npad
     }
 }
 
-// C (mode) sum_r D_r 2^(ea_i + fb_j - 12 - 7 (r - 2)), exact in 192 bits,
-// rounded once to DD.
+// C (mode) sum_r D_r 2^(ea_i + fb_j - 12 - 7 (r - 2)), exact in a 192-bit
+// (DD) or 288-bit (QD) word, rounded once: DD = leading 53 bits and the next
+// 53 (truncated), summed by TwoSum; QD = four such 53-bit pieces,
+// renormalised.
+template <int L>
 __global__ void oz_recombine_kernel(int64_t m, int64_t n, int s, int64_t mpad, int64_t npad,
                                     const int32_t* D, const int* exa, const int* exb, mat C, int mode) {
+  constexpr int NW = L == 2 ? 6 : 9;
+  using N = num<L>;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = blockIdx.y;
   if (j >= n || i >= m) return;
-  uint32_t acc[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+  uint32_t acc[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) acc[w] = 0u;
   const int64_t plane = mpad * npad;
   for (int r = 2; r <= s + 1; ++r) {
     const int32_t v = D[(int64_t)(r - 2) * plane + i * npad + j];
@@ -256,43 +297,53 @@ __global__ void oz_recombine_kernel(int64_t m, int64_t n, int s, int64_t mpad, i
     const long long x = (long long)v * (long long)(1u << b);  // |x| < 2^62
     const uint32_t lo = (uint32_t)x, hi = (uint32_t)((unsigned long long)x >> 32);
     const uint32_t ext = x < 0 ? 0xFFFFFFFFu : 0u;
-    uint32_t d[6];
+    uint32_t d[NW];
 #pragma unroll
-    for (int t = 0; t < 6; ++t) d[t] = t < w ? 0u : (t == w ? lo : (t == w + 1 ? hi : ext));
-    fx::acc_add<6>(acc, d, 0u);
+    for (int t = 0; t < NW; ++t) d[t] = t < w ? 0u : (t == w ? lo : (t == w + 1 ? hi : ext));
+    fx::acc_add<NW>(acc, d, 0u);
   }
   const int T = 6 + 7 * (s - 1);
   // a ~ 2^(ea - T) sum_p d_p 128^(s - p), likewise b, so
   // c = 2^(ea + fb - 2T) sum_r D_r 128^(2s - r) = V 2^(ea + fb - T - 6),
   // with ea = exa - 1022, fb = exb - 1022.
   const int lsb = (exa[i] - 1022) + (exb[j] - 1022) - T - 6;
-  const uint32_t neg = fx::acc_abs<6>(acc);
-  uint64_t ch[2];
-  int ex[2];
-  dd_t v{0.0, 0.0};
-  if (fx::acc_chunks<6, 2>(acc, ch, ex)) {
-    auto sc = [&](uint64_t c, int k) {
-      if (c == 0 || k < -2044) return 0.0;
-      double x = fx::pow2_product(__ull2double_rn(c), k > 2046 ? 2046 : k);
-      return neg ? -x : x;
-    };
-    two_sum(sc(ch[0], lsb + ex[0]), sc(ch[1], lsb + ex[1]), v.hi, v.lo);
+  const uint32_t neg = fx::acc_abs<NW>(acc);
+  uint64_t ch[L];
+  int ex[L];
+  double x[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) x[q] = 0.0;
+  if (fx::acc_chunks<NW, L>(acc, ch, ex)) {
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+      const int k = lsb + ex[q];
+      double v = (ch[q] == 0 || k < -2044) ? 0.0 : fx::pow2_product(__ull2double_rn(ch[q]), k > 2046 ? 2046 : k);
+      x[q] = neg ? -v : v;
+    }
+  }
+  typename N::T v;
+  if constexpr (L == 2) {
+    two_sum(x[0], x[1], v.hi, v.lo);
+  } else {
+    v = qd_renorm<4>(x);
   }
   const int64_t off = i * C.ld + j;
-  if (mode == MODE_ADD) v = dd_add(dd_t{C.p[0][off], C.p[1][off]}, v);
-  else if (mode == MODE_SUB) v = dd_add(dd_t{C.p[0][off], C.p[1][off]}, dd_neg(v));
-  C.p[0][off] = v.hi;
-  C.p[1][off] = v.lo;
+  if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
+  else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));
+  N::store(C.p, off, v);
 }
 
 // ------------------------------------------------------------------ host --
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-ddg_status ozaki_dd_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
-                         int mode, int s, cudaStream_t st) {
+ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
+                      int mode, int s, cudaStream_t st) {
   if (m == 0 || n == 0) return DDG_OK;
-  // X < 2^T must fit the 128-bit digit loop and the 192-bit split word: T <= 125
-  if (s < 2 || s > 18) return set_error(DDG_EINVAL, "ozaki slices must be in [2, 18]");
+  // X < 2^T must fit the digit loop and the split word: T <= 125 (DD, 192
+  // bits) or T <= 223 (QD, 288 bits)
+  const int smax = L == 2 ? 18 : 32;
+  if (s < 2 || s > smax)
+    return set_error(DDG_EINVAL, "ozaki slices must be in [2, " + std::to_string(smax) + "]");
   const int64_t mpad = (m + OBM - 1) / OBM * OBM, npad = (n + OBN - 1) / OBN * OBN;
   const int64_t lpad = std::max<int64_t>(OBK, (l + OBK - 1) / OBK * OBK);
   if ((int64_t)s * lpad * 4096 >= ((int64_t)1 << 31))
@@ -321,9 +372,15 @@ ddg_status ozaki_dd_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const ma
   launched();
   oz_exp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(l, n, B, 0, exb);
   launched();
-  oz_split_a_kernel<<<dim3((unsigned)((lpad + 255) / 256), (unsigned)mpad), 256, 0, st>>>(m, l, A, exa, s, mpad, lpad, As);
+  const dim3 ga((unsigned)((lpad + 255) / 256), (unsigned)mpad), gb((unsigned)(npad / 32), (unsigned)(lpad / 32));
+  if (L == 2) {
+    oz_split_a_kernel<2><<<ga, 256, 0, st>>>(m, l, A, exa, s, mpad, lpad, As);
+    oz_split_b_kernel<2><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, s, npad, lpad, Bs);
+  } else {
+    oz_split_a_kernel<4><<<ga, 256, 0, st>>>(m, l, A, exa, s, mpad, lpad, As);
+    oz_split_b_kernel<4><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, s, npad, lpad, Bs);
+  }
   launched();
-  oz_split_b_kernel<<<dim3((unsigned)(npad / 32), (unsigned)(lpad / 32)), dim3(32, 8), 0, st>>>(l, n, B, exb, s, npad, lpad, Bs);
   launched();
   prof_begin_launch(st, &ev);
   oz_gemm_kernel<<<dim3((unsigned)(npad / OBN), (unsigned)(mpad / OBM), (unsigned)s), 256, OZ_SMEM, st>>>(
@@ -336,7 +393,9 @@ ddg_status ozaki_dd_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const ma
                     (double)s * (mpad + npad) * lpad + 4.0 * s * mpad * npad);
   }
   if (e == cudaSuccess) {
-    oz_recombine_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)m), 256, 0, st>>>(m, n, s, mpad, npad, D, exa, exb, C, mode);
+    const dim3 gr((unsigned)((n + 255) / 256), (unsigned)m);
+    if (L == 2) oz_recombine_kernel<2><<<gr, 256, 0, st>>>(m, n, s, mpad, npad, D, exa, exb, C, mode);
+    else oz_recombine_kernel<4><<<gr, 256, 0, st>>>(m, n, s, mpad, npad, D, exa, exb, C, mode);
     launched();
     e = cudaGetLastError();
   }

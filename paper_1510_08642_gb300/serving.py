@@ -13,6 +13,8 @@ requests that arrive over time:
 * batching: all GEMM requests admitted together form one batch plan
   (grouped persistent launches of the library); each LU solve takes a slot
   of its own (dd_getrf with Winograd trailing updates, then dd_getrs);
+  slots are split between GEMM batches and LU solves so that short products
+  do not wait behind long solves;
 * continuous: requests that arrive while others run are admitted as slots
   and memory free up, so their work overlaps on the device;
 * completion: a CUDA event per unit of work; latency = completion time on
@@ -113,13 +115,20 @@ class Unit:
 
 class Server:
     def __init__(self, device=None, slots: int = 4, hbm_budget: int = 64 << 30, max_batch: int = 32,
+                 lu_slots: int | None = None,
                  gemm_algo: str = "winograd", gemm_cutoff: int = 256, lu_K: int = 256,
                  lu_algo: str = "winograd", lu_cutoff: int = 512, keep_results: bool = False):
         import torch
         self.torch = torch
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         capi.load()
-        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        # slots [0, lu_slots) take LU solves, the others GEMM batches, so that
+        # short products are not queued behind long solves; GEMM slots get the
+        # higher stream priority, so their blocks are scheduled first while a
+        # solve keeps the GPU busy
+        self.lu_slots = max(1, slots // 2) if lu_slots is None else lu_slots
+        self.streams = [torch.cuda.Stream(device=self.device, priority=0 if i < self.lu_slots else -1)
+                        for i in range(slots)]
         self.budget = hbm_budget
         self.max_batch = max_batch
         self.gemm_algo, self.gemm_cutoff = gemm_algo, gemm_cutoff
@@ -170,7 +179,10 @@ class Server:
         torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival)
         queue, inflight = [], []
-        free_slots = list(range(len(self.streams)))
+        free_lu = list(range(self.lu_slots))
+        free_gemm = list(range(self.lu_slots, len(self.streams)))
+        if not free_gemm:
+            free_gemm = free_lu  # one shared pool
         used = 0
         torch.cuda.synchronize(self.device)
         ref = torch.cuda.Event(enable_timing=True)
@@ -196,38 +208,39 @@ class Server:
                         if not self.keep_results:
                             r.result = None
                     used -= u.bytes
-                    free_slots.append(u.slot)
+                    (free_lu if u.kind == "lu" else free_gemm).append(u.slot)
                     done += len(u.reqs)
                 else:
                     still.append(u)
             inflight = still
-            # admission: GEMMs in one batch per free slot, LU one per slot
             progressed = False
-            while queue and free_slots:
-                head = queue[0]
-                if head.kind == "lu":
-                    if used + footprint(head) > self.budget and inflight:
+            # GEMMs: every queued GEMM that fits, in arrival order, one batch per free slot
+            while free_gemm:
+                take, b = [], 0
+                for r in queue:
+                    if r.kind != "gemm" or len(take) >= self.max_batch:
+                        continue
+                    if used + b + footprint(r) > self.budget and (inflight or take):
                         break
-                    queue.pop(0)
-                    head.admitted = time.perf_counter() - t0
-                    slot = free_slots.pop(0)
-                    u = self._start_lu(head, slot)
-                else:
-                    take, b = [], 0
-                    for r in queue:
-                        if r.kind != "gemm" or len(take) >= self.max_batch:
-                            break
-                        if used + b + footprint(r) > self.budget and (inflight or take):
-                            break
-                        take.append(r)
-                        b += footprint(r)
-                    if not take:
-                        break
-                    for r in take:
-                        queue.remove(r)
-                        r.admitted = time.perf_counter() - t0
-                    slot = free_slots.pop(0)
-                    u = self._start_gemms(take, slot)
+                    take.append(r)
+                    b += footprint(r)
+                if not take:
+                    break
+                for r in take:
+                    queue.remove(r)
+                    r.admitted = time.perf_counter() - t0
+                u = self._start_gemms(take, free_gemm.pop(0))
+                inflight.append(u)
+                used += u.bytes
+                progressed = True
+            # LU solves: the oldest queued one that fits, one per free slot
+            while free_lu:
+                lu = next((r for r in queue if r.kind == "lu"), None)
+                if lu is None or (used + footprint(lu) > self.budget and inflight):
+                    break
+                queue.remove(lu)
+                lu.admitted = time.perf_counter() - t0
+                u = self._start_lu(lu, free_lu.pop(0))
                 inflight.append(u)
                 used += u.bytes
                 progressed = True

@@ -88,3 +88,39 @@ def test_n4096_normwise(kind):
         fb = OZ.row_fields(B[0][:, cols], axis=0)
         scale = np.ldexp(1.0, (fa - 1022) + (fb - 1022))
         assert np.all(np.abs(err) <= (n * (s + 3) * 2.0 ** (-7 * s) + 2.0 ** -104) * scale)
+
+
+def run_qd(A, B, s, C0=None, mode="set"):
+    return run(A, B, s, C0, mode)
+
+
+@pytest.mark.parametrize("s", [2, 9, 24, 32])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (9, 40, 13), (130, 65, 129)])
+def test_qd_bit_exact_vs_oracle(s, shape):
+    m, l, n = shape
+    A = I.uniform(m, l, 4, seed=60 + s)
+    B = I.uniform(l, n, 4, seed=70 + s)
+    got = run_qd(A, B, s)
+    want, _ = OZ.gemm(A, B, s)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+@pytest.mark.parametrize("mode", ["add", "sub"])
+def test_qd_modes_bit_exact(mode):
+    A = I.uniform(17, 30, 4, seed=61)
+    B = I.uniform(30, 11, 4, seed=62)
+    C0 = I.uniform(17, 11, 4, seed=63)
+    got = run_qd(A, B, 32, C0, mode)
+    want, _ = OZ.gemm(A, B, 32, C0=C0, mode=mode)
+    assert np.array_equal(got, want)
+
+
+def test_qd_n2048_normwise_qd_accuracy():
+    n = 2048
+    A = I.uniform(n, n, 4, seed=64)
+    B = I.uniform(n, n, 4, seed=65)
+    rows, cols = sample_entries(n, n, 32, seed=66)
+    C = run_qd(A, B, 32)
+    err = O.gemm_error(A, B, C, rows=rows, cols=cols)
+    est = np.sqrt(n * n * np.mean(err ** 2)) / (np.linalg.norm(A[0]) * np.linalg.norm(B[0]))
+    assert est <= 8 * n * 2.0 ** -208, est

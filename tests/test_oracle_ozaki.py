@@ -71,3 +71,31 @@ def test_ozaki_modes():
         C, _ = OZ.gemm(A, B, 16, C0=C0, mode=mode)
         err = O.gemm_error(A, B, C, C0=C0, mode=mode)
         assert np.abs(err).max() < 2.0 ** -95
+
+
+@pytest.mark.parametrize("s", [12, 24, 32])
+def test_ozaki_qd_within_bound(s):
+    m, l, n = 5, 21, 4
+    A = I.uniform(m, l, 4, seed=20)
+    B = I.uniform(l, n, 4, seed=21)
+    C, (SA, SB, D, fa, fb) = OZ.gemm(A, B, s)
+    assert np.abs(D).max() < 2 ** 31
+    err = O.gemm_error(A, B, C)
+    for i in range(m):
+        for j in range(n):
+            scale = 2.0 ** (int(fa[i]) - 1022 + int(fb[j]) - 1022)
+            assert abs(err[i, j]) <= l * (s + 3) * 2.0 ** (-7 * s) * scale + 2.0 ** -208 * scale
+
+
+def test_ozaki_qd_split_reconstructs():
+    s = 32
+    A = I.uniform(3, 5, 4, seed=22)
+    T = 6 + 7 * (s - 1)
+    S, f = OZ.split(A, s, by_row=True)
+    assert np.all(np.abs(S) <= 64)
+    for i in range(3):
+        e = int(f[i]) - 1022
+        for k in range(5):
+            X = sum(int(S[p, i, k]) * 128 ** (s - 1 - p) for p in range(s))
+            exact = sum(Fraction(float(A[q, i, k])) for q in range(4)) * Fraction(2) ** (T - e)
+            assert abs(X - exact) <= Fraction(1, 2) + Fraction(4, 1 << 64)
