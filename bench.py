@@ -322,11 +322,12 @@ def run_e2e(P, torch, w, args, dist, device, stream, hA, hB, hC, dA, dB, dC, cut
 
 
 def time_lu(P, torch, w, device, stream, K):
-    """Section 4 solve: dd_getrf (Winograd trailing updates) + dd_getrs, b = A 1."""
+    """Section 4 solve: dd_getrf / qd_getrf (Winograd trailing updates) +
+    dd_getrs / qd_getrs, b = A 1."""
     from paper_1510_08642_gb300 import inputs as I
     n = w.n
-    A0 = torch.from_numpy(I.uniform(n, n, 2, seed=w.seed_a)).to(device)
-    ones = torch.zeros((2, n, 1), dtype=torch.float64, device=device)
+    A0 = torch.from_numpy(I.uniform(n, n, w.limbs, seed=w.seed_a)).to(device)
+    ones = torch.zeros((w.limbs, n, 1), dtype=torch.float64, device=device)
     ones[0] = 1.0
     b0 = P.gemm(A0, ones, algo="block")
     times = []
@@ -343,7 +344,7 @@ def time_lu(P, torch, w, device, stream, K):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = times[-1]
-    err = float((b[0] - 1.0 + b[1]).abs().max().item())
+    err = float((b[0] - 1.0 + b[1:].sum(dim=0)).abs().max().item())
     return {"value": (2.0 * n ** 3 / 3.0) / (ms * 1e-3) / 1e9, "unit": "G 2mnl/s (2n^3/3 per solve)",
             "ms": ms, "K": K, "cutoff": w.cutoff, "pivot": "partial", "steps": 1, "warmup": 1,
             "max_abs_err_x_minus_1": err}
@@ -466,6 +467,7 @@ def run_ours(args, w):
             del XA, XB, XC
             torch.cuda.empty_cache()
         extras[WL.DD_LU_4096.name] = time_lu(P, torch, WL.DD_LU_4096, device, stream, K=256)
+        extras[WL.QD_LU_2048.name] = time_lu(P, torch, WL.QD_LU_2048, device, stream, K=256)
         extras["batched_1000_mixed"] = time_batched(P, torch, device, stream)
         line["extras"] = extras
 
@@ -512,7 +514,7 @@ def main():
     w = workload_by_name(args.workload)
     if args.impl == "reference":
         return run_reference(args, w)
-    if w.name.startswith("dd_lu"):
+    if w.name.startswith(("dd_lu", "qd_lu")):
         return run_lu_only(args, w)
     if w.name == "serving":
         return run_serving(args)

@@ -64,13 +64,14 @@ typedef enum {
   DDG_BLOCK = 1,    /* C_ij = sum_k A_ik B_kj over register/shared tiles */
   DDG_STRASSEN = 2, /* Strassen 1969: 7 products, 18 quadrant sums per level */
   DDG_WINOGRAD = 3, /* Winograd's variant: 7 products, 15 quadrant sums */
-  DDG_OZAKI = 4     /* not in the paper: DD only. A and B split exactly into
-                       `slices` INT8 digit matrices per row / column scale
-                       (balanced base 128), slice products on the INT8 tensor
-                       cores with INT32 accumulation, recombined exactly and
-                       rounded to DD. Error <= l (s + 3) 2^-7s max|a_i.|
-                       max|b_.j| per entry (normwise, not elementwise, DD
-                       accuracy); l * slices <= 2^19 / 1 */
+  DDG_OZAKI = 4     /* not in the paper (the Ozaki scheme): A and B split
+                       exactly into `slices` INT8 digit matrices per row /
+                       column scale (balanced base 128), slice products on the
+                       INT8 tensor cores with INT32 accumulation, recombined
+                       exactly and rounded to DD / QD. Error <= l (s + 3)
+                       2^-7s max|a_i.| max|b_.j| per entry (normwise, not
+                       elementwise, DD / QD accuracy); slices * l < 2^19,
+                       m <= 65535 */
 } ddg_algo;
 
 /* How C is written: C := A B, C := C + A B or C := C - A B. */
@@ -102,8 +103,9 @@ typedef struct {
                       integer pipe, cross terms by FMA (2 FP64 instructions
                       per DD multiply-add, 4 per QD); 1 = TwoSum accumulation
                       on the FP64 pipe (12 per DD, 113 per QD) */
-  int32_t slices;  /* DDG_OZAKI: number of INT8 slices s in [2, 18];
-                      0 = 16 (about 2^-110 of the row/column maxima) */
+  int32_t slices;  /* DDG_OZAKI: number of INT8 slices s, DD in [2, 18]
+                      (0 = 16, about 2^-110 of the row / column maxima), QD
+                      in [2, 32] (0 = 32, about 2^-222) */
   int32_t reserved[2]; /* must be zero */
 } ddg_opts;
 
@@ -158,6 +160,13 @@ ddg_status dd_getrf(int64_t n, dd_mat A, int64_t* ipiv, int32_t K, int32_t pivot
  * comes from the stream-ordered allocator. Asynchronous.
  */
 ddg_status dd_getrs(int64_t n, int64_t nrhs, dd_mat LU, const int64_t* ipiv, dd_mat B, void* stream);
+
+/* qd_getrf / qd_getrs: the same LU and solve in quad-double (the paper's
+ * QD LU with Winograd updates, Section 4), same arguments with qd_mat; the
+ * quotients use one QD reciprocal of each pivot (five-digit long division). */
+ddg_status qd_getrf(int64_t n, qd_mat A, int64_t* ipiv, int32_t K, int32_t pivot, const ddg_opts* opts,
+                    int64_t* info, void* stream);
+ddg_status qd_getrs(int64_t n, int64_t nrhs, qd_mat LU, const int64_t* ipiv, qd_mat B, void* stream);
 
 /*
  * dd_gemm_noalloc: dd_gemm without any device allocation at call time.

@@ -55,6 +55,10 @@ def lib():
         L.orc_dd_residual.argtypes = [i64, i64, vp, vp, i64, vp, vp, i64, vp, vp, i64, vp, ci]
         L.orc_dd_getrf.argtypes = [i64, vp, vp, i64, vp, ci]
         L.orc_dd_getrf.restype = ci
+        L.orc_residual.argtypes = [ci, i64, i64, vp, i64, vp, i64, vp, i64, vp, ci]
+        L.orc_qd_getrf.argtypes = [i64, vp, i64, vp, ci]
+        L.orc_qd_getrf.restype = ci
+        L.orc_qd_div.argtypes = [vp, vp, vp]
         _lib = L
     return _lib
 
@@ -108,6 +112,10 @@ def qd_mul(a, b):
 
 def qd_add(a, b):
     return _binop(lib().orc_qd_add, a, b, 4)
+
+
+def qd_div(a, b):
+    return _binop(lib().orc_qd_div, a, b, 4)
 
 
 def renorm(x):
@@ -213,6 +221,26 @@ def dd_getrf(A, pivot: bool = True):
     ipiv = np.zeros(n, dtype=np.int64)
     info = lib().orc_dd_getrf(n, LU[0].ctypes.data, LU[1].ctypes.data, n, ipiv.ctypes.data,
                               1 if pivot else 0)
+    return LU, ipiv, info
+
+
+def residual(A, X, Bv, nthreads: int | None = None) -> np.ndarray:
+    """Exact b - A x per entry for DD or QD operands (Section 4, Eq. 2)."""
+    limbs, n = A.shape[0], A.shape[1]
+    nrhs = X.shape[2]
+    A, X, Bv = (np.ascontiguousarray(v, dtype=np.float64) for v in (A, X, Bv))
+    r = np.zeros(n * nrhs)
+    lib().orc_residual(limbs, n, nrhs, _planes(A), n, _planes(X), nrhs, _planes(Bv), nrhs, _p(r),
+                       nthreads or threads())
+    return r.reshape(n, nrhs)
+
+
+def qd_getrf(A, pivot: bool = True):
+    """Unblocked QD LU in place on a copy; returns (LU, ipiv, info)."""
+    n = A.shape[1]
+    LU = np.array(A, dtype=np.float64, order="C")
+    ipiv = np.zeros(n, dtype=np.int64)
+    info = lib().orc_qd_getrf(n, _planes(LU), n, ipiv.ctypes.data, 1 if pivot else 0)
     return LU, ipiv, info
 
 

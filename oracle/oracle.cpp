@@ -27,13 +27,14 @@
 //         Joldes, Marty, Muller, Popescu 2016);
 //       QD product: all limb products of order <= 2 (in units of the limb
 //         spacing) by TwoProd, order-3 products and errors summed plainly,
-//         then the same renormalisation (Hida, Li, Bailey 2001 keep the same
-//         orders).
+//         the terms sorted by decreasing magnitude, then the same
+//         renormalisation (Hida, Li, Bailey 2001 keep the same orders).
 //   * An exact checker: a Kulisch-style long accumulator that forms every
 //     limb product exactly (integer significands, __int128) and returns, per
 //     output entry, the exact error (C_exact - C_computed) rounded to double.
-//   * An exact residual checker b - A x for the Section 4 linear systems and
-//     an unblocked LU with partial pivoting for reference solutions.
+//   * An exact residual checker b - A x for the Section 4 linear systems
+//     (DD or QD) and unblocked DD and QD LU with partial pivoting for
+//     reference solutions (QD quotients by long division).
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fno-fast-math (every
 // product and sum below must round exactly once; fma is always spelled out).
@@ -143,6 +144,9 @@ inline qd qd_mul(const qd& a, const qd& b) {
   o3 = o3 + q11;
   o3 = o3 + q20;
   double t[10] = {p00, p01, p10, q00, p02, p11, p20, q01, q10, o3};
+  // decreasing magnitude, ties in the order above (a limb far below its
+  // position would otherwise leave tiny terms among larger ones)
+  std::stable_sort(t, t + 10, [](double x, double y) { return std::fabs(x) > std::fabs(y); });
   return renorm(t, 10);
 }
 
@@ -416,6 +420,84 @@ int orc_dd_residual(int64_t n, int64_t nrhs,
     r[t] = acc.to_double();
   });
   return 0;
+}
+
+// The same exact residual for DD (limbs = 2) or QD (limbs = 4) operands,
+// each argument an array of limb planes.
+int orc_residual(int limbs, int64_t n, int64_t nrhs, const double* const* A, int64_t lda,
+                 const double* const* X, int64_t ldx, const double* const* B, int64_t ldb,
+                 double* r, int nthreads) {
+  parallel_for(n * nrhs, nthreads, [&](int64_t t) {
+    int64_t i = t / nrhs, c = t % nrhs;
+    Kulisch acc;
+    for (int p = 0; p < limbs; ++p) acc.add_double(B[p][i * ldb + c], false);
+    for (int64_t k = 0; k < n; ++k)
+      for (int p = 0; p < limbs; ++p)
+        for (int q = 0; q < limbs; ++q) {
+          const double a = A[p][i * lda + k], x = X[q][k * ldx + c];
+          if (a != 0.0 && x != 0.0) acc.add_product(a, x, true);
+        }
+    r[t] = acc.to_double();
+  });
+  return 0;
+}
+
+// QD quotient a / b by long division: each digit is the leading limb of the
+// running remainder over the leading limb of b, the remainder loses that
+// digit times b (QD arithmetic), and five digits are renormalised.
+inline qd qd_div(const qd& a, const qd& b) {
+  double q[5];
+  qd r = a;
+  for (int k = 0; k < 5; ++k) {
+    q[k] = r.x[0] / b.x[0];
+    if (k < 4) {
+      qd t = qd_mul(qd{{-q[k], 0.0, 0.0, 0.0}}, b);
+      r = qd_add(r, t);
+    }
+  }
+  return renorm(q, 5);
+}
+
+// Unblocked right-looking QD LU (Section 4 with block size 1), in place on
+// four limb planes, the pivot rule of the DD version on the first two limbs
+// (|x0|, then x1 with the sign of x0); l_ij = a_ij / a_jj by qd_div.
+int orc_qd_getrf(int64_t n, double* const* A, int64_t lda, int64_t* ipiv, int pivot) {
+  auto at = [&](int64_t i, int64_t c) {
+    return qd{{A[0][i * lda + c], A[1][i * lda + c], A[2][i * lda + c], A[3][i * lda + c]}};
+  };
+  auto put = [&](int64_t i, int64_t c, const qd& v) {
+    for (int q = 0; q < 4; ++q) A[q][i * lda + c] = v.x[q];
+  };
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = j;
+    if (pivot) {
+      double bh = std::fabs(A[0][j * lda + j]);
+      double bl = A[0][j * lda + j] < 0 ? -A[1][j * lda + j] : A[1][j * lda + j];
+      for (int64_t i = j + 1; i < n; ++i) {
+        double h = std::fabs(A[0][i * lda + j]);
+        double lo = A[0][i * lda + j] < 0 ? -A[1][i * lda + j] : A[1][i * lda + j];
+        if (h > bh || (h == bh && lo > bl)) { bh = h; bl = lo; p = i; }
+      }
+    }
+    ipiv[j] = p;
+    if (p != j)
+      for (int64_t c = 0; c < n; ++c)
+        for (int q = 0; q < 4; ++q) std::swap(A[q][p * lda + c], A[q][j * lda + c]);
+    const qd piv = at(j, j);
+    if (piv.x[0] == 0.0 && piv.x[1] == 0.0 && piv.x[2] == 0.0 && piv.x[3] == 0.0) return (int)(1 + j);
+    for (int64_t i = j + 1; i < n; ++i) {
+      const qd l = qd_div(at(i, j), piv);
+      put(i, j, l);
+      const qd nl{{-l.x[0], -l.x[1], -l.x[2], -l.x[3]}};
+      for (int64_t c = j + 1; c < n; ++c) put(i, c, qd_add(at(i, c), qd_mul(nl, at(j, c))));
+    }
+  }
+  return 0;
+}
+
+void orc_qd_div(const double* a, const double* b, double* out) {
+  qd r = qd_div(qd{{a[0], a[1], a[2], a[3]}}, qd{{b[0], b[1], b[2], b[3]}});
+  for (int q = 0; q < 4; ++q) out[q] = r.x[q];
 }
 
 // Unblocked right-looking DD LU (Section 4 steps 1-3 with block size 1),

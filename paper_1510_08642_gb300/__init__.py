@@ -55,25 +55,28 @@ def gemm(A, B, C=None, algo: str = "winograd", cutoff: int = 512, mode: str = "s
 
 def getrf(A, K: int = 64, pivot: bool = True, algo: str = "winograd", cutoff: int = 32,
           accum: str = "fx", info=None, stream=None):
-    """In-place DD LU through dd_getrf; returns the device ipiv (int64, n)."""
+    """In-place DD / QD LU through dd_getrf / qd_getrf (by A's limb count);
+    returns the device ipiv (int64, n)."""
     import torch
 
-    n = A.shape[1]
+    limbs, n = A.shape[0], A.shape[1]
     ipiv = torch.empty(n, dtype=torch.int64, device=A.device)
     o = capi.opts(algo, cutoff, False, 7, accum)
     s = (stream or torch.cuda.current_stream(A.device)).cuda_stream
-    capi.check(capi.dd_getrf(n, _mat(A, 2), ipiv.data_ptr(), K, 1 if pivot else 0, o,
-                             info.data_ptr() if info is not None else None, s))
+    fn = capi.dd_getrf if limbs == 2 else capi.qd_getrf
+    capi.check(fn(n, _mat(A, limbs), ipiv.data_ptr(), K, 1 if pivot else 0, o,
+                  info.data_ptr() if info is not None else None, s))
     return ipiv
 
 
 def getrs(LU, ipiv, B, stream=None):
-    """Solve with dd_getrs; B (2, n, nrhs) is overwritten with X and returned."""
+    """Solve with dd_getrs / qd_getrs; B (limbs, n, nrhs) is overwritten with X."""
     import torch
 
-    n, nrhs = B.shape[1], B.shape[2]
+    limbs, n, nrhs = B.shape
     s = (stream or torch.cuda.current_stream(LU.device)).cuda_stream
-    capi.check(capi.dd_getrs(n, nrhs, _mat(LU, 2), ipiv.data_ptr(), _mat(B, 2), s))
+    fn = capi.dd_getrs if limbs == 2 else capi.qd_getrs
+    capi.check(fn(n, nrhs, _mat(LU, limbs), ipiv.data_ptr(), _mat(B, limbs), s))
     return B
 
 

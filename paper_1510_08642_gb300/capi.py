@@ -84,6 +84,8 @@ SIGNATURES = {
     "dd_gemm_batched": (c_i32, [c_i32, ctypes.POINTER(ddg_problem), c_vp]),
     "dd_getrf": (c_i32, [c_i64, dd_mat, c_vp, c_i32, c_i32, ctypes.POINTER(ddg_opts), c_vp, c_vp]),
     "dd_getrs": (c_i32, [c_i64, c_i64, dd_mat, c_vp, dd_mat, c_vp]),
+    "qd_getrf": (c_i32, [c_i64, qd_mat, c_vp, c_i32, c_i32, ctypes.POINTER(ddg_opts), c_vp, c_vp]),
+    "qd_getrs": (c_i32, [c_i64, c_i64, qd_mat, c_vp, qd_mat, c_vp]),
     "ddg_last_error": (ctypes.c_char_p, []),
     "ddg_kernel_launches": (ctypes.c_uint64, []),
     "ddg_profile_begin": (c_i32, []),
@@ -208,3 +210,13 @@ def ddg_batch_destroy(handle: int, stream: int = 0) -> None:
 def dd_gemm_batched(problems, stream: int = 0) -> int:
     arr = (ddg_problem * max(len(problems), 1))(*problems)
     return load().dd_gemm_batched(len(problems), arr, c_vp(stream))
+
+
+def qd_getrf(n, A: qd_mat, ipiv: int, K: int, pivot: int, o: ddg_opts | None, info: int | None,
+             stream: int = 0) -> int:
+    return load().qd_getrf(n, A, c_vp(ipiv), K, pivot, ctypes.byref(o) if o is not None else None,
+                           c_vp(info) if info else None, c_vp(stream))
+
+
+def qd_getrs(n, nrhs, LU: qd_mat, ipiv: int, B: qd_mat, stream: int = 0) -> int:
+    return load().qd_getrs(n, nrhs, LU, c_vp(ipiv), B, c_vp(stream))

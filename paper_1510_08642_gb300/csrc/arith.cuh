@@ -19,8 +19,9 @@
 //   QD sum: limbs merged by decreasing magnitude, then renormalisation by
 //     VecSum and a compaction pass (Joldes, Marty, Muller, Popescu 2016);
 //   QD product: limb products of order <= 2 by TwoProd, order-3 terms summed
-//     plainly (the orders kept by Hida, Li, Bailey 2001), then the same
-//     renormalisation.
+//     plainly (the orders kept by Hida, Li, Bailey 2001), the terms sorted
+//     by decreasing magnitude, then the same renormalisation;
+//   QD quotient: long division, five double digits.
 #pragma once
 
 #include <cstdint>
@@ -153,6 +154,33 @@ __device__ __forceinline__ qd_t qd_add(const qd_t& a, const qd_t& b) {
   return qd_renorm<8>(m);
 }
 
+// Stable sort by decreasing magnitude: odd-even transposition (N rounds of
+// adjacent compare-exchanges that swap only on a strictly larger magnitude,
+// so equal magnitudes keep their order). The keys are the magnitude bits,
+// compared as integers, so the sort runs on the integer pipe. The product's
+// terms are listed by order (i + j of a_i b_j); a limb far below its
+// position (a QD number close to a short one, e.g. an integer plus a tiny
+// correction) puts tiny terms among larger ones, and the renormalisation
+// below needs them in decreasing order to keep four full limbs.
+template <int N>
+__device__ __forceinline__ void sort_by_magnitude(double (&t)[N]) {
+  unsigned long long k[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) k[i] = (unsigned long long)__double_as_longlong(t[i]) & 0x7FFFFFFFFFFFFFFFull;
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+#pragma unroll
+    for (int i = r & 1; i + 1 < N; i += 2)
+      if (k[i + 1] > k[i]) {
+        const unsigned long long kk = k[i];
+        k[i] = k[i + 1];
+        k[i + 1] = kk;
+        const double tt = t[i];
+        t[i] = t[i + 1];
+        t[i + 1] = tt;
+      }
+}
+
 __device__ __forceinline__ qd_t qd_mul(const qd_t& a, const qd_t& b) {
   double p00, q00, p01, q01, p10, q10, p02, q02, p11, q11, p20, q20;
   two_prod(a.x[0], b.x[0], p00, q00);
@@ -169,11 +197,26 @@ __device__ __forceinline__ qd_t qd_mul(const qd_t& a, const qd_t& b) {
   o3 = __dadd_rn(o3, q11);
   o3 = __dadd_rn(o3, q20);
   double t[10] = {p00, p01, p10, q00, p02, p11, p20, q01, q10, o3};
+  sort_by_magnitude(t);
   return qd_renorm<10>(t);
 }
 
 __device__ __forceinline__ qd_t qd_neg(const qd_t& a) {
   return qd_t{{-a.x[0], -a.x[1], -a.x[2], -a.x[3]}};
+}
+
+// QD quotient a / b by long division: five double quotient digits, each
+// remainder formed with the QD product and sum above, renormalised.
+__device__ __forceinline__ qd_t qd_div(const qd_t& a, const qd_t& b) {
+  double q[5];
+  qd_t r = a;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    q[k] = __ddiv_rn(r.x[0], b.x[0]);
+    r = qd_add(r, qd_neg(qd_mul(qd_t{{q[k], 0.0, 0.0, 0.0}}, b)));
+  }
+  q[4] = __ddiv_rn(r.x[0], b.x[0]);
+  return qd_renorm<5>(q);
 }
 
 // ---------------------------------------------------------------------------
@@ -185,6 +228,10 @@ template <> struct num<2> {
   static __device__ __forceinline__ T add(const T& a, const T& b) { return dd_add(a, b); }
   static __device__ __forceinline__ T mul(const T& a, const T& b) { return dd_mul(a, b); }
   static __device__ __forceinline__ T neg(const T& a) { return dd_neg(a); }
+  static __device__ __forceinline__ T div(const T& a, const T& b) { return dd_div(a, b); }
+  static __device__ __forceinline__ T one() { return dd_t{1.0, 0.0}; }
+  static __device__ __forceinline__ double lead(const T& a) { return a.hi; }
+  static __device__ __forceinline__ double second(const T& a) { return a.lo; }
   static __device__ __forceinline__ T load(const double* const* p, int64_t off) {
     return dd_t{p[0][off], p[1][off]};
   }
@@ -199,6 +246,10 @@ template <> struct num<4> {
   static __device__ __forceinline__ T add(const T& a, const T& b) { return qd_add(a, b); }
   static __device__ __forceinline__ T mul(const T& a, const T& b) { return qd_mul(a, b); }
   static __device__ __forceinline__ T neg(const T& a) { return qd_neg(a); }
+  static __device__ __forceinline__ T div(const T& a, const T& b) { return qd_div(a, b); }
+  static __device__ __forceinline__ T one() { return qd_t{{1.0, 0.0, 0.0, 0.0}}; }
+  static __device__ __forceinline__ double lead(const T& a) { return a.x[0]; }
+  static __device__ __forceinline__ double second(const T& a) { return a.x[1]; }
   static __device__ __forceinline__ T load(const double* const* p, int64_t off) {
     return qd_t{{p[0][off], p[1][off], p[2][off], p[3][off]}};
   }

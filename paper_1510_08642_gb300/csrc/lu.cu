@@ -1,8 +1,9 @@
-// DD LU decomposition and solve (Kouya 2015, Section 4): the blocked
+// DD and QD LU decomposition and solve (Kouya 2015, Section 4): the blocked
 // right-looking LU whose trailing update A22 := A22 - L21 U12 (step 3, the
-// underlined product) is a DD matrix product, here dd_gemm with mode SUB and
-// the caller's algorithm (Winograd by default), and the solution of A x = b
-// (Eq. 2) by forward and back substitution.
+// underlined product) is a DD / QD matrix product, here the library's
+// product with mode SUB and the caller's algorithm (Winograd by default),
+// and the solution of A x = b (Eq. 2) by forward and back substitution. One
+// code path for both precisions (template on the limb count).
 //
 // Steps per block column of width K (the paper's K = alpha n_min):
 //   1. panel: for each column j of the block, pivot search (the first row of
@@ -38,27 +39,28 @@ constexpr int TB = 32;       // triangle size of the substitution base case (one
 constexpr int KMAX = 512;    // widest block column
 constexpr int PANEL_BASE = 16;  // widest panel factored column by column
 
-// Pivot candidates compare by integer keys of |x| as a DD number (leading
-// magnitude, then the trailing limb with the leading limb's sign): no FP64
-// compare instructions on the pivot search's critical path.
+// Pivot candidates compare by integer keys of |x| (leading limb magnitude,
+// then the second limb with the leading limb's sign): no FP64 compare
+// instructions on the pivot search's critical path.
 struct partial_t {
   unsigned long long kh, kl;
   int64_t idx;
 };
 
-// Per-call device state of the column steps.
+// Per-call device state of the column steps (large enough for a QD value).
 struct col_state {
   unsigned int counter;  // CTAs finished in the current launch
   unsigned int pad;
-  dd_t rinv;             // 1 / pivot of the column being eliminated (0 if zero)
+  double rinv[4];        // 1 / pivot of the column being eliminated (0 if zero)
 };
 
-__device__ __forceinline__ dd_t ldA(const mat& A, int64_t i, int64_t j) {
-  return dd_t{A.p[0][i * A.ld + j], A.p[1][i * A.ld + j]};
+template <int L>
+__device__ __forceinline__ typename num<L>::T ldA(const mat& A, int64_t i, int64_t j) {
+  return num<L>::load(A.p, i * A.ld + j);
 }
-__device__ __forceinline__ void stA(const mat& A, int64_t i, int64_t j, dd_t v) {
-  A.p[0][i * A.ld + j] = v.hi;
-  A.p[1][i * A.ld + j] = v.lo;
+template <int L>
+__device__ __forceinline__ void stA(const mat& A, int64_t i, int64_t j, const typename num<L>::T& v) {
+  num<L>::store(A.p, i * A.ld + j, v);
 }
 
 __device__ __forceinline__ unsigned long long dkey(double x) {
@@ -66,10 +68,11 @@ __device__ __forceinline__ unsigned long long dkey(double x) {
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);  // order of doubles
 }
 
-__device__ __forceinline__ partial_t cand(dd_t v, int64_t i) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v.hi);
-  const double lo = (b >> 63) ? -v.lo : v.lo;
-  return partial_t{b & 0x7FFFFFFFFFFFFFFFull, dkey(lo), i};
+template <int L>
+__device__ __forceinline__ partial_t cand(const typename num<L>::T& v, int64_t i) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(num<L>::lead(v));
+  const double s2 = num<L>::second(v);
+  return partial_t{b & 0x7FFFFFFFFFFFFFFFull, dkey((b >> 63) ? -s2 : s2), i};
 }
 
 __device__ __forceinline__ partial_t none() { return partial_t{0ull, 0ull, INT64_MAX}; }
@@ -90,17 +93,33 @@ __device__ __forceinline__ void warp_best(partial_t& v) {
   }
 }
 
-__device__ __forceinline__ bool dd_is_zero(dd_t v) {
-  return ((unsigned long long)__double_as_longlong(v.hi) & 0x7FFFFFFFFFFFFFFFull) == 0ull &&
-         ((unsigned long long)__double_as_longlong(v.lo) & 0x7FFFFFFFFFFFFFFFull) == 0ull;
+template <int L>
+__device__ __forceinline__ bool is_zero(const typename num<L>::T& v) {
+  const double* x = reinterpret_cast<const double*>(&v);
+  bool z = true;
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    z = z && (((unsigned long long)__double_as_longlong(x[q]) & 0x7FFFFFFFFFFFFFFFull) == 0ull);
+  return z;
+}
+
+template <int L>
+__device__ __forceinline__ typename num<L>::T get_rinv(const col_state* cs) {
+  typename num<L>::T v;
+  double* x = reinterpret_cast<double*>(&v);
+#pragma unroll
+  for (int q = 0; q < L; ++q) x[q] = cs->rinv[q];
+  return v;
 }
 
 // Executed by the last CTA of a launch (all its threads): choose the pivot
 // of column j from the partial arg-maxes (or row j without pivoting),
 // record it, flag an exactly zero pivot, swap rows j and p across all
 // columns, and publish 1 / pivot for the quotients of column j.
+template <int L>
 __device__ void finish_pivot(int64_t n, const mat& A, int64_t j, int64_t nparts, const partial_t* part,
                              int64_t* ipiv, int64_t* info, int pivot, col_state* cs) {
+  using T = typename num<L>::T;
   __shared__ partial_t sbest[8];
   __shared__ int64_t sp;
   const int tid = threadIdx.x;
@@ -126,7 +145,7 @@ __device__ void finish_pivot(int64_t n, const mat& A, int64_t j, int64_t nparts,
   if (p != j) {
     for (int64_t c = tid; c < n; c += blockDim.x)
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
+      for (int q = 0; q < L; ++q) {
         double* rj = A.p[q] + j * A.ld + c;
         double* rp = A.p[q] + p * A.ld + c;
         const double t = *rj;
@@ -137,10 +156,13 @@ __device__ void finish_pivot(int64_t n, const mat& A, int64_t j, int64_t nparts,
   __syncthreads();
   if (tid == 0) {
     ipiv[j] = p;
-    const dd_t piv = ldA(A, j, j);
-    const bool zero = dd_is_zero(piv);
+    const T piv = ldA<L>(A, j, j);
+    const bool zero = is_zero<L>(piv);
     if (zero && *info == 0) *info = j + 1;
-    cs->rinv = zero ? dd_t{0.0, 0.0} : dd_div(dd_t{1.0, 0.0}, piv);
+    const T r = zero ? num<L>::zero() : num<L>::div(num<L>::one(), piv);
+    const double* x = reinterpret_cast<const double*>(&r);
+#pragma unroll
+    for (int q = 0; q < L; ++q) cs->rinv[q] = x[q];
     cs->counter = 0u;
   }
 }
@@ -163,17 +185,18 @@ __device__ __forceinline__ bool last_block(col_state* cs) {
 
 // First column j of a narrow panel: partial arg-maxes of column j over rows
 // [j, n) (RB rows per CTA), then the last CTA chooses and swaps the pivot.
+template <int L>
 __global__ void __launch_bounds__(256) lu_start_kernel(int64_t n, mat A, int64_t j, partial_t* part,
                                                        int64_t* ipiv, int64_t* info, int pivot,
                                                        col_state* cs) {
   const int tid = threadIdx.x;
   if (pivot && tid < 32) {
     const int64_t i = j + (int64_t)blockIdx.x * RB + tid;
-    partial_t v = i < n ? cand(ldA(A, i, j), i) : none();
+    partial_t v = i < n ? cand<L>(ldA<L>(A, i, j), i) : none();
     warp_best(v);
     if (tid == 0) part[blockIdx.x] = v;
   }
-  if (last_block(cs)) finish_pivot(n, A, j, gridDim.x, part, ipiv, info, pivot, cs);
+  if (last_block(cs)) finish_pivot<L>(n, A, j, gridDim.x, part, ipiv, info, pivot, cs);
 }
 
 // Column j (its pivot row already in place, 1 / pivot in cs): quotients
@@ -181,87 +204,106 @@ __global__ void __launch_bounds__(256) lu_start_kernel(int64_t n, mat A, int64_t
 // of those rows; then, if column j + 1 belongs to the same panel, the
 // partial arg-maxes of the updated column j + 1 and, in the last CTA, its
 // pivot.
+template <int L>
 __global__ void __launch_bounds__(256) lu_col_kernel(int64_t n, mat A, int64_t j, int64_t pe,
                                                      partial_t* part, int64_t* ipiv, int64_t* info,
                                                      int pivot, col_state* cs) {
-  __shared__ dd_t u[KMAX];
-  __shared__ dd_t lq[RB];
+  using N = num<L>;
+  using T = typename N::T;
+  __shared__ T u[KMAX];
+  __shared__ T lq[RB];
   const int tid = threadIdx.x;
   const int64_t r0 = j + 1 + (int64_t)blockIdx.x * RB;
   const int rows = (int)(n - r0 < RB ? n - r0 : RB);
   const int cols = (int)(pe - j - 1);
-  const dd_t rinv = cs->rinv;
-  const bool zero = dd_is_zero(rinv);
+  const T rinv = get_rinv<L>(cs);
+  const bool zero = is_zero<L>(rinv);
   if (tid < rows) {
-    dd_t l{0.0, 0.0};
+    T l = N::zero();
     if (!zero) {
-      l = dd_mul(ldA(A, r0 + tid, j), rinv);
-      stA(A, r0 + tid, j, l);
+      l = N::mul(ldA<L>(A, r0 + tid, j), rinv);
+      stA<L>(A, r0 + tid, j, l);
     }
     lq[tid] = l;
   }
-  for (int c = tid; c < cols; c += blockDim.x) u[c] = ldA(A, j, j + 1 + c);
+  for (int c = tid; c < cols; c += blockDim.x) u[c] = ldA<L>(A, j, j + 1 + c);
   __syncthreads();
   for (int e = tid; e < rows * cols; e += blockDim.x) {
     const int r = e / cols, c = e % cols;
     const int64_t i = r0 + r, jc = j + 1 + c;
-    stA(A, i, jc, dd_add(ldA(A, i, jc), dd_mul(dd_neg(lq[r]), u[c])));
+    stA<L>(A, i, jc, N::add(ldA<L>(A, i, jc), N::mul(N::neg(lq[r]), u[c])));
   }
   if (j + 1 >= pe) return;  // the next panel starts with lu_start_kernel
   __syncthreads();
   if (pivot && tid < 32) {
-    partial_t v = tid < rows ? cand(ldA(A, r0 + tid, j + 1), r0 + tid) : none();
+    partial_t v = tid < rows ? cand<L>(ldA<L>(A, r0 + tid, j + 1), r0 + tid) : none();
     warp_best(v);
     if (tid == 0) part[blockIdx.x] = v;
   }
-  if (last_block(cs)) finish_pivot(n, A, j + 1, gridDim.x, part, ipiv, info, pivot, cs);
+  if (last_block(cs)) finish_pivot<L>(n, A, j + 1, gridDim.x, part, ipiv, info, pivot, cs);
 }
 
-// X := L^-1 X for a unit lower triangle L (m <= TB rows): one warp per
-// column of X, lane i holding row i. At step k lane k's value is final and
-// is broadcast by a shuffle; lanes below it subtract l_ik x_k. A GB300 SM
+template <int L>
+__device__ __forceinline__ typename num<L>::T shfl(const typename num<L>::T& v, int k) {
+  typename num<L>::T r;
+  const double* x = reinterpret_cast<const double*>(&v);
+  double* y = reinterpret_cast<double*>(&r);
+#pragma unroll
+  for (int q = 0; q < L; ++q) y[q] = __shfl_sync(0xffffffffu, x[q], k);
+  return r;
+}
+
+// X := L^-1 X for a unit lower triangle (m <= TB rows): one warp per column
+// of X, lane i holding row i. At step k lane k's value is final and is
+// broadcast by a shuffle; lanes below it subtract l_ik x_k. A GB300 SM
 // issues one FP64 warp instruction per 16 cycles, so spreading the rows of
-// a column over the lanes (one DD multiply-add per step) keeps the chain
+// a column over the lanes (one multiply-add per step) keeps the chain
 // short: TB steps instead of TB (TB - 1) / 2 multiply-adds per thread.
+template <int L>
 __global__ void __launch_bounds__(128) trsm_lower_unit_base(int64_t m, int64_t r, mat Lm, mat X) {
-  __shared__ dd_t T[TB][TB];
+  using N = num<L>;
+  using T = typename N::T;
+  __shared__ T Tr[TB][TB];
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     const int i = e / TB, k = e % TB;
-    T[i][k] = (i < m && k < i) ? ldA(Lm, i, k) : dd_t{0.0, 0.0};
+    Tr[i][k] = (i < m && k < i) ? ldA<L>(Lm, i, k) : N::zero();
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (c >= r) return;
-  dd_t acc = lane < m ? ldA(X, lane, c) : dd_t{0.0, 0.0};
+  T acc = lane < m ? ldA<L>(X, lane, c) : N::zero();
   for (int k = 0; k < m; ++k) {
-    const dd_t xk{__shfl_sync(0xffffffffu, acc.hi, k), __shfl_sync(0xffffffffu, acc.lo, k)};
-    if (lane > k) acc = dd_add(acc, dd_mul(dd_neg(T[lane][k]), xk));
+    const T xk = shfl<L>(acc, k);
+    if (lane > k) acc = N::add(acc, N::mul(N::neg(Tr[lane][k]), xk));
   }
-  if (lane < m) stA(X, lane, c, acc);
+  if (lane < m) stA<L>(X, lane, c, acc);
 }
 
-// X := U^-1 X for an upper triangle U with nonzero diagonal (m <= TB rows),
+// X := U^-1 X for an upper triangle with nonzero diagonal (m <= TB rows),
 // one warp per column as above, from the last row up; each lane first forms
-// the DD reciprocal of its diagonal entry.
+// the reciprocal of its diagonal entry.
+template <int L>
 __global__ void __launch_bounds__(128) trsm_upper_base(int64_t m, int64_t r, mat U, mat X) {
-  __shared__ dd_t T[TB][TB];
+  using N = num<L>;
+  using T = typename N::T;
+  __shared__ T Tr[TB][TB];
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     const int i = e / TB, k = e % TB;
-    T[i][k] = (i < m && k < m && k >= i) ? ldA(U, i, k) : dd_t{i == k ? 1.0 : 0.0, 0.0};
+    Tr[i][k] = (i < m && k < m && k >= i) ? ldA<L>(U, i, k) : (i == k ? N::one() : N::zero());
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (c >= r) return;
-  const dd_t rinv = dd_div(dd_t{1.0, 0.0}, T[lane][lane]);
-  dd_t acc = lane < m ? ldA(X, lane, c) : dd_t{0.0, 0.0};
+  const T rinv = N::div(N::one(), Tr[lane][lane]);
+  T acc = lane < m ? ldA<L>(X, lane, c) : N::zero();
   for (int k = (int)m - 1; k >= 0; --k) {
-    if (lane == k) acc = dd_mul(acc, rinv);
-    const dd_t xk{__shfl_sync(0xffffffffu, acc.hi, k), __shfl_sync(0xffffffffu, acc.lo, k)};
-    if (lane < k) acc = dd_add(acc, dd_mul(dd_neg(T[lane][k]), xk));
+    if (lane == k) acc = N::mul(acc, rinv);
+    const T xk = shfl<L>(acc, k);
+    if (lane < k) acc = N::add(acc, N::mul(N::neg(Tr[lane][k]), xk));
   }
-  if (lane < m) stA(X, lane, c, acc);
+  if (lane < m) stA<L>(X, lane, c, acc);
 }
 
 // Row permutation of the interchanges ipiv[0..n): perm[i] = source row of
@@ -294,11 +336,12 @@ __global__ void lu_perm_kernel(int64_t n, const int64_t* ipiv, int64_t* perm) {
   }
 }
 
+template <int L>
 __global__ void lu_gather_kernel(int64_t n, int64_t r, const int64_t* perm, mat B, mat X) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * r) return;
   const int64_t i = e / r, c = e % r;
-  stA(X, i, c, ldA(B, perm[i], c));
+  stA<L>(X, i, c, ldA<L>(B, perm[i], c));
 }
 
 // ------------------------------------------------------------------ host --
@@ -315,68 +358,69 @@ static cudaError_t counted(cudaError_t e) {
 }
 
 // X := L^-1 X (L unit lower, m x m), X m x r.
+template <int L>
 static ddg_status trsm_lower_unit(int64_t m, int64_t r, const mat& Lm, const mat& X, cudaStream_t s) {
   if (m == 0 || r == 0) return DDG_OK;
   if (m <= TB) {
-    trsm_lower_unit_base<<<(unsigned)((r + 3) / 4), 128, 0, s>>>(m, r, Lm, X);
+    trsm_lower_unit_base<L><<<(unsigned)((r + 3) / 4), 128, 0, s>>>(m, r, Lm, X);
     return counted(cudaGetLastError()) == cudaSuccess ? DDG_OK : set_error(DDG_ECUDA, "trsm launch");
   }
   const int64_t m1 = std::max<int64_t>(TB, (m / 2) / TB * TB);
-  ddg_status st = trsm_lower_unit(m1, r, Lm, X, s);
+  ddg_status st = trsm_lower_unit<L>(m1, r, Lm, X, s);
   if (st != DDG_OK) return st;
-  st = gemm_run(2, m - m1, m1, r, view(Lm, m1, 0), X, view(X, m1, 0), MODE_SUB, block_opts(), s);
+  st = gemm_run(L, m - m1, m1, r, view(Lm, m1, 0), X, view(X, m1, 0), MODE_SUB, block_opts(), s);
   if (st != DDG_OK) return st;
-  return trsm_lower_unit(m - m1, r, view(Lm, m1, m1), view(X, m1, 0), s);
+  return trsm_lower_unit<L>(m - m1, r, view(Lm, m1, m1), view(X, m1, 0), s);
 }
 
 // X := U^-1 X (U upper, m x m), X m x r.
+template <int L>
 static ddg_status trsm_upper(int64_t m, int64_t r, const mat& U, const mat& X, cudaStream_t s) {
   if (m == 0 || r == 0) return DDG_OK;
   if (m <= TB) {
-    trsm_upper_base<<<(unsigned)((r + 3) / 4), 128, 0, s>>>(m, r, U, X);
+    trsm_upper_base<L><<<(unsigned)((r + 3) / 4), 128, 0, s>>>(m, r, U, X);
     return counted(cudaGetLastError()) == cudaSuccess ? DDG_OK : set_error(DDG_ECUDA, "trsm launch");
   }
   const int64_t m1 = std::max<int64_t>(TB, (m / 2) / TB * TB);
-  ddg_status st = trsm_upper(m - m1, r, view(U, m1, m1), view(X, m1, 0), s);
+  ddg_status st = trsm_upper<L>(m - m1, r, view(U, m1, m1), view(X, m1, 0), s);
   if (st != DDG_OK) return st;
-  st = gemm_run(2, m1, m - m1, r, view(U, 0, m1), view(X, m1, 0), X, MODE_SUB, block_opts(), s);
+  st = gemm_run(L, m1, m - m1, r, view(U, 0, m1), view(X, m1, 0), X, MODE_SUB, block_opts(), s);
   if (st != DDG_OK) return st;
-  return trsm_upper(m1, r, U, X, s);
+  return trsm_upper<L>(m1, r, U, X, s);
 }
 
-static bool bad_dd(const dd_mat& M, int64_t rows, int64_t cols) {
+static bool bad_planes(int L, const mat& M, int64_t rows, int64_t cols) {
   if (rows == 0 || cols == 0) return false;
-  return !M.hi || !M.lo || M.ld < cols || M.ld < 1;
+  if (M.ld < cols || M.ld < 1) return true;
+  for (int q = 0; q < L; ++q)
+    if (!M.p[q]) return true;
+  return false;
 }
 
-}  // namespace ddg
-
-extern "C" {
-
-ddg_status dd_getrf(int64_t n, dd_mat A, int64_t* ipiv, int32_t K, int32_t pivot, const ddg_opts* opts,
-                    int64_t* info, void* stream) {
-  using namespace ddg;
+template <int L>
+static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t* ipiv, int32_t K,
+                             int32_t pivot, const ddg_opts* opts, int64_t* info, void* stream) {
   clear_error();
-  if (n < 0) return set_error(DDG_EINVAL, "negative size");
-  if (K < 1 || K > KMAX) return set_error(DDG_EINVAL, "block size K must be in [1, 512]");
-  if (pivot != 0 && pivot != 1) return set_error(DDG_EINVAL, "pivot must be 0 or 1");
-  if (bad_dd(A, n, n)) return set_error(DDG_EINVAL, "A: null plane or ld < n");
-  if (n > 0 && !ipiv) return set_error(DDG_EINVAL, "ipiv is null");
+  const std::string nm(name);
+  if (n < 0) return set_error(DDG_EINVAL, nm + ": negative size");
+  if (K < 1 || K > KMAX) return set_error(DDG_EINVAL, nm + ": block size K must be in [1, 512]");
+  if (pivot != 0 && pivot != 1) return set_error(DDG_EINVAL, nm + ": pivot must be 0 or 1");
+  if (bad_planes(L, M, n, n)) return set_error(DDG_EINVAL, nm + ": A: null plane or ld < n");
+  if (n > 0 && !ipiv) return set_error(DDG_EINVAL, nm + ": ipiv is null");
   ddg_opts o;
   ddg_opts_default(&o);
   if (opts) o = *opts;
-  if (o.algo < DDG_SIMPLE || o.algo > DDG_WINOGRAD || o.cutoff < 1 || (o.accum != 0 && o.accum != 1) ||
+  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI || o.cutoff < 1 || (o.accum != 0 && o.accum != 1) ||
       (o.pad != 0 && o.pad != 1) || (o.streams != 0 && o.streams != 1 && o.streams != 7))
-    return set_error(DDG_EINVAL, "invalid options");
+    return set_error(DDG_EINVAL, nm + ": invalid options");
   if (n == 0) return DDG_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const mat M{{A.hi, A.lo, nullptr, nullptr}, A.ld};
   const int64_t maxparts = (n + RB - 1) / RB;
   const size_t bytes = sizeof(partial_t) * (size_t)maxparts + 512;
   void* ws = nullptr;
   if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
     cudaGetLastError();
-    return set_error(DDG_ENOMEM, "dd_getrf: scratch allocation failed");
+    return set_error(DDG_ENOMEM, nm + ": scratch allocation failed");
   }
   partial_t* part = reinterpret_cast<partial_t*>(static_cast<char*>(ws) + 512);
   int64_t* dinfo = info ? info : reinterpret_cast<int64_t*>(ws);
@@ -384,26 +428,26 @@ ddg_status dd_getrf(int64_t n, dd_mat A, int64_t* ipiv, int32_t K, int32_t pivot
   ddg_status st = DDG_OK;
   auto cu = [&](cudaError_t e) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (e != cudaSuccess && st == DDG_OK) st = set_error(DDG_ECUDA, std::string("dd_getrf: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess && st == DDG_OK) st = set_error(DDG_ECUDA, nm + ": " + cudaGetErrorString(e));
   };
   if (cudaMemsetAsync(dinfo, 0, sizeof(int64_t), s) != cudaSuccess ||
       cudaMemsetAsync(cs, 0, sizeof(col_state), s) != cudaSuccess)
-    st = set_error(DDG_ECUDA, "memset");
+    st = set_error(DDG_ECUDA, nm + ": memset");
   // Panel of columns [c0, c0 + w), rows [c0, n): per-column kernels for
   // narrow panels; wider ones split in halves (left half, its triangular
   // solve and Block update of the right half, then the right half), so the
-  // rank-1 updates in pinned DD arithmetic stay within PANEL_BASE columns and
-  // the rest of the panel work runs in the Block kernel.
+  // rank-1 updates stay within PANEL_BASE columns and the rest of the panel
+  // work runs in the Block kernel.
   std::function<void(int64_t, int64_t)> panel = [&](int64_t c0, int64_t w) {
     if (st != DDG_OK || w <= 0) return;
     if (w <= PANEL_BASE) {
       const int64_t pe = c0 + w;
       const int64_t nstart = pivot ? (n - c0 + RB - 1) / RB : 1;
-      lu_start_kernel<<<(unsigned)nstart, 256, 0, s>>>(n, M, c0, part, ipiv, dinfo, pivot, cs);
+      lu_start_kernel<L><<<(unsigned)nstart, 256, 0, s>>>(n, M, c0, part, ipiv, dinfo, pivot, cs);
       cu(cudaGetLastError());
       for (int64_t j = c0; j < pe && j + 1 < n && st == DDG_OK; ++j) {
         const int64_t blocks = (n - j - 1 + RB - 1) / RB;
-        lu_col_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, M, j, pe, part, ipiv, dinfo, pivot, cs);
+        lu_col_kernel<L><<<(unsigned)blocks, 256, 0, s>>>(n, M, j, pe, part, ipiv, dinfo, pivot, cs);
         cu(cudaGetLastError());
       }
       return;
@@ -412,10 +456,10 @@ ddg_status dd_getrf(int64_t n, dd_mat A, int64_t* ipiv, int32_t K, int32_t pivot
     panel(c0, w1);
     if (st != DDG_OK) return;
     const int64_t w2 = w - w1, c1 = c0 + w1;
-    st = trsm_lower_unit(w1, w2, view(M, c0, c0), view(M, c0, c1), s);
+    st = trsm_lower_unit<L>(w1, w2, view(M, c0, c0), view(M, c0, c1), s);
     if (st != DDG_OK) return;
     if (n - c1 > 0)
-      st = gemm_run(2, n - c1, w1, w2, view(M, c1, c0), view(M, c0, c1), view(M, c1, c1), MODE_SUB,
+      st = gemm_run(L, n - c1, w1, w2, view(M, c1, c0), view(M, c0, c1), view(M, c1, c1), MODE_SUB,
                     block_opts(), s);
     if (st != DDG_OK) return;
     panel(c1, w2);
@@ -425,43 +469,46 @@ ddg_status dd_getrf(int64_t n, dd_mat A, int64_t* ipiv, int32_t K, int32_t pivot
     panel(j0, pe - j0);
     if (st != DDG_OK || pe >= n) break;
     const int64_t kb = pe - j0, rest = n - pe;
-    st = trsm_lower_unit(kb, rest, view(M, j0, j0), view(M, j0, pe), s);
+    st = trsm_lower_unit<L>(kb, rest, view(M, j0, j0), view(M, j0, pe), s);
     if (st != DDG_OK) break;
     // Section 4 step 3: A22 := A22 - L21 U12
-    st = gemm_run(2, rest, kb, rest, view(M, pe, j0), view(M, j0, pe), view(M, pe, pe), MODE_SUB, o, s);
+    st = gemm_run(L, rest, kb, rest, view(M, pe, j0), view(M, j0, pe), view(M, pe, pe), MODE_SUB, o, s);
   }
   int64_t hinfo = 0;
   if (st == DDG_OK && !info) {
     if (cudaMemcpyAsync(&hinfo, dinfo, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
-      st = set_error(DDG_ECUDA, "dd_getrf: reading the pivot status");
+      st = set_error(DDG_ECUDA, nm + ": reading the pivot status");
   }
   cudaFreeAsync(ws, s);
   if (st == DDG_OK && hinfo != 0)
-    return set_error(DDG_ESINGULAR, "dd_getrf: exactly zero pivot in column " + std::to_string(hinfo - 1));
+    return set_error(DDG_ESINGULAR, nm + ": exactly zero pivot in column " + std::to_string(hinfo - 1));
   return st;
 }
 
-ddg_status dd_getrs(int64_t n, int64_t nrhs, dd_mat LU, const int64_t* ipiv, dd_mat B, void* stream) {
-  using namespace ddg;
+template <int L>
+static ddg_status getrs_impl(const char* name, int64_t n, int64_t nrhs, const mat& LUm, const int64_t* ipiv,
+                             const mat& Bm, void* stream) {
   clear_error();
-  if (n < 0 || nrhs < 0) return set_error(DDG_EINVAL, "negative size");
-  if (bad_dd(LU, n, n) || bad_dd(B, n, nrhs)) return set_error(DDG_EINVAL, "null plane or ld too small");
-  if (n > 0 && !ipiv) return set_error(DDG_EINVAL, "ipiv is null");
+  const std::string nm(name);
+  if (n < 0 || nrhs < 0) return set_error(DDG_EINVAL, nm + ": negative size");
+  if (bad_planes(L, LUm, n, n) || bad_planes(L, Bm, n, nrhs))
+    return set_error(DDG_EINVAL, nm + ": null plane or ld too small");
+  if (n > 0 && !ipiv) return set_error(DDG_EINVAL, nm + ": ipiv is null");
   if (n == 0 || nrhs == 0) return DDG_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const mat L{{LU.hi, LU.lo, nullptr, nullptr}, LU.ld};
-  const mat Bm{{B.hi, B.lo, nullptr, nullptr}, B.ld};
   const size_t plane = ((size_t)n * nrhs * sizeof(double) + 255) & ~(size_t)255;
-  const size_t bytes = 2 * plane + (((size_t)n * sizeof(int64_t) + 255) & ~(size_t)255);
+  const size_t bytes = L * plane + (((size_t)n * sizeof(int64_t) + 255) & ~(size_t)255);
   void* ws = nullptr;
   if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
     cudaGetLastError();
-    return set_error(DDG_ENOMEM, "dd_getrs: scratch allocation failed");
+    return set_error(DDG_ENOMEM, nm + ": scratch allocation failed");
   }
   char* base = static_cast<char*>(ws);
-  const mat X{{reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + plane), nullptr, nullptr}, nrhs};
-  int64_t* perm = reinterpret_cast<int64_t*>(base + 2 * plane);
+  mat X{};
+  X.ld = nrhs;
+  for (int q = 0; q < L; ++q) X.p[q] = reinterpret_cast<double*>(base + q * plane);
+  int64_t* perm = reinterpret_cast<int64_t*>(base + L * plane);
   ddg_status st = DDG_OK;
   const size_t sm = n <= 12288 ? (size_t)n * sizeof(int32_t) : 0;
   lu_perm_kernel<<<1, 32, sm, s>>>(n, ipiv, perm);
@@ -469,20 +516,48 @@ ddg_status dd_getrs(int64_t n, int64_t nrhs, dd_mat LU, const int64_t* ipiv, dd_
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     const int64_t tot = n * nrhs;
-    lu_gather_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, nrhs, perm, Bm, X);
+    lu_gather_kernel<L><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, nrhs, perm, Bm, X);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     e = cudaGetLastError();
   }
-  if (e != cudaSuccess) st = set_error(DDG_ECUDA, std::string("dd_getrs: ") + cudaGetErrorString(e));
-  if (st == DDG_OK) st = trsm_lower_unit(n, nrhs, L, X, s);
-  if (st == DDG_OK) st = trsm_upper(n, nrhs, L, X, s);
+  if (e != cudaSuccess) st = set_error(DDG_ECUDA, nm + ": " + cudaGetErrorString(e));
+  if (st == DDG_OK) st = trsm_lower_unit<L>(n, nrhs, LUm, X, s);
+  if (st == DDG_OK) st = trsm_upper<L>(n, nrhs, LUm, X, s);
   if (st == DDG_OK)
-    for (int q = 0; q < 2 && st == DDG_OK; ++q)
+    for (int q = 0; q < L && st == DDG_OK; ++q)
       if (cudaMemcpy2DAsync(Bm.p[q], Bm.ld * sizeof(double), X.p[q], nrhs * sizeof(double),
                             nrhs * sizeof(double), n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        st = set_error(DDG_ECUDA, "dd_getrs: copy-back");
+        st = set_error(DDG_ECUDA, nm + ": copy-back");
   cudaFreeAsync(ws, s);
   return st;
+}
+
+}  // namespace ddg
+
+extern "C" {
+
+ddg_status dd_getrf(int64_t n, dd_mat A, int64_t* ipiv, int32_t K, int32_t pivot, const ddg_opts* opts,
+                    int64_t* info, void* stream) {
+  const ddg::mat M{{A.hi, A.lo, nullptr, nullptr}, A.ld};
+  return ddg::getrf_impl<2>("dd_getrf", n, M, ipiv, K, pivot, opts, info, stream);
+}
+
+ddg_status dd_getrs(int64_t n, int64_t nrhs, dd_mat LU, const int64_t* ipiv, dd_mat B, void* stream) {
+  const ddg::mat L{{LU.hi, LU.lo, nullptr, nullptr}, LU.ld};
+  const ddg::mat Bm{{B.hi, B.lo, nullptr, nullptr}, B.ld};
+  return ddg::getrs_impl<2>("dd_getrs", n, nrhs, L, ipiv, Bm, stream);
+}
+
+ddg_status qd_getrf(int64_t n, qd_mat A, int64_t* ipiv, int32_t K, int32_t pivot, const ddg_opts* opts,
+                    int64_t* info, void* stream) {
+  const ddg::mat M{{A.x[0], A.x[1], A.x[2], A.x[3]}, A.ld};
+  return ddg::getrf_impl<4>("qd_getrf", n, M, ipiv, K, pivot, opts, info, stream);
+}
+
+ddg_status qd_getrs(int64_t n, int64_t nrhs, qd_mat LU, const int64_t* ipiv, qd_mat B, void* stream) {
+  const ddg::mat L{{LU.x[0], LU.x[1], LU.x[2], LU.x[3]}, LU.ld};
+  const ddg::mat Bm{{B.x[0], B.x[1], B.x[2], B.x[3]}, B.ld};
+  return ddg::getrs_impl<4>("qd_getrs", n, nrhs, L, ipiv, Bm, stream);
 }
 
 }  // extern "C"

@@ -117,3 +117,80 @@ def test_section4_winograd_vs_block(n):
     # cond ~ 1e6..1e7 (Section 4): forward error ~ cond * 2^-104, both similar
     assert errs["winograd"] < 1e-20 and errs["block"] < 1e-20
     assert errs["winograd"] < 100 * errs["block"] + 1e-28
+
+
+# ------------------------------------------------------------------ QD LU --
+def qd_problem(n, seed, nrhs=1):
+    A = I.uniform(n, n, 4, seed=seed)
+    X = np.zeros((4, n, nrhs))
+    for c in range(nrhs):
+        X[0, :, c] = np.arange(n) + c
+    return A, X, O.gemm_simple(A, X)
+
+
+def qd_rel_residual(A, Xh, Bv):
+    r = O.residual(A, Xh, Bv)
+    if not np.abs(r).max():
+        return 0.0
+    return np.abs(r).max() / (np.abs(A[0]).sum(axis=1).max() * np.abs(Xh[0]).max())
+
+
+@pytest.mark.parametrize("n,K,cutoff,algo", [(1, 1, 8, "winograd"), (9, 4, 2, "winograd"),
+                                             (100, 16, 8, "winograd"), (161, 64, 16, "strassen"),
+                                             (130, 1, 8, "block"), (97, 512, 16, "winograd")])
+def test_qd_getrf_getrs_residual_and_pivots(n, K, cutoff, algo):
+    """qd_getrf / qd_getrs: exact residual <= n 2^-200 (QD unit 2^-212 with
+    the growth of a pivoted LU), pivots equal to the oracle's unblocked QD LU."""
+    A, X, Bv = qd_problem(n, seed=100 + n)
+    LU, ipiv, Xh = lu_solve(A, Bv, K, cutoff=cutoff, algo=algo)
+    assert qd_rel_residual(A, Xh, Bv) <= n * 2.0 ** -200
+    _, piv_o, info = O.qd_getrf(A, pivot=True)
+    assert info == 0
+    assert np.array_equal(ipiv, piv_o)
+
+
+def test_qd_no_pivot_matches_oracle_factors():
+    n = 72
+    A = I.uniform(n, n, 4, seed=41)
+    A[0] += np.eye(n) * n
+    import paper_1510_08642_gb300 as P
+    dA = to_dev(A)
+    ipiv = P.getrf(dA, K=16, pivot=False, algo="winograd", cutoff=8)
+    torch.cuda.synchronize()
+    LU = to_host(dA)
+    LUo, _, info = O.qd_getrf(A, pivot=False)
+    assert info == 0 and np.array_equal(ipiv.cpu().numpy(), np.arange(n))
+    from fractions import Fraction
+    worst = 0.0
+    for i in range(0, n, 7):
+        for j in range(0, n, 5):
+            d = sum(Fraction(float(v)) for v in LU[:, i, j]) - sum(Fraction(float(v)) for v in LUo[:, i, j])
+            worst = max(worst, abs(float(d)))
+    assert worst <= 2.0 ** -196 * max(1.0, np.abs(LUo[0]).max())
+
+
+def test_qd_zero_pivot_reported():
+    import paper_1510_08642_gb300 as P
+    from paper_1510_08642_gb300 import capi
+    n = 33
+    A = I.uniform(n, n, 4, seed=42)
+    A[:, :, 20] = 0.0
+    with pytest.raises(capi.DDGError) as e:
+        P.getrf(to_dev(A), K=8)
+    assert e.value.status == capi.DDG_ESINGULAR
+    info = torch.zeros(1, dtype=torch.int64, device="cuda")
+    P.getrf(to_dev(A), K=8, info=info)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 21
+
+
+def test_qd_section4_forward_error():
+    """The paper's QD setting (Winograd trailing updates): forward error of
+    x = [0, 1, ..., n-1] at cond * 2^-212 level, far below DD's."""
+    n = 384
+    A, X, Bv = qd_problem(n, seed=43)
+    _, _, Xh = lu_solve(A, Bv, K=64, algo="winograd", cutoff=32)
+    assert qd_rel_residual(A, Xh, Bv) <= n * 2.0 ** -200
+    from fractions import Fraction
+    fe = max(abs(float(sum(Fraction(float(v)) for v in Xh[:, i, 0]) - i)) / max(i, 1) for i in range(n))
+    assert fe < 1e-50

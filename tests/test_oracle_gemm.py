@@ -205,3 +205,69 @@ def test_lu_oracle_solves_section4_system():
     # err = exact(L U) - PA  (sign irrelevant): backward error of DD LU
     rel = np.abs(err).max() / (np.abs(A[0]).max())
     assert rel < n * 2.0 ** -100
+
+
+def test_generic_residual_matches_dd_and_closed_form():
+    """orc_residual on DD operands equals the DD checker; on QD operands
+    with an exactly representable product, b - A x is exactly 0, and a
+    perturbation of one limb of b by 2^-180 shows up exactly."""
+    n = 20
+    A = I.uniform(n, n, 2, seed=21)
+    X = I.uniform(n, 2, 2, seed=22)
+    Bv = O.gemm_simple(A, X)
+    assert np.array_equal(O.residual(A, X, Bv), O.dd_residual(A, X, Bv))
+    Aq = np.zeros((4, n, n)); Aq[0] = np.round(A[0] * 64)
+    Xq = np.zeros((4, n, 1)); Xq[0, :, 0] = np.arange(n)
+    Bq = np.zeros((4, n, 1)); Bq[0] = Aq[0] @ Xq[0]  # small integers: exact
+    assert not np.abs(O.residual(Aq, Xq, Bq)).any()
+    Bq[3, 5, 0] = 2.0 ** -180
+    r = O.residual(Aq, Xq, Bq)
+    assert r[5, 0] == 2.0 ** -180 and np.count_nonzero(r) == 1
+
+
+def test_qd_lu_oracle_reconstructs_PA():
+    """Unblocked QD LU: pivots as LAPACK on the leading limbs, and
+    L U = P A to QD accuracy (exact checker on the QD product)."""
+    n = 40
+    A = I.uniform(n, n, 4, seed=23)
+    LU, ipiv, info = O.qd_getrf(A, pivot=True)
+    assert info == 0
+    import scipy.linalg
+    _, piv = scipy.linalg.lu_factor(A[0])
+    assert np.array_equal(piv, ipiv)
+    L = np.zeros_like(LU); U_ = np.zeros_like(LU)
+    for k in range(4):
+        L[k] = np.tril(LU[k], -1) + (np.eye(n) if k == 0 else 0)
+        U_[k] = np.triu(LU[k])
+    PA = A.copy()
+    for j in range(n):
+        p = ipiv[j]
+        PA[:, [j, p], :] = PA[:, [p, j], :]
+    err = O.gemm_error(L, U_, PA, C0=None)
+    assert np.abs(err).max() / np.abs(A[0]).max() < n * 2.0 ** -200
+    # a zero column is reported as 1 + its index
+    A[:, :, 9] = 0.0
+    assert O.qd_getrf(A, pivot=True)[2] == 10
+
+
+def test_qd_lu_solution_of_section4_system():
+    """QD LU + substitution in the oracle (plain QD sums on the factors):
+    residual of the Section 4 system below n 2^-200."""
+    n = 24
+    A = I.uniform(n, n, 4, seed=24)
+    X = np.zeros((4, n, 1)); X[0, :, 0] = np.arange(n)
+    Bv = O.gemm_simple(A, X)
+    LU, ipiv, info = O.qd_getrf(A)
+    y = [np.array(Bv[:, i, 0]) for i in range(n)]
+    for j in range(n):
+        y[j], y[ipiv[j]] = y[ipiv[j]], y[j]
+    for i in range(n):
+        for k in range(i):
+            y[i] = O.qd_add(y[i], O.qd_mul(-LU[:, i, k], y[k]))
+    for i in reversed(range(n)):
+        for k in range(i + 1, n):
+            y[i] = O.qd_add(y[i], O.qd_mul(-LU[:, i, k], y[k]))
+        y[i] = O.qd_div(y[i], LU[:, i, i])
+    Xh = np.stack(y, axis=1)[:, :, None]
+    r = O.residual(A, Xh, Bv)
+    assert np.abs(r).max() / (np.abs(A[0]).sum(axis=1).max() * np.abs(Xh[0]).max()) <= n * 2.0 ** -200

@@ -178,3 +178,54 @@ def test_renorm_reproduces_short_sums_exactly():
         x = [rand_double(rng, -5, 5) for _ in range(3)]
         r = O.renorm(np.array(x))
         assert limbs_value(r) == sum(F(v) for v in x)
+
+
+def test_qd_div_bound():
+    """QD long division (the LU quotients): |a/b - q| <= 2^-205 |a/b|."""
+    rng = random.Random(9)
+    worst = Fraction(0)
+    for _ in range(1000):
+        a, b = rand_qd(rng, rng.randint(-20, 20)), rand_qd(rng, rng.randint(-20, 20))
+        q = O.qd_div(a, b)
+        ex = limbs_value(a) / limbs_value(b)
+        worst = max(worst, abs(limbs_value(q) - ex) / abs(ex))
+        assert qd_separated(q)
+    assert 0 < worst <= Fraction(1, 1 << 205)
+    # exact quotients stay exact
+    assert np.array_equal(O.qd_div([6.0, 0, 0, 0], [3.0, 0, 0, 0]), [2.0, 0, 0, 0])
+    assert np.array_equal(O.qd_div([0.0, 0, 0, 0], [3.0, 0, 0, 0]), [0.0, 0, 0, 0])
+
+
+def sparse_qd(rng):
+    """QD numbers whose lower limbs sit far below their positions (an
+    integer or short value plus tiny corrections, as in LU solutions)."""
+    x = [rand_double(rng, -3, 3)]
+    if rng.random() < 0.3:
+        x[0] = float(rng.randint(1, 1000)) * rng.choice([-1.0, 1.0])
+    for _ in range(3):
+        gap = rng.choice([53, 54, 60, 80, 106, 150, 300])
+        x.append(x[-1] * 2.0 ** -gap * (rng.random() - 0.5) if rng.random() < 0.9 else 0.0)
+    return O.renorm(np.array(x))
+
+
+def test_qd_mul_bound_sparse_limbs():
+    """The QD product keeps the 2^-210 bound when limbs are far below their
+    positions (without ordering its terms by magnitude the renormalisation
+    spends limbs on overlapping pieces: ~2^-160 on these inputs)."""
+    rng = random.Random(10)
+    worst = Fraction(0)
+    for _ in range(1500):
+        a, b = sparse_qd(rng), sparse_qd(rng)
+        r = O.qd_mul(a, b)
+        ex = limbs_value(a) * limbs_value(b)
+        if ex:
+            worst = max(worst, abs(limbs_value(r) - ex) / abs(ex))
+        assert qd_separated(r)
+    # the failing case of an LU back substitution: x = 23 + 2^-208-ish
+    a = np.array([-3.70949070e+00, 1.68262898e-18, -1.75943975e-35, -2.09907835e-52])
+    b = np.array([2.3e+01, -5.24109001e-63, 1.02562329e-79, -5.68207668e-96])
+    a, b = O.renorm(a), O.renorm(b)
+    r = O.qd_mul(a, b)
+    ex = limbs_value(a) * limbs_value(b)
+    worst = max(worst, abs(limbs_value(r) - ex) / abs(ex))
+    assert worst <= Fraction(1, 1 << 210)
