@@ -56,6 +56,7 @@ def parse():
                    help="CPU oracle sample length; 0 skips the CPU baseline")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     p.add_argument("--lu-k", type=int, default=256, help="LU block column width K")
+    p.add_argument("--sweep-n", type=int, default=1024, help="lu_alpha_sweep: matrix order")
     p.add_argument("--requests", type=int, default=120, help="serving: requests per rate point")
     p.add_argument("--rates", type=float, nargs="+", default=[0.25, 0.5, 0.75, 0.9, 1.1],
                    help="serving: arrival rates as fractions of the saturation rate")
@@ -509,8 +510,54 @@ def run_lu_only(args, w):
     return 0
 
 
+def run_lu_alpha_sweep(args):
+    """Section 4 Fig. 5 setting: no pivoting, K = alpha n_min (alpha = 1..10,
+    n_min = 32), random [-1, 1] matrix, x = [0, 1, ..., n-1], b = A x; time
+    of dd_getrf + dd_getrs (and the QD pair) and the maximum relative error
+    of x, with Winograd and Block trailing updates."""
+    import torch
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    import paper_1510_08642_gb300 as P
+    from paper_1510_08642_gb300 import capi, inputs as I
+    capi.load()
+    stream = torch.cuda.current_stream(device)
+    n, nmin = args.sweep_n, 32
+    rows = []
+    for limbs in (2, 4):
+        A0 = torch.from_numpy(I.uniform(n, n, limbs, seed=116)).to(device)
+        X = torch.zeros((limbs, n, 1), dtype=torch.float64, device=device)
+        X[0, :, 0] = torch.arange(n, dtype=torch.float64, device=device)
+        b0 = P.gemm(A0, X, algo="block")
+        for alpha in range(1, 11):
+            for algo in ("winograd", "block"):
+                K = alpha * nmin
+                times = []
+                for _ in range(2):  # one warm-up, one timed
+                    A, b = A0.clone(), b0.clone()
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ipiv = P.getrf(A, K=K, pivot=False, algo=algo, cutoff=nmin)
+                    P.getrs(A, ipiv, b)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                xi = X[0, 1:, 0]
+                d = (b[0, 1:, 0] - xi) + b[1:, 1:, 0].sum(dim=0)
+                rel = float((d.abs() / xi).max().item())
+                rows.append({"limbs": limbs, "alpha": alpha, "K": K, "algo": algo, "ms": times[-1],
+                             "max_rel_err": rel})
+    print(json.dumps({"workload": "lu_alpha_sweep", "n": n, "n_min": nmin, "pivot": "none",
+                      "matrix": "uniform [-1, 1], x = [0..n-1]", "points": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "lu_alpha_sweep":
+        return run_lu_alpha_sweep(args)
     w = workload_by_name(args.workload)
     if args.impl == "reference":
         return run_reference(args, w)
