@@ -458,7 +458,7 @@ def run_ours(args, w):
         extras = {}
         for xw in (WL.DD_BLOCK_4096, WL.QD_WINOGRAD_4096, WL.QD_BLOCK_4096, WL.DD_OZAKI_4096_S16,
                    WL.DD_OZAKI_4096_S13, WL.DD_WINOGRAD_8192, WL.DD_OZAKI_8192_S16,
-                   WL.QD_OZAKI_4096_S32):
+                   WL.QD_OZAKI_4096_S32, WL.DD_OZAKI2_4096_N32, WL.DD_OZAKI2_8192_N32):
             XA = torch.from_numpy(I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_a)).to(device)
             XB = torch.from_numpy(I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_b)).to(device)
             XC = torch.empty((xw.limbs, xw.n, xw.n), dtype=torch.float64, device=device)

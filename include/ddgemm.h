@@ -71,7 +71,17 @@ typedef enum {
                        exactly and rounded to DD / QD. Error <= l (s + 3)
                        2^-7s max|a_i.| max|b_.j| per entry (normwise, not
                        elementwise, DD / QD accuracy); slices * l < 2^19,
-                       m <= 65535 */
+                       m <= 65535 */,
+  DDG_OZAKI2 = 5    /* not in the paper (Ozaki scheme II, Ozaki, Uchino and
+                       Imamura 2025), DD only: rows of A / columns of B scaled
+                       and rounded to integers of P bits, one INT8 product of
+                       their residues per modulus (`slices` = the number N of
+                       pairwise-coprime moduli <= 256), the integer product
+                       recovered exactly by the Chinese remainder theorem and
+                       rounded to DD. Error <= l 2^-P max|a_i.| max|b_.j| per
+                       entry plus the DD rounding, P from
+                       ddg_ozaki2_precision (N = 32, l = 4096: P = 113);
+                       l <= 65536, m <= 65535; QD gives DDG_ENOTSUP */
 } ddg_algo;
 
 /* How C is written: C := A B, C := C + A B or C := C - A B. */
@@ -105,7 +115,8 @@ typedef struct {
                       on the FP64 pipe (12 per DD, 113 per QD) */
   int32_t slices;  /* DDG_OZAKI: number of INT8 slices s, DD in [2, 18]
                       (0 = 16, about 2^-110 of the row / column maxima), QD
-                      in [2, 32] (0 = 32, about 2^-222) */
+                      in [2, 32] (0 = 32, about 2^-222); DDG_OZAKI2: number
+                      of moduli N in [2, 40] (0 = 32) */
   int32_t reserved[2]; /* must be zero */
 } ddg_opts;
 
@@ -252,6 +263,12 @@ ddg_status dd_gemm_batched(int32_t count, const ddg_problem* probs, void* stream
  * the Block kernel's inner loop for accumulation scheme `accum` (0 or 1, as
  * in ddg_opts), counted from its source (for rooflines); -1 if invalid. */
 int32_t ddg_block_fp64_ops_per_mac(int32_t limbs, int32_t accum);
+
+/* DDG_OZAKI2: the bits P of the integer scaling used with N moduli at inner
+ * dimension l, min(120, floor((bitlen(M) - 2 - ceil(log2 l)) / 2)) with M
+ * the product of the moduli (so that l 2^(2P) < M / 2 and the recovered
+ * integer product is exact); -1 if N is outside [2, 40], l < 1 or P < 1. */
+int32_t ddg_ozaki2_precision(int32_t moduli, int64_t l);
 
 /* Launch profiling. Between ddg_profile_begin() and ddg_profile_end() every
  * kernel launch of the library is bracketed by CUDA events on its stream.

@@ -18,6 +18,18 @@ documents for its DDG_OZAKI algorithm, step by step:
    53-bit pieces, renormalised (the oracle's VecSum + compaction).
 
 Slow and obviously exact; for small matrices.
+
+The CRT variant (Ozaki, Uchino, Imamura 2025, "scheme II"; DDG_OZAKI2):
+1. moduli m_1 > m_2 > ... > m_N: the N largest pairwise-coprime integers
+   <= 256, taken greedily from 256 downward; M = m_1 ... m_N;
+2. P = min(120, floor((bitlen(M) - 2 - ceil(log2 l)) / 2)), so that
+   l 2^(2P) < M / 2;
+3. X_ik = round-half-up of a_ik 2^(P - e_i) (step 2 above with T = P),
+   likewise Y_kj per column;
+4. Z = X Y exactly. The library obtains Z from the residues Z mod m_t (one
+   INT8 product per modulus) by the Chinese remainder theorem, which is exact
+   because |Z| <= l 2^(2P) < M / 2; the oracle forms Z directly;
+5. c = Z 2^(e_i + e_j - 2P) rounded to DD as in step 5.
 """
 from __future__ import annotations
 
@@ -43,7 +55,12 @@ def row_fields(M0: np.ndarray, axis: int) -> np.ndarray:
 
 
 def to_integer(limbs, field: int, s: int) -> int:
-    T = 6 + 7 * (s - 1)
+    return to_integer_T(limbs, field, 6 + 7 * (s - 1))
+
+
+def to_integer_T(limbs, field: int, T: int) -> int:
+    """round-half-up of x 2^(T - e), e = field - 1022, each limb truncated
+    toward zero at 2^-64 units first."""
     e = field - 1022
     acc = 0
     for limb in limbs:
@@ -133,3 +150,82 @@ def gemm(A: np.ndarray, B: np.ndarray, s: int = 16, C0=None, mode: str = "set"):
                 v = add(C0[:, i, j], -v)
             C[:, i, j] = v
     return C, (SA, SB, D, fa, fb)
+
+
+# ------------------------------------------------------------- CRT scheme --
+def crt_moduli(N: int) -> list:
+    """The N largest pairwise-coprime integers <= 256, greedily from 256 down."""
+    out = []
+    m = 256
+    while len(out) < N and m > 1:
+        if all(math.gcd(m, x) == 1 for x in out):
+            out.append(m)
+        m -= 1
+    if len(out) < N:
+        raise ValueError("not enough moduli")
+    return out
+
+
+def crt_precision(N: int, l: int) -> int:
+    """Bits P of the integer scaling: l 2^(2P) < M / 2, at most 120."""
+    M = math.prod(crt_moduli(N))
+    clog = (max(l, 1) - 1).bit_length()
+    return min(120, (M.bit_length() - 2 - clog) // 2)
+
+
+def crt_reconstruct(residues, moduli) -> int:
+    """The integer Z with |Z| < M / 2 and Z = r_t (mod m_t) for every t."""
+    M = math.prod(moduli)
+    z = 0
+    for r, m in zip(residues, moduli):
+        Mt = M // m
+        z += r * Mt * pow(Mt, -1, m)
+    z %= M
+    return z - M if 2 * z >= M else z
+
+
+def gemm_crt(A: np.ndarray, B: np.ndarray, N: int = 32, C0=None, mode: str = "set"):
+    """DD C (mode) A B by the CRT scheme above; returns (2, m, n)."""
+    limbs, m, l = A.shape
+    assert limbs == 2
+    n = B.shape[2]
+    P = crt_precision(N, l)
+    if P < 1:
+        raise ValueError("too few moduli for this l")
+    fa = row_fields(A[0], axis=1)
+    fb = row_fields(B[0], axis=0)
+    X = np.empty((m, l), dtype=object)
+    Y = np.empty((l, n), dtype=object)
+    for i in range(m):
+        for k in range(l):
+            X[i, k] = to_integer_T(A[:, i, k], int(fa[i]), P)
+    for k in range(l):
+        for j in range(n):
+            Y[k, j] = to_integer_T(B[:, k, j], int(fb[j]), P)
+    Z = X.dot(Y) if l else np.zeros((m, n), dtype=object)
+    C = np.zeros((2, m, n))
+    for i in range(m):
+        for j in range(n):
+            lsb = (int(fa[i]) - 1022) + (int(fb[j]) - 1022) - 2 * P
+            v = np.array(_chunk_dd(int(Z[i, j]), lsb))
+            if mode == "add":
+                v = dd_add(C0[:, i, j], v)
+            elif mode == "sub":
+                v = dd_add(C0[:, i, j], -v)
+            C[:, i, j] = v
+    return C, (X, Y, Z, fa, fb, P)
+
+
+def gemm_crt_entries(A: np.ndarray, B: np.ndarray, N: int, rows, cols) -> np.ndarray:
+    """Entries (rows[t], cols[t]) of gemm_crt(A, B, N), one by one: (2, count)."""
+    limbs, m, l = A.shape
+    P = crt_precision(N, l)
+    out = np.zeros((2, len(rows)))
+    for t, (i, j) in enumerate(zip(rows, cols)):
+        fa = int(row_fields(A[0][i:i + 1], axis=1)[0])
+        fb = int(row_fields(B[0][:, j:j + 1], axis=0)[0])
+        Z = 0
+        for k in range(l):
+            Z += to_integer_T(A[:, i, k], fa, P) * to_integer_T(B[:, k, j], fb, P)
+        out[:, t] = _chunk_dd(Z, (fa - 1022) + (fb - 1022) - 2 * P)
+    return out

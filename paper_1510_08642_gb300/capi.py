@@ -19,9 +19,9 @@ c_i32, c_i64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
 DDG_OK, DDG_EINVAL, DDG_ENOMEM, DDG_ECUDA, DDG_ESINGULAR, DDG_ETIMEOUT, DDG_ENOTSUP = range(7)
 STATUS_NAMES = ["DDG_OK", "DDG_EINVAL", "DDG_ENOMEM", "DDG_ECUDA", "DDG_ESINGULAR",
                 "DDG_ETIMEOUT", "DDG_ENOTSUP"]
-DDG_SIMPLE, DDG_BLOCK, DDG_STRASSEN, DDG_WINOGRAD, DDG_OZAKI = range(5)
+DDG_SIMPLE, DDG_BLOCK, DDG_STRASSEN, DDG_WINOGRAD, DDG_OZAKI, DDG_OZAKI2 = range(6)
 ALGOS = {"simple": DDG_SIMPLE, "block": DDG_BLOCK, "strassen": DDG_STRASSEN,
-         "winograd": DDG_WINOGRAD, "ozaki": DDG_OZAKI}
+         "winograd": DDG_WINOGRAD, "ozaki": DDG_OZAKI, "ozaki2": DDG_OZAKI2}
 DDG_SET, DDG_ADD, DDG_SUB = range(3)
 MODES = {"set": DDG_SET, "add": DDG_ADD, "sub": DDG_SUB}
 
@@ -77,6 +77,7 @@ SIGNATURES = {
     "dd_gemm_noalloc": (c_i32, [c_i64, c_i64, c_i64, dd_mat, dd_mat, dd_mat, c_i32,
                                 ctypes.POINTER(ddg_opts), c_vp]),
     "ddg_block_fp64_ops_per_mac": (c_i32, [c_i32, c_i32]),
+    "ddg_ozaki2_precision": (c_i32, [c_i32, c_i64]),
     "ddg_batch_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(ddg_problem), c_i32, c_vp]),
     "ddg_batch_run": (c_i32, [c_vp, c_vp]),
     "ddg_batch_get_stats": (c_i32, [c_vp, ctypes.POINTER(ddg_batch_stats)]),
@@ -157,6 +158,10 @@ def dd_gemm_noalloc(m, l, n, A: dd_mat, B: dd_mat, C: dd_mat, mode: int, o: ddg_
 
 def ddg_block_fp64_ops_per_mac(limbs: int, accum: int = 0) -> int:
     return load().ddg_block_fp64_ops_per_mac(limbs, accum)
+
+
+def ddg_ozaki2_precision(moduli: int, l: int) -> int:
+    return load().ddg_ozaki2_precision(moduli, l)
 
 
 def ddg_kernel_launches() -> int:

@@ -305,9 +305,10 @@ static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& 
   if (opts) o = *opts;
   if (m < 0 || l < 0 || n < 0) return fail(DDG_EINVAL, "negative size");
   if (mode < DDG_SET || mode > DDG_SUB) return fail(DDG_EINVAL, "mode must be DDG_SET, DDG_ADD or DDG_SUB");
-  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI) return fail(DDG_EINVAL, "unknown algo");
-  if (o.slices != 0 && (o.slices < 2 || o.slices > (L == 2 ? 18 : 32)))
-    return fail(DDG_EINVAL, "slices must be 0 or in [2, 18] (DD) / [2, 32] (QD)");
+  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI2) return fail(DDG_EINVAL, "unknown algo");
+  if (o.algo == DDG_OZAKI2 ? (o.slices != 0 && (o.slices < 2 || o.slices > 40))
+                           : (o.slices != 0 && (o.slices < 2 || o.slices > (L == 2 ? 18 : 32))))
+    return fail(DDG_EINVAL, "slices must be 0 or in [2, 18] (DD) / [2, 32] (QD); moduli in [2, 40]");
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
   if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
   if (o.streams != 0 && o.streams != 1 && o.streams != 7) return fail(DDG_EINVAL, "streams must be 0, 1 or 7");
@@ -339,6 +340,16 @@ ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const 
       return mode == MODE_SET ? zero_mat(z, C, m, n, s) : DDG_OK;
     }
     return ozaki_gemm(L, m, l, n, A, B, C, mode, o.slices ? o.slices : (L == 2 ? 16 : 32), s);
+  }
+  if (o.algo == DDG_OZAKI2) {
+    if (L != 2) return fail(DDG_ENOTSUP, "DDG_OZAKI2: DD only (the moduli <= 256 give at most ~2^369)");
+    if (m > 65535) return fail(DDG_EINVAL, "DDG_OZAKI2: m must be <= 65535");
+    if (l == 0) {
+      Ctx z;
+      z.L = L;
+      return mode == MODE_SET ? zero_mat(z, C, m, n, s) : DDG_OK;
+    }
+    return ozaki_crt_gemm(m, l, n, A, B, C, mode, o.slices ? o.slices : 32, s);
   }
   Ctx c;
   c.L = L;
@@ -417,6 +428,12 @@ int32_t ddg_block_fp64_ops_per_mac(int32_t limbs, int32_t accum) {
   return accum == 0 ? ddg::block_fx_fp64_ops_per_mac(limbs) : ddg::block_fp64_ops_per_mac(limbs);
 }
 
+int32_t ddg_ozaki2_precision(int32_t moduli, int64_t l) {
+  if (moduli < 2 || moduli > 40 || l < 1) return -1;
+  const int P = ddg::ozaki_crt_precision(moduli, l);
+  return P >= 1 ? P : -1;
+}
+
 const char* ddg_last_error(void) { return ddg::g_err.c_str(); }
 
 uint64_t ddg_kernel_launches(void) { return ddg::g_launches.load(std::memory_order_relaxed); }
@@ -463,9 +480,10 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
   if (opts) o = *opts;
   if (m < 0 || l < 0 || n < 0) return fail(DDG_EINVAL, "negative size");
   if (mode < DDG_SET || mode > DDG_SUB) return fail(DDG_EINVAL, "mode must be DDG_SET, DDG_ADD or DDG_SUB");
-  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI) return fail(DDG_EINVAL, "unknown algo");
-  if (o.slices != 0 && (o.slices < 2 || o.slices > (L == 2 ? 18 : 32)))
-    return fail(DDG_EINVAL, "slices must be 0 or in [2, 18] (DD) / [2, 32] (QD)");
+  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI2) return fail(DDG_EINVAL, "unknown algo");
+  if (o.algo == DDG_OZAKI2 ? (o.slices != 0 && (o.slices < 2 || o.slices > 40))
+                           : (o.slices != 0 && (o.slices < 2 || o.slices > (L == 2 ? 18 : 32))))
+    return fail(DDG_EINVAL, "slices must be 0 or in [2, 18] (DD) / [2, 32] (QD); moduli in [2, 40]");
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
   if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
   if (o.accum != 0 && o.accum != 1) return fail(DDG_EINVAL, "accum must be 0 or 1");
@@ -477,7 +495,8 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
   if (overlaps(L, C, m, n, A, m, l) || overlaps(L, C, m, n, B, l, n))
     return fail(DDG_EINVAL, "C overlaps A or B");
   if (m > (int64_t)65535 * 8 || n > ((int64_t)1 << 36)) return fail(DDG_EINVAL, "matrix too large");
-  if (o.algo == DDG_OZAKI) return fail(DDG_EINVAL, "dd_gemm_noalloc: DDG_OZAKI needs a workspace; use dd_gemm");
+  if (o.algo == DDG_OZAKI || o.algo == DDG_OZAKI2)
+    return fail(DDG_EINVAL, "dd_gemm_noalloc: the INT8 products need a workspace; use dd_gemm");
   if (m == 0 || n == 0) return DDG_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (o.algo == DDG_SIMPLE) {

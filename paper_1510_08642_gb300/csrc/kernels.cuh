@@ -110,6 +110,12 @@ ddg_status set_error(ddg_status st, const std::string& msg);
 ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
                     int mode, const ddg_opts& o, cudaStream_t s);
 
+// DD product by INT8 residues and the Chinese remainder theorem (Ozaki
+// scheme II), N moduli (ozaki.cu); the integer scaling precision it uses.
+ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C, int mode,
+                          int N, cudaStream_t st);
+int ozaki_crt_precision(int N, int64_t l);
+
 // DD / QD product by INT8 slices (Ozaki scheme), s slices (ozaki.cu).
 ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
                       int mode, int s, cudaStream_t st);

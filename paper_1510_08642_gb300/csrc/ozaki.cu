@@ -21,7 +21,22 @@
 // to DD (and combined with C for the update modes).
 // Error per entry <= l (s + 3) 2^(-7 s) 2^(ea_i + fb_j) (slice rounding and
 // dropped pairs) plus the final DD rounding.
+//
+// CRT variant (Ozaki, Uchino, Imamura 2025, "Ozaki scheme II"; DD only).
+// Rows of A and columns of B are scaled and rounded to integers X, Y with
+// |X|, |Y| <= 2^P as above (T = P); Z = X Y is then an integer matrix with
+// |Z| <= l 2^(2P). Instead of slicing X into digits, take N pairwise-coprime
+// moduli m_t <= 256 with M = prod m_t > 2 l 2^(2P): the residues X mod m_t
+// and Y mod m_t fit in int8, one INT8 product per modulus gives Z mod m_t
+// (INT32 accumulation, exact for l <= 2^16, reduced mod m_t in the
+// epilogue), and the Chinese remainder theorem recovers Z exactly:
+//   Z = (sum_t r_t c_t) mod M, c_t = (M / m_t) ((M / m_t)^-1 mod m_t),
+// taken in (-M/2, M/2). N products instead of s (s + 1) / 2: N = 32 gives
+// P = 113 at l = 4096 with 32 INT8 products, where slicing needs 136 for
+// the same precision.
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <string>
 
 #include "arith.cuh"
@@ -35,7 +50,10 @@ namespace {
 constexpr int OBM = 128, OBN = 128, OBK = 64, OST = 3, OROW = OBK + 16;
 constexpr int STAGE_BYTES = (OBM + OBN) * OROW;
 constexpr int OZ_SMEM = OST * STAGE_BYTES;
-constexpr int OZ_MAXS = 32;  // most slices (QD); DD allows 18
+constexpr int OZ_MAXS = 40;  // most slices (QD: 32; DD: 18) or CRT moduli (40)
+constexpr int CRT_MAXN = 40;
+constexpr int CRT_NW = 10;   // 320-bit CRT reconstruction word
+constexpr int CRT_PMAX = 120;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -88,11 +106,10 @@ __global__ void oz_exp_kernel(int64_t rows, int64_t cols, mat X, int byrow, int*
 // half up to the integer X, and X is cut into digits from the least
 // significant end: d_p = the balanced residue of X mod 128, X = (X - d_p) / 128.
 template <int L>
-__device__ __forceinline__ void oz_digits(const double (&x)[L], int field, int s, int8_t* out,
-                                          int64_t stride) {
+__device__ __forceinline__ void oz_integer(const double (&x)[L], int field, int T,
+                                           unsigned long long (&X)[L == 2 ? 2 : 4]) {
   constexpr int NW = L == 2 ? 6 : 9;   // split word: 192 / 288 bits
   constexpr int KW = L == 2 ? 2 : 4;   // X in 64-bit words (X < 2^T)
-  const int T = 6 + 7 * (s - 1);
   uint32_t acc[NW];
 #pragma unroll
   for (int w = 0; w < NW; ++w) acc[w] = 0u;
@@ -109,7 +126,6 @@ __device__ __forceinline__ void oz_digits(const double (&x)[L], int field, int s
 #pragma unroll
   for (int w = 0; w < NW; ++w) half[w] = w == 1 ? 0x80000000u : 0u;
   fx::acc_add<NW>(acc, half, 0u);
-  unsigned long long X[KW];
 #pragma unroll
   for (int k = 0; k < KW; ++k) {
     const int w0 = 2 + 2 * k, w1 = 3 + 2 * k;
@@ -119,6 +135,14 @@ __device__ __forceinline__ void oz_digits(const double (&x)[L], int field, int s
     const uint32_t hi = w1 < NW ? acc[w1 < NW ? w1 : 0] : sext;
     X[k] = ((unsigned long long)hi << 32) | lo;
   }
+}
+
+template <int L>
+__device__ __forceinline__ void oz_digits(const double (&x)[L], int field, int s, int8_t* out,
+                                          int64_t stride) {
+  constexpr int KW = L == 2 ? 2 : 4;
+  unsigned long long X[KW];
+  oz_integer<L>(x, field, 6 + 7 * (s - 1), X);
   for (int p = s; p >= 2; --p) {
     int d = (int)(X[0] & 127u);
     d = d >= 64 ? d - 128 : d;
@@ -141,10 +165,60 @@ __device__ __forceinline__ void oz_digits(const double (&x)[L], int field, int s
   out[0] = (int8_t)(int)(long long)X[0];  // remaining top digit in [-64, 64]
 }
 
+// The CRT moduli: the 40 largest pairwise-coprime integers <= 256, taken
+// greedily from 256 downward.
+__host__ __device__ constexpr int crt_mod(int t) {
+  constexpr int tab[CRT_MAXN] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199,
+                                 197, 193, 191, 181, 179, 173, 167, 163, 157, 151, 149, 139, 137, 131,
+                                 127, 113, 109, 107, 103, 101, 97,  89,  83,  79,  73,  71};
+  return tab[t];
+}
+
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+constexpr bool crt_mods_ok() {
+  for (int a = 0; a < CRT_MAXN; ++a) {
+    if (crt_mod(a) < 2 || crt_mod(a) > 256 || (a > 0 && crt_mod(a) >= crt_mod(a - 1))) return false;
+    for (int b = 0; b < a; ++b)
+      if (gcd_c(crt_mod(a), crt_mod(b)) != 1) return false;
+  }
+  return true;
+}
+static_assert(crt_mods_ok(), "CRT moduli must be pairwise coprime, decreasing, <= 256");
+
+// Residues of the integer round(x 2^(P - e)) modulo m_0 .. m_(N-1), each as
+// an int8 representative (r or r - m_t). |X| < 2^121 is taken as four 32-bit
+// words w_k; X mod m = sum_k (w_k mod m) (2^(32 k) mod m) mod m, with every
+// modulus a compile-time constant (the loop is unrolled), so each reduction
+// is a multiply-high sequence on the integer pipe.
+__device__ __forceinline__ void oz_residues(const double (&x)[2], int field, int N, int P, int8_t* out,
+                                            int64_t stride) {
+  unsigned long long X[2];
+  oz_integer<2>(x, field, P, X);
+  const bool neg = (long long)X[1] < 0;
+  if (neg) {  // |X| (128-bit two's complement negate)
+    X[0] = ~X[0] + 1ull;
+    X[1] = ~X[1] + (X[0] == 0ull ? 1ull : 0ull);
+  }
+  const uint32_t w0 = (uint32_t)X[0], w1 = (uint32_t)(X[0] >> 32), w2 = (uint32_t)X[1],
+                 w3 = (uint32_t)(X[1] >> 32);
+#pragma unroll
+  for (int t = 0; t < CRT_MAXN; ++t) {
+    if (t < N) {
+      const uint32_t m = (uint32_t)crt_mod(t);
+      const uint32_t p32 = (uint32_t)((1ull << 32) % m);
+      const uint32_t p64 = (p32 * p32) % m, p96 = (p64 * p32) % m;
+      uint32_t r = (w0 % m + (w1 % m) * p32 + (w2 % m) * p64 + (w3 % m) * p96) % m;
+      if (neg && r != 0u) r = m - r;
+      out[(int64_t)t * stride] = (int8_t)(r < 128u ? (int)r : (int)r - (int)m);
+    }
+  }
+}
+
 // Slices of A (per row) into As[s][mpad][lpad], of B (per column, stored
-// transposed) into Bs[s][npad][lpad]; padding is zero.
-template <int L>
-__global__ void oz_split_a_kernel(int64_t m, int64_t l, mat A, const int* ex, int s, int64_t mpad,
+// transposed) into Bs[s][npad][lpad]; padding is zero. With CRT, the N
+// residue planes instead (s = N, T = P).
+template <int L, bool CRT>
+__global__ void oz_split_a_kernel(int64_t m, int64_t l, mat A, const int* ex, int s, int P, int64_t mpad,
                                   int64_t lpad, int8_t* As) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = blockIdx.y;
@@ -155,14 +229,15 @@ __global__ void oz_split_a_kernel(int64_t m, int64_t l, mat A, const int* ex, in
     double x[L];
 #pragma unroll
     for (int q = 0; q < L; ++q) x[q] = A.p[q][i * A.ld + k];
-    oz_digits<L>(x, ex[i], s, out, stride);
+    if constexpr (CRT) oz_residues(x, ex[i], s, P, out, stride);
+    else oz_digits<L>(x, ex[i], s, out, stride);
   } else {
     for (int p = 0; p < s; ++p) out[(int64_t)p * stride] = 0;
   }
 }
 
-template <int L>
-__global__ void oz_split_b_kernel(int64_t l, int64_t n, mat B, const int* ex, int s, int64_t npad,
+template <int L, bool CRT>
+__global__ void oz_split_b_kernel(int64_t l, int64_t n, mat B, const int* ex, int s, int P, int64_t npad,
                                   int64_t lpad, int8_t* Bs) {
   // tile: 32 k x 32 j; digits staged in shared memory and written k-contiguous
   __shared__ int8_t t[OZ_MAXS][32][33];
@@ -175,7 +250,8 @@ __global__ void oz_split_b_kernel(int64_t l, int64_t n, mat B, const int* ex, in
       double x[L];
 #pragma unroll
       for (int q = 0; q < L; ++q) x[q] = B.p[q][k * B.ld + j];
-      oz_digits<L>(x, ex[j], s, dig, 1);
+      if constexpr (CRT) oz_residues(x, ex[j], s, P, dig, 1);
+      else oz_digits<L>(x, ex[j], s, dig, 1);
     } else {
       for (int p = 0; p < s; ++p) dig[p] = 0;
     }
@@ -190,23 +266,45 @@ __global__ void oz_split_b_kernel(int64_t l, int64_t n, mat B, const int* ex, in
   }
 }
 
-// D[r - 2] = sum_{p + q = r} alpha^(p) beta^(q) for the diagonal of blockIdx.z
-// (z = 0 is the longest diagonal, r = s + 1, scheduled first).
+// Reduction constants of each CRT modulus for the GEMM epilogue: for
+// |v| <= 2^30, u = v + bias (bias = m ceil(2^30 / m)) lies in [0, 2^32) and
+// u mod m = u - m q with q = umulhi(u, floor(2^32 / m)) or q + 1. Fixed at
+// compile time (constant memory, no per-call state).
+struct crt_red {
+  uint32_t m[CRT_MAXN], magic[CRT_MAXN], bias[CRT_MAXN];
+};
+constexpr crt_red make_crt_red() {
+  crt_red r{};
+  for (int t = 0; t < CRT_MAXN; ++t) {
+    const uint32_t m = (uint32_t)crt_mod(t);
+    r.m[t] = m;
+    r.magic[t] = (uint32_t)((1ull << 32) / m);
+    r.bias[t] = m * (((1u << 30) + m - 1u) / m);
+  }
+  return r;
+}
+__constant__ crt_red c_crt_red = make_crt_red();
+
+// Slices: D[r - 2] = sum_{p + q = r} alpha^(p) beta^(q) for the diagonal of
+// blockIdx.z (z = 0 is the longest diagonal, r = s + 1, scheduled first).
+// CRT: R[t] = (alpha^(t) beta^(t)) mod m_t as bytes, t = blockIdx.z.
+template <bool CRT>
 __global__ void __launch_bounds__(256) oz_gemm_kernel(int64_t mpad, int64_t npad, int64_t lpad, int s,
                                                       const int8_t* __restrict__ As,
-                                                      const int8_t* __restrict__ Bs, int32_t* D) {
+                                                      const int8_t* __restrict__ Bs, int32_t* D,
+                                                      uint8_t* R) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps: 64 x 32 each
-  const int r = s + 1 - (int)blockIdx.z;
-  const int nseg = r - 1;
+  const int r = CRT ? 0 : s + 1 - (int)blockIdx.z;
+  const int nseg = CRT ? 1 : r - 1;
   const int64_t m0 = (int64_t)blockIdx.y * OBM, n0 = (int64_t)blockIdx.x * OBN;
   const int kps = (int)(lpad / OBK);
   const int total = nseg * kps;
 
   auto load = [&](int q, int stage) {
     const int seg = q / kps, kk = q % kps;
-    const int pa = seg + 1, pb = r - pa;
+    const int pa = CRT ? (int)blockIdx.z + 1 : seg + 1, pb = CRT ? pa : r - pa;
     const int8_t* ga = As + (int64_t)(pa - 1) * mpad * lpad + m0 * lpad + (int64_t)kk * OBK;
     const int8_t* gb = Bs + (int64_t)(pb - 1) * npad * lpad + n0 * lpad + (int64_t)kk * OBK;
     uint8_t* sa = smem + stage * STAGE_BYTES;
@@ -261,8 +359,30 @@ __global__ void __launch_bounds__(256) oz_gemm_kernel(int64_t mpad, int64_t npad
     }
   }
   cp_wait<0>();
-  int32_t* Dr = D + (int64_t)(r - 2) * mpad * npad;
   const int g = lane >> 2, tq = lane & 3;
+  if constexpr (CRT) {
+    const int t = blockIdx.z;
+    const uint32_t m = c_crt_red.m[t], magic = c_crt_red.magic[t], bias = c_crt_red.bias[t];
+    auto res = [&](int v) -> uint32_t {
+      const uint32_t u = (uint32_t)v + bias;
+      uint32_t x = u - __umulhi(u, magic) * m;
+      return x >= m ? x - m : x;
+    };
+    uint8_t* Rt = R + (int64_t)t * mpad * npad;
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        const int64_t row = m0 + wm * 64 + mi * 16 + g;
+        const int64_t col = n0 + wn * 32 + ni * 8 + 2 * tq;
+        *reinterpret_cast<uchar2*>(Rt + row * npad + col) =
+            make_uchar2((uint8_t)res(acc[mi][ni][0]), (uint8_t)res(acc[mi][ni][1]));
+        *reinterpret_cast<uchar2*>(Rt + (row + 8) * npad + col) =
+            make_uchar2((uint8_t)res(acc[mi][ni][2]), (uint8_t)res(acc[mi][ni][3]));
+      }
+    return;
+  }
+  int32_t* Dr = D + (int64_t)(r - 2) * mpad * npad;
 #pragma unroll
   for (int mi = 0; mi < 4; ++mi)
 #pragma unroll
@@ -333,8 +453,196 @@ __global__ void oz_recombine_kernel(int64_t m, int64_t n, int s, int64_t mpad, i
   N::store(C.p, off, v);
 }
 
+// CRT reconstruction constants for N moduli (passed by value).
+struct crt_consts {
+  uint32_t c[CRT_MAXN][CRT_NW];  // c_t = (M / m_t) ((M / m_t)^-1 mod m_t)
+  uint32_t M[CRT_NW];
+  uint32_t halfM[CRT_NW];        // floor(M / 2)
+  double inv_scaled;             // 2^(32 (wt - 2)) / M
+  int wt;                        // highest word of sum_t r_t c_t that can be nonzero (>= 2)
+};
+
+// C (mode) Z 2^(ea_i + fb_j - 2P), Z from its residues by the CRT:
+// S = sum_t r_t c_t (lazy carries in 64-bit words), q = floor(S / M) from
+// the three top words (off by at most one, corrected), Z = S - q M in
+// [0, M), then Z - M if Z > M / 2; rounded to DD as in the slice scheme.
+__global__ void oz_crt_recombine_kernel(int64_t m, int64_t n, int N, int P, int64_t mpad, int64_t npad,
+                                        const uint8_t* __restrict__ R, const int* exa, const int* exb,
+                                        mat C, int mode, crt_consts cc) {
+  using Nm = num<2>;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= n || i >= m) return;
+  const int64_t plane = mpad * npad;
+  unsigned long long w[CRT_NW];
+#pragma unroll
+  for (int k = 0; k < CRT_NW; ++k) w[k] = 0ull;
+#pragma unroll
+  for (int t = 0; t < CRT_MAXN; ++t) {  // unrolled: static indices into the constants
+    if (t < N) {
+      const unsigned long long r = R[(int64_t)t * plane + i * npad + j];
+#pragma unroll
+      for (int k = 0; k < CRT_NW; ++k) w[k] += r * cc.c[t][k];  // < 40 * 2^40
+    }
+  }
+  uint32_t S[CRT_NW];
+  unsigned long long carry = 0ull;
+#pragma unroll
+  for (int k = 0; k < CRT_NW; ++k) {
+    const unsigned long long v = w[k] + carry;
+    S[k] = (uint32_t)v;
+    carry = v >> 32;
+  }
+  // q estimate from words wt, wt - 1, wt - 2 (selected without dynamic indexing)
+  uint32_t s2 = 0u, s1 = 0u, s0 = 0u;
+#pragma unroll
+  for (int k = 0; k < CRT_NW; ++k) {
+    s2 = k == cc.wt ? S[k] : s2;
+    s1 = k == cc.wt - 1 ? S[k] : s1;
+    s0 = k == cc.wt - 2 ? S[k] : s0;
+  }
+  const double sd = __fma_rn((double)s2, 18446744073709551616.0, __fma_rn((double)s1, 4294967296.0, (double)s0));
+  const uint32_t q = (uint32_t)floor(__dmul_rn(sd, cc.inv_scaled));
+  // Z = S - q M
+  uint32_t Z[CRT_NW];
+  unsigned long long pc = 0ull;
+  uint32_t borrow = 0u;
+#pragma unroll
+  for (int k = 0; k < CRT_NW; ++k) {
+    const unsigned long long pm = (unsigned long long)q * cc.M[k] + pc;
+    pc = pm >> 32;
+    const uint32_t sub = (uint32_t)pm;
+    const unsigned long long d = (unsigned long long)S[k] - sub - borrow;
+    Z[k] = (uint32_t)d;
+    borrow = (uint32_t)(d >> 63);
+  }
+  // correct q by one either way: Z < 0 -> Z += M; Z >= M -> Z -= M
+  auto add_m = [&](uint32_t sgn) {  // Z += M (sgn = 0) or Z -= M (sgn = 1)
+    const uint32_t msk = 0u - sgn;
+    unsigned long long c = sgn;
+#pragma unroll
+    for (int k = 0; k < CRT_NW; ++k) {
+      const unsigned long long v = (unsigned long long)Z[k] + (cc.M[k] ^ msk) + c;
+      Z[k] = (uint32_t)v;
+      c = v >> 32;
+    }
+  };
+  auto greater = [&](const uint32_t (&b)[CRT_NW]) {  // Z > b (both nonnegative)
+    int res = 0;
+#pragma unroll
+    for (int k = 0; k < CRT_NW; ++k) res = Z[k] > b[k] ? 1 : (Z[k] < b[k] ? -1 : res);
+    return res > 0;
+  };
+  auto is_neg = [&]() { return (Z[CRT_NW - 1] >> 31) != 0u; };
+  if (is_neg()) add_m(0u);
+  else {
+    // Z >= M  <=>  Z > M - 1; compare against M directly
+    int res = 0;
+#pragma unroll
+    for (int k = 0; k < CRT_NW; ++k) res = Z[k] > cc.M[k] ? 1 : (Z[k] < cc.M[k] ? -1 : res);
+    if (res >= 0) add_m(1u);
+  }
+  if (greater(cc.halfM)) add_m(1u);  // symmetric range: Z - M < 0
+  const int lsb = (exa[i] - 1022) + (exb[j] - 1022) - 2 * P;
+  const uint32_t neg = fx::acc_abs<CRT_NW>(Z);
+  uint64_t ch[2];
+  int ex[2];
+  double x[2] = {0.0, 0.0};
+  if (fx::acc_chunks<CRT_NW, 2>(Z, ch, ex)) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int e = lsb + ex[k];
+      double v = (ch[k] == 0 || e < -2044) ? 0.0 : fx::pow2_product(__ull2double_rn(ch[k]), e > 2046 ? 2046 : e);
+      x[k] = neg ? -v : v;
+    }
+  }
+  dd_t v;
+  two_sum(x[0], x[1], v.hi, v.lo);
+  const int64_t off = i * C.ld + j;
+  if (mode == MODE_ADD) v = Nm::add(Nm::load(C.p, off), v);
+  else if (mode == MODE_SUB) v = Nm::add(Nm::load(C.p, off), Nm::neg(v));
+  Nm::store(C.p, off, v);
+}
+
 // ------------------------------------------------------------------ host --
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static void set_gemm_attrs() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    done = true;
+  }
+}
+
+// Multiword helpers for the CRT constants (little-endian 32-bit words).
+using bigw = uint32_t[CRT_NW];
+static void big_mul_small(bigw& a, uint32_t k) {
+  uint64_t c = 0;
+  for (int i = 0; i < CRT_NW; ++i) {
+    const uint64_t v = (uint64_t)a[i] * k + c;
+    a[i] = (uint32_t)v;
+    c = v >> 32;
+  }
+}
+static uint32_t big_div_small(bigw& a, uint32_t k) {  // a /= k, returns a mod k
+  uint64_t r = 0;
+  for (int i = CRT_NW - 1; i >= 0; --i) {
+    const uint64_t v = (r << 32) | a[i];
+    a[i] = (uint32_t)(v / k);
+    r = v % k;
+  }
+  return (uint32_t)r;
+}
+static int big_bitlen(const bigw& a) {
+  for (int i = CRT_NW - 1; i >= 0; --i)
+    if (a[i]) return 32 * i + 32 - __builtin_clz(a[i]);
+  return 0;
+}
+static uint32_t inv_mod(uint32_t a, uint32_t m) {  // a^-1 mod m (gcd(a, m) = 1), extended Euclid
+  int64_t t0 = 0, t1 = 1, r0 = m, r1 = a % m;
+  while (r1 != 0) {
+    const int64_t q = r0 / r1;
+    int64_t x = r0 - q * r1; r0 = r1; r1 = x;
+    x = t0 - q * t1; t0 = t1; t1 = x;
+  }
+  return (uint32_t)((t0 % (int64_t)m + m) % m);
+}
+
+// Integer scaling precision for N moduli and inner dimension l:
+// P = min(120, floor((bitlen(M) - 2 - ceil(log2 l)) / 2)), so l 2^(2P) < M / 2.
+static int crt_precision(int N, int64_t l, crt_consts* cc) {
+  bigw M = {0};
+  M[0] = 1;
+  for (int t = 0; t < N; ++t) big_mul_small(M, (uint32_t)crt_mod(t));
+  const int B = big_bitlen(M);
+  int clog = 0;
+  while (((int64_t)1 << clog) < l) ++clog;
+  const int P = std::min(CRT_PMAX, (B - 2 - clog) / 2);
+  if (cc) {
+    std::memset(cc, 0, sizeof(*cc));
+    for (int k = 0; k < CRT_NW; ++k) cc->M[k] = M[k];
+    for (int t = 0; t < N; ++t) {
+      const uint32_t mt = (uint32_t)crt_mod(t);
+      bigw Mt;
+      for (int k = 0; k < CRT_NW; ++k) Mt[k] = M[k];
+      big_div_small(Mt, mt);  // exact
+      bigw tmp;
+      for (int k = 0; k < CRT_NW; ++k) tmp[k] = Mt[k];
+      const uint32_t y = inv_mod(big_div_small(tmp, mt), mt);
+      big_mul_small(Mt, y);
+      for (int k = 0; k < CRT_NW; ++k) cc->c[t][k] = Mt[k];
+    }
+    for (int k = 0; k < CRT_NW; ++k)
+      cc->halfM[k] = (M[k] >> 1) | (k + 1 < CRT_NW ? (M[k + 1] << 31) : 0u);
+    cc->wt = std::max(2, (B + 13) / 32);
+    double md = 0.0;
+    for (int k = CRT_NW - 1; k >= 0; --k) md = md * 4294967296.0 + (double)M[k];
+    cc->inv_scaled = std::ldexp(1.0 / md, 32 * (cc->wt - 2));
+  }
+  return P;
+}
 
 ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
                       int mode, int s, cudaStream_t st) {
@@ -361,11 +669,7 @@ ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, cons
   int32_t* D = reinterpret_cast<int32_t*>(base + bA + bB);
   int* exa = reinterpret_cast<int*>(base + bA + bB + bD);
   int* exb = exa + m;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
-    attr_done = true;
-  }
+  set_gemm_attrs();
   cudaEvent_t ev = nullptr;
   auto launched = [&]() { g_launches.fetch_add(1, std::memory_order_relaxed); };
   oz_exp_kernel<<<(unsigned)((m + 7) / 8), 256, 0, st>>>(m, l, A, 1, exa);
@@ -374,17 +678,17 @@ ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, cons
   launched();
   const dim3 ga((unsigned)((lpad + 255) / 256), (unsigned)mpad), gb((unsigned)(npad / 32), (unsigned)(lpad / 32));
   if (L == 2) {
-    oz_split_a_kernel<2><<<ga, 256, 0, st>>>(m, l, A, exa, s, mpad, lpad, As);
-    oz_split_b_kernel<2><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, s, npad, lpad, Bs);
+    oz_split_a_kernel<2, false><<<ga, 256, 0, st>>>(m, l, A, exa, s, 0, mpad, lpad, As);
+    oz_split_b_kernel<2, false><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, s, 0, npad, lpad, Bs);
   } else {
-    oz_split_a_kernel<4><<<ga, 256, 0, st>>>(m, l, A, exa, s, mpad, lpad, As);
-    oz_split_b_kernel<4><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, s, npad, lpad, Bs);
+    oz_split_a_kernel<4, false><<<ga, 256, 0, st>>>(m, l, A, exa, s, 0, mpad, lpad, As);
+    oz_split_b_kernel<4, false><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, s, 0, npad, lpad, Bs);
   }
   launched();
   launched();
   prof_begin_launch(st, &ev);
-  oz_gemm_kernel<<<dim3((unsigned)(npad / OBN), (unsigned)(mpad / OBM), (unsigned)s), 256, OZ_SMEM, st>>>(
-      mpad, npad, lpad, s, As, Bs, D);
+  oz_gemm_kernel<false><<<dim3((unsigned)(npad / OBN), (unsigned)(mpad / OBM), (unsigned)s), 256, OZ_SMEM, st>>>(
+      mpad, npad, lpad, s, As, Bs, D, nullptr);
   launched();
   cudaError_t e = cudaGetLastError();
   if (ev) {
@@ -403,5 +707,62 @@ ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, cons
   if (e != cudaSuccess) return set_error(DDG_ECUDA, std::string("ozaki: ") + cudaGetErrorString(e));
   return DDG_OK;
 }
+
+ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C, int mode,
+                          int N, cudaStream_t st) {
+  if (m == 0 || n == 0) return DDG_OK;
+  if (N < 2 || N > CRT_MAXN)
+    return set_error(DDG_EINVAL, "ozaki2: moduli must be in [2, " + std::to_string(CRT_MAXN) + "]");
+  const int64_t mpad = (m + OBM - 1) / OBM * OBM, npad = (n + OBN - 1) / OBN * OBN;
+  const int64_t lpad = std::max<int64_t>(OBK, (l + OBK - 1) / OBK * OBK);
+  if (lpad > 65536) return set_error(DDG_EINVAL, "ozaki2: l must be <= 65536 (exact INT32 residue products)");
+  crt_consts cc;
+  const int P = crt_precision(N, l, &cc);
+  if (P < 1) return set_error(DDG_EINVAL, "ozaki2: too few moduli for this l");
+  const size_t bA = al256((size_t)N * mpad * lpad), bB = al256((size_t)N * npad * lpad);
+  const size_t bR = al256((size_t)N * mpad * npad), bE = al256((size_t)(m + n) * 4);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, bA + bB + bR + bE, st) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(DDG_ENOMEM, "ozaki2: workspace allocation failed");
+  }
+  char* base = static_cast<char*>(ws);
+  int8_t* As = reinterpret_cast<int8_t*>(base);
+  int8_t* Bs = reinterpret_cast<int8_t*>(base + bA);
+  uint8_t* R = reinterpret_cast<uint8_t*>(base + bA + bB);
+  int* exa = reinterpret_cast<int*>(base + bA + bB + bR);
+  int* exb = exa + m;
+  set_gemm_attrs();
+  cudaEvent_t ev = nullptr;
+  auto launched = [&]() { g_launches.fetch_add(1, std::memory_order_relaxed); };
+  oz_exp_kernel<<<(unsigned)((m + 7) / 8), 256, 0, st>>>(m, l, A, 1, exa);
+  launched();
+  oz_exp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(l, n, B, 0, exb);
+  launched();
+  const dim3 ga((unsigned)((lpad + 255) / 256), (unsigned)mpad), gb((unsigned)(npad / 32), (unsigned)(lpad / 32));
+  oz_split_a_kernel<2, true><<<ga, 256, 0, st>>>(m, l, A, exa, N, P, mpad, lpad, As);
+  launched();
+  oz_split_b_kernel<2, true><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, N, P, npad, lpad, Bs);
+  launched();
+  prof_begin_launch(st, &ev);
+  oz_gemm_kernel<true><<<dim3((unsigned)(npad / OBN), (unsigned)(mpad / OBM), (unsigned)N), 256, OZ_SMEM, st>>>(
+      mpad, npad, lpad, N, As, Bs, nullptr, R);
+  launched();
+  cudaError_t e = cudaGetLastError();
+  if (ev)
+    prof_end_launch(st, ev, PROF_OZAKI, 2.0 * N * (double)mpad * (double)npad * (double)lpad,
+                    (double)N * (mpad + npad) * lpad + (double)N * mpad * npad);
+  if (e == cudaSuccess) {
+    const dim3 gr((unsigned)((n + 255) / 256), (unsigned)m);
+    oz_crt_recombine_kernel<<<gr, 256, 0, st>>>(m, n, N, P, mpad, npad, R, exa, exb, C, mode, cc);
+    launched();
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(ws, st);
+  if (e != cudaSuccess) return set_error(DDG_ECUDA, std::string("ozaki2: ") + cudaGetErrorString(e));
+  return DDG_OK;
+}
+
+int ozaki_crt_precision(int N, int64_t l) { return crt_precision(N, l, nullptr); }
 
 }  // namespace ddg

@@ -47,6 +47,10 @@ DD_LU_4096 = Workload("dd_lu_n4096", 2, 4096, "winograd", 512, 111, 0)
 # operands 200 MB > L2, small enough for a counter capture.
 DD_WINOGRAD_2048 = Workload("dd_winograd_n2048", 2, 2048, "winograd", 512, 112, 113)
 DD_LU_1024 = Workload("dd_lu_n1024", 2, 1024, "winograd", 512, 114, 0)
+# The CRT (Ozaki scheme II) DD product with 32 moduli (P = 113 at l = 4096).
+DD_OZAKI2_4096_N32 = Workload("dd_ozaki2_n4096_n32", 2, 4096, "ozaki2", 512, 101, 102, 32)
+DD_OZAKI2_8192_N32 = Workload("dd_ozaki2_n8192_n32", 2, 8192, "ozaki2", 512, 109, 110, 32)
 # Section 4 QD LU solve (the paper's QD Winograd LU), n = 2048.
 QD_LU_2048 = Workload("qd_lu_n2048", 4, 2048, "winograd", 256, 115, 0)
+QD_LU_1024 = Workload("qd_lu_n1024", 4, 1024, "winograd", 256, 117, 0)
 QD_OZAKI_4096_S32 = Workload("qd_ozaki_n4096_s32", 4, 4096, "ozaki", 512, 103, 104, 32)
