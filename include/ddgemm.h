@@ -234,7 +234,7 @@ typedef struct {
   int64_t pass_tasks;       /* fused quadrant passes */
   int64_t launches_per_run; /* kernels per ddg_batch_run */
   uint64_t workspace_bytes;
-  double fp64_ops;          /* algorithmic FP64 instructions of the leaves */
+  double leaf_macs;         /* multiply-adds of the base-case products (sum of m l n) */
 } ddg_batch_stats;
 
 typedef struct ddg_batch_s* ddg_batch;
@@ -261,7 +261,9 @@ ddg_status dd_gemm_batched(int32_t count, const ddg_problem* probs, void* stream
 
 /* FP64 instructions per DD (limbs = 2) or QD (limbs = 4) multiply-add in
  * the Block kernel's inner loop for accumulation scheme `accum` (0 or 1, as
- * in ddg_opts), counted from its source (for rooflines); -1 if invalid. */
+ * in ddg_opts), counted from its source (for rooflines): 0 for the
+ * fixed-point scheme, whose inner loop runs on the integer pipe; -1 if
+ * invalid. */
 int32_t ddg_block_fp64_ops_per_mac(int32_t limbs, int32_t accum);
 
 /* DDG_OZAKI2: the bits P of the integer scaling used with N moduli at inner
@@ -276,14 +278,15 @@ int32_t ddg_ozaki2_precision(int32_t moduli, int64_t l);
  * kinds k = 0 (Simple), 1 (Block), 2 (quadrant passes), 3 (INT8 slice
  * products), k < nkinds:
  * launches, sum of launch durations, busy time (union of the launch
- * intervals), and algorithmic FP64 instructions and bytes of those launches.
+ * intervals), and the algorithmic work and bytes of those launches.
  * For measurement only: it adds two event records per launch. */
 typedef struct {
   uint64_t launches;
   double sum_ms;
   double busy_ms;
-  double ops;   /* FP64 instructions (kinds 0-2) or INT8 operations, 2 per
-                   multiply-add (kind 3, the slice products) */
+  double ops;   /* FP64 instructions (kinds 0 and 2), multiply-adds (kind 1)
+                   or INT8 operations, 2 per multiply-add (kind 3, the INT8
+                   products) */
   double bytes;
 } ddg_kernel_prof;
 ddg_status ddg_profile_begin(void);

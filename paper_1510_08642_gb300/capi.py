@@ -57,7 +57,7 @@ class ddg_problem(ctypes.Structure):
 class ddg_batch_stats(ctypes.Structure):
     _fields_ = [("problems", c_i64), ("leaf_tasks", c_i64), ("leaf_tiles", c_i64),
                 ("pass_tasks", c_i64), ("launches_per_run", c_i64),
-                ("workspace_bytes", ctypes.c_uint64), ("fp64_ops", ctypes.c_double)]
+                ("workspace_bytes", ctypes.c_uint64), ("leaf_macs", ctypes.c_double)]
 
 
 class DDGError(RuntimeError):
@@ -173,7 +173,7 @@ def ddg_profile_begin() -> None:
 
 
 def ddg_profile_end() -> dict:
-    """Per kernel kind: launches, sum_ms, busy_ms, fp64_ops, bytes."""
+    """Per kernel kind: launches, sum_ms, busy_ms, ops (see ddg_kernel_prof), bytes."""
     arr = (ddg_kernel_prof * len(PROF_KINDS))()
     check(load().ddg_profile_end(arr, len(PROF_KINDS)))
     return {k: {f: getattr(arr[i], f) for f, _ in ddg_kernel_prof._fields_}

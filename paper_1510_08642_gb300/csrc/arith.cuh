@@ -87,6 +87,21 @@ __device__ __forceinline__ dd_t dd_div(dd_t a, dd_t b) {
   return dd_add(q, dd_t{q3, 0.0});
 }
 
+// 1 / b in DD by one Newton step from the double reciprocal y0: with
+// r = 1 - b y0 (two FMAs; |r| <= 2^-52), 1 / b = y0 (1 + r + r^2 + ...), so
+// y0 + y0 r (1 + r) is accurate to ~2^-105. Short dependency chain: a
+// GB300 SM issues a single thread's FP64 instructions slowly, and the LU's
+// pivot reciprocal sits on its critical path.
+__device__ __forceinline__ dd_t dd_recip(dd_t b) {
+  const double y0 = __ddiv_rn(1.0, b.hi);
+  double r = __fma_rn(-b.hi, y0, 1.0);
+  r = __fma_rn(-b.lo, y0, r);
+  const double c = __dmul_rn(y0, r);
+  dd_t y;
+  fast_two_sum(y0, __fma_rn(c, r, c), y.hi, y.lo);
+  return y;
+}
+
 // |a| > |b| as DD numbers (compares hi, then the lo of the same sign).
 __device__ __forceinline__ bool dd_abs_greater(dd_t a, dd_t b) {
   const double ah = fabs(a.hi), bh = fabs(b.hi);
@@ -219,6 +234,20 @@ __device__ __forceinline__ qd_t qd_div(const qd_t& a, const qd_t& b) {
   return qd_renorm<5>(q);
 }
 
+// 1 / b in QD: the DD reciprocal y1 (~2^-105), then one Newton step in QD:
+// e = 1 - b y1 (QD product and sum; |e| ~ 2^-105, accurate to ~2^-210),
+// 1 / b = y1 (1 + e + e^2 + ...) ~ y1 + y1 e + y1 e0^2. About a quarter of
+// the instructions of the long division.
+__device__ __forceinline__ qd_t qd_recip(const qd_t& b) {
+  const dd_t y1 = dd_recip(dd_t{b.x[0], b.x[1]});
+  const qd_t p = qd_mul(b, qd_t{{y1.hi, y1.lo, 0.0, 0.0}});
+  const qd_t e = qd_add(qd_t{{1.0, 0.0, 0.0, 0.0}}, qd_neg(p));
+  const dd_t c = dd_mul(y1, dd_t{e.x[0], e.x[1]});
+  const double c2 = __dmul_rn(c.hi, e.x[0]);
+  const double t[5] = {y1.hi, y1.lo, c.hi, c.lo, c2};
+  return qd_renorm<5>(t);
+}
+
 // ---------------------------------------------------------------------------
 // Limb-generic wrappers so that kernels can be written once for DD and QD.
 template <int L> struct num;
@@ -229,6 +258,7 @@ template <> struct num<2> {
   static __device__ __forceinline__ T mul(const T& a, const T& b) { return dd_mul(a, b); }
   static __device__ __forceinline__ T neg(const T& a) { return dd_neg(a); }
   static __device__ __forceinline__ T div(const T& a, const T& b) { return dd_div(a, b); }
+  static __device__ __forceinline__ T recip(const T& b) { return dd_recip(b); }
   static __device__ __forceinline__ T one() { return dd_t{1.0, 0.0}; }
   static __device__ __forceinline__ double lead(const T& a) { return a.hi; }
   static __device__ __forceinline__ double second(const T& a) { return a.lo; }
@@ -247,6 +277,7 @@ template <> struct num<4> {
   static __device__ __forceinline__ T mul(const T& a, const T& b) { return qd_mul(a, b); }
   static __device__ __forceinline__ T neg(const T& a) { return qd_neg(a); }
   static __device__ __forceinline__ T div(const T& a, const T& b) { return qd_div(a, b); }
+  static __device__ __forceinline__ T recip(const T& b) { return qd_recip(b); }
   static __device__ __forceinline__ T one() { return qd_t{{1.0, 0.0, 0.0, 0.0}}; }
   static __device__ __forceinline__ double lead(const T& a) { return a.x[0]; }
   static __device__ __forceinline__ double second(const T& a) { return a.x[1]; }

@@ -49,7 +49,7 @@ struct Builder {
   std::map<std::tuple<int, int>, std::vector<gtask>> fix;  // (depth, limbs)
   std::vector<gtask> leaves[5];
   int maxdepth = 0;
-  double fp64_ops = 0.0;
+  double leaf_macs = 0.0;
 
   mat alloc(int L, int64_t rows, int64_t cols) {
     mat M{};
@@ -97,7 +97,7 @@ void expand(Builder& b, int L, int algo, int cutoff, int64_t m, int64_t l, int64
   b.maxdepth = std::max(b.maxdepth, depth);
   if (!splits_b(algo, cutoff, m, l, n)) {
     b.leaves[L].push_back(leaf(m, l, n, A, B, C, mode));
-    b.fp64_ops += (double)m * l * n * block_fx_fp64_ops_per_mac(L);
+    b.leaf_macs += (double)m * l * n;
     return;
   }
   const int64_t m2 = m & ~int64_t(1), l2 = l & ~int64_t(1), n2 = n & ~int64_t(1);
@@ -277,7 +277,7 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
     if (v.empty()) return;
     const int64_t total = number_g(v, L);
     Launch la{1, L, 0, 0, (int)v.size(), total, 0, 0.0};
-    for (const gtask& g : v) la.ops += (double)g.m * g.l * g.n * block_fx_fp64_ops_per_mac(L);
+    for (const gtask& g : v) la.ops += (double)g.m * g.l * g.n;  // multiply-adds
     la.task_off = push_tasks(v.data(), v.size() * sizeof(gtask));
     const uint64_t zero = 0;
     la.counter_off = push_tasks(&zero, sizeof(zero));
@@ -322,7 +322,7 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
   b->stats.problems = count;
   b->stats.launches_per_run = (int64_t)launches.size();
   b->stats.workspace_bytes = (uint64_t)b->bytes;
-  b->stats.fp64_ops = real.fp64_ops;
+  b->stats.leaf_macs = real.leaf_macs;
   if (use_graph && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFreeAsync(b->buf, cs);
     delete b;

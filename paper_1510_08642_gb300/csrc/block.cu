@@ -204,7 +204,7 @@ cudaError_t launch_block(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat 
   if (ev) {
     const double macs = (double)m * (double)l * (double)n;
     const double bytes = 8.0 * limbs * ((double)m * l + (double)l * n + (double)m * n * (mode == MODE_SET ? 1 : 2));
-    prof_end_launch(s, ev, PROF_BLOCK, macs * (limbs == 2 ? kOpsDD : kOpsQD), bytes);
+    prof_end_launch(s, ev, PROF_BLOCK, macs, bytes);
   }
   return e;
 }

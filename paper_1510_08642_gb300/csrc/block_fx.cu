@@ -1,25 +1,23 @@
-// Block product with exact fixed-point accumulation (Kouya 2015, Section 2,
-// Block: C_ij = sum_k A_ik B_kj over tiles; the recursion's base case).
+// Block product with fixed-point accumulation on the integer pipe (Kouya
+// 2015, Section 2, Block: C_ij = sum_k A_ik B_kj over tiles; the recursion's
+// base case).
 //
-// Same tiling as block.cu (CTA tile of C, k-slabs of the limb planes staged
-// in shared memory, a register micro-tile per thread), but the multiply-add
-// moves the exact part of every product to the integer pipe (fx.cuh):
-//   DD: a_hi b_hi exactly (integer significand product) into a 192-bit
-//       window accumulator; the cross terms a_hi b_lo + a_lo b_hi by two FMAs
-//       into an FP64 sum (they are 2^-53 below the leading product, so one
-//       rounding per term is 2^-106 relative). 2 FP64 instructions per
-//       multiply-add instead of 12 (TwoSum scheme) or 27 (DD multiply then
-//       DD add).
-//   QD: the six limb products of order <= 2 exactly into a 288-bit window;
-//       the four order-3 products by FMA into an FP64 sum. 4 FP64
-//       instructions per multiply-add instead of 113 / ~218.
-// Before the k loop every CTA scans its row panel of A and column panel of B
-// for the largest exponent per row / column; the window of c_ij is scaled so
-// that sum_k |a_ik0 b_kj0| < 2^31 times the largest product fits below the
-// sign bit, making the integer accumulation exact for l < 2^31.
-// Error: truncation below the window (2^-159 resp. 2^-255 of the largest
-// product of row i and column j, per term) plus one rounding per FP64 term
-// and the final rounding to DD/QD.
+// GB300 retires 2 FP64 instructions per clock per SM but 64 IMAD and 128
+// other integer instructions, so the multiply-add runs without FP64:
+//   * staging: every element of the A and B tiles is converted once into a
+//     W-word fixed-point integer M (its limbs summed exactly at their own
+//     offsets below the leading limb's significand; W = 4 words for DD,
+//     7 for QD), its exponent field and sign (fx::to_fixed);
+//   * multiply-add: the K = 2 W - D leading words of M_a M_b from the
+//     partial products with i + j >= D (fx::mul_top, D = 3 / 6: 10 / 28
+//     32x32-bit multiply-adds), shifted into a two's-complement window of
+//     NW words per output entry (fx::place_shr) whose scale is fixed before
+//     the k loop from the largest exponent of row i of A and column j of B;
+//   * epilogue: the window rounded to DD / QD once.
+// Error per term: the dropped partial products, < 2^-123 (DD) / 2^-219
+// (QD) of |a_ik b_kj|, and the truncation below the window, 2^-159 (DD) /
+// 2^-255 (QD) of the largest product of row i and column j; the sum in the
+// window is exact for l < 2^31. One final rounding to DD / QD.
 #include <algorithm>
 
 #include "arith.cuh"
@@ -33,13 +31,15 @@ namespace {
 template <int L> struct fxcfg;
 template <> struct fxcfg<2> {
   static constexpr int BM = 16, BN = 32, BK = 16, TM = 2, TN = 2, NW = 6;
-  static constexpr int POS0 = 53;     // pos of a product = (ea - fa) + (eb - fb) + POS0
-  static constexpr int LSB0 = -2203;  // LSB exponent = fa + fb + LSB0
+  static constexpr int W = 4, D = 3, K = 2 * W - D;  // operand words, dropped / kept product words
+  static constexpr int MINB = 8;                      // resident CTAs per SM (register cap 64)
+  static constexpr int LSB0 = -2204;  // window LSB exponent = row_f + col_f + LSB0
 };
 template <> struct fxcfg<4> {
   static constexpr int BM = 8, BN = 32, BK = 8, TM = 1, TN = 2, NW = 9;
-  static constexpr int POS0 = 149;
-  static constexpr int LSB0 = -2299;
+  static constexpr int W = 7, D = 6, K = 2 * W - D;
+  static constexpr int MINB = 8;
+  static constexpr int LSB0 = -2300;
 };
 
 __device__ __forceinline__ double scaled(uint64_t chunk, int k, uint32_t neg) {
@@ -50,12 +50,39 @@ __device__ __forceinline__ double scaled(uint64_t chunk, int k, uint32_t neg) {
 
 }  // namespace
 
+// Operand tiles in fixed-point form: the W words of each element stored
+// contiguously (padded to WV 16-byte vectors), and per element its shift
+// below the largest exponent of its row (A) / column (B) and its sign mask.
+// The A tile is padded by one row: its staging writes run along k.
 template <int L>
 struct fx_smem {
-  double As[L][fxcfg<L>::BK][fxcfg<L>::BM];
-  double Bs[L][fxcfg<L>::BK][fxcfg<L>::BN];
+  static constexpr int WV = (fxcfg<L>::W + 3) / 4;
+  uint4 Aw[fxcfg<L>::BK][fxcfg<L>::BM + 1][WV];
+  uint4 Bw[fxcfg<L>::BK][fxcfg<L>::BN][WV];
+  int2 Ae[fxcfg<L>::BK][fxcfg<L>::BM + 1];
+  int2 Be[fxcfg<L>::BK][fxcfg<L>::BN];
   int row_f[fxcfg<L>::BM], col_f[fxcfg<L>::BN];
 };
+
+namespace {
+
+// Convert one element and store its words, shift and sign mask; a zero gets
+// shift 0 (its products are zero and stay on the fast path).
+template <int L>
+__device__ __forceinline__ void stage(const double (&x)[L], int fmax, uint4* w, int2* e) {
+  constexpr int W = fxcfg<L>::W, WV = (W + 3) / 4;
+  uint32_t M[4 * WV];
+  uint32_t(&Mw)[W] = *reinterpret_cast<uint32_t(*)[W]>(M);
+  const int es = fx::to_fixed<L, W>(x, Mw);
+#pragma unroll
+  for (int t = W; t < 4 * WV; ++t) M[t] = 0u;
+  const bool zero = (fx::dbits(x[0]) << 1) == 0u;
+#pragma unroll
+  for (int v = 0; v < WV; ++v) w[v] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
+  *e = make_int2(zero ? 0 : fmax - (es & 0xFFFF), (es >> 16) ? -1 : 0);
+}
+
+}  // namespace
 
 // One BM x BN tile of C at (i0, j0): C (mode) A B restricted to the tile.
 template <int L>
@@ -63,10 +90,9 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
                                         const mat& C, int mode, int64_t i0, int64_t j0, fx_smem<L>& sm) {
   using P = fxcfg<L>;
   constexpr int BM = P::BM, BN = P::BN, BK = P::BK, TM = P::TM, TN = P::TN, NW = P::NW;
+  constexpr int W = P::W, D = P::D, K = P::K, WV = fx_smem<L>::WV;
   constexpr int NX = BN / TN, NY = BM / TM, NT = NX * NY;
   static_assert(NT == 128, "block kernel assumes 128 threads");
-  auto& As = sm.As;
-  auto& Bs = sm.Bs;
   auto& row_f = sm.row_f;
   auto& col_f = sm.col_f;
 
@@ -94,18 +120,13 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
   }
   __syncthreads();
 
-  int base[TM][TN];
   uint32_t acc[TM][TN][NW];
-  double ef[TM][TN];
 #pragma unroll
   for (int r = 0; r < TM; ++r)
 #pragma unroll
-    for (int c = 0; c < TN; ++c) {
-      base[r][c] = P::POS0 - row_f[ty + r * NY] - col_f[tx + c * NX];
-      ef[r][c] = 0.0;
+    for (int c = 0; c < TN; ++c)
 #pragma unroll
       for (int w = 0; w < NW; ++w) acc[r][c][w] = 0u;
-    }
 
   for (int64_t k0 = 0; k0 < l; k0 += BK) {
 #pragma unroll
@@ -113,79 +134,53 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
       const int r = idx / BK, c = idx % BK;
       const int64_t gi = i0 + r, gk = k0 + c;
       const bool ok = gi < m && gk < l;
+      double x[L];
 #pragma unroll
-      for (int q = 0; q < L; ++q) As[q][c][r] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
+      for (int q = 0; q < L; ++q) x[q] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
+      stage<L>(x, row_f[r], sm.Aw[c][r], &sm.Ae[c][r]);
     }
 #pragma unroll
     for (int idx = tid; idx < BK * BN; idx += NT) {
       const int r = idx / BN, c = idx % BN;
       const int64_t gk = k0 + r, gj = j0 + c;
       const bool ok = gk < l && gj < n;
+      double x[L];
 #pragma unroll
-      for (int q = 0; q < L; ++q) Bs[q][r][c] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
+      for (int q = 0; q < L; ++q) x[q] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
+      stage<L>(x, col_f[c], sm.Bw[r][c], &sm.Be[r][c]);
     }
     __syncthreads();
 #pragma unroll 1
     for (int kk = 0; kk < BK; ++kk) {
-      double a[TM][L], b[TN][L];
+      uint32_t a[TM][4 * WV], b[TN][4 * WV];
+      int2 ea[TM], eb[TN];
+#pragma unroll
+      for (int r = 0; r < TM; ++r) {
+#pragma unroll
+        for (int v = 0; v < WV; ++v) {
+          const uint4 q = sm.Aw[kk][ty + r * NY][v];
+          a[r][4 * v] = q.x; a[r][4 * v + 1] = q.y; a[r][4 * v + 2] = q.z; a[r][4 * v + 3] = q.w;
+        }
+        ea[r] = sm.Ae[kk][ty + r * NY];
+      }
+#pragma unroll
+      for (int c = 0; c < TN; ++c) {
+#pragma unroll
+        for (int v = 0; v < WV; ++v) {
+          const uint4 q = sm.Bw[kk][tx + c * NX][v];
+          b[c][4 * v] = q.x; b[c][4 * v + 1] = q.y; b[c][4 * v + 2] = q.z; b[c][4 * v + 3] = q.w;
+        }
+        eb[c] = sm.Be[kk][tx + c * NX];
+      }
 #pragma unroll
       for (int r = 0; r < TM; ++r)
 #pragma unroll
-        for (int q = 0; q < L; ++q) a[r][q] = As[q][kk][ty + r * NY];
-#pragma unroll
-      for (int c = 0; c < TN; ++c)
-#pragma unroll
-        for (int q = 0; q < L; ++q) b[c][q] = Bs[q][kk][tx + c * NX];
-      if constexpr (L == 2) {
-        fx::unpacked ua[TM], ub[TN];
-#pragma unroll
-        for (int r = 0; r < TM; ++r) ua[r] = fx::unpack(a[r][0]);
-#pragma unroll
-        for (int c = 0; c < TN; ++c) ub[c] = fx::unpack(b[c][0]);
-#pragma unroll
-        for (int r = 0; r < TM; ++r)
-#pragma unroll
-          for (int c = 0; c < TN; ++c) {
-            uint32_t p[4];
-            fx::mant_mul(ua[r], ub[c], p);
-            fx::place<NW, 1>(acc[r][c], p, ua[r].e + ub[c].e + base[r][c], ua[r].s ^ ub[c].s);
-            ef[r][c] = __fma_rn(a[r][0], b[c][1], ef[r][c]);
-            ef[r][c] = __fma_rn(a[r][1], b[c][0], ef[r][c]);
-          }
-      } else {
-        fx::unpacked ua[TM][3], ub[TN][3];
-#pragma unroll
-        for (int r = 0; r < TM; ++r)
-#pragma unroll
-          for (int q = 0; q < 3; ++q) ua[r][q] = fx::unpack(a[r][q]);
-#pragma unroll
-        for (int c = 0; c < TN; ++c)
-#pragma unroll
-          for (int q = 0; q < 3; ++q) ub[c][q] = fx::unpack(b[c][q]);
-#pragma unroll
-        for (int r = 0; r < TM; ++r)
-#pragma unroll
-          for (int c = 0; c < TN; ++c) {
-            uint32_t p[4];
-            const int bs = base[r][c];
-#define DDG_PAIR(I, J, WF)                                                                  \
-            fx::mant_mul(ua[r][I], ub[c][J], p);                                            \
-            fx::place<NW, WF>(acc[r][c], p, ua[r][I].e + ub[c][J].e + bs, ua[r][I].s ^ ub[c][J].s);
-            DDG_PAIR(0, 0, 4)
-            DDG_PAIR(0, 1, 3)
-            DDG_PAIR(1, 0, 3)
-            DDG_PAIR(0, 2, 1)
-            DDG_PAIR(1, 1, 1)
-            DDG_PAIR(2, 0, 1)
-#undef DDG_PAIR
-            double e = ef[r][c];
-            e = __fma_rn(a[r][0], b[c][3], e);
-            e = __fma_rn(a[r][1], b[c][2], e);
-            e = __fma_rn(a[r][2], b[c][1], e);
-            e = __fma_rn(a[r][3], b[c][0], e);
-            ef[r][c] = e;
-          }
-      }
+        for (int c = 0; c < TN; ++c) {
+          uint32_t p[K];
+          fx::mul_top<W, D>(*reinterpret_cast<const uint32_t(*)[W]>(a[r]),
+                            *reinterpret_cast<const uint32_t(*)[W]>(b[c]), p);
+          fx::place_shr<NW, K>(acc[r][c], p, ea[r].x + eb[c].x, (uint32_t)(ea[r].y ^ eb[c].y));
+        }
     }
     __syncthreads();
   }
@@ -208,18 +203,16 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
             hi = scaled(ch[0], lsb + ex[0], neg);
             lo = scaled(ch[1], lsb + ex[1], neg);
           }
-          double s, e1;
-          two_sum(hi, ef[r][c], s, e1);
-          two_sum(s, __dadd_rn(e1, lo), v.hi, v.lo);
+          two_sum(hi, lo, v.hi, v.lo);
         } else {
           uint64_t ch[4];
           int ex[4];
-          double x[5] = {0.0, 0.0, 0.0, 0.0, ef[r][c]};
+          double x[4] = {0.0, 0.0, 0.0, 0.0};
           if (fx::acc_chunks<NW, 4>(acc[r][c], ch, ex)) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) x[q] = scaled(ch[q], lsb + ex[q], neg);
           }
-          v = qd_renorm<5>(x);
+          v = qd_renorm<4>(x);
         }
         const int64_t off = gi * C.ld + gj;
         if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
@@ -230,7 +223,7 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
 }
 
 template <int L>
-__global__ void __launch_bounds__(128) block_fx_kernel(int64_t m, int64_t l, int64_t n, mat A, mat B,
+__global__ void __launch_bounds__(128, fxcfg<L>::MINB) block_fx_kernel(int64_t m, int64_t l, int64_t n, mat A, mat B,
                                                        mat C, int mode) {
   __shared__ fx_smem<L> sm;
   fx_tile<L>(m, l, n, A, B, C, mode, (int64_t)blockIdx.y * fxcfg<L>::BM,
@@ -241,7 +234,7 @@ __global__ void __launch_bounds__(128) block_fx_kernel(int64_t m, int64_t l, int
 // (tiles numbered task by task, tasks sorted by decreasing l by the planner)
 // from a global counter until none is left. No CTA waits on another.
 template <int L>
-__global__ void __launch_bounds__(128) grouped_fx_kernel(const gtask* __restrict__ tasks, int ntasks,
+__global__ void __launch_bounds__(128, fxcfg<L>::MINB - 1) grouped_fx_kernel(const gtask* __restrict__ tasks, int ntasks,
                                                          int64_t total, unsigned long long* counter) {
   __shared__ fx_smem<L> sm;
   __shared__ int64_t st;
@@ -280,7 +273,7 @@ cudaError_t launch_grouped_fx(int limbs, const gtask* tasks, int ntasks, int64_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 152;
   }
-  const int per_sm = limbs == 2 ? 5 : 3;  // resident CTAs per SM (register limited)
+  const int per_sm = (limbs == 2 ? fxcfg<2>::MINB : fxcfg<4>::MINB) - 1;  // resident CTAs per SM
   const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)sms * per_sm);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
@@ -311,11 +304,11 @@ cudaError_t launch_block_fx(int limbs, int64_t m, int64_t l, int64_t n, mat A, m
   if (ev) {
     const double macs = (double)m * (double)l * (double)n;
     const double bytes = 8.0 * limbs * ((double)m * l + (double)l * n + (double)m * n * (mode == MODE_SET ? 1 : 2));
-    prof_end_launch(s, ev, PROF_BLOCK, macs * block_fx_fp64_ops_per_mac(limbs), bytes);
+    prof_end_launch(s, ev, PROF_BLOCK, macs, bytes);
   }
   return e;
 }
 
-int block_fx_fp64_ops_per_mac(int limbs) { return limbs == 2 ? 2 : 4; }
+int block_fx_fp64_ops_per_mac(int limbs) { return limbs == 2 || limbs == 4 ? 0 : -1; }
 
 }  // namespace ddg

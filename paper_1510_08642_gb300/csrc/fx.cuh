@@ -283,5 +283,171 @@ __host__ __device__ __forceinline__ bool acc_chunks(const uint32_t (&A)[NW], uin
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Per-operand fixed-point form (the Block kernel's second scheme).
+//
+// A DD / QD number x = x0 + x1 + ... is converted once, when its tile is
+// staged, into an unsigned W-word integer M with |x| ~= M 2^(f - 1075 -
+// (32 W - 53)), f = the biased exponent field of x0 (1 for zero and
+// subnormals) and the sign of x0: x0's 53-bit significand fills the top of
+// M and each further limb is added or subtracted at its own offset
+// (truncated toward zero below bit 0, i.e. 2^-(32 W - 1) of |x|). Since the
+// expansion is normalised, 0 <= M < 2^(32 W). Returns f | (sign << 16).
+template <int L, int W>
+__host__ __device__ __forceinline__ int to_fixed(const double (&x)[L], uint32_t (&M)[W]) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) M[w] = 0u;
+  const unpacked u0 = unpack(x[0]);
+  if (u0.m0 == 0u && u0.m1 == 0u) return 1;
+  constexpr int TOP = 32 * W - 53;  // bit offset of x0's significand
+#pragma unroll
+  for (int q = 0; q < L; ++q) {
+    const unpacked u = q == 0 ? u0 : unpack(x[q]);
+    int sh = q == 0 ? TOP : (u.e - u0.e) + TOP;  // bit offset of this limb's LSB
+    uint64_t m = ((uint64_t)u.m1 << 32) | u.m0;
+    if (m == 0u || sh <= -53) continue;
+    if (sh < 0) {
+      m >>= -sh;
+      sh = 0;
+    }
+    // the limb as W words at offset sh (53 bits span at most 3 words)
+    const int wo = sh >> 5, r = sh & 31;
+    const uint32_t p0 = (uint32_t)m << r;
+    const uint32_t p1 = shl_funnel((uint32_t)m, (uint32_t)(m >> 32), r);
+    const uint32_t p2 = shl_funnel((uint32_t)(m >> 32), 0u, r);
+    const uint32_t neg = q == 0 ? 0u : (u.s ^ u0.s);
+    const uint32_t msk = 0u - neg;
+    uint64_t c = neg;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const uint32_t d = w == wo ? p0 : (w == wo + 1 ? p1 : (w == wo + 2 ? p2 : 0u));
+      const uint64_t v = (uint64_t)M[w] + (d ^ msk) + c;
+      M[w] = (uint32_t)v;
+      c = v >> 32;
+    }
+  }
+  return u0.e | (int)(u0.s << 16);
+}
+
+// The K = 2 W - D leading words of a b from the column sums of the partial
+// products with i + j >= D (Comba order, a three-word running sum; the
+// columns below D and their carries are dropped). The result is below the
+// exact floor(a b / 2^(32 D)) by less than (D + 1) 2^32 units.
+template <int W, int D>
+__host__ __device__ __forceinline__ void mul_top(const uint32_t (&a)[W], const uint32_t (&b)[W],
+                                                 uint32_t (&p)[2 * W - D]) {
+  uint32_t c0 = 0u, c1 = 0u, c2 = 0u;
+#pragma unroll
+  for (int k = D; k <= 2 * W - 2; ++k) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const int j = k - i;
+      if (j < 0 || j >= W) continue;
+#ifdef __CUDA_ARCH__
+      asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+          "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+          "addc.u32 %2, %2, 0;"
+          : "+r"(c0), "+r"(c1), "+r"(c2)
+          : "r"(a[i]), "r"(b[j]));
+#else
+      const uint64_t pr = (uint64_t)a[i] * b[j];
+      const uint64_t lo = (uint64_t)c0 + (uint32_t)pr;
+      const uint64_t hi = (uint64_t)c1 + (uint32_t)(pr >> 32) + (lo >> 32);
+      c0 = (uint32_t)lo;
+      c1 = (uint32_t)hi;
+      c2 += (uint32_t)(hi >> 32);
+#endif
+    }
+    p[k - D] = c0;
+    c0 = c1;
+    c1 = c2;
+    c2 = 0u;
+  }
+  p[2 * W - 1 - D] = c0;
+}
+
+// (hi:lo >> r) low word, r in [0, 31]
+__host__ __device__ __forceinline__ uint32_t shr_funnel(uint32_t lo, uint32_t hi, int r) {
+#ifdef __CUDA_ARCH__
+  return __funnelshift_r(lo, hi, r);
+#else
+  return (uint32_t)(((((uint64_t)hi) << 32) | lo) >> r);
+#endif
+}
+
+// acc += (d XOR m) + (m & 1) for a mask m = 0 (add d) or ~0 (subtract d).
+template <int NW>
+__host__ __device__ __forceinline__ void acc_add_mask(uint32_t (&A)[NW], const uint32_t (&d)[NW], uint32_t m) {
+#ifdef __CUDA_ARCH__
+  if constexpr (NW == 6) {
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %6, %6;\n\t"  // carry = top bit of the mask
+        "addc.cc.u32 %0, %0, %7;\n\t"
+        "addc.cc.u32 %1, %1, %8;\n\t"
+        "addc.cc.u32 %2, %2, %9;\n\t"
+        "addc.cc.u32 %3, %3, %10;\n\t"
+        "addc.cc.u32 %4, %4, %11;\n\t"
+        "addc.u32 %5, %5, %12;\n\t}"
+        : "+r"(A[0]), "+r"(A[1]), "+r"(A[2]), "+r"(A[3]), "+r"(A[4]), "+r"(A[5])
+        : "r"(m), "r"(d[0] ^ m), "r"(d[1] ^ m), "r"(d[2] ^ m), "r"(d[3] ^ m), "r"(d[4] ^ m),
+          "r"(d[5] ^ m));
+  } else if constexpr (NW == 9) {
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %9, %9;\n\t"
+        "addc.cc.u32 %0, %0, %10;\n\t"
+        "addc.cc.u32 %1, %1, %11;\n\t"
+        "addc.cc.u32 %2, %2, %12;\n\t"
+        "addc.cc.u32 %3, %3, %13;\n\t"
+        "addc.cc.u32 %4, %4, %14;\n\t"
+        "addc.cc.u32 %5, %5, %15;\n\t"
+        "addc.cc.u32 %6, %6, %16;\n\t"
+        "addc.cc.u32 %7, %7, %17;\n\t"
+        "addc.u32 %8, %8, %18;\n\t}"
+        : "+r"(A[0]), "+r"(A[1]), "+r"(A[2]), "+r"(A[3]), "+r"(A[4]), "+r"(A[5]), "+r"(A[6]),
+          "+r"(A[7]), "+r"(A[8])
+        : "r"(m), "r"(d[0] ^ m), "r"(d[1] ^ m), "r"(d[2] ^ m), "r"(d[3] ^ m), "r"(d[4] ^ m),
+          "r"(d[5] ^ m), "r"(d[6] ^ m), "r"(d[7] ^ m), "r"(d[8] ^ m));
+  } else {
+    static_assert(NW == 6 || NW == 9, "accumulator width");
+  }
+#else
+  uint64_t c = m >> 31;
+  for (int t = 0; t < NW; ++t) {
+    const uint64_t v = (uint64_t)A[t] + (uint64_t)(d[t] ^ m) + c;
+    A[t] = (uint32_t)v;
+    c = v >> 32;
+  }
+#endif
+}
+
+// A += sign * floor(p / 2^sh) for a K-word p, sh >= 0 and the sign as a
+// mask m (0: add, ~0: subtract); bits shifted out are dropped. Fast path for
+// sh < 32 (a funnel shift per word); larger shifts take the general path.
+template <int NW, int K>
+__host__ __device__ __forceinline__ void place_shr(uint32_t (&A)[NW], const uint32_t (&p)[K], int sh,
+                                                   uint32_t m) {
+  static_assert(K <= NW, "product wider than the window");
+  uint32_t d[NW];
+  const int r = sh & 31;
+  if (sh < 32) {
+#pragma unroll
+    for (int t = 0; t < NW; ++t) d[t] = t < K ? shr_funnel(p[t], t + 1 < K ? p[t + 1] : 0u, r) : 0u;
+  } else {
+    const int w = sh >> 5;
+#pragma unroll
+    for (int t = 0; t < NW; ++t) {
+      uint32_t v = 0u;
+#pragma unroll
+      for (int s = 1; s < K; ++s) {
+        if (t + s >= K) continue;
+        const uint32_t x = shr_funnel(p[t + s], t + s + 1 < K ? p[t + s + 1] : 0u, r);
+        v = (w == s) ? x : v;
+      }
+      d[t] = v;
+    }
+  }
+  acc_add_mask<NW>(A, d, m);
+}
+
 }  // namespace fx
 }  // namespace ddg

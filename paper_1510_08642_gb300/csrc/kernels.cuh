@@ -29,7 +29,7 @@ extern std::atomic<uint64_t> g_launches;
 enum ProfKind { PROF_SIMPLE = 0, PROF_BLOCK = 1, PROF_PASS = 2, PROF_OZAKI = 3 };
 bool prof_enabled();
 void prof_begin_launch(cudaStream_t s, cudaEvent_t* start);
-void prof_end_launch(cudaStream_t s, cudaEvent_t start, int kind, double fp64_ops, double bytes);
+void prof_end_launch(cudaStream_t s, cudaEvent_t start, int kind, double ops, double bytes);
 
 enum Mode { MODE_SET = 0, MODE_ADD = 1, MODE_SUB = 2 };
 

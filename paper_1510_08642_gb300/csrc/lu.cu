@@ -114,11 +114,13 @@ __device__ __forceinline__ typename num<L>::T get_rinv(const col_state* cs) {
 
 // Executed by the last CTA of a launch (all its threads): choose the pivot
 // of column j from the partial arg-maxes (or row j without pivoting),
-// record it, flag an exactly zero pivot, swap rows j and p across all
-// columns, and publish 1 / pivot for the quotients of column j.
+// record it, flag an exactly zero pivot, swap rows j and p within the
+// columns [c0, c1) of the narrow panel being factored (the other columns
+// receive the interchanges in one pass per panel, lu_laswp_kernel), and
+// publish 1 / pivot for the quotients of column j.
 template <int L>
-__device__ void finish_pivot(int64_t n, const mat& A, int64_t j, int64_t nparts, const partial_t* part,
-                             int64_t* ipiv, int64_t* info, int pivot, col_state* cs) {
+__device__ void finish_pivot(int64_t n, const mat& A, int64_t j, int64_t c0, int64_t c1, int64_t nparts,
+                             const partial_t* part, int64_t* ipiv, int64_t* info, int pivot, col_state* cs) {
   using T = typename num<L>::T;
   __shared__ partial_t sbest[8];
   __shared__ int64_t sp;
@@ -143,7 +145,7 @@ __device__ void finish_pivot(int64_t n, const mat& A, int64_t j, int64_t nparts,
   __syncthreads();
   const int64_t p = sp;
   if (p != j) {
-    for (int64_t c = tid; c < n; c += blockDim.x)
+    for (int64_t c = c0 + tid; c < c1; c += blockDim.x)
 #pragma unroll
       for (int q = 0; q < L; ++q) {
         double* rj = A.p[q] + j * A.ld + c;
@@ -159,7 +161,7 @@ __device__ void finish_pivot(int64_t n, const mat& A, int64_t j, int64_t nparts,
     const T piv = ldA<L>(A, j, j);
     const bool zero = is_zero<L>(piv);
     if (zero && *info == 0) *info = j + 1;
-    const T r = zero ? num<L>::zero() : num<L>::div(num<L>::one(), piv);
+    const T r = zero ? num<L>::zero() : num<L>::recip(piv);
     const double* x = reinterpret_cast<const double*>(&r);
 #pragma unroll
     for (int q = 0; q < L; ++q) cs->rinv[q] = x[q];
@@ -183,10 +185,11 @@ __device__ __forceinline__ bool last_block(col_state* cs) {
 
 }  // namespace
 
-// First column j of a narrow panel: partial arg-maxes of column j over rows
-// [j, n) (RB rows per CTA), then the last CTA chooses and swaps the pivot.
+// First column j of a narrow panel [j, pe): partial arg-maxes of column j
+// over rows [j, n) (RB rows per CTA), then the last CTA chooses and swaps
+// the pivot.
 template <int L>
-__global__ void __launch_bounds__(256) lu_start_kernel(int64_t n, mat A, int64_t j, partial_t* part,
+__global__ void __launch_bounds__(256) lu_start_kernel(int64_t n, mat A, int64_t j, int64_t pe, partial_t* part,
                                                        int64_t* ipiv, int64_t* info, int pivot,
                                                        col_state* cs) {
   const int tid = threadIdx.x;
@@ -196,21 +199,21 @@ __global__ void __launch_bounds__(256) lu_start_kernel(int64_t n, mat A, int64_t
     warp_best(v);
     if (tid == 0) part[blockIdx.x] = v;
   }
-  if (last_block(cs)) finish_pivot<L>(n, A, j, gridDim.x, part, ipiv, info, pivot, cs);
+  if (last_block(cs)) finish_pivot<L>(n, A, j, j, pe, gridDim.x, part, ipiv, info, pivot, cs);
 }
 
-// Column j (its pivot row already in place, 1 / pivot in cs): quotients
-// l_ij = a_ij (1 / a_jj) for rows below j, rank-1 update of columns (j, pe)
-// of those rows; then, if column j + 1 belongs to the same panel, the
-// partial arg-maxes of the updated column j + 1 and, in the last CTA, its
-// pivot.
+// Column j of the narrow panel [c0, pe) (its pivot row already in place,
+// 1 / pivot in cs): quotients l_ij = a_ij (1 / a_jj) for rows below j,
+// rank-1 update of columns (j, pe) of those rows; then, if column j + 1
+// belongs to the same panel, the partial arg-maxes of the updated column
+// j + 1 and, in the last CTA, its pivot.
 template <int L>
-__global__ void __launch_bounds__(256) lu_col_kernel(int64_t n, mat A, int64_t j, int64_t pe,
+__global__ void __launch_bounds__(256) lu_col_kernel(int64_t n, mat A, int64_t c0, int64_t j, int64_t pe,
                                                      partial_t* part, int64_t* ipiv, int64_t* info,
                                                      int pivot, col_state* cs) {
   using N = num<L>;
   using T = typename N::T;
-  __shared__ T u[KMAX];
+  __shared__ T u[PANEL_BASE];  // pe - j - 1 < PANEL_BASE
   __shared__ T lq[RB];
   const int tid = threadIdx.x;
   const int64_t r0 = j + 1 + (int64_t)blockIdx.x * RB;
@@ -240,7 +243,27 @@ __global__ void __launch_bounds__(256) lu_col_kernel(int64_t n, mat A, int64_t j
     warp_best(v);
     if (tid == 0) part[blockIdx.x] = v;
   }
-  if (last_block(cs)) finish_pivot<L>(n, A, j + 1, gridDim.x, part, ipiv, info, pivot, cs);
+  if (last_block(cs)) finish_pivot<L>(n, A, j + 1, c0, pe, gridDim.x, part, ipiv, info, pivot, cs);
+}
+
+// The interchanges ipiv[k0 .. k1) (in order) applied to every column outside
+// [k0, k1): one thread per column.
+template <int L>
+__global__ void lu_laswp_kernel(int64_t n, mat A, int64_t k0, int64_t k1, const int64_t* ipiv) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n || (c >= k0 && c < k1)) return;
+  for (int64_t k = k0; k < k1; ++k) {
+    const int64_t p = ipiv[k];
+    if (p == k || p < 0 || p >= n) continue;
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+      double* rk = A.p[q] + k * A.ld + c;
+      double* rp = A.p[q] + p * A.ld + c;
+      const double t = *rk;
+      *rk = *rp;
+      *rp = t;
+    }
+  }
 }
 
 template <int L>
@@ -296,7 +319,7 @@ __global__ void __launch_bounds__(128) trsm_upper_base(int64_t m, int64_t r, mat
   const int lane = threadIdx.x & 31;
   const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (c >= r) return;
-  const T rinv = N::div(N::one(), Tr[lane][lane]);
+  const T rinv = N::recip(Tr[lane][lane]);
   T acc = lane < m ? ldA<L>(X, lane, c) : N::zero();
   for (int k = (int)m - 1; k >= 0; --k) {
     if (lane == k) acc = N::mul(acc, rinv);
@@ -443,11 +466,15 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
     if (w <= PANEL_BASE) {
       const int64_t pe = c0 + w;
       const int64_t nstart = pivot ? (n - c0 + RB - 1) / RB : 1;
-      lu_start_kernel<L><<<(unsigned)nstart, 256, 0, s>>>(n, M, c0, part, ipiv, dinfo, pivot, cs);
+      lu_start_kernel<L><<<(unsigned)nstart, 256, 0, s>>>(n, M, c0, pe, part, ipiv, dinfo, pivot, cs);
       cu(cudaGetLastError());
       for (int64_t j = c0; j < pe && j + 1 < n && st == DDG_OK; ++j) {
         const int64_t blocks = (n - j - 1 + RB - 1) / RB;
-        lu_col_kernel<L><<<(unsigned)blocks, 256, 0, s>>>(n, M, j, pe, part, ipiv, dinfo, pivot, cs);
+        lu_col_kernel<L><<<(unsigned)blocks, 256, 0, s>>>(n, M, c0, j, pe, part, ipiv, dinfo, pivot, cs);
+        cu(cudaGetLastError());
+      }
+      if (pivot && st == DDG_OK) {
+        lu_laswp_kernel<L><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, M, c0, pe, ipiv);
         cu(cudaGetLastError());
       }
       return;

@@ -17,7 +17,7 @@ namespace ddg {
 namespace {
 struct rec_t {
   int kind;
-  double fp64_ops;
+  double ops;
   double bytes;
   cudaEvent_t start, stop;
 };
@@ -37,13 +37,13 @@ void prof_begin_launch(cudaStream_t s, cudaEvent_t* start) {
   cudaEventRecord(*start, s);
 }
 
-void prof_end_launch(cudaStream_t s, cudaEvent_t start, int kind, double fp64_ops, double bytes) {
+void prof_end_launch(cudaStream_t s, cudaEvent_t start, int kind, double ops, double bytes) {
   if (!g_on || !start) return;
   cudaEvent_t stop;
   if (cudaEventCreate(&stop) != cudaSuccess) return;
   cudaEventRecord(stop, s);
   std::lock_guard<std::mutex> lk(g_mu);
-  g_recs.push_back({kind, fp64_ops, bytes, start, stop});
+  g_recs.push_back({kind, ops, bytes, start, stop});
 }
 
 }  // namespace ddg
@@ -80,7 +80,7 @@ ddg_status ddg_profile_end(ddg_kernel_prof* out, int32_t nkinds) {
       ddg_kernel_prof& o = out[r.kind];
       o.launches += 1;
       o.sum_ms += d;
-      o.ops += r.fp64_ops;
+      o.ops += r.ops;
       o.bytes += r.bytes;
       iv[r.kind].push_back({t0, t1});
     }

@@ -30,8 +30,8 @@ def test_header_symbols_exported():
 def test_block_ops_per_mac():
     assert capi.ddg_block_fp64_ops_per_mac(2, 1) == 12
     assert capi.ddg_block_fp64_ops_per_mac(4, 1) == 113
-    assert capi.ddg_block_fp64_ops_per_mac(2, 0) == 2
-    assert capi.ddg_block_fp64_ops_per_mac(4, 0) == 4
+    assert capi.ddg_block_fp64_ops_per_mac(2, 0) == 0
+    assert capi.ddg_block_fp64_ops_per_mac(4, 0) == 0
     assert capi.ddg_block_fp64_ops_per_mac(3, 0) == -1
 
 

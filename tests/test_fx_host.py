@@ -1,0 +1,118 @@
+"""Host checks of the Block kernel's fixed-point helpers (fx.cuh), compiled
+for the CPU with nvcc and compared with exact integer arithmetic:
+
+* to_fixed: the W-word integer M of a DD / QD number equals the exact sum
+  of its limbs at the scale of the leading limb, truncated below bit 0
+  (at most one unit per lower limb), with the leading limb's sign;
+* mul_top: the kept words of a b lie within (D + 1) 2^32 units below
+  floor(a b / 2^(32 D));
+* place_shr: the window gains exactly sign * floor(p / 2^sh) (mod 2^(32 NW)),
+  on the two fast-path offsets and the general path.
+"""
+import math
+import os
+import random
+import shutil
+import struct
+import subprocess
+from fractions import Fraction
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "tests", "native", "fx_check.cu")
+CSRC = os.path.join(ROOT, "paper_1510_08642_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def fxbin(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("fx") / "fx_check")
+    subprocess.check_call([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-o", out, SRC])
+    return out
+
+
+def run(binary, lines):
+    r = subprocess.run([binary], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    return r.stdout.strip().splitlines()
+
+
+def hexd(x):
+    return "%016x" % struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def words(v, n):
+    return [(v >> (32 * i)) & 0xFFFFFFFF for i in range(n)]
+
+
+def value(ws):
+    return sum(w << (32 * i) for i, w in enumerate(ws))
+
+
+def expansion(rng, L, sparse=False):
+    x = [math.ldexp(rng.random() + 0.5, rng.randint(-40, 40)) * rng.choice([-1, 1])]
+    for _ in range(L - 1):
+        gap = rng.choice([53, 54, 60, 90, 200]) if sparse else 53
+        x.append(x[-1] * 2.0 ** -gap * (rng.random() - 0.5) if rng.random() < 0.9 else 0.0)
+    # renormalise with exact rationals: greedy nearest doubles
+    v = sum(Fraction(t) for t in x)
+    out = []
+    for _ in range(L):
+        d = float(v)
+        out.append(d)
+        v -= Fraction(d)
+    return out
+
+
+@pytest.mark.parametrize("L,W", [(2, 4), (4, 7)])
+def test_to_fixed_exact_up_to_truncation(fxbin, L, W):
+    rng = random.Random(L)
+    cases = [expansion(rng, L, sparse=(i % 3 == 0)) for i in range(400)]
+    cases += [[0.0] * L, [1.0] + [0.0] * (L - 1), [-(2.0 ** 1023)] + [0.0] * (L - 1),
+              [5e-324] + [0.0] * (L - 1), [1.0, -2.0 ** -54] + [0.0] * (L - 2)]
+    out = run(fxbin, [f"T {L} " + " ".join(hexd(t) for t in x) for x in cases])
+    for x, line in zip(cases, out):
+        vals = [int(t) for t in line.split()]
+        es, M = vals[0], value(vals[1:])
+        exact = sum(Fraction(t) for t in x)
+        if x[0] == 0.0:
+            assert M == 0
+            continue
+        f, s = es & 0xFFFF, es >> 16
+        assert s == (1 if x[0] < 0 else 0)
+        assert M < 2 ** (32 * W)
+        unit = Fraction(2) ** (max(f, 1) - 1075 - (32 * W - 53))
+        got = M * unit
+        diff = abs(exact) - got
+        assert -(L - 1) * unit <= diff <= (L - 1) * unit, (x, float(diff / unit))
+
+
+@pytest.mark.parametrize("W,D", [(4, 3), (7, 6)])
+def test_mul_top_within_dropped_columns(fxbin, W, D):
+    rng = random.Random(W)
+    cases = [(rng.getrandbits(32 * W), rng.getrandbits(32 * W)) for _ in range(300)]
+    cases += [(2 ** (32 * W) - 1, 2 ** (32 * W) - 1), (0, 12345), (1 << (32 * W - 1), 3)]
+    lines = [f"M {W} {D} " + " ".join(map(str, words(a, W) + words(b, W))) for a, b in cases]
+    for (a, b), line in zip(cases, run(fxbin, lines)):
+        p = value([int(t) for t in line.split()])
+        exact = (a * b) >> (32 * D)
+        assert 0 <= exact - p < (D + 1) * 2 ** 32
+
+
+@pytest.mark.parametrize("NW,K", [(6, 5), (9, 8)])
+def test_place_shr_exact(fxbin, NW, K):
+    rng = random.Random(NW)
+    cases = []
+    for i in range(400):
+        sh = rng.choice([0, 1, 31, 32, 33, 63, 64, 65, 95, 127, 32 * K - 1, 32 * K, 32 * K + 40,
+                         rng.randint(0, 40 * K)])
+        cases.append((sh, rng.randint(0, 1), rng.getrandbits(32 * NW - 2), rng.getrandbits(32 * K)))
+    lines = [f"P {NW} {K} {sh} {neg} " + " ".join(map(str, words(acc, NW) + words(p, K)))
+             for sh, neg, acc, p in cases]
+    mod = 2 ** (32 * NW)
+    for (sh, neg, acc, p), line in zip(cases, run(fxbin, lines)):
+        got = value([int(t) for t in line.split()])
+        want = (acc + (-(p >> sh) if neg else (p >> sh))) % mod
+        assert got == want, (sh, neg)
