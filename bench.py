@@ -41,6 +41,9 @@ SM_MAX_MHZ = 2070.0               # profiling recipe / MEASURED_PEAKS.json
 FP64_PEAK = SM_COUNT * FP64_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # FP64 instructions per second
 PINNED_MAC_OPS = {2: 27, 4: 218}  # DD / QD multiply then add of the Simple kernel
 INT8_MMA_PEAK = 1.50e14           # mma.sync m16n8k32 s8 ops/s, measured by the same probe
+HBM_GBS = 6790.7                  # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
+ISSUE_PER_CLK_PER_SM = 4 * 32     # 4 schedulers x one warp instruction (32 lanes) per clock
+ISSUE_PEAK = SM_COUNT * ISSUE_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # thread instructions per second
 
 
 def parse():
@@ -224,11 +227,11 @@ def run_reference(args, w):
 
 
 # ----------------------------------------------------------------- GPU leg --
-def traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json),
-    or None when the kernel's sources changed since the counters were taken."""
+def profile_record(kernel: str):
+    """The committed ncu counters of a Block leaf launch (profiles/block_fx_counts.json),
+    or None when the kernel's sources changed since they were taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "block_fx_counts.json")
     try:
         rec = json.load(open(path))[kernel]
         h = hashlib.sha256()
@@ -236,14 +239,17 @@ def traffic_for(kernel: str):
             h.update(open(os.path.join(ROOT, f), "rb").read())
         if h.hexdigest() != rec["sources_sha256"]:
             return None
-        return rec["bytes_per_launch"]
+        return rec
     except (OSError, KeyError, ValueError):
         return None
 
 
 def roofline_of(prof, limbs):
-    """Dominant kernel: the Block base case (FP64 instructions per busy
-    second) or, for the INT8-slice product, its slice GEMM (INT8 ops)."""
+    """Dominant kernel: the Block base case (thread instructions issued per
+    busy second, from its multiply-adds and the committed ncu count of
+    instructions per multiply-add, against the SM issue rate) or, for the
+    INT8 products, the INT8 GEMM (INT8 ops against the measured mma.sync
+    peak)."""
     oz = prof.get("ozaki")
     if oz and oz["launches"]:
         achieved = oz["ops"] / (oz["busy_ms"] * 1e-3)
@@ -257,21 +263,27 @@ def roofline_of(prof, limbs):
     b = prof["block"]
     if not b["launches"]:
         return None
-    achieved = b["ops"] / (b["busy_ms"] * 1e-3)
+    macs_per_s = b["ops"] / (b["busy_ms"] * 1e-3)  # kind 1 counts multiply-adds
     avg_ms = b["sum_ms"] / b["launches"]
-    from paper_1510_08642_gb300 import capi
-    ops_mac = capi.ddg_block_fp64_ops_per_mac(limbs, 0)
-    return {"bound": "alu", "kernel": f"block_fx_kernel<{limbs}> (FP64 pipe + exact integer accumulation)",
-            "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "T FP64-instr/s",
-            "frac": achieved / FP64_PEAK,
-            "traffic": traffic_for("block_fx_kernel<2>") if limbs == 2 else None,
-            "traffic_note": "DRAM bytes per 512^3 leaf launch (ncu, profiles/traffic.json); "
-                            "algorithmic 12.6 MB per leaf",
-            "peak_source": f"derived: {SM_COUNT} SMs x {FP64_PER_CLK_PER_SM} FP64 instr/clk (measured "
-                           f"by the DFMA probe) x {SM_MAX_MHZ:.0f} MHz; no FP64 figure in MEASURED_PEAKS.json",
-            "fp64_ops_per_mac": ops_mac, "pinned_mac_ops": PINNED_MAC_OPS[limbs],
-            "launches": int(b["launches"]), "avg_launch_ms": avg_ms, "busy_ms": b["busy_ms"],
-            "sum_launch_ms": b["sum_ms"]}
+    kernel = f"block_fx_kernel<{limbs}>"
+    rec = profile_record(kernel)
+    out = {"bound": "alu", "kernel": f"{kernel} (multiply-add on the integer pipe, no FP64)",
+           "peak": ISSUE_PEAK / 1e12, "unit": "T instr/s",
+           "peak_source": f"derived: {SM_COUNT} SMs x 4 schedulers x 32 lanes (one warp instruction "
+                          f"per scheduler per clock) x {SM_MAX_MHZ:.0f} MHz",
+           "macs_per_s": macs_per_s, "launches": int(b["launches"]), "avg_launch_ms": avg_ms,
+           "busy_ms": b["busy_ms"], "sum_launch_ms": b["sum_ms"]}
+    if rec is None:
+        out.update({"achieved": None, "frac": None, "traffic": None,
+                    "note": "kernel sources changed since the committed ncu counts"})
+        return out
+    achieved = macs_per_s * rec["inst_per_mac"]
+    out.update({"achieved": achieved / 1e12, "frac": achieved / ISSUE_PEAK,
+                "inst_per_mac": rec["inst_per_mac"],
+                "traffic": rec.get("dram_bytes_per_launch"),
+                "traffic_note": rec.get("dram_note"),
+                "counts_source": "profiles/block_fx_counts.json (ncu, same sources)"})
+    return out
 
 
 def time_gpu(P, torch, w, dA, dB, dC, cutoff, steps, warmup, stream, dist=None, device=None,
@@ -444,12 +456,13 @@ def run_ours(args, w):
     line["fp64_roofline_2mnl"] = {
         "value": 2.0 * FP64_PEAK / PINNED_MAC_OPS[limbs] / 1e9,
         "frac": value / world / (2.0 * FP64_PEAK / PINNED_MAC_OPS[limbs] / 1e9),
-        "note": "2 x FP64 peak / FP64 instructions of the pinned DD multiply-add (27)"}
+        "note": "2 x FP64 peak / FP64 instructions of the pinned multiply-add (DD 27, QD 218)"}
     passes = prof["pass"]
     if passes["launches"]:
         line["passes"] = {"launches": int(passes["launches"]), "busy_ms": passes["busy_ms"] / args.steps,
                           "GB_per_s": passes["bytes"] / (passes["busy_ms"] * 1e-3) / 1e9,
-                          "fp64_frac": passes["ops"] / (passes["busy_ms"] * 1e-3) / FP64_PEAK}
+                          "hbm_frac": passes["bytes"] / (passes["busy_ms"] * 1e-3) / 1e9 / HBM_GBS,
+                          "sums_per_s": passes["ops"] / (passes["busy_ms"] * 1e-3)}
     del dA, dB, dC, hA, hB, hC
     torch.cuda.empty_cache()
 

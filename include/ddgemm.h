@@ -284,9 +284,9 @@ typedef struct {
   uint64_t launches;
   double sum_ms;
   double busy_ms;
-  double ops;   /* FP64 instructions (kinds 0 and 2), multiply-adds (kind 1)
-                   or INT8 operations, 2 per multiply-add (kind 3, the INT8
-                   products) */
+  double ops;   /* FP64 instructions (kind 0), multiply-adds (kind 1), DD / QD
+                   sums (kind 2) or INT8 operations, 2 per multiply-add
+                   (kind 3, the INT8 products) */
   double bytes;
 } ddg_kernel_prof;
 ddg_status ddg_profile_begin(void);

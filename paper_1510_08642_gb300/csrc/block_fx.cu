@@ -36,7 +36,7 @@ template <> struct fxcfg<2> {
   static constexpr int LSB0 = -2204;  // window LSB exponent = row_f + col_f + LSB0
 };
 template <> struct fxcfg<4> {
-  static constexpr int BM = 8, BN = 32, BK = 8, TM = 1, TN = 2, NW = 9;
+  static constexpr int BM = 8, BN = 32, BK = 16, TM = 1, TN = 2, NW = 9;
   static constexpr int W = 7, D = 6, K = 2 * W - D;
   static constexpr int MINB = 8;
   static constexpr int LSB0 = -2300;
@@ -50,15 +50,16 @@ __device__ __forceinline__ double scaled(uint64_t chunk, int k, uint32_t neg) {
 
 }  // namespace
 
-// Operand tiles in fixed-point form: the W words of each element stored
-// contiguously (padded to WV 16-byte vectors), and per element its shift
+// Operand tiles in fixed-point form: the W words of each element as WV
+// 16-byte vectors (vector v of all elements in one plane, so that a warp's
+// reads of consecutive elements are consecutive), and per element its shift
 // below the largest exponent of its row (A) / column (B) and its sign mask.
 // The A tile is padded by one row: its staging writes run along k.
 template <int L>
 struct fx_smem {
   static constexpr int WV = (fxcfg<L>::W + 3) / 4;
-  uint4 Aw[fxcfg<L>::BK][fxcfg<L>::BM + 1][WV];
-  uint4 Bw[fxcfg<L>::BK][fxcfg<L>::BN][WV];
+  uint4 Aw[WV][fxcfg<L>::BK][fxcfg<L>::BM + 1];
+  uint4 Bw[WV][fxcfg<L>::BK][fxcfg<L>::BN];
   int2 Ae[fxcfg<L>::BK][fxcfg<L>::BM + 1];
   int2 Be[fxcfg<L>::BK][fxcfg<L>::BN];
   int row_f[fxcfg<L>::BM], col_f[fxcfg<L>::BN];
@@ -69,7 +70,7 @@ namespace {
 // Convert one element and store its words, shift and sign mask; a zero gets
 // shift 0 (its products are zero and stay on the fast path).
 template <int L>
-__device__ __forceinline__ void stage(const double (&x)[L], int fmax, uint4* w, int2* e) {
+__device__ __forceinline__ void stage(const double (&x)[L], int fmax, uint4* w, int stride, int2* e) {
   constexpr int W = fxcfg<L>::W, WV = (W + 3) / 4;
   uint32_t M[4 * WV];
   uint32_t(&Mw)[W] = *reinterpret_cast<uint32_t(*)[W]>(M);
@@ -78,7 +79,7 @@ __device__ __forceinline__ void stage(const double (&x)[L], int fmax, uint4* w, 
   for (int t = W; t < 4 * WV; ++t) M[t] = 0u;
   const bool zero = (fx::dbits(x[0]) << 1) == 0u;
 #pragma unroll
-  for (int v = 0; v < WV; ++v) w[v] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
+  for (int v = 0; v < WV; ++v) w[v * stride] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
   *e = make_int2(zero ? 0 : fmax - (es & 0xFFFF), (es >> 16) ? -1 : 0);
 }
 
@@ -137,7 +138,7 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
       double x[L];
 #pragma unroll
       for (int q = 0; q < L; ++q) x[q] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
-      stage<L>(x, row_f[r], sm.Aw[c][r], &sm.Ae[c][r]);
+      stage<L>(x, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
     }
 #pragma unroll
     for (int idx = tid; idx < BK * BN; idx += NT) {
@@ -147,7 +148,7 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
       double x[L];
 #pragma unroll
       for (int q = 0; q < L; ++q) x[q] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
-      stage<L>(x, col_f[c], sm.Bw[r][c], &sm.Be[r][c]);
+      stage<L>(x, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
     }
     __syncthreads();
 #pragma unroll 1
@@ -158,7 +159,7 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
       for (int r = 0; r < TM; ++r) {
 #pragma unroll
         for (int v = 0; v < WV; ++v) {
-          const uint4 q = sm.Aw[kk][ty + r * NY][v];
+          const uint4 q = sm.Aw[v][kk][ty + r * NY];
           a[r][4 * v] = q.x; a[r][4 * v + 1] = q.y; a[r][4 * v + 2] = q.z; a[r][4 * v + 3] = q.w;
         }
         ea[r] = sm.Ae[kk][ty + r * NY];
@@ -167,7 +168,7 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
       for (int c = 0; c < TN; ++c) {
 #pragma unroll
         for (int v = 0; v < WV; ++v) {
-          const uint4 q = sm.Bw[kk][tx + c * NX][v];
+          const uint4 q = sm.Bw[v][kk][tx + c * NX];
           b[c][4 * v] = q.x; b[c][4 * v + 1] = q.y; b[c][4 * v + 2] = q.z; b[c][4 * v + 3] = q.w;
         }
         eb[c] = sm.Be[kk][tx + c * NX];

@@ -346,7 +346,7 @@ __host__ __device__ __forceinline__ void mul_top(const uint32_t (&a)[W], const u
 #ifdef __CUDA_ARCH__
       asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
           "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
-          "addc.u32 %2, %2, 0;"
+          "madc.lo.u32 %2, %2, 1, 0;"
           : "+r"(c0), "+r"(c1), "+r"(c2)
           : "r"(a[i]), "r"(b[j]));
 #else
@@ -382,27 +382,27 @@ __host__ __device__ __forceinline__ void acc_add_mask(uint32_t (&A)[NW], const u
   if constexpr (NW == 6) {
     asm("{\n\t.reg .u32 t;\n\t"
         "add.cc.u32 t, %6, %6;\n\t"  // carry = top bit of the mask
-        "addc.cc.u32 %0, %0, %7;\n\t"
-        "addc.cc.u32 %1, %1, %8;\n\t"
-        "addc.cc.u32 %2, %2, %9;\n\t"
-        "addc.cc.u32 %3, %3, %10;\n\t"
-        "addc.cc.u32 %4, %4, %11;\n\t"
-        "addc.u32 %5, %5, %12;\n\t}"
+        "madc.lo.cc.u32 %0, %7, 1, %0;\n\t"
+        "madc.lo.cc.u32 %1, %8, 1, %1;\n\t"
+        "madc.lo.cc.u32 %2, %9, 1, %2;\n\t"
+        "madc.lo.cc.u32 %3, %10, 1, %3;\n\t"
+        "madc.lo.cc.u32 %4, %11, 1, %4;\n\t"
+        "madc.lo.u32 %5, %12, 1, %5;\n\t}"
         : "+r"(A[0]), "+r"(A[1]), "+r"(A[2]), "+r"(A[3]), "+r"(A[4]), "+r"(A[5])
         : "r"(m), "r"(d[0] ^ m), "r"(d[1] ^ m), "r"(d[2] ^ m), "r"(d[3] ^ m), "r"(d[4] ^ m),
           "r"(d[5] ^ m));
   } else if constexpr (NW == 9) {
     asm("{\n\t.reg .u32 t;\n\t"
         "add.cc.u32 t, %9, %9;\n\t"
-        "addc.cc.u32 %0, %0, %10;\n\t"
-        "addc.cc.u32 %1, %1, %11;\n\t"
-        "addc.cc.u32 %2, %2, %12;\n\t"
-        "addc.cc.u32 %3, %3, %13;\n\t"
-        "addc.cc.u32 %4, %4, %14;\n\t"
-        "addc.cc.u32 %5, %5, %15;\n\t"
-        "addc.cc.u32 %6, %6, %16;\n\t"
-        "addc.cc.u32 %7, %7, %17;\n\t"
-        "addc.u32 %8, %8, %18;\n\t}"
+        "madc.lo.cc.u32 %0, %10, 1, %0;\n\t"
+        "madc.lo.cc.u32 %1, %11, 1, %1;\n\t"
+        "madc.lo.cc.u32 %2, %12, 1, %2;\n\t"
+        "madc.lo.cc.u32 %3, %13, 1, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, 1, %4;\n\t"
+        "madc.lo.cc.u32 %5, %15, 1, %5;\n\t"
+        "madc.lo.cc.u32 %6, %16, 1, %6;\n\t"
+        "madc.lo.cc.u32 %7, %17, 1, %7;\n\t"
+        "madc.lo.u32 %8, %18, 1, %8;\n\t}"
         : "+r"(A[0]), "+r"(A[1]), "+r"(A[2]), "+r"(A[3]), "+r"(A[4]), "+r"(A[5]), "+r"(A[6]),
           "+r"(A[7]), "+r"(A[8])
         : "r"(m), "r"(d[0] ^ m), "r"(d[1] ^ m), "r"(d[2] ^ m), "r"(d[3] ^ m), "r"(d[4] ^ m),
@@ -447,6 +447,105 @@ __host__ __device__ __forceinline__ void place_shr(uint32_t (&A)[NW], const uint
     }
   }
   acc_add_mask<NW>(A, d, m);
+}
+
+// ---------------------------------------------------------------------------
+// Exact sums of DD / QD numbers (the quadrant passes).
+//
+// All operands of one element are placed at a common scale, unit
+// 2^(emax - 1075 - top) with emax the largest leading-limb exponent field
+// among them, as signed NW-word integers (limbs below bit 0 truncated toward
+// zero: 2^-(top + 52) of the largest operand); sums and differences are then
+// exact multiword additions, and each result is converted back once.
+
+// V += sign * x (x an expansion of L limbs) at the common scale.
+template <int L, int NW>
+__host__ __device__ __forceinline__ void add_at(uint32_t (&V)[NW], const double (&x)[L], int emax, int top,
+                                                uint32_t negate) {
+#pragma unroll
+  for (int q = 0; q < L; ++q) {
+    const unpacked u = unpack(x[q]);
+    uint64_t m = ((uint64_t)u.m1 << 32) | u.m0;
+    int sh = (u.e - emax) + top;
+    if (m == 0u || sh <= -53) continue;
+    if (sh < 0) {
+      m >>= -sh;
+      sh = 0;
+    }
+    const int wo = sh >> 5, r = sh & 31;
+    const uint32_t p0 = (uint32_t)m << r;
+    const uint32_t p1 = shl_funnel((uint32_t)m, (uint32_t)(m >> 32), r);
+    const uint32_t p2 = shl_funnel((uint32_t)(m >> 32), 0u, r);
+    const uint32_t msk = 0u - (u.s ^ negate);
+    uint64_t c = msk & 1u;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      const uint32_t d = w == wo ? p0 : (w == wo + 1 ? p1 : (w == wo + 2 ? p2 : 0u));
+      const uint64_t v = (uint64_t)V[w] + (d ^ msk) + c;
+      V[w] = (uint32_t)v;
+      c = v >> 32;
+    }
+  }
+}
+
+// R = X + Y or X - Y (two's complement, NW words).
+template <int NW>
+__host__ __device__ __forceinline__ void vadd(uint32_t (&R)[NW], const uint32_t (&X)[NW], const uint32_t (&Y)[NW],
+                                              bool sub) {
+  const uint32_t msk = sub ? 0xFFFFFFFFu : 0u;
+  uint64_t c = sub ? 1u : 0u;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const uint64_t v = (uint64_t)X[w] + (Y[w] ^ msk) + c;
+    R[w] = (uint32_t)v;
+    c = v >> 32;
+  }
+}
+
+// mag 2^e2 with the sign bit neg as a double (mag < 2^54): the bit pattern
+// is assembled on the integer pipe when the result is a normal number; other
+// cases take the FP64 scaling.
+__host__ __device__ __forceinline__ double make_double(uint64_t mag, int e2, uint32_t neg) {
+  if (mag == 0u) return neg ? -0.0 : 0.0;
+  const int lz = clz32((uint32_t)(mag >> 32)) + ((mag >> 32) == 0u ? clz32((uint32_t)mag) : 0);
+  const int sh = 11 - lz;  // leading one to bit 52
+  const uint64_t m = sh >= 0 ? (mag >> sh) : (mag << -sh);
+  const int be = e2 + sh + 1075;
+  if (be >= 1 && be <= 2046 && (sh <= 0 || (mag & ((1ull << sh) - 1u)) == 0u))
+    return bitsd(((uint64_t)neg << 63) | ((uint64_t)be << 52) | (m & 0xFFFFFFFFFFFFFull));
+  const double v = pow2_product((double)mag, e2 < -2044 ? -2044 : (e2 > 2046 ? 2046 : e2));
+  return neg ? -v : v;
+}
+
+// The L-limb expansion nearest the signed integer V 2^lsb (V is destroyed):
+// the leading L 53-bit pieces of |V| and the next bit, turned into balanced
+// digits from the least significant end (a digit >= 2^52 becomes digit -
+// 2^53 and carries one into the next), so the leading limb is |V| rounded to
+// 53 bits and each further limb is at most half a unit of the one above.
+// Bits below the L + 1 pieces are truncated. For L = 2 this is the DD
+// nearest V (hi = V rounded to 53 bits, |lo| <= ulp(hi) / 2).
+template <int L, int NW>
+__host__ __device__ __forceinline__ void from_fixed(uint32_t (&V)[NW], int lsb, double (&out)[L]) {
+  const uint32_t neg = acc_abs<NW>(V);
+  uint64_t ch[L + 1];
+  int ex[L + 1];
+  if (!acc_chunks<NW, L + 1>(V, ch, ex)) {
+#pragma unroll
+    for (int q = 0; q < L; ++q) out[q] = 0.0;
+    return;
+  }
+  uint64_t c = ch[L] >> 52;  // the bit after the last piece
+#pragma unroll
+  for (int q = L - 1; q >= 0; --q) {
+    int64_t v = (int64_t)ch[q] + (int64_t)c;
+    c = 0u;
+    if (q > 0 && v >= (int64_t)1 << 52) {
+      v -= (int64_t)1 << 53;
+      c = 1u;
+    }
+    const uint32_t dn = v < 0 ? 1u : 0u;
+    out[q] = make_double((uint64_t)(v < 0 ? -v : v), lsb + ex[q], neg ^ dn);
+  }
 }
 
 }  // namespace fx

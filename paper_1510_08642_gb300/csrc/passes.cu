@@ -19,80 +19,157 @@
 //   M7 = (A12 - A22)(B21 + B22)
 //   C11 = M1 + M4 - M5 + M7, C12 = M3 + M5, C21 = M2 + M4,
 //   C22 = M1 - M2 + M3 + M6
-// Every sum is the accurate DD / QD addition of arith.cuh. On GB300 these
-// passes are FP64-issue bound rather than HBM bound (20 FP64 instructions per
-// DD sum against 48 bytes moved); they are O(n^2) against the O(n^3)
-// products.
+// Every sum is exact in fixed point on the integer pipe (one rounding per
+// output): the accurate DD / QD additions of arith.cuh cost 20 / 91 FP64
+// instructions each, which made these O(n^2) passes FP64-issue bound on
+// GB300 rather than HBM bound.
 #include <algorithm>
 
 #include "arith.cuh"
+#include "fx.cuh"
 #include "kernels.cuh"
 
 namespace ddg {
 
 
-// One element (i, j) of a fused pass.
+// Fixed-point width per limb count: NW words, the largest operand's leading
+// significand at bit TOP (headroom for sums of up to 8 operands below the
+// sign bit).
+template <int L> struct pfx;
+template <> struct pfx<2> { static constexpr int NW = 5, TOP = 32 * 5 - 58; };
+template <> struct pfx<4> { static constexpr int NW = 9, TOP = 32 * 9 - 58; };
+
+// One element (i, j) of a fused pass. The operands (and C for the update
+// modes) are placed at one common scale as exact integers on the integer
+// pipe (fx::add_at), every sum of the pass is an exact multiword addition,
+// and each output is rounded back once (fx::from_fixed; QD limbs then
+// renormalised). Error per output: one rounding to DD / QD (a DD output is
+// the DD nearest the exact sum, up to 2^-(top + 52) of the largest operand).
 template <int L, int KIND>
 __device__ __forceinline__ void pass_elem(const pass_args& a, int mode, int64_t i, int64_t j) {
   using N = num<L>;
   using T = typename N::T;
-  auto ld = [&](int q) { return N::load(a.in[q].p, i * a.in[q].ld + j); };
-  auto st = [&](int q, const T& v) { N::store(a.out[q].p, i * a.out[q].ld + j, v); };
-  auto st_mode = [&](int q, const T& v) {
-    const int64_t off = i * a.out[q].ld + j;
-    if (mode == MODE_SET) N::store(a.out[q].p, off, v);
-    else if (mode == MODE_ADD) N::store(a.out[q].p, off, N::add(N::load(a.out[q].p, off), v));
-    else N::store(a.out[q].p, off, N::add(N::load(a.out[q].p, off), N::neg(v)));
+  constexpr int NW = pfx<L>::NW, TOP = pfx<L>::TOP;
+  using V = uint32_t[NW];
+  constexpr int NIN = (KIND == PASS_WINOGRAD_C || KIND == PASS_STRASSEN_C) ? 7 : (KIND == PASS_COMBINE ? 1 : 4);
+  constexpr int NOUT = (KIND == PASS_STRASSEN_A || KIND == PASS_STRASSEN_B) ? 5 : (KIND == PASS_COMBINE ? 1 : 4);
+  constexpr bool UPD = KIND == PASS_WINOGRAD_C || KIND == PASS_STRASSEN_C || KIND == PASS_COMBINE;
+  const bool upd = UPD && mode != MODE_SET;
+  double x[NIN][L], c[NOUT][L];
+#pragma unroll
+  for (int q = 0; q < NIN; ++q) {
+    const int64_t off = i * a.in[q].ld + j;
+#pragma unroll
+    for (int t = 0; t < L; ++t) x[q][t] = a.in[q].p[t][off];
+  }
+  int emax = 1;
+#pragma unroll
+  for (int q = 0; q < NIN; ++q) emax = max(emax, fx::expfield(x[q][0]));
+  if (upd) {
+#pragma unroll
+    for (int q = 0; q < NOUT; ++q) {
+      const int64_t off = i * a.out[q].ld + j;
+#pragma unroll
+      for (int t = 0; t < L; ++t) c[q][t] = a.out[q].p[t][off];
+      emax = max(emax, fx::expfield(c[q][0]));
+    }
+  }
+  V X[NIN];
+#pragma unroll
+  for (int q = 0; q < NIN; ++q) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) X[q][w] = 0u;
+    fx::add_at<L, NW>(X[q], x[q], emax, TOP, 0u);
+  }
+  const int lsb = emax - 1075 - TOP;
+  auto put = [&](int q, V& r) {
+    if (UPD && upd) {
+      if (mode == MODE_SUB) {  // r := -r, then + C: C - sum
+        uint32_t cy = 1u;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const uint64_t v = (uint64_t)(~r[w]) + cy;
+          r[w] = (uint32_t)v;
+          cy = (uint32_t)(v >> 32);
+        }
+      }
+      fx::add_at<L, NW>(r, c[q], emax, TOP, 0u);
+    }
+    double o[L];
+    fx::from_fixed<L, NW>(r, lsb, o);
+    T v;
+    if constexpr (L == 2) {
+      v = dd_t{o[0], o[1]};
+    } else {
+      v = qd_renorm<4>(o);
+    }
+    N::store(a.out[q].p, i * a.out[q].ld + j, v);
   };
-  auto add = [](const T& x, const T& y) { return N::add(x, y); };
-  auto sub = [](const T& x, const T& y) { return N::add(x, N::neg(y)); };
+  V r0, r1, r2;
   if constexpr (KIND == PASS_WINOGRAD_A) {
-    const T x11 = ld(0), x12 = ld(1), x21 = ld(2), x22 = ld(3);
-    const T s1 = add(x21, x22);
-    const T s2 = sub(s1, x11);
-    st(0, s1);
-    st(1, s2);
-    st(2, sub(x11, x21));
-    st(3, sub(x12, s2));
+    // x: A11, A12, A21, A22 -> S1, S2, S3, S4
+    fx::vadd<NW>(r0, X[2], X[3], false);  // S1 = A21 + A22
+    fx::vadd<NW>(r1, r0, X[0], true);     // S2 = S1 - A11
+    fx::vadd<NW>(r2, X[1], r1, true);     // S4 = A12 - S2
+    put(0, r0);
+    put(1, r1);
+    put(3, r2);
+    fx::vadd<NW>(r0, X[0], X[2], true);   // S3 = A11 - A21
+    put(2, r0);
   } else if constexpr (KIND == PASS_WINOGRAD_B) {
-    const T x11 = ld(0), x12 = ld(1), x21 = ld(2), x22 = ld(3);
-    const T t1 = sub(x12, x11);
-    const T t2 = sub(x22, t1);
-    st(0, t1);
-    st(1, t2);
-    st(2, sub(x22, x12));
-    st(3, sub(t2, x21));
+    // x: B11, B12, B21, B22 -> T1, T2, T3, T4
+    fx::vadd<NW>(r0, X[1], X[0], true);   // T1 = B12 - B11
+    fx::vadd<NW>(r1, X[3], r0, true);     // T2 = B22 - T1
+    fx::vadd<NW>(r2, r1, X[2], true);     // T4 = T2 - B21
+    put(0, r0);
+    put(1, r1);
+    put(3, r2);
+    fx::vadd<NW>(r0, X[3], X[1], true);   // T3 = B22 - B12
+    put(2, r0);
   } else if constexpr (KIND == PASS_WINOGRAD_C) {
-    const T p1 = ld(0), p2 = ld(1), p3 = ld(2), p4 = ld(3), p5 = ld(4), p6 = ld(5), p7 = ld(6);
-    const T u2 = add(p1, p6);
-    const T u3 = add(u2, p7);
-    const T u4 = add(u2, p5);
-    st_mode(0, add(p1, p2));
-    st_mode(1, add(u4, p3));
-    st_mode(2, sub(u3, p4));
-    st_mode(3, add(u3, p5));
+    // x: P1 .. P7 -> C11, C12, C21, C22 (mode)
+    V u2, u3;
+    fx::vadd<NW>(u2, X[0], X[5], false);  // U2 = P1 + P6
+    fx::vadd<NW>(u3, u2, X[6], false);    // U3 = U2 + P7
+    fx::vadd<NW>(r0, X[0], X[1], false);  // C11 = P1 + P2
+    put(0, r0);
+    fx::vadd<NW>(r0, u2, X[4], false);    // U4 = U2 + P5
+    fx::vadd<NW>(r1, r0, X[2], false);    // C12 = U4 + P3
+    put(1, r1);
+    fx::vadd<NW>(r0, u3, X[3], true);     // C21 = U3 - P4
+    put(2, r0);
+    fx::vadd<NW>(r0, u3, X[4], false);    // C22 = U3 + P5
+    put(3, r0);
   } else if constexpr (KIND == PASS_STRASSEN_A) {
-    const T x11 = ld(0), x12 = ld(1), x21 = ld(2), x22 = ld(3);
-    st(0, add(x11, x22));
-    st(1, add(x21, x22));
-    st(2, add(x11, x12));
-    st(3, sub(x21, x11));
-    st(4, sub(x12, x22));
+    // x: A11, A12, A21, A22
+    fx::vadd<NW>(r0, X[0], X[3], false); put(0, r0);  // A11 + A22
+    fx::vadd<NW>(r0, X[2], X[3], false); put(1, r0);  // A21 + A22
+    fx::vadd<NW>(r0, X[0], X[1], false); put(2, r0);  // A11 + A12
+    fx::vadd<NW>(r0, X[2], X[0], true);  put(3, r0);  // A21 - A11
+    fx::vadd<NW>(r0, X[1], X[3], true);  put(4, r0);  // A12 - A22
   } else if constexpr (KIND == PASS_STRASSEN_B) {
-    const T x11 = ld(0), x12 = ld(1), x21 = ld(2), x22 = ld(3);
-    st(0, add(x11, x22));
-    st(1, sub(x12, x22));
-    st(2, sub(x21, x11));
-    st(3, add(x11, x12));
-    st(4, add(x21, x22));
+    // x: B11, B12, B21, B22
+    fx::vadd<NW>(r0, X[0], X[3], false); put(0, r0);  // B11 + B22
+    fx::vadd<NW>(r0, X[1], X[3], true);  put(1, r0);  // B12 - B22
+    fx::vadd<NW>(r0, X[2], X[0], true);  put(2, r0);  // B21 - B11
+    fx::vadd<NW>(r0, X[0], X[1], false); put(3, r0);  // B11 + B12
+    fx::vadd<NW>(r0, X[2], X[3], false); put(4, r0);  // B21 + B22
   } else if constexpr (KIND == PASS_STRASSEN_C) {
-    const T m1 = ld(0), m2 = ld(1), m3 = ld(2), m4 = ld(3), m5 = ld(4), m6 = ld(5), m7 = ld(6);
-    st_mode(0, add(sub(add(m1, m4), m5), m7));
-    st_mode(1, add(m3, m5));
-    st_mode(2, add(m2, m4));
-    st_mode(3, add(add(sub(m1, m2), m3), m6));
+    // x: M1 .. M7
+    fx::vadd<NW>(r0, X[0], X[3], false);  // M1 + M4
+    fx::vadd<NW>(r1, r0, X[4], true);     // - M5
+    fx::vadd<NW>(r0, r1, X[6], false);    // + M7
+    put(0, r0);
+    fx::vadd<NW>(r0, X[2], X[4], false); put(1, r0);  // M3 + M5
+    fx::vadd<NW>(r0, X[1], X[3], false); put(2, r0);  // M2 + M4
+    fx::vadd<NW>(r0, X[0], X[1], true);   // M1 - M2
+    fx::vadd<NW>(r1, r0, X[2], false);    // + M3
+    fx::vadd<NW>(r0, r1, X[5], false);    // + M6
+    put(3, r0);
   } else {  // PASS_COMBINE
-    st_mode(0, ld(0));
+#pragma unroll
+    for (int w = 0; w < NW; ++w) r0[w] = X[0][w];
+    put(0, r0);
   }
 }
 
@@ -185,13 +262,14 @@ cudaError_t launch_pass(int limbs, int kind, int64_t rows, int64_t cols, const m
     const int nadd = adds[kind] + (upd ? nout : 0);
     const double elems = (double)rows * (double)cols;
     const double moved = (double)(nin + nout + (upd ? nout : 0));
-    prof_end_launch(s, ev, PROF_PASS, elems * nadd * add_fp64_ops(limbs), elems * moved * limbs * 8.0);
+    prof_end_launch(s, ev, PROF_PASS, elems * nadd, elems * moved * limbs * 8.0);
   }
   return e;
 }
 
-// FP64 instructions of one accurate sum: DD 20 (two TwoSums, two FastTwoSums,
-// two adds); QD: the merge compares 7 and two 7-step TwoSum chains 84.
+// FP64 instructions of one accurate DD / QD sum of arith.cuh (DD 20: two
+// TwoSums, two FastTwoSums, two adds; QD: the merge compares 7 and two
+// 7-step TwoSum chains 84), which the fixed-point passes replace.
 int add_fp64_ops(int limbs) { return limbs == 2 ? 20 : 91; }
 
 }  // namespace ddg

@@ -27,7 +27,7 @@ class Workload:
 # algorithm, Table 1), cutoff chosen by the cutoff sweep.
 DD_WINOGRAD_4096 = Workload("dd_winograd_n4096", 2, 4096, "winograd", 512, 101, 102)
 DD_BLOCK_4096 = Workload("dd_block_n4096", 2, 4096, "block", 512, 101, 102)
-QD_WINOGRAD_4096 = Workload("qd_winograd_n4096", 4, 4096, "winograd", 256, 103, 104)
+QD_WINOGRAD_4096 = Workload("qd_winograd_n4096", 4, 4096, "winograd", 512, 103, 104)
 QD_BLOCK_4096 = Workload("qd_block_n4096", 4, 4096, "block", 512, 103, 104)
 # The small case the oracle finishes in well under a second (Simple, n = 128).
 DD_SIMPLE_128 = Workload("dd_simple_n128", 2, 128, "simple", 512, 0, 1)

@@ -4,18 +4,26 @@
 //   T L x0 .. x(L-1)          -> to_fixed: es M[0] .. M[W-1]   (W = 4 / 7)
 //   M W D a[0..W-1] b[0..W-1]  -> mul_top: p[0 .. 2W-D-1]
 //   P NW K sh neg acc[0..NW-1] p[0..K-1] -> place_shr: acc[0 .. NW-1]
+//   A L emax top n (sign x0 .. x(L-1)) x n -> add_at into V (NW = 5 / 9),
+//                              then from_fixed: V[0..NW-1] ; limbs (hex)
 // Doubles are read as 16 hex digits of their bit pattern.
 #include <cinttypes>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "fx.cuh"
 
 using namespace ddg;
 
+template <class... A>
+static void scan(const char* f, A... a) {
+  if (std::scanf(f, a...) != (int)sizeof...(A)) std::exit(2);
+}
+
 static double rd() {
   unsigned long long b;
-  if (std::scanf("%llx", &b) != 1) return 0.0;
+  scan("%llx", &b);
   return fx::bitsd(b);
 }
 
@@ -33,8 +41,8 @@ static void do_fixed() {
 template <int W, int D>
 static void do_mul() {
   uint32_t a[W], b[W], p[2 * W - D];
-  for (int i = 0; i < W; ++i) std::scanf("%u", &a[i]);
-  for (int i = 0; i < W; ++i) std::scanf("%u", &b[i]);
+  for (int i = 0; i < W; ++i) scan("%u", &a[i]);
+  for (int i = 0; i < W; ++i) scan("%u", &b[i]);
   fx::mul_top<W, D>(a, b, p);
   for (int i = 0; i < 2 * W - D; ++i) std::printf("%u%c", p[i], i + 1 < 2 * W - D ? ' ' : '\n');
 }
@@ -43,12 +51,32 @@ template <int NW, int K>
 static void do_place() {
   int sh;
   unsigned neg;
-  std::scanf("%d %u", &sh, &neg);
+  scan("%d %u", &sh, &neg);
   uint32_t acc[NW], p[K];
-  for (int i = 0; i < NW; ++i) std::scanf("%u", &acc[i]);
-  for (int i = 0; i < K; ++i) std::scanf("%u", &p[i]);
+  for (int i = 0; i < NW; ++i) scan("%u", &acc[i]);
+  for (int i = 0; i < K; ++i) scan("%u", &p[i]);
   fx::place_shr<NW, K>(acc, p, sh, neg ? 0xFFFFFFFFu : 0u);
   for (int i = 0; i < NW; ++i) std::printf("%u%c", acc[i], i + 1 < NW ? ' ' : '\n');
+}
+
+template <int L, int NW>
+static void do_sum() {
+  int emax, top, n;
+  scan("%d %d %d", &emax, &top, &n);
+  uint32_t V[NW] = {0};
+  for (int i = 0; i < n; ++i) {
+    unsigned sg;
+    scan("%u", &sg);
+    double x[L];
+    for (int q = 0; q < L; ++q) x[q] = rd();
+    fx::add_at<L, NW>(V, x, emax, top, sg);
+  }
+  for (int w = 0; w < NW; ++w) std::printf("%u ", V[w]);
+  double out[L];
+  fx::from_fixed<L, NW>(V, emax - 1075 - top, out);
+  std::printf(";");
+  for (int q = 0; q < L; ++q) std::printf(" %016llx", (unsigned long long)fx::dbits(out[q]));
+  std::printf("\n");
 }
 
 int main() {
@@ -56,15 +84,19 @@ int main() {
   while (std::scanf("%3s", cmd) == 1) {
     int a, b;
     if (cmd[0] == 'T') {
-      std::scanf("%d", &a);
+      scan("%d", &a);
       if (a == 2) do_fixed<2, 4>();
       else do_fixed<4, 7>();
     } else if (cmd[0] == 'M') {
-      std::scanf("%d %d", &a, &b);
+      scan("%d %d", &a, &b);
       if (a == 4) do_mul<4, 3>();
       else do_mul<7, 6>();
+    } else if (cmd[0] == 'A') {
+      scan("%d", &a);
+      if (a == 2) do_sum<2, 5>();
+      else do_sum<4, 9>();
     } else if (cmd[0] == 'P') {
-      std::scanf("%d %d", &a, &b);
+      scan("%d %d", &a, &b);
       if (a == 6) do_place<6, 5>();
       else do_place<9, 8>();
     }

@@ -116,3 +116,56 @@ def test_place_shr_exact(fxbin, NW, K):
         got = value([int(t) for t in line.split()])
         want = (acc + (-(p >> sh) if neg else (p >> sh))) % mod
         assert got == want, (sh, neg)
+
+
+def unhex(h):
+    return struct.unpack("<d", struct.pack("<Q", int(h, 16)))[0]
+
+
+def limb_contrib(x, emax, top):
+    """x 2^(top - (emax - 1075)) truncated toward zero, as an exact integer."""
+    if x == 0.0:
+        return 0
+    fr = Fraction(x) * Fraction(2) ** (top - (emax - 1075))
+    return int(fr)  # truncation toward zero
+
+
+@pytest.mark.parametrize("L,NW", [(2, 5), (4, 9)])
+def test_exact_sums_and_rounding_back(fxbin, L, NW):
+    """add_at places every limb exactly (truncated below the common unit);
+    from_fixed returns the expansion nearest the sum: for DD hi = sum rounded
+    to 53 bits and |lo| <= ulp(hi) / 2; the expansion's value is within
+    2^-(53 L - 1) of the sum."""
+    rng = random.Random(10 + L)
+    top = 32 * NW - 58
+    lines, cases = [], []
+    for i in range(300):
+        n = rng.randint(1, 7)
+        xs = [expansion(rng, L, sparse=(i % 4 == 0)) for _ in range(n)]
+        if i % 5 == 0 and n >= 2:  # heavy cancellation
+            xs[1] = [-t for t in xs[0]]
+            xs[1][L - 1] = xs[1][L - 1] * 0.5
+        sg = [rng.randint(0, 1) for _ in range(n)]
+        emax = max(max(1, (struct.unpack("<Q", struct.pack("<d", x[0]))[0] >> 52) & 0x7FF) for x in xs)
+        cases.append((xs, sg, emax))
+        lines.append(f"A {L} {emax} {top} {n} " + " ".join(
+            f"{s_} " + " ".join(hexd(t) for t in x) for x, s_ in zip(xs, sg)))
+    mod = 2 ** (32 * NW)
+    for (xs, sg, emax), line in zip(cases, run(fxbin, lines)):
+        vw, limbs = line.split(";")
+        V = value([int(t) for t in vw.split()])
+        want = sum((-1 if s_ else 1) * limb_contrib(t, emax, top) for x, s_ in zip(xs, sg) for t in x)
+        assert V == want % mod
+        Vs = V - mod if V >= mod // 2 else V
+        exact = Fraction(Vs) * Fraction(2) ** (emax - 1075 - top)
+        out = [unhex(h) for h in limbs.split()]
+        got = sum(Fraction(t) for t in out)
+        if exact == 0:
+            assert got == 0
+            continue
+        assert abs(got - exact) <= abs(exact) * Fraction(1, 2 ** (53 * L - 1))
+        hi = Fraction(out[0])
+        ulp = Fraction(2) ** (math.frexp(out[0])[1] - 53)
+        assert abs(exact - hi) <= ulp / 2 + abs(exact) * Fraction(1, 2 ** 150)
+        if L == 2:
+            assert abs(Fraction(out[1])) <= ulp / 2
