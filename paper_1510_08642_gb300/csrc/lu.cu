@@ -34,7 +34,8 @@ namespace ddg {
 
 namespace {
 
-constexpr int RB = 32;       // rows per CTA in the column kernels
+constexpr int RB = 8;        // rows per CTA in the column kernels (many CTAs: the
+                             // rank-1 updates of a column spread over the SMs)
 constexpr int TB = 32;       // triangle size of the substitution base case (one warp)
 constexpr int KMAX = 512;    // widest block column
 constexpr int PANEL_BASE = 16;  // widest panel factored column by column
@@ -246,24 +247,45 @@ __global__ void __launch_bounds__(256) lu_col_kernel(int64_t n, mat A, int64_t c
   if (last_block(cs)) finish_pivot<L>(n, A, j + 1, c0, pe, gridDim.x, part, ipiv, info, pivot, cs);
 }
 
-// The interchanges ipiv[k0 .. k1) (in order) applied to every column outside
-// [k0, k1): one thread per column.
+// The interchanges ipiv[k0 .. k1) (in order, at most 16) applied to every
+// column outside [k0, k1). The composed permutation of the (at most 32)
+// rows involved is worked out once per CTA; then each thread reads those
+// rows of its column (independent loads) and writes them back permuted.
 template <int L>
 __global__ void lu_laswp_kernel(int64_t n, mat A, int64_t k0, int64_t k1, const int64_t* ipiv) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n || (c >= k0 && c < k1)) return;
-  for (int64_t k = k0; k < k1; ++k) {
-    const int64_t p = ipiv[k];
-    if (p == k || p < 0 || p >= n) continue;
-#pragma unroll
-    for (int q = 0; q < L; ++q) {
-      double* rk = A.p[q] + k * A.ld + c;
-      double* rp = A.p[q] + p * A.ld + c;
-      const double t = *rk;
-      *rk = *rp;
-      *rp = t;
+  __shared__ int64_t dst[2 * PANEL_BASE], src[2 * PANEL_BASE];
+  __shared__ int cnt;
+  if (threadIdx.x == 0) {
+    int c = 0;
+    auto slot = [&](int64_t r) {
+      for (int t = 0; t < c; ++t)
+        if (dst[t] == r) return t;
+      dst[c] = r;
+      src[c] = r;
+      return c++;
+    };
+    for (int64_t k = k0; k < k1; ++k) {
+      const int64_t p = ipiv[k];
+      if (p == k || p < 0 || p >= n) continue;
+      const int a = slot(k), b = slot(p);
+      const int64_t t = src[a];
+      src[a] = src[b];
+      src[b] = t;
     }
+    cnt = c;
   }
+  __syncthreads();
+  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nrows = cnt;
+  if (col >= n || (col >= k0 && col < k1) || nrows == 0) return;
+  const int q = blockIdx.y;  // limb plane
+  double v[2 * PANEL_BASE];
+#pragma unroll
+  for (int t = 0; t < 2 * PANEL_BASE; ++t)
+    if (t < nrows) v[t] = A.p[q][src[t] * A.ld + col];
+#pragma unroll
+  for (int t = 0; t < 2 * PANEL_BASE; ++t)
+    if (t < nrows) A.p[q][dst[t] * A.ld + col] = v[t];
 }
 
 template <int L>
@@ -474,7 +496,7 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
         cu(cudaGetLastError());
       }
       if (pivot && st == DDG_OK) {
-        lu_laswp_kernel<L><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, M, c0, pe, ipiv);
+        lu_laswp_kernel<L><<<dim3((unsigned)((n + 127) / 128), L), 128, 0, s>>>(n, M, c0, pe, ipiv);
         cu(cudaGetLastError());
       }
       return;
