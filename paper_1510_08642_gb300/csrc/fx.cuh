@@ -548,5 +548,57 @@ __host__ __device__ __forceinline__ void from_fixed(uint32_t (&V)[NW], int lsb, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fixed-point scalars for latency-bound kernels (the LU's triangular solves).
+
+// M = the W leading words of the nonnegative NW-word integer A, its leading
+// one moved to bit 32 W - 1 (bits shifted out below are dropped); returns
+// the position of A's leading one, or -1 if A = 0 (M = 0).
+template <int NW, int W>
+__host__ __device__ __forceinline__ int acc_normalize(const uint32_t (&A)[NW], uint32_t (&M)[W]) {
+  int top = -1;
+#pragma unroll
+  for (int t = 0; t < NW; ++t)
+    if (A[t] != 0u) top = t;
+  if (top < 0) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) M[w] = 0u;
+    return -1;
+  }
+  uint32_t g[W + 1];  // g[i] = A[top - i]
+#pragma unroll
+  for (int i = 0; i <= W; ++i) {
+    uint32_t v = 0u;
+#pragma unroll
+    for (int u = 0; u < NW; ++u) v = (u == top - i) ? A[u] : v;
+    g[i] = v;
+  }
+  const int lz = clz32(g[0]);
+#pragma unroll
+  for (int i = 0; i < W; ++i) M[W - 1 - i] = shl_funnel(g[i + 1], g[i], lz);
+  return 32 * top + 31 - lz;
+}
+
+// Arithmetic right shift of the two's-complement NW-word A by s >= 0 bits.
+template <int NW>
+__host__ __device__ __forceinline__ void acc_sar(uint32_t (&A)[NW], int s) {
+  if (s <= 0) return;
+  const uint32_t fill = (A[NW - 1] >> 31) ? 0xFFFFFFFFu : 0u;
+  const int w = s >> 5, r = s & 31;
+  uint32_t out[NW];
+#pragma unroll
+  for (int t = 0; t < NW; ++t) {
+    uint32_t lo = fill, hi = fill;
+#pragma unroll
+    for (int u = 0; u < NW; ++u) {
+      lo = (u == t + w) ? A[u] : lo;
+      hi = (u == t + w + 1) ? A[u] : hi;
+    }
+    out[t] = r == 0 ? lo : shr_funnel(lo, hi, r);
+  }
+#pragma unroll
+  for (int t = 0; t < NW; ++t) A[t] = out[t];
+}
+
 }  // namespace fx
 }  // namespace ddg

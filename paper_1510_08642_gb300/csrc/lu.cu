@@ -28,6 +28,7 @@
 #include <string>
 
 #include "arith.cuh"
+#include "fx.cuh"
 #include "kernels.cuh"
 
 namespace ddg {
@@ -298,57 +299,208 @@ __device__ __forceinline__ typename num<L>::T shfl(const typename num<L>::T& v, 
   return r;
 }
 
-// X := L^-1 X for a unit lower triangle (m <= TB rows): one warp per column
-// of X, lane i holding row i. At step k lane k's value is final and is
-// broadcast by a shuffle; lanes below it subtract l_ik x_k. A GB300 SM
-// issues one FP64 warp instruction per 16 cycles, so spreading the rows of
-// a column over the lanes (one multiply-add per step) keeps the chain
-// short: TB steps instead of TB (TB - 1) / 2 multiply-adds per thread.
+// Fixed-point widths of the triangular bases: operands as W-word integers
+// (fx::to_fixed), products' K = 2 W - D leading words, NW-word windows
+// with an operand of exponent field A at bit TOPA (so that a product of
+// exponent fields e_l + e_x = A + 1023 lands at shift 0).
+template <int L> struct tfx;
+template <> struct tfx<2> { static constexpr int W = 4, D = 3, K = 5, NW = 6, TOPA = 106; };
+template <> struct tfx<4> { static constexpr int W = 7, D = 6, K = 8, NW = 9, TOPA = 202; };
+
+// One lane's running value x = acc 2^(A - 1075 - TOPA) as a fixed-point
+// operand: leading one at bit 32 W - 1 of M, exponent field e, sign s; z set
+// when the value is zero.
 template <int L>
-__global__ void __launch_bounds__(128) trsm_lower_unit_base(int64_t m, int64_t r, mat Lm, mat X) {
-  using N = num<L>;
-  using T = typename N::T;
-  __shared__ T Tr[TB][TB];
+__device__ __forceinline__ void window_operand(const uint32_t (&acc)[tfx<L>::NW], int A, uint32_t (&M)[tfx<L>::W],
+                                               int& e, uint32_t& s, bool& z) {
+  constexpr int NW = tfx<L>::NW, W = tfx<L>::W;
+  uint32_t mag[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) mag[w] = acc[w];
+  s = fx::acc_abs<NW>(mag);
+  const int p = fx::acc_normalize<NW, W>(mag, M);
+  z = p < 0;
+  e = p + A - 52 - tfx<L>::TOPA;
+}
+
+// acc -= (l x) for fixed-point operands l = (Ml, el, sl), x = (Mx, ex, sx):
+// the product's leading words placed into the window, which moves up
+// (arithmetic shift, A grows) when the product would not fit below its top.
+template <int L>
+__device__ __forceinline__ void window_sub_product(uint32_t (&acc)[tfx<L>::NW], int& A, const uint32_t (&Ml)[tfx<L>::W],
+                                                   int el, uint32_t sl, const uint32_t (&Mx)[tfx<L>::W], int ex,
+                                                   uint32_t sx) {
+  constexpr int W = tfx<L>::W, D = tfx<L>::D, K = tfx<L>::K, NW = tfx<L>::NW;
+  uint32_t P[K];
+  fx::mul_top<W, D>(Ml, Mx, P);
+  int shl = el + ex - A - 1023;
+  if (shl > 0) {
+    fx::acc_sar<NW>(acc, shl);
+    A += shl;
+    shl = 0;
+  }
+  fx::place_shr<NW, K>(acc, P, -shl, (sl ^ sx) ? 0u : 0xFFFFFFFFu);
+}
+
+// The window rounded to an L-limb expansion and stored.
+template <int L>
+__device__ __forceinline__ void window_store(uint32_t (&acc)[tfx<L>::NW], int A, const mat& X, int64_t i, int64_t c) {
+  double o[L];
+  fx::from_fixed<L, tfx<L>::NW>(acc, A - 1075 - tfx<L>::TOPA, o);
+  typename num<L>::T v;
+  if constexpr (L == 2) v = dd_t{o[0], o[1]};
+  else v = qd_renorm<4>(o);
+  stA<L>(X, i, c, v);
+}
+
+// Triangle entries staged in fixed-point form, lane-contiguous: Tw[k][w][i]
+// is word w of entry (i, k), Te[k][i] its exponent field | sign << 16.
+template <int L>
+struct tri_smem {
+  uint32_t Tw[TB][tfx<L>::W][TB];
+  int Te[TB][TB];
+};
+
+template <int L>
+__device__ __forceinline__ void stage_triangle(tri_smem<L>& sm, const mat& T, int64_t m, bool upper) {
+  constexpr int W = tfx<L>::W;
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     const int i = e / TB, k = e % TB;
-    Tr[i][k] = (i < m && k < i) ? ldA<L>(Lm, i, k) : N::zero();
+    const bool use = i < m && k < m && (upper ? k > i : k < i);
+    double x[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) x[q] = use ? T.p[q][i * T.ld + k] : 0.0;
+    uint32_t M[W];
+    const int es = fx::to_fixed<L, W>(x, M);
+#pragma unroll
+    for (int w = 0; w < W; ++w) sm.Tw[k][w][i] = M[w];
+    sm.Te[k][i] = es;
   }
+}
+
+// X := L^-1 X for a unit lower triangle (m <= TB rows): one warp per column
+// of X, lane i holding row i as an exact fixed-point window on the integer
+// pipe. At step k lane k's value is final: it is normalised to a W-word
+// operand and broadcast by shuffles, and the lanes below subtract l_ik x_k
+// (W-word product, one placement). Each value is rounded to DD / QD once,
+// at the end. (The FP64 form of this loop ran a single warp's DD / QD
+// chain through an FP64 pipe that issues one warp instruction per 16
+// cycles per SM.)
+template <int L>
+__global__ void __launch_bounds__(128) trsm_lower_unit_base(int64_t m, int64_t r, mat Lm, mat X) {
+  constexpr int W = tfx<L>::W, NW = tfx<L>::NW;
+  __shared__ tri_smem<L> sm;
+  stage_triangle<L>(sm, Lm, m, false);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (c >= r) return;
-  T acc = lane < m ? ldA<L>(X, lane, c) : N::zero();
-  for (int k = 0; k < m; ++k) {
-    const T xk = shfl<L>(acc, k);
-    if (lane > k) acc = N::add(acc, N::mul(N::neg(Tr[lane][k]), xk));
+  double b[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) b[q] = lane < m ? X.p[q][lane * X.ld + c] : 0.0;
+  int A = max(1, fx::expfield(b[0]));
+  uint32_t acc[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) acc[w] = 0u;
+  fx::add_at<L, NW>(acc, b, A, tfx<L>::TOPA, 0u);
+  for (int k = 0; k < (int)m; ++k) {
+    uint32_t Mx[W], sx;
+    int ex;
+    bool zx;
+    window_operand<L>(acc, A, Mx, ex, sx, zx);
+#pragma unroll
+    for (int w = 0; w < W; ++w) Mx[w] = __shfl_sync(0xffffffffu, Mx[w], k);
+    ex = __shfl_sync(0xffffffffu, ex, k);
+    sx = __shfl_sync(0xffffffffu, sx, k);
+    zx = __shfl_sync(0xffffffffu, (int)zx, k) != 0;
+    if (lane > k && lane < m && !zx) {
+      uint32_t Ml[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) Ml[w] = sm.Tw[k][w][lane];
+      const int es = sm.Te[k][lane];
+      window_sub_product<L>(acc, A, Ml, es & 0xFFFF, (uint32_t)es >> 16, Mx, ex, sx);
+    }
   }
-  if (lane < m) stA<L>(X, lane, c, acc);
+  if (lane < m) window_store<L>(acc, A, X, lane, c);
 }
 
 // X := U^-1 X for an upper triangle with nonzero diagonal (m <= TB rows),
-// one warp per column as above, from the last row up; each lane first forms
-// the reciprocal of its diagonal entry.
+// one warp per column as above, from the last row up. Each lane forms the
+// reciprocal of its diagonal entry once (DD / QD Newton step) as a
+// fixed-point operand; at step k lane k multiplies its value by it, the
+// quotient is broadcast and the lanes above subtract u_ik x_k.
 template <int L>
 __global__ void __launch_bounds__(128) trsm_upper_base(int64_t m, int64_t r, mat U, mat X) {
   using N = num<L>;
-  using T = typename N::T;
-  __shared__ T Tr[TB][TB];
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    const int i = e / TB, k = e % TB;
-    Tr[i][k] = (i < m && k < m && k >= i) ? ldA<L>(U, i, k) : (i == k ? N::one() : N::zero());
-  }
+  constexpr int W = tfx<L>::W, D = tfx<L>::D, K = tfx<L>::K, NW = tfx<L>::NW;
+  __shared__ tri_smem<L> sm;
+  stage_triangle<L>(sm, U, m, true);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (c >= r) return;
-  const T rinv = N::recip(Tr[lane][lane]);
-  T acc = lane < m ? ldA<L>(X, lane, c) : N::zero();
-  for (int k = (int)m - 1; k >= 0; --k) {
-    if (lane == k) acc = N::mul(acc, rinv);
-    const T xk = shfl<L>(acc, k);
-    if (lane < k) acc = N::add(acc, N::mul(N::neg(Tr[lane][k]), xk));
+  uint32_t Mr[W];
+  int er;
+  uint32_t sr;
+  {
+    const typename N::T d = lane < m ? ldA<L>(U, lane, lane) : N::one();
+    const typename N::T ri = N::recip(d);
+    const int es = fx::to_fixed<L, W>(*reinterpret_cast<const double(*)[L]>(&ri), Mr);
+    er = es & 0xFFFF;
+    sr = (uint32_t)es >> 16;
   }
-  if (lane < m) stA<L>(X, lane, c, acc);
+  double b[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) b[q] = lane < m ? X.p[q][lane * X.ld + c] : 0.0;
+  int A = max(1, fx::expfield(b[0]));
+  uint32_t acc[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) acc[w] = 0u;
+  fx::add_at<L, NW>(acc, b, A, tfx<L>::TOPA, 0u);
+  for (int k = (int)m - 1; k >= 0; --k) {
+    // x = value * (1 / u_kk): the product's K words normalised to W words
+    uint32_t Ma[W], sa;
+    int ea;
+    bool za;
+    window_operand<L>(acc, A, Ma, ea, sa, za);
+    uint32_t P[K], Mx[W];
+    fx::mul_top<W, D>(Ma, Mr, P);
+    const int p = fx::acc_normalize<K, W>(P, Mx);
+    // P ~ Ma Mr 2^(32 D - 2 TOPW - 2150 + ea + er) with TOPW = 32 W - 53
+    int ex = p + ea + er - 1075 - 2 * (32 * W - 53) + 32 * D - 52;
+    uint32_t sx = sa ^ sr;
+    bool zx = za || p < 0;
+    if (lane == k) {
+      // lane k's final value x_k = Mx 2^(ex - 1075 - TOPW), TOPW = 32 W - 53:
+      // as the window of anchor A = ex + TOPA - TOPW it is Mx itself
+#pragma unroll
+      for (int w = 0; w < NW; ++w) acc[w] = 0u;
+      if (!zx) {
+        A = ex + tfx<L>::TOPA - (32 * W - 53);
+        const uint32_t msk = sx ? 0xFFFFFFFFu : 0u;
+        uint64_t cy = msk & 1u;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const uint64_t v = (uint64_t)((w < W ? Mx[w] : 0u) ^ msk) + cy;
+          acc[w] = (uint32_t)v;
+          cy = v >> 32;
+        }
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) Mx[w] = __shfl_sync(0xffffffffu, Mx[w], k);
+    ex = __shfl_sync(0xffffffffu, ex, k);
+    sx = __shfl_sync(0xffffffffu, sx, k);
+    zx = __shfl_sync(0xffffffffu, (int)zx, k) != 0;
+    if (lane < k && !zx) {
+      uint32_t Mu[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) Mu[w] = sm.Tw[k][w][lane];
+      const int es = sm.Te[k][lane];
+      window_sub_product<L>(acc, A, Mu, es & 0xFFFF, (uint32_t)es >> 16, Mx, ex, sx);
+    }
+  }
+  if (lane < m) window_store<L>(acc, A, X, lane, c);
 }
 
 // Row permutation of the interchanges ipiv[0..n): perm[i] = source row of

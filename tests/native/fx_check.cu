@@ -4,6 +4,8 @@
 //   T L x0 .. x(L-1)          -> to_fixed: es M[0] .. M[W-1]   (W = 4 / 7)
 //   M W D a[0..W-1] b[0..W-1]  -> mul_top: p[0 .. 2W-D-1]
 //   P NW K sh neg acc[0..NW-1] p[0..K-1] -> place_shr: acc[0 .. NW-1]
+//   N NW W A[0..NW-1]          -> acc_normalize: p M[0..W-1]   (6,4) / (9,7)
+//   R NW s A[0..NW-1]          -> acc_sar: A[0..NW-1]          (NW = 6 / 9)
 //   A L emax top n (sign x0 .. x(L-1)) x n -> add_at into V (NW = 5 / 9),
 //                              then from_fixed: V[0..NW-1] ; limbs (hex)
 // Doubles are read as 16 hex digits of their bit pattern.
@@ -79,6 +81,26 @@ static void do_sum() {
   std::printf("\n");
 }
 
+template <int NW, int W>
+static void do_norm() {
+  uint32_t A[NW], M[W];
+  for (int i = 0; i < NW; ++i) scan("%u", &A[i]);
+  const int p = fx::acc_normalize<NW, W>(A, M);
+  std::printf("%d", p);
+  for (int i = 0; i < W; ++i) std::printf(" %u", M[i]);
+  std::printf("\n");
+}
+
+template <int NW>
+static void do_sar() {
+  int sh;
+  scan("%d", &sh);
+  uint32_t A[NW];
+  for (int i = 0; i < NW; ++i) scan("%u", &A[i]);
+  fx::acc_sar<NW>(A, sh);
+  for (int i = 0; i < NW; ++i) std::printf("%u%c", A[i], i + 1 < NW ? ' ' : '\n');
+}
+
 int main() {
   char cmd[4];
   while (std::scanf("%3s", cmd) == 1) {
@@ -91,6 +113,14 @@ int main() {
       scan("%d %d", &a, &b);
       if (a == 4) do_mul<4, 3>();
       else do_mul<7, 6>();
+    } else if (cmd[0] == 'N') {
+      scan("%d %d", &a, &b);
+      if (a == 6) do_norm<6, 4>();
+      else do_norm<9, 7>();
+    } else if (cmd[0] == 'R') {
+      scan("%d", &a);
+      if (a == 6) do_sar<6>();
+      else do_sar<9>();
     } else if (cmd[0] == 'A') {
       scan("%d", &a);
       if (a == 2) do_sum<2, 5>();

@@ -169,3 +169,29 @@ def test_exact_sums_and_rounding_back(fxbin, L, NW):
         assert abs(exact - hi) <= ulp / 2 + abs(exact) * Fraction(1, 2 ** 150)
         if L == 2:
             assert abs(Fraction(out[1])) <= ulp / 2
+
+
+@pytest.mark.parametrize("NW,W", [(6, 4), (9, 7)])
+def test_normalize_and_arithmetic_shift(fxbin, NW, W):
+    """acc_normalize: leading one found and moved to bit 32 W - 1, the W
+    words are the leading bits (truncated); acc_sar: floor(A / 2^s) for a
+    two's-complement A."""
+    rng = random.Random(NW)
+    cases = [rng.getrandbits(rng.randint(1, 32 * NW - 1)) for _ in range(300)] + [0, 1, 2 ** (32 * NW - 1) - 1]
+    out = run(fxbin, [f"N {NW} {W} " + " ".join(map(str, words(a, NW))) for a in cases])
+    for a, line in zip(cases, out):
+        vals = [int(t) for t in line.split()]
+        p, M = vals[0], value(vals[1:])
+        if a == 0:
+            assert p == -1 and M == 0
+            continue
+        assert p == a.bit_length() - 1
+        sh = (32 * W - 1) - p
+        assert M == (a << sh if sh >= 0 else a >> -sh) % 2 ** (32 * W)
+    mod = 2 ** (32 * NW)
+    sc = [(rng.choice([0, 1, 5, 31, 32, 33, 64, 100, 32 * NW - 1, 32 * NW + 7]), rng.getrandbits(32 * NW)) for _ in range(300)]
+    out = run(fxbin, [f"R {NW} {s} " + " ".join(map(str, words(a, NW))) for s, a in sc])
+    for (s, a), line in zip(sc, out):
+        got = value([int(t) for t in line.split()])
+        signed = a - mod if a >= mod // 2 else a
+        assert got == (signed >> s) % mod
