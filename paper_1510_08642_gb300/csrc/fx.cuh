@@ -242,27 +242,43 @@ __host__ __device__ __forceinline__ uint32_t acc_abs(uint32_t (&A)[NW]) {
   return neg;
 }
 
+// B = A shifted up by whole words so that A's highest nonzero word lands in
+// B[NW - 1]; returns the index of that word in A, or -1 if A = 0. A barrel
+// shifter (conditional shifts by 8, 4, 2, 1 words with fixed indices): no
+// select over a computed word index, a form that was seen miscompiled at
+// -O3 on this toolchain.
+template <int NW>
+__host__ __device__ __forceinline__ int acc_top_align(const uint32_t (&A)[NW], uint32_t (&B)[NW]) {
+  int top = -1;
+#pragma unroll
+  for (int t = 0; t < NW; ++t) {
+    if (A[t] != 0u) top = t;
+    B[t] = A[t];
+  }
+  const int s = NW - 1 - top;
+#pragma unroll
+  for (int step = 8; step >= 1; step >>= 1) {
+    if (step >= NW) continue;
+    const bool on = top >= 0 && (s & step) != 0;
+#pragma unroll
+    for (int t = NW - 1; t >= 0; --t) B[t] = on ? (t >= step ? B[t - step] : 0u) : B[t];
+  }
+  return top;
+}
+
 // Split the magnitude |A| into K chunks of 53 bits from its leading bit down:
 // |A| ~= sum_c chunk[c] * 2^(exp[c]) (in units of the LSB), truncated below.
 // Returns false if A is zero.
 template <int NW, int K>
 __host__ __device__ __forceinline__ bool acc_chunks(const uint32_t (&A)[NW], uint64_t (&chunk)[K], int (&exp)[K]) {
-  int top = -1;
-#pragma unroll
-  for (int t = 0; t < NW; ++t)
-    if (A[t] != 0u) top = t;
+  uint32_t B[NW];
+  const int top = acc_top_align<NW>(A, B);
   if (top < 0) return false;
-  // gather the top word and the words below it into a bit string g (MSB first)
+  // the top word and the words below it as a bit string g (MSB first)
   constexpr int G = (53 * K + 31) / 32 + 2;  // words needed below the leading bit
   uint32_t g[G];
 #pragma unroll
-  for (int i = 0; i < G; ++i) {
-    const int t = top - i;
-    uint32_t v = 0u;
-#pragma unroll
-    for (int u = 0; u < NW; ++u) v = (u == t) ? A[u] : v;
-    g[i] = v;
-  }
+  for (int i = 0; i < G; ++i) g[i] = i < NW ? B[NW - 1 - (i < NW ? i : 0)] : 0u;
   const int lz = clz32(g[0]);
   // left-align: shift the string so that the leading one is bit 31 of g[0]
 #pragma unroll
@@ -517,7 +533,14 @@ __host__ __device__ __forceinline__ double make_double(uint64_t mag, int e2, uin
   return neg ? -v : v;
 }
 
-// The L-limb expansion nearest the signed integer V 2^lsb (V is destroyed):
+template <int L, int W>
+__host__ __device__ __forceinline__ void operand_to_limbs(const uint32_t (&M)[W], int e, uint32_t s, double (&out)[L]);
+template <int NW, int W>
+__host__ __device__ __forceinline__ int acc_normalize(const uint32_t (&A)[NW], uint32_t (&M)[W]);
+
+// The L-limb expansion nearest the signed integer V 2^lsb (V is destroyed).
+// QD: the leading 224 bits of |V| rounded greedily limb by limb
+// (operand_to_limbs: canonical). DD:
 // the leading L 53-bit pieces of |V| and the next bit, turned into balanced
 // digits from the least significant end (a digit >= 2^52 becomes digit -
 // 2^53 and carries one into the next), so the leading limb is |V| rounded to
@@ -527,6 +550,17 @@ __host__ __device__ __forceinline__ double make_double(uint64_t mag, int e2, uin
 template <int L, int NW>
 __host__ __device__ __forceinline__ void from_fixed(uint32_t (&V)[NW], int lsb, double (&out)[L]) {
   const uint32_t neg = acc_abs<NW>(V);
+  if constexpr (L == 4) {
+    uint32_t M[7];
+    const int p = acc_normalize<NW, 7>(V, M);
+    if (p < 0) {
+#pragma unroll
+      for (int q = 0; q < L; ++q) out[q] = 0.0;
+      return;
+    }
+    operand_to_limbs<4, 7>(M, p + lsb + 1023, neg, out);
+    return;
+  }
   uint64_t ch[L + 1];
   int ex[L + 1];
   if (!acc_chunks<NW, L + 1>(V, ch, ex)) {
@@ -556,48 +590,100 @@ __host__ __device__ __forceinline__ void from_fixed(uint32_t (&V)[NW], int lsb, 
 // the position of A's leading one, or -1 if A = 0 (M = 0).
 template <int NW, int W>
 __host__ __device__ __forceinline__ int acc_normalize(const uint32_t (&A)[NW], uint32_t (&M)[W]) {
-  int top = -1;
-#pragma unroll
-  for (int t = 0; t < NW; ++t)
-    if (A[t] != 0u) top = t;
+  static_assert(W <= NW, "operand wider than the source");
+  uint32_t B[NW];
+  const int top = acc_top_align<NW>(A, B);
   if (top < 0) {
 #pragma unroll
     for (int w = 0; w < W; ++w) M[w] = 0u;
     return -1;
   }
-  uint32_t g[W + 1];  // g[i] = A[top - i]
+  const int lz = clz32(B[NW - 1]);
 #pragma unroll
-  for (int i = 0; i <= W; ++i) {
-    uint32_t v = 0u;
-#pragma unroll
-    for (int u = 0; u < NW; ++u) v = (u == top - i) ? A[u] : v;
-    g[i] = v;
-  }
-  const int lz = clz32(g[0]);
-#pragma unroll
-  for (int i = 0; i < W; ++i) M[W - 1 - i] = shl_funnel(g[i + 1], g[i], lz);
+  for (int i = 0; i < W; ++i) M[W - 1 - i] = shl_funnel(NW - 2 - i >= 0 ? B[NW - 2 - i] : 0u, B[NW - 1 - i], lz);
   return 32 * top + 31 - lz;
 }
 
-// Arithmetic right shift of the two's-complement NW-word A by s >= 0 bits.
+// Arithmetic right shift of the two's-complement NW-word A by s >= 0 bits
+// (word shifts by a barrel shifter with fixed indices, then a funnel shift).
 template <int NW>
 __host__ __device__ __forceinline__ void acc_sar(uint32_t (&A)[NW], int s) {
   if (s <= 0) return;
   const uint32_t fill = (A[NW - 1] >> 31) ? 0xFFFFFFFFu : 0u;
   const int w = s >> 5, r = s & 31;
-  uint32_t out[NW];
+  if (w >= NW) {
 #pragma unroll
-  for (int t = 0; t < NW; ++t) {
-    uint32_t lo = fill, hi = fill;
-#pragma unroll
-    for (int u = 0; u < NW; ++u) {
-      lo = (u == t + w) ? A[u] : lo;
-      hi = (u == t + w + 1) ? A[u] : hi;
-    }
-    out[t] = r == 0 ? lo : shr_funnel(lo, hi, r);
+    for (int t = 0; t < NW; ++t) A[t] = fill;
+    return;
   }
 #pragma unroll
-  for (int t = 0; t < NW; ++t) A[t] = out[t];
+  for (int step = 8; step >= 1; step >>= 1) {
+    if (step >= NW) continue;
+    const bool on = (w & step) != 0;
+#pragma unroll
+    for (int t = 0; t < NW; ++t) A[t] = on ? (t + step < NW ? A[t + step < NW ? t + step : 0] : fill) : A[t];
+  }
+  if (r != 0) {
+#pragma unroll
+    for (int t = 0; t < NW; ++t) A[t] = shr_funnel(A[t], t + 1 < NW ? A[t + 1 < NW ? t + 1 : 0] : fill, r);
+  }
+}
+
+// The expansion of L limbs nearest M 2^(e - 1075 - (32 W - 53)) (M with its
+// leading one at bit 32 W - 1, sign s), greedily: each limb is the
+// remaining value rounded to 53 bits (half up), the remainder kept exactly
+// in W words and renormalised. Canonical (each limb at most half a unit
+// in the last place of the one above) and integer-only except for
+// assembling the doubles.
+template <int L, int W>
+__host__ __device__ __forceinline__ void operand_to_limbs(const uint32_t (&M)[W], int e, uint32_t s, double (&out)[L]) {
+  uint32_t R[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) R[w] = M[w];
+  int lead = e;  // exponent field of R's leading bit (R normalised)
+  uint32_t neg = s;
+#pragma unroll
+  for (int q = 0; q < L; ++q) {
+    // top 53 bits and the rounding bit of the normalised R
+    const uint64_t top64 = ((uint64_t)R[W - 1] << 32) | R[W - 2];
+    uint64_t h = top64 >> 11;                 // 53 bits
+    const uint32_t rb = (uint32_t)(top64 >> 10) & 1u;
+    if (h == 0u) {
+#pragma unroll
+      for (int t = q; t < L; ++t) out[t] = 0.0;
+      return;
+    }
+    out[q] = make_double(h + rb, lead - 1075, neg);
+    if (q + 1 == L) break;
+    // remainder: R - (h + rb) 2^(32 W - 53); below the top 53 bits R holds
+    // the rest r; if rb, the remainder is -(2^(32 W - 53) - r)
+    R[W - 1] = 0u;
+    R[W - 2] &= 0x7FFu;  // bits below the leading 53 (32 W - 53 = 32 (W - 2) + 11)
+    if (rb) {
+      // rounded up: the remainder is -(2^(32 W - 53) - r) with r >= 2^(32 W - 54)
+      // the rest, i.e. the low 32 W - 53 bits of -r
+      uint64_t c = 1u;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const uint64_t v = (uint64_t)(~R[w]) + c;
+        R[w] = (uint32_t)v;
+        c = v >> 32;
+      }
+      R[W - 1] = 0u;
+      R[W - 2] &= 0x7FFu;
+      neg ^= 1u;
+    }
+    uint32_t Rn[W];
+    const int p = acc_normalize<W, W>(R, Rn);
+    if (p < 0) {
+#pragma unroll
+      for (int t = q + 1; t < L; ++t) out[t] = 0.0;
+      return;
+    }
+    lead -= (32 * W - 1) - p;
+#pragma unroll
+    for (int w = 0; w < W; ++w) R[w] = Rn[w];
+  }
 }
 
 }  // namespace fx

@@ -29,6 +29,7 @@
 
 #include "arith.cuh"
 #include "fx.cuh"
+#include "fxscalar.cuh"
 #include "kernels.cuh"
 
 namespace ddg {
@@ -114,6 +115,42 @@ __device__ __forceinline__ typename num<L>::T get_rinv(const col_state* cs) {
   return v;
 }
 
+// The window rounded to an L-limb expansion and stored.
+template <int L>
+__device__ __forceinline__ void window_store(uint32_t (&acc)[tfx<L>::NW], int A, const mat& X, int64_t i, int64_t c) {
+  double o[L];
+  fx::from_fixed<L, tfx<L>::NW>(acc, A - 1075 - tfx<L>::TOPA, o);
+  typename num<L>::T v;
+  if constexpr (L == 2) v = dd_t{o[0], o[1]};
+  else v = qd_t{{o[0], o[1], o[2], o[3]}};
+  stA<L>(X, i, c, v);
+}
+
+// Triangle entries staged in fixed-point form, lane-contiguous: Tw[k][w][i]
+// is word w of entry (i, k), Te[k][i] its exponent field | sign << 16.
+template <int L>
+struct tri_smem {
+  uint32_t Tw[TB][tfx<L>::W][TB];
+  int Te[TB][TB];
+};
+
+template <int L>
+__device__ __forceinline__ void stage_triangle(tri_smem<L>& sm, const mat& T, int64_t m, bool upper) {
+  constexpr int W = tfx<L>::W;
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    const int i = e / TB, k = e % TB;
+    const bool use = i < m && k < m && (upper ? k > i : k < i);
+    double x[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) x[q] = use ? T.p[q][i * T.ld + k] : 0.0;
+    uint32_t M[W];
+    const int es = fx::to_fixed<L, W>(x, M);
+#pragma unroll
+    for (int w = 0; w < W; ++w) sm.Tw[k][w][i] = M[w];
+    sm.Te[k][i] = es;
+  }
+}
+
 // Executed by the last CTA of a launch (all its threads): choose the pivot
 // of column j from the partial arg-maxes (or row j without pivoting),
 // record it, flag an exactly zero pivot, swap rows j and p within the
@@ -163,7 +200,14 @@ __device__ void finish_pivot(int64_t n, const mat& A, int64_t j, int64_t c0, int
     const T piv = ldA<L>(A, j, j);
     const bool zero = is_zero<L>(piv);
     if (zero && *info == 0) *info = j + 1;
-    const T r = zero ? num<L>::zero() : num<L>::recip(piv);
+    T r = num<L>::zero();
+    if (!zero) {
+      if constexpr (L == 4) {
+        const dd_t y = dd_recip(dd_t{piv.x[0], piv.x[1]});
+        qd_recip_refine(piv.x, y.hi, y.lo, r.x);
+      }
+      else r = num<L>::recip(piv);
+    }
     const double* x = reinterpret_cast<const double*>(&r);
 #pragma unroll
     for (int q = 0; q < L; ++q) cs->rinv[q] = x[q];
@@ -208,35 +252,111 @@ __global__ void __launch_bounds__(256) lu_start_kernel(int64_t n, mat A, int64_t
 // 1 / pivot in cs): quotients l_ij = a_ij (1 / a_jj) for rows below j,
 // rank-1 update of columns (j, pe) of those rows; then, if column j + 1
 // belongs to the same panel, the partial arg-maxes of the updated column
-// j + 1 and, in the last CTA, its pivot.
+// j + 1 and, in the last CTA, its pivot. For QD the quotients and updates
+// run on the integer pipe: operands as W-word fixed-point integers, each
+// quotient one multiword product (kept at full width for the updates,
+// stored rounded), each update a - l u exact in a window and rounded once.
 template <int L>
 __global__ void __launch_bounds__(256) lu_col_kernel(int64_t n, mat A, int64_t c0, int64_t j, int64_t pe,
                                                      partial_t* part, int64_t* ipiv, int64_t* info,
                                                      int pivot, col_state* cs) {
   using N = num<L>;
-  using T = typename N::T;
-  __shared__ T u[PANEL_BASE];  // pe - j - 1 < PANEL_BASE
-  __shared__ T lq[RB];
+  constexpr int W = tfx<L>::W, D = tfx<L>::D, K = tfx<L>::K, NW = tfx<L>::NW;
+  constexpr int TOPW = 32 * W - 53;
+  __shared__ uint32_t uw[PANEL_BASE][W];  // pe - j - 1 < PANEL_BASE
+  __shared__ int ue[PANEL_BASE];           // exponent field | sign << 16, or -1 for zero
+  __shared__ uint32_t lw[RB][W];
+  __shared__ int le[RB], ls[RB];           // exponent field, sign; le = -1 for zero
   const int tid = threadIdx.x;
   const int64_t r0 = j + 1 + (int64_t)blockIdx.x * RB;
   const int rows = (int)(n - r0 < RB ? n - r0 : RB);
   const int cols = (int)(pe - j - 1);
-  const T rinv = get_rinv<L>(cs);
-  const bool zero = is_zero<L>(rinv);
-  if (tid < rows) {
-    T l = N::zero();
-    if (!zero) {
-      l = N::mul(ldA<L>(A, r0 + tid, j), rinv);
-      stA<L>(A, r0 + tid, j, l);
+  if constexpr (L == 2) {
+    // DD: the FP64 sequences are short (7 + 20 instructions per update)
+    // and beat the fixed-point form here
+    using T = typename N::T;
+    __shared__ T u[PANEL_BASE];
+    __shared__ T lq[RB];
+    const T rinv = get_rinv<L>(cs);
+    const bool zero = is_zero<L>(rinv);
+    if (tid < rows) {
+      T l = N::zero();
+      if (!zero) {
+        l = N::mul(ldA<L>(A, r0 + tid, j), rinv);
+        stA<L>(A, r0 + tid, j, l);
+      }
+      lq[tid] = l;
     }
-    lq[tid] = l;
+    for (int c = tid; c < cols; c += blockDim.x) u[c] = ldA<L>(A, j, j + 1 + c);
+    __syncthreads();
+    for (int e = tid; e < rows * cols; e += blockDim.x) {
+      const int r = e / cols, c = e % cols;
+      const int64_t i = r0 + r, jc = j + 1 + c;
+      stA<L>(A, i, jc, N::add(ldA<L>(A, i, jc), N::mul(N::neg(lq[r]), u[c])));
+    }
+  } else {
+  if (tid < rows) {
+    le[tid] = -1;
+    double rv[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) rv[q] = cs->rinv[q];
+    if ((fx::dbits(rv[0]) << 1) != 0u) {
+      double a[L];
+#pragma unroll
+      for (int q = 0; q < L; ++q) a[q] = A.p[q][(r0 + tid) * A.ld + j];
+      if ((fx::dbits(a[0]) << 1) != 0u) {
+        uint32_t Ma[W], Mr[W], P[K], Ml[W];
+        const int ea = fx::to_fixed<L, W>(a, Ma), er = fx::to_fixed<L, W>(rv, Mr);
+        fx::mul_top<W, D>(Ma, Mr, P);
+        const int p = fx::acc_normalize<K, W>(P, Ml);
+        const int el = p + (ea & 0xFFFF) + (er & 0xFFFF) - 1075 - 2 * TOPW + 32 * D - 52;
+        const int sl = ((ea ^ er) >> 16) & 1;
+        // store l rounded to DD / QD
+        double o[L];
+        fx::operand_to_limbs<L, W>(Ml, el, (uint32_t)sl, o);
+        typename N::T v;
+        if constexpr (L == 2) v = dd_t{o[0], o[1]};
+        else v = qd_t{{o[0], o[1], o[2], o[3]}};
+        stA<L>(A, r0 + tid, j, v);
+#pragma unroll
+        for (int w = 0; w < W; ++w) lw[tid][w] = Ml[w];
+        le[tid] = el;
+        ls[tid] = sl;
+      }
+    }
   }
-  for (int c = tid; c < cols; c += blockDim.x) u[c] = ldA<L>(A, j, j + 1 + c);
+  for (int c = tid; c < cols; c += blockDim.x) {
+    double u[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) u[q] = A.p[q][j * A.ld + j + 1 + c];
+    uint32_t M[W];
+    const int es = fx::to_fixed<L, W>(u, M);
+#pragma unroll
+    for (int w = 0; w < W; ++w) uw[c][w] = M[w];
+    ue[c] = (fx::dbits(u[0]) << 1) == 0u ? -1 : es;
+  }
   __syncthreads();
   for (int e = tid; e < rows * cols; e += blockDim.x) {
     const int r = e / cols, c = e % cols;
+    if (le[r] < 0 || ue[c] < 0) continue;  // l = 0 or u = 0: nothing to subtract
     const int64_t i = r0 + r, jc = j + 1 + c;
-    stA<L>(A, i, jc, N::add(ldA<L>(A, i, jc), N::mul(N::neg(lq[r]), u[c])));
+    double a[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) a[q] = A.p[q][i * A.ld + jc];
+    int Aw = max(1, fx::expfield(a[0]));
+    uint32_t acc[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) acc[w] = 0u;
+    fx::add_at<L, NW>(acc, a, Aw, tfx<L>::TOPA, 0u);
+    uint32_t Ml[W], Mu[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      Ml[w] = lw[r][w];
+      Mu[w] = uw[c][w];
+    }
+    window_sub_product<L>(acc, Aw, Ml, le[r], (uint32_t)ls[r], Mu, ue[c] & 0xFFFF, (uint32_t)ue[c] >> 16);
+    window_store<L>(acc, Aw, A, i, jc);
+  }
   }
   if (j + 1 >= pe) return;  // the next panel starts with lu_start_kernel
   __syncthreads();
@@ -297,85 +417,6 @@ __device__ __forceinline__ typename num<L>::T shfl(const typename num<L>::T& v, 
 #pragma unroll
   for (int q = 0; q < L; ++q) y[q] = __shfl_sync(0xffffffffu, x[q], k);
   return r;
-}
-
-// Fixed-point widths of the triangular bases: operands as W-word integers
-// (fx::to_fixed), products' K = 2 W - D leading words, NW-word windows
-// with an operand of exponent field A at bit TOPA (so that a product of
-// exponent fields e_l + e_x = A + 1023 lands at shift 0).
-template <int L> struct tfx;
-template <> struct tfx<2> { static constexpr int W = 4, D = 3, K = 5, NW = 6, TOPA = 106; };
-template <> struct tfx<4> { static constexpr int W = 7, D = 6, K = 8, NW = 9, TOPA = 202; };
-
-// One lane's running value x = acc 2^(A - 1075 - TOPA) as a fixed-point
-// operand: leading one at bit 32 W - 1 of M, exponent field e, sign s; z set
-// when the value is zero.
-template <int L>
-__device__ __forceinline__ void window_operand(const uint32_t (&acc)[tfx<L>::NW], int A, uint32_t (&M)[tfx<L>::W],
-                                               int& e, uint32_t& s, bool& z) {
-  constexpr int NW = tfx<L>::NW, W = tfx<L>::W;
-  uint32_t mag[NW];
-#pragma unroll
-  for (int w = 0; w < NW; ++w) mag[w] = acc[w];
-  s = fx::acc_abs<NW>(mag);
-  const int p = fx::acc_normalize<NW, W>(mag, M);
-  z = p < 0;
-  e = p + A - 52 - tfx<L>::TOPA;
-}
-
-// acc -= (l x) for fixed-point operands l = (Ml, el, sl), x = (Mx, ex, sx):
-// the product's leading words placed into the window, which moves up
-// (arithmetic shift, A grows) when the product would not fit below its top.
-template <int L>
-__device__ __forceinline__ void window_sub_product(uint32_t (&acc)[tfx<L>::NW], int& A, const uint32_t (&Ml)[tfx<L>::W],
-                                                   int el, uint32_t sl, const uint32_t (&Mx)[tfx<L>::W], int ex,
-                                                   uint32_t sx) {
-  constexpr int W = tfx<L>::W, D = tfx<L>::D, K = tfx<L>::K, NW = tfx<L>::NW;
-  uint32_t P[K];
-  fx::mul_top<W, D>(Ml, Mx, P);
-  int shl = el + ex - A - 1023;
-  if (shl > 0) {
-    fx::acc_sar<NW>(acc, shl);
-    A += shl;
-    shl = 0;
-  }
-  fx::place_shr<NW, K>(acc, P, -shl, (sl ^ sx) ? 0u : 0xFFFFFFFFu);
-}
-
-// The window rounded to an L-limb expansion and stored.
-template <int L>
-__device__ __forceinline__ void window_store(uint32_t (&acc)[tfx<L>::NW], int A, const mat& X, int64_t i, int64_t c) {
-  double o[L];
-  fx::from_fixed<L, tfx<L>::NW>(acc, A - 1075 - tfx<L>::TOPA, o);
-  typename num<L>::T v;
-  if constexpr (L == 2) v = dd_t{o[0], o[1]};
-  else v = qd_renorm<4>(o);
-  stA<L>(X, i, c, v);
-}
-
-// Triangle entries staged in fixed-point form, lane-contiguous: Tw[k][w][i]
-// is word w of entry (i, k), Te[k][i] its exponent field | sign << 16.
-template <int L>
-struct tri_smem {
-  uint32_t Tw[TB][tfx<L>::W][TB];
-  int Te[TB][TB];
-};
-
-template <int L>
-__device__ __forceinline__ void stage_triangle(tri_smem<L>& sm, const mat& T, int64_t m, bool upper) {
-  constexpr int W = tfx<L>::W;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    const int i = e / TB, k = e % TB;
-    const bool use = i < m && k < m && (upper ? k > i : k < i);
-    double x[L];
-#pragma unroll
-    for (int q = 0; q < L; ++q) x[q] = use ? T.p[q][i * T.ld + k] : 0.0;
-    uint32_t M[W];
-    const int es = fx::to_fixed<L, W>(x, M);
-#pragma unroll
-    for (int w = 0; w < W; ++w) sm.Tw[k][w][i] = M[w];
-    sm.Te[k][i] = es;
-  }
 }
 
 // X := L^-1 X for a unit lower triangle (m <= TB rows): one warp per column
@@ -471,20 +512,12 @@ __global__ void __launch_bounds__(128) trsm_upper_base(int64_t m, int64_t r, mat
     uint32_t sx = sa ^ sr;
     bool zx = za || p < 0;
     if (lane == k) {
-      // lane k's final value x_k = Mx 2^(ex - 1075 - TOPW), TOPW = 32 W - 53:
-      // as the window of anchor A = ex + TOPA - TOPW it is Mx itself
+      // lane k's final value x_k (kept exactly as its window)
+      if (zx) {
 #pragma unroll
-      for (int w = 0; w < NW; ++w) acc[w] = 0u;
-      if (!zx) {
-        A = ex + tfx<L>::TOPA - (32 * W - 53);
-        const uint32_t msk = sx ? 0xFFFFFFFFu : 0u;
-        uint64_t cy = msk & 1u;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const uint64_t v = (uint64_t)((w < W ? Mx[w] : 0u) ^ msk) + cy;
-          acc[w] = (uint32_t)v;
-          cy = v >> 32;
-        }
+        for (int w = 0; w < NW; ++w) acc[w] = 0u;
+      } else {
+        window_from_operand<L>(acc, A, Mx, ex, sx);
       }
     }
 #pragma unroll

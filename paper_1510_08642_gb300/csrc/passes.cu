@@ -42,8 +42,7 @@ template <> struct pfx<4> { static constexpr int NW = 9, TOP = 32 * 9 - 58; };
 // One element (i, j) of a fused pass. The operands (and C for the update
 // modes) are placed at one common scale as exact integers on the integer
 // pipe (fx::add_at), every sum of the pass is an exact multiword addition,
-// and each output is rounded back once (fx::from_fixed; QD limbs then
-// renormalised). Error per output: one rounding to DD / QD (a DD output is
+// and each output is rounded back once (fx::from_fixed). Error per output: one rounding to DD / QD (a DD output is
 // the DD nearest the exact sum, up to 2^-(top + 52) of the largest operand).
 template <int L, int KIND>
 __device__ __forceinline__ void pass_elem(const pass_args& a, int mode, int64_t i, int64_t j) {
@@ -96,13 +95,10 @@ __device__ __forceinline__ void pass_elem(const pass_args& a, int mode, int64_t 
       fx::add_at<L, NW>(r, c[q], emax, TOP, 0u);
     }
     double o[L];
-    fx::from_fixed<L, NW>(r, lsb, o);
+    fx::from_fixed<L, NW>(r, lsb, o);  // canonical DD / QD
     T v;
-    if constexpr (L == 2) {
-      v = dd_t{o[0], o[1]};
-    } else {
-      v = qd_renorm<4>(o);
-    }
+    if constexpr (L == 2) v = dd_t{o[0], o[1]};
+    else v = qd_t{{o[0], o[1], o[2], o[3]}};
     N::store(a.out[q].p, i * a.out[q].ld + j, v);
   };
   V r0, r1, r2;

@@ -6,6 +6,9 @@
 //   P NW K sh neg acc[0..NW-1] p[0..K-1] -> place_shr: acc[0 .. NW-1]
 //   N NW W A[0..NW-1]          -> acc_normalize: p M[0..W-1]   (6,4) / (9,7)
 //   R NW s A[0..NW-1]          -> acc_sar: A[0..NW-1]          (NW = 6 / 9)
+//   O L e s M[0..W-1]          -> operand_to_limbs: limbs (hex)  (L = 2: W = 4, 4: W = 7)
+//   Q b0..b3 y0 y1             -> qd_recip_refine: 4 limbs (hex)
+//   F L x(L) l(L) y(L)         -> window: x - l y, rounded to L limbs (hex)
 //   A L emax top n (sign x0 .. x(L-1)) x n -> add_at into V (NW = 5 / 9),
 //                              then from_fixed: V[0..NW-1] ; limbs (hex)
 // Doubles are read as 16 hex digits of their bit pattern.
@@ -15,6 +18,7 @@
 #include <cstring>
 
 #include "fx.cuh"
+#include "fxscalar.cuh"
 
 using namespace ddg;
 
@@ -101,6 +105,44 @@ static void do_sar() {
   for (int i = 0; i < NW; ++i) std::printf("%u%c", A[i], i + 1 < NW ? ' ' : '\n');
 }
 
+template <int L, int W>
+static void do_limbs() {
+  int e;
+  unsigned sg;
+  scan("%d %u", &e, &sg);
+  uint32_t M[W];
+  for (int i = 0; i < W; ++i) scan("%u", &M[i]);
+  double out[L];
+  fx::operand_to_limbs<L, W>(M, e, sg, out);
+  for (int q = 0; q < L; ++q) std::printf("%016llx%c", (unsigned long long)fx::dbits(out[q]), q + 1 < L ? ' ' : '\n');
+}
+
+template <int L>
+static void do_fms() {
+  constexpr int W = ddg::tfx<L>::W, NW = ddg::tfx<L>::NW;
+  double x[L], l[L], y[L];
+  for (int q = 0; q < L; ++q) x[q] = rd();
+  for (int q = 0; q < L; ++q) l[q] = rd();
+  for (int q = 0; q < L; ++q) y[q] = rd();
+  uint32_t acc[NW] = {0}, Ml[W], My[W];
+  int A = fx::expfield(x[0]) > 1 ? fx::expfield(x[0]) : 1;
+  fx::add_at<L, NW>(acc, x, A, ddg::tfx<L>::TOPA, 0u);
+  const int el = fx::to_fixed<L, W>(l, Ml), ey = fx::to_fixed<L, W>(y, My);
+  if ((fx::dbits(l[0]) << 1) != 0u && (fx::dbits(y[0]) << 1) != 0u)
+    ddg::window_sub_product<L>(acc, A, Ml, el & 0xFFFF, (uint32_t)el >> 16, My, ey & 0xFFFF, (uint32_t)ey >> 16);
+  double out[L];
+  fx::from_fixed<L, NW>(acc, A - 1075 - ddg::tfx<L>::TOPA, out);
+  for (int q = 0; q < L; ++q) std::printf("%016llx%c", (unsigned long long)fx::dbits(out[q]), q + 1 < L ? ' ' : '\n');
+}
+
+static void do_recip() {
+  double b[4], out[4];
+  for (int q = 0; q < 4; ++q) b[q] = rd();
+  const double y0 = rd(), y1 = rd();
+  ddg::qd_recip_refine(b, y0, y1, out);
+  for (int q = 0; q < 4; ++q) std::printf("%016llx%c", (unsigned long long)fx::dbits(out[q]), q < 3 ? ' ' : '\n');
+}
+
 int main() {
   char cmd[4];
   while (std::scanf("%3s", cmd) == 1) {
@@ -113,6 +155,16 @@ int main() {
       scan("%d %d", &a, &b);
       if (a == 4) do_mul<4, 3>();
       else do_mul<7, 6>();
+    } else if (cmd[0] == 'F') {
+      scan("%d", &a);
+      if (a == 2) do_fms<2>();
+      else do_fms<4>();
+    } else if (cmd[0] == 'Q') {
+      do_recip();
+    } else if (cmd[0] == 'O') {
+      scan("%d", &a);
+      if (a == 2) do_limbs<2, 4>();
+      else do_limbs<4, 7>();
     } else if (cmd[0] == 'N') {
       scan("%d %d", &a, &b);
       if (a == 6) do_norm<6, 4>();

@@ -195,3 +195,90 @@ def test_normalize_and_arithmetic_shift(fxbin, NW, W):
         got = value([int(t) for t in line.split()])
         signed = a - mod if a >= mod // 2 else a
         assert got == (signed >> s) % mod
+
+
+@pytest.mark.parametrize("L,W", [(2, 4), (4, 7)])
+def test_operand_to_limbs_canonical(fxbin, L, W):
+    """operand_to_limbs: greedy round-to-nearest limbs of M 2^(e - 1075 -
+    (32 W - 53)): each limb is the remaining value rounded to 53 bits, so
+    |limb_{q+1}| <= ulp(limb_q) / 2 and the sum is within half an ulp of the
+    last limb of the exact value."""
+    rng = random.Random(20 + L)
+    cases = []
+    for i in range(300):
+        M = rng.getrandbits(32 * W - 1) | (1 << (32 * W - 1))
+        if i % 4 == 0:  # long runs of zeros / ones below the leading bits
+            M = (1 << (32 * W - 1)) | (rng.getrandbits(20) << rng.randint(0, 32 * W - 30))
+        if i % 7 == 0:
+            M = (2 ** (32 * W) - 1) ^ rng.getrandbits(8)
+        cases.append((M, rng.randint(900, 1100), rng.randint(0, 1)))
+    out = run(fxbin, [f"O {L} {e} {s_} " + " ".join(map(str, words(M, W))) for M, e, s_ in cases])
+    for (M, e, s_), line in zip(cases, out):
+        limbs = [unhex(h) for h in line.split()]
+        exact = Fraction(M) * Fraction(2) ** (e - 1075 - (32 * W - 53)) * (-1 if s_ else 1)
+        rem = exact
+        for q, x in enumerate(limbs):
+            if x == 0.0:
+                assert all(t == 0.0 for t in limbs[q:])
+                break
+            ulp = Fraction(2) ** (math.frexp(x)[1] - 53)
+            assert abs(rem - Fraction(x)) <= ulp / 2, (q, M)
+            rem -= Fraction(x)
+        assert abs(rem) <= abs(exact) * Fraction(1, 2 ** (53 * L - 1))
+
+
+def test_qd_reciprocal_refinement(fxbin):
+    """qd_recip_refine (the LU's QD pivot reciprocal): from a DD
+    approximation the result is within 2^-208 of 1/b and canonical."""
+    rng = random.Random(33)
+    cases = []
+    for i in range(200):
+        b = expansion(rng, 4, sparse=(i % 3 == 0))
+        if i % 10 == 0:
+            b = [float(rng.randint(1, 1000)) * rng.choice([-1, 1]), 0.0, 0.0, 0.0]
+        exact = 1 / sum(Fraction(t) for t in b)
+        y0 = float(exact)
+        y1 = float(exact - Fraction(y0))
+        if i % 5 == 0:  # a double-only start (~53 bits)
+            y1 = 0.0
+        cases.append((b, exact, y0, y1))
+    out = run(fxbin, ["Q " + " ".join(hexd(t) for t in b) + f" {hexd(y0)} {hexd(y1)}" for b, _, y0, y1 in cases])
+    for (b, exact, _, _), line in zip(cases, out):
+        r = [unhex(h) for h in line.split()]
+        got = sum(Fraction(t) for t in r)
+        assert abs(got - exact) <= abs(exact) * Fraction(1, 2 ** 208), b
+        for q in range(3):
+            if r[q + 1] != 0.0:
+                assert abs(r[q + 1]) <= 2.0 ** (math.frexp(r[q])[1] - 54)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_window_multiply_subtract(fxbin, L):
+    """x - l y in a window (the LU's column update and triangular-solve
+    step): one rounding of the exact value plus 2^-120 (DD) / 2^-216 (QD)
+    of max(|x|, |l y|), including the window moving up for a large product
+    and cancellation."""
+    rng = random.Random(40 + L)
+    cases = []
+    for i in range(300):
+        x, l, y = (expansion(rng, L, sparse=(i % 3 == 0)) for _ in range(3))
+        if i % 4 == 0:
+            x = [t * 2.0 ** -60 for t in x]  # product far above x: window moves up
+        if i % 5 == 0:  # cancellation: x ~ l y
+            p = sum(Fraction(t) for t in l) * sum(Fraction(t) for t in y)
+            x = [float(p)] + [0.0] * (L - 1)
+        if i % 11 == 0:
+            l = [0.0] * L
+        cases.append((x, l, y))
+    out = run(fxbin, [f"F {L} " + " ".join(hexd(t) for t in x + l + y) for x, l, y in cases])
+    for (x, l, y), line in zip(cases, out):
+        r = [unhex(h) for h in line.split()]
+        X = sum(Fraction(t) for t in x)
+        P = sum(Fraction(t) for t in l) * sum(Fraction(t) for t in y)
+        exact = X - P
+        scale = max(abs(X), abs(P))
+        got = sum(Fraction(t) for t in r)
+        # one rounding to L limbs, plus the dropped partial products of the
+        # W-word product (2^-123 / 2^-219 of |l y|) and the window's floor
+        slack = Fraction(1, 2 ** (120 if L == 2 else 216))
+        assert abs(got - exact) <= abs(exact) * Fraction(1, 2 ** (53 * L - 1)) + scale * slack, (x, l, y)
