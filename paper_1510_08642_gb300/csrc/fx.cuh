@@ -1,16 +1,17 @@
-// Fixed-point window accumulation of exact products (the GB300 Block kernel's
-// multiply-add).
+// Fixed-point integer arithmetic for DD / QD numbers on the integer pipe.
 //
-// GB300 retires 2 FP64 instructions per clock per SM but 64 IMAD and 128
-// integer add/logic/shift instructions. The Block kernel therefore forms the
-// exact product of two doubles' significands on the integer pipe
-// (53 x 53 -> 106 bits by four 32x32->64 multiplies) and adds it, shifted
-// by the exponent, into a wide two's-complement fixed-point accumulator
-// (Kulisch-style, but only as wide as the product's range needs). Per output
-// entry c_ij the accumulator's scale is fixed before the k loop from the
-// largest exponent of row i of A and of column j of B, so no product can
-// overflow it and the accumulation is exact; bits below the window (2^-159
-// of the largest product for DD, 2^-255 for QD) are truncated.
+// GB300 retires 2 FP64 instructions per clock per SM but 64 IMAD and ~128
+// other integer instructions, so the library's DD / QD arithmetic runs on
+// the integer pipe wherever it is hot:
+//   * operands: an expansion x0 + x1 + ... summed exactly into a W-word
+//     integer M at the scale of x0 (to_fixed), or placed at a common scale
+//     shared by several operands (add_at);
+//   * products: the leading words of M_a M_b by multiword multiplication
+//     (mul_top), placed into a two's-complement window (place_shr);
+//   * windows: wide accumulators (Kulisch-style, only as wide as the
+//     products' range needs) whose scale is fixed from the largest operands,
+//     so the sums are exact; bits below the window are truncated;
+//   * rounding back: acc_chunks / from_fixed / operand_to_limbs.
 //
 // Word layout: acc[0] is the least significant 32-bit word; the top word
 // carries the sign. A double x is unpacked as |x| = (m1:m0) 2^(e - 1075) with
@@ -84,21 +85,6 @@ __host__ __device__ __forceinline__ int clz32(uint32_t x) {
 #else
   return x ? __builtin_clz(x) : 32;
 #endif
-}
-
-// Exact 106-bit product of two significands, as four 32-bit words.
-__host__ __device__ __forceinline__ void mant_mul(const unpacked& a, const unpacked& b, uint32_t (&p)[4]) {
-  const uint64_t t00 = (uint64_t)a.m0 * b.m0;
-  const uint64_t t01 = (uint64_t)a.m0 * b.m1;
-  const uint64_t t10 = (uint64_t)a.m1 * b.m0;
-  const uint64_t t11 = (uint64_t)a.m1 * b.m1;
-  const uint64_t mid = t01 + t10;  // < 2^54
-  const uint64_t lo = t00 + (mid << 32);
-  const uint64_t hi = t11 + (mid >> 32) + (lo < t00 ? 1u : 0u);
-  p[0] = (uint32_t)lo;
-  p[1] = (uint32_t)(lo >> 32);
-  p[2] = (uint32_t)hi;
-  p[3] = (uint32_t)(hi >> 32);
 }
 
 // acc += (d XOR mask) + neg, mask = -neg: adds d, or subtracts it when neg = 1.
@@ -548,9 +534,12 @@ __host__ __device__ __forceinline__ int acc_normalize(const uint32_t (&A)[NW], u
 // Bits below the L + 1 pieces are truncated. For L = 2 this is the DD
 // nearest V (hi = V rounded to 53 bits, |lo| <= ulp(hi) / 2).
 template <int L, int NW>
+__host__ __device__ __forceinline__ void from_fixed_balanced(uint32_t (&V)[NW], int lsb, double (&out)[L]);
+
+template <int L, int NW>
 __host__ __device__ __forceinline__ void from_fixed(uint32_t (&V)[NW], int lsb, double (&out)[L]) {
-  const uint32_t neg = acc_abs<NW>(V);
   if constexpr (L == 4) {
+    const uint32_t neg = acc_abs<NW>(V);
     uint32_t M[7];
     const int p = acc_normalize<NW, 7>(V, M);
     if (p < 0) {
@@ -559,8 +548,18 @@ __host__ __device__ __forceinline__ void from_fixed(uint32_t (&V)[NW], int lsb, 
       return;
     }
     operand_to_limbs<4, 7>(M, p + lsb + 1023, neg, out);
-    return;
+  } else {
+    from_fixed_balanced<L, NW>(V, lsb, out);
   }
+}
+
+// The balanced-digit form of the above for any L (V is destroyed): the
+// leading L 53-bit pieces and the next bit of |V| as balanced digits; for
+// L = 2 the nearest DD, for L = 4 a nonoverlapping expansion that a QD
+// renormalisation turns canonical.
+template <int L, int NW>
+__host__ __device__ __forceinline__ void from_fixed_balanced(uint32_t (&V)[NW], int lsb, double (&out)[L]) {
+  const uint32_t neg = acc_abs<NW>(V);
   uint64_t ch[L + 1];
   int ex[L + 1];
   if (!acc_chunks<NW, L + 1>(V, ch, ex)) {
