@@ -274,8 +274,11 @@ def saturation_rate(server: Server, count: int = 40, seed: int = 1) -> float:
 
 
 def sweep(rates=(0.25, 0.5, 0.75, 0.9, 1.1), count: int = 60, seed: int = 2, server: Server | None = None):
-    """p50 / p99 latency and throughput at fractions of the saturation rate."""
+    """p50 / p99 latency and throughput at fractions of the saturation rate
+    (measured after one warm-up run: the first run of a process pays for
+    module loading and the growth of the stream-ordered memory pools)."""
     server = server or Server()
+    saturation_rate(server)  # warm-up
     mu = saturation_rate(server)
     rows = []
     for i, f in enumerate(rates):
