@@ -481,6 +481,7 @@ def run_ours(args, w):
             del XA, XB, XC
             torch.cuda.empty_cache()
         extras[WL.DD_LU_4096.name] = time_lu(P, torch, WL.DD_LU_4096, device, stream, K=256)
+        extras[WL.DD_LU_4096_OZ2.name] = time_lu(P, torch, WL.DD_LU_4096_OZ2, device, stream, K=256)
         extras[WL.QD_LU_2048.name] = time_lu(P, torch, WL.QD_LU_2048, device, stream, K=256)
         extras["batched_1000_mixed"] = time_batched(P, torch, device, stream)
         line["extras"] = extras

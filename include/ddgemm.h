@@ -143,8 +143,9 @@ ddg_status qd_gemm(int64_t m, int64_t l, int64_t n, qd_mat A, qd_mat B, qd_mat C
  * (Section 4, steps 1-3): right-looking blocked LU with block columns of K
  * (1 <= K <= 512; the paper takes K = alpha n_min) whose trailing update
  * A22 := A22 - L21 U12 is the DD product of `opts` (algo, cutoff, ...;
- * NULL = defaults, Winograd) in mode DDG_SUB. On return A holds L (unit
- * lower, below the diagonal) and U.
+ * NULL = defaults, Winograd; DDG_OZAKI / DDG_OZAKI2 give the INT8 products'
+ * normwise accuracy for the updates) in mode DDG_SUB. On return A holds L
+ * (unit lower, below the diagonal) and U.
  *   pivot = 1: partial pivoting, pivot of column j = the first row i >= j
  *              with the largest |a_ij| compared as DD; pivot = 0: none (the
  *              paper's setting, Section 4).

@@ -43,6 +43,8 @@ DD_WINOGRAD_8192 = Workload("dd_winograd_n8192", 2, 8192, "winograd", 512, 109, 
 DD_OZAKI_8192_S16 = Workload("dd_ozaki_n8192_s16", 2, 8192, "ozaki", 512, 109, 110, 16)
 # Section 4 LU solve (random [-1, 1] matrix), block column K, Winograd update.
 DD_LU_4096 = Workload("dd_lu_n4096", 2, 4096, "winograd", 512, 111, 0)
+# The same solve with the trailing updates as INT8 residue products (CRT).
+DD_LU_4096_OZ2 = Workload("dd_lu_n4096_ozaki2", 2, 4096, "ozaki2", 512, 111, 0)
 # Same 512^3 leaves as the headline at n = 2048 (two levels, 49 leaves):
 # operands 200 MB > L2, small enough for a counter capture.
 DD_WINOGRAD_2048 = Workload("dd_winograd_n2048", 2, 2048, "winograd", 512, 112, 113)

@@ -194,3 +194,16 @@ def test_qd_section4_forward_error():
     from fractions import Fraction
     fe = max(abs(float(sum(Fraction(float(v)) for v in Xh[:, i, 0]) - i)) / max(i, 1) for i in range(n))
     assert fe < 1e-50
+
+
+@pytest.mark.parametrize("algo", ["ozaki", "ozaki2"])
+def test_int8_trailing_updates(algo):
+    """DD LU whose trailing updates are INT8 products (slices / residues +
+    CRT): normwise-accurate updates keep the exact residual below n 2^-100
+    and the pivots of the oracle's unblocked LU."""
+    n = 257
+    A, X, Bv = section4_problem(n, seed=61)
+    LU, ipiv, Xh = lu_solve(A, Bv, K=64, algo=algo, cutoff=16)
+    assert rel_residual(A, Xh, Bv) <= n * 2.0 ** -100
+    _, piv_o, info = O.dd_getrf(A, pivot=True)
+    assert np.array_equal(ipiv, piv_o)
