@@ -505,6 +505,7 @@ def run_serving(args):
     srv = S.Server(slots=4, hbm_budget=96 << 30, max_batch=32, gemm_cutoff=512, lu_K=256,
                    lu_cutoff=512)
     res = S.sweep(rates=tuple(args.rates), count=args.requests, seed=3, server=srv)
+    srv.close()
     print(json.dumps({"workload": "serving_dd_gemm_lu_mix", "requests_per_point": args.requests, **res}),
           flush=True)
     return 0

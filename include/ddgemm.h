@@ -19,9 +19,11 @@
  *     (|lo| <= ulp(hi)/2, and likewise between QD limbs); non-finite values
  *     give undefined results (they are not checked).
  *   - The caller owns all matrices. The library owns nothing it returns:
- *     temporary storage for a call is taken from the CUDA stream-ordered
- *     allocator on the call's stream and released on it before the call's
- *     work completes.
+ *     temporary storage for a call is taken from the library's
+ *     stream-ordered workspace pool of the current device (see
+ *     ddg_workspace_reserve) on the call's stream and released on it before
+ *     the call's work completes. The current device must be the one that
+ *     `stream` and the matrices belong to.
  *   - Calls are asynchronous with respect to the host: work is queued on
  *     `stream` (a cudaStream_t, NULL = the legacy default stream) and may
  *     fork onto library-owned streams that join back into `stream`. Results
@@ -61,7 +63,9 @@ typedef enum {
                        reference order (the DD/QD multiply then add of each
                        term is the pinned sequence documented with the
                        kernels) */
-  DDG_BLOCK = 1,    /* C_ij = sum_k A_ik B_kj over register/shared tiles */
+  DDG_BLOCK = 1,    /* C_ij = sum_k A_ik B_kj over register/shared tiles
+                       (for n <= 8 columns: one warp per c_ij, its lanes
+                       splitting k, same arithmetic) */
   DDG_STRASSEN = 2, /* Strassen 1969: 7 products, 18 quadrant sums per level */
   DDG_WINOGRAD = 3, /* Winograd's variant: 7 products, 15 quadrant sums */
   DDG_OZAKI = 4     /* not in the paper (the Ozaki scheme): A and B split
@@ -274,10 +278,11 @@ int32_t ddg_block_fp64_ops_per_mac(int32_t limbs, int32_t accum);
 int32_t ddg_ozaki2_precision(int32_t moduli, int64_t l);
 
 /* Launch profiling. Between ddg_profile_begin() and ddg_profile_end() every
- * kernel launch of the library is bracketed by CUDA events on its stream.
- * ddg_profile_end() waits for those events and fills out[k] for kernel
- * kinds k = 0 (Simple), 1 (Block), 2 (quadrant passes), 3 (INT8 slice
- * products), k < nkinds:
+ * product and pass launch of the library is bracketed by CUDA events on its
+ * stream. ddg_profile_end() waits for those events and fills out[k] for
+ * kernel kinds k = 0 (Simple), 1 (Block), 2 (quadrant passes), 3 (INT8
+ * products), 4 (Block products with at most 8 columns, one warp per
+ * output), k < nkinds:
  * launches, sum of launch durations, busy time (union of the launch
  * intervals), and the algorithmic work and bytes of those launches.
  * For measurement only: it adds two event records per launch. */
@@ -285,13 +290,39 @@ typedef struct {
   uint64_t launches;
   double sum_ms;
   double busy_ms;
-  double ops;   /* FP64 instructions (kind 0), multiply-adds (kind 1), DD / QD
-                   sums (kind 2) or INT8 operations, 2 per multiply-add
-                   (kind 3, the INT8 products) */
+  double ops;   /* FP64 instructions (kind 0), multiply-adds (kinds 1 and 4),
+                   DD / QD sums (kind 2) or INT8 operations, 2 per
+                   multiply-add (kind 3, the INT8 products) */
   double bytes;
 } ddg_kernel_prof;
 ddg_status ddg_profile_begin(void);
 ddg_status ddg_profile_end(ddg_kernel_prof* out, int32_t nkinds);
+
+/* Workspace pool (no counterpart in the paper; for services). The
+ * temporaries of every call come from one stream-ordered memory pool per
+ * device owned by the library. By default it keeps no memory between calls
+ * (unused memory returns to the device at the next synchronisation).
+ *
+ * ddg_workspace_reserve(device, bytes): keep up to `bytes` of unused pool
+ * memory mapped between calls and grow the pool to `bytes` now (blocking
+ * until done), so that calls needing at most that much in total are served
+ * without mapping memory. bytes = 0 only sets the threshold back to 0.
+ * DDG_EINVAL for a device index that does not exist, DDG_ENOMEM if the
+ * memory cannot be had (the threshold is then 0 again).
+ * ddg_workspace_release(device): threshold 0 and return every unused byte
+ * of the pool to the device now (memory of calls still in flight stays
+ * until they complete).
+ * ddg_workspace_stats(device, out): the pool's current mapped and used
+ * bytes, its threshold and the largest used size so far. */
+typedef struct {
+  uint64_t reserved_bytes;  /* memory mapped by the pool */
+  uint64_t used_bytes;      /* of which held by calls in flight */
+  uint64_t threshold_bytes; /* unused memory kept between calls */
+  uint64_t used_high_bytes; /* high-water mark of used_bytes */
+} ddg_workspace_info;
+ddg_status ddg_workspace_reserve(int32_t device, uint64_t bytes);
+ddg_status ddg_workspace_release(int32_t device);
+ddg_status ddg_workspace_stats(int32_t device, ddg_workspace_info* out);
 
 /* Number of CUDA kernels this library has launched in this process, all
  * threads and devices together (monotonic; for launch accounting). */

@@ -45,7 +45,7 @@ class ddg_kernel_prof(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
-PROF_KINDS = ("simple", "block", "pass", "ozaki")
+PROF_KINDS = ("simple", "block", "pass", "ozaki", "gemv")
 
 
 class ddg_problem(ctypes.Structure):
@@ -58,6 +58,11 @@ class ddg_batch_stats(ctypes.Structure):
     _fields_ = [("problems", c_i64), ("leaf_tasks", c_i64), ("leaf_tiles", c_i64),
                 ("pass_tasks", c_i64), ("launches_per_run", c_i64),
                 ("workspace_bytes", ctypes.c_uint64), ("leaf_macs", ctypes.c_double)]
+
+
+class ddg_workspace_info(ctypes.Structure):
+    _fields_ = [("reserved_bytes", ctypes.c_uint64), ("used_bytes", ctypes.c_uint64),
+                ("threshold_bytes", ctypes.c_uint64), ("used_high_bytes", ctypes.c_uint64)]
 
 
 class DDGError(RuntimeError):
@@ -87,6 +92,9 @@ SIGNATURES = {
     "dd_getrs": (c_i32, [c_i64, c_i64, dd_mat, c_vp, dd_mat, c_vp]),
     "qd_getrf": (c_i32, [c_i64, qd_mat, c_vp, c_i32, c_i32, ctypes.POINTER(ddg_opts), c_vp, c_vp]),
     "qd_getrs": (c_i32, [c_i64, c_i64, qd_mat, c_vp, qd_mat, c_vp]),
+    "ddg_workspace_reserve": (c_i32, [c_i32, ctypes.c_uint64]),
+    "ddg_workspace_release": (c_i32, [c_i32]),
+    "ddg_workspace_stats": (c_i32, [c_i32, ctypes.POINTER(ddg_workspace_info)]),
     "ddg_last_error": (ctypes.c_char_p, []),
     "ddg_kernel_launches": (ctypes.c_uint64, []),
     "ddg_profile_begin": (c_i32, []),
@@ -225,3 +233,17 @@ def qd_getrf(n, A: qd_mat, ipiv: int, K: int, pivot: int, o: ddg_opts | None, in
 
 def qd_getrs(n, nrhs, LU: qd_mat, ipiv: int, B: qd_mat, stream: int = 0) -> int:
     return load().qd_getrs(n, nrhs, LU, c_vp(ipiv), B, c_vp(stream))
+
+
+def ddg_workspace_reserve(device: int, nbytes: int) -> None:
+    check(load().ddg_workspace_reserve(device, nbytes))
+
+
+def ddg_workspace_release(device: int) -> None:
+    check(load().ddg_workspace_release(device))
+
+
+def ddg_workspace_stats(device: int) -> dict:
+    st = ddg_workspace_info()
+    check(load().ddg_workspace_stats(device, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in ddg_workspace_info._fields_}

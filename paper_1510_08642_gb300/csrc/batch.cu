@@ -245,7 +245,7 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
     b->bytes = temps + tb + 4096;
   }
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaMallocAsync(reinterpret_cast<void**>(&b->buf), std::max<size_t>(b->bytes, 256), cs) != cudaSuccess) {
+  if (ddg::ws_alloc(reinterpret_cast<void**>(&b->buf), std::max<size_t>(b->bytes, 256), cs) != cudaSuccess) {
     cudaGetLastError();
     delete b;
     return set_error(DDG_ENOMEM, "ddg_batch_create: workspace of " + std::to_string(b->bytes) + " bytes");
@@ -306,14 +306,14 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
       if (std::get<0>(kv.first) == d) add_g(kv.second, std::get<1>(kv.first));
   }
   if (temps + host.size() > b->bytes) {
-    cudaFreeAsync(b->buf, cs);
+    ddg::ws_free(b->buf, cs);
     delete b;
     return set_error(DDG_ECUDA, "ddg_batch_create: task list larger than planned");
   }
   // pageable source: the copy is staged before the call returns
   if (!host.empty() &&
       cudaMemcpyAsync(b->buf + temps, host.data(), host.size(), cudaMemcpyHostToDevice, cs) != cudaSuccess) {
-    cudaFreeAsync(b->buf, cs);
+    ddg::ws_free(b->buf, cs);
     delete b;
     return set_error(DDG_ECUDA, "ddg_batch_create: task upload");
   }
@@ -324,7 +324,7 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
   b->stats.workspace_bytes = (uint64_t)b->bytes;
   b->stats.leaf_macs = real.leaf_macs;
   if (use_graph && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaFreeAsync(b->buf, cs);
+    ddg::ws_free(b->buf, cs);
     delete b;
     return set_error(DDG_ECUDA, "ddg_batch_create: capture stream");
   }
@@ -383,7 +383,7 @@ ddg_status ddg_batch_destroy(ddg_batch b, void* stream) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
   }
-  if (b->buf && cudaFreeAsync(b->buf, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess && st == DDG_OK)
+  if (b->buf && ddg::ws_free(b->buf, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess && st == DDG_OK)
     st = ddg::set_error(DDG_ECUDA, "ddg_batch_destroy: free");
   cudaSetDevice(cur);
   delete b;

@@ -22,6 +22,7 @@
 
 #include "arith.cuh"
 #include "fx.cuh"
+#include "fx_round.cuh"
 #include "kernels.cuh"
 
 namespace ddg {
@@ -29,24 +30,14 @@ namespace ddg {
 namespace {
 
 template <int L> struct fxcfg;
-template <> struct fxcfg<2> {
-  static constexpr int BM = 16, BN = 32, BK = 16, TM = 2, TN = 2, NW = 6;
-  static constexpr int W = 4, D = 3, K = 2 * W - D;  // operand words, dropped / kept product words
-  static constexpr int MINB = 8;                      // resident CTAs per SM (register cap 64)
-  static constexpr int LSB0 = -2204;  // window LSB exponent = row_f + col_f + LSB0
+template <> struct fxcfg<2> : fxwin<2> {
+  static constexpr int BM = 16, BN = 32, BK = 16, TM = 2, TN = 2;
+  static constexpr int MINB = 8;  // resident CTAs per SM (register cap 64)
 };
-template <> struct fxcfg<4> {
-  static constexpr int BM = 8, BN = 32, BK = 16, TM = 1, TN = 2, NW = 9;
-  static constexpr int W = 7, D = 6, K = 2 * W - D;
+template <> struct fxcfg<4> : fxwin<4> {
+  static constexpr int BM = 8, BN = 32, BK = 16, TM = 1, TN = 2;
   static constexpr int MINB = 8;
-  static constexpr int LSB0 = -2300;
 };
-
-__device__ __forceinline__ double scaled(uint64_t chunk, int k, uint32_t neg) {
-  if (chunk == 0 || k < -2044) return 0.0;
-  double v = fx::pow2_product(__ull2double_rn(chunk), k > 2046 ? 2046 : k);
-  return neg ? -v : v;
-}
 
 }  // namespace
 
@@ -194,27 +185,7 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
       const int64_t gi = i0 + ty + r * NY, gj = j0 + tx + c * NX;
       if (gi < m && gj < n) {
         const int lsb = row_f[ty + r * NY] + col_f[tx + c * NX] + P::LSB0;
-        const uint32_t neg = fx::acc_abs<NW>(acc[r][c]);
-        typename N::T v;
-        if constexpr (L == 2) {
-          uint64_t ch[2];
-          int ex[2];
-          double hi = 0.0, lo = 0.0;
-          if (fx::acc_chunks<NW, 2>(acc[r][c], ch, ex)) {
-            hi = scaled(ch[0], lsb + ex[0], neg);
-            lo = scaled(ch[1], lsb + ex[1], neg);
-          }
-          two_sum(hi, lo, v.hi, v.lo);
-        } else {
-          uint64_t ch[4];
-          int ex[4];
-          double x[4] = {0.0, 0.0, 0.0, 0.0};
-          if (fx::acc_chunks<NW, 4>(acc[r][c], ch, ex)) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) x[q] = scaled(ch[q], lsb + ex[q], neg);
-          }
-          v = qd_renorm<4>(x);
-        }
+        typename N::T v = window_round<L, NW>(acc[r][c], lsb);
         const int64_t off = gi * C.ld + gj;
         if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
         else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));

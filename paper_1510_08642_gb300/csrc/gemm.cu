@@ -123,8 +123,9 @@ static ddg_status copy_mat(const Ctx& c, const mat& dst, const mat& src, int64_t
 
 static cudaError_t base_case(const Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
                              const mat& C, int mode, cudaStream_t s) {
-  return c.accum == 0 ? launch_block_fx(c.L, m, l, n, A, B, C, mode, s)
-                      : launch_block(c.L, m, l, n, A, B, C, mode, s);
+  if (c.accum != 0) return launch_block(c.L, m, l, n, A, B, C, mode, s);
+  return n <= GEMV_MAX_N ? launch_gemv_fx(c.L, m, l, n, A, B, C, mode, s)
+                         : launch_block_fx(c.L, m, l, n, A, B, C, mode, s);
 }
 
 static bool splits(const Ctx& c, int64_t m, int64_t l, int64_t n) {
@@ -378,7 +379,7 @@ ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const 
   c.dry = false;
   void* ws = nullptr;
   if (total) {
-    cudaError_t e = cudaMallocAsync(&ws, total, s);
+    cudaError_t e = ddg::ws_alloc(&ws, total, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(DDG_ENOMEM, "cudaMallocAsync of " + std::to_string(total) + " bytes: " + cudaGetErrorString(e));
@@ -387,7 +388,7 @@ ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const 
   c.base = static_cast<char*>(ws);
   ddg_status st = top(c, m, l, n, A, B, C, mode, o.pad == 1, s);
   if (ws) {
-    cudaError_t e = cudaFreeAsync(ws, s);
+    cudaError_t e = ddg::ws_free(ws, s);
     if (st == DDG_OK && e != cudaSuccess) return fail(DDG_ECUDA, std::string("cudaFreeAsync: ") + cudaGetErrorString(e));
   }
   return st;

@@ -26,7 +26,7 @@ inline mat view(const mat& M, int64_t r0, int64_t c0) {
 extern std::atomic<uint64_t> g_launches;
 
 // Launch profiling hooks (profile.cu); no-ops unless ddg_profile_begin ran.
-enum ProfKind { PROF_SIMPLE = 0, PROF_BLOCK = 1, PROF_PASS = 2, PROF_OZAKI = 3 };
+enum ProfKind { PROF_SIMPLE = 0, PROF_BLOCK = 1, PROF_PASS = 2, PROF_OZAKI = 3, PROF_GEMV = 4 };
 bool prof_enabled();
 void prof_begin_launch(cudaStream_t s, cudaEvent_t* start);
 void prof_end_launch(cudaStream_t s, cudaEvent_t start, int kind, double ops, double bytes);
@@ -55,6 +55,12 @@ cudaError_t launch_simple(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat
 cudaError_t launch_block_fx(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,
                             int mode, cudaStream_t s);
 int block_fx_fp64_ops_per_mac(int limbs);
+
+// The same product for n <= GEMV_MAX_N columns: one warp per output, lanes
+// splitting k (gemv_fx.cu); the Block base case dispatches to it.
+constexpr int64_t GEMV_MAX_N = 8;
+cudaError_t launch_gemv_fx(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C, int mode,
+                           cudaStream_t s);
 
 // One product of a grouped launch (device-resident task list). Tiles are
 // numbered consecutively: task t owns tiles [tile0, tile0 + tiles_m tiles_n).
@@ -104,6 +110,11 @@ namespace ddg {
 // Error text of the calling host thread (ddg_last_error).
 void clear_error();
 ddg_status set_error(ddg_status st, const std::string& msg);
+
+// Temporaries of a call: the library's workspace pool of the current device
+// (pool.cu), stream-ordered like cudaMallocAsync / cudaFreeAsync.
+cudaError_t ws_alloc(void** p, size_t bytes, cudaStream_t s);
+cudaError_t ws_free(void* p, cudaStream_t s);
 
 // C (mode) A B with options o (validated by the caller): the body of
 // dd_gemm / qd_gemm, used by the LU routines.

@@ -648,7 +648,7 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
   const int64_t maxparts = (n + RB - 1) / RB;
   const size_t bytes = sizeof(partial_t) * (size_t)maxparts + 512;
   void* ws = nullptr;
-  if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
+  if (ddg::ws_alloc(&ws, bytes, s) != cudaSuccess) {
     cudaGetLastError();
     return set_error(DDG_ENOMEM, nm + ": scratch allocation failed");
   }
@@ -714,7 +714,7 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
         cudaStreamSynchronize(s) != cudaSuccess)
       st = set_error(DDG_ECUDA, nm + ": reading the pivot status");
   }
-  cudaFreeAsync(ws, s);
+  ddg::ws_free(ws, s);
   if (st == DDG_OK && hinfo != 0)
     return set_error(DDG_ESINGULAR, nm + ": exactly zero pivot in column " + std::to_string(hinfo - 1));
   return st;
@@ -734,7 +734,7 @@ static ddg_status getrs_impl(const char* name, int64_t n, int64_t nrhs, const ma
   const size_t plane = ((size_t)n * nrhs * sizeof(double) + 255) & ~(size_t)255;
   const size_t bytes = L * plane + (((size_t)n * sizeof(int64_t) + 255) & ~(size_t)255);
   void* ws = nullptr;
-  if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
+  if (ddg::ws_alloc(&ws, bytes, s) != cudaSuccess) {
     cudaGetLastError();
     return set_error(DDG_ENOMEM, nm + ": scratch allocation failed");
   }
@@ -762,7 +762,7 @@ static ddg_status getrs_impl(const char* name, int64_t n, int64_t nrhs, const ma
       if (cudaMemcpy2DAsync(Bm.p[q], Bm.ld * sizeof(double), X.p[q], nrhs * sizeof(double),
                             nrhs * sizeof(double), n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         st = set_error(DDG_ECUDA, nm + ": copy-back");
-  cudaFreeAsync(ws, s);
+  ddg::ws_free(ws, s);
   return st;
 }
 

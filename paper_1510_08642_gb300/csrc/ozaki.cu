@@ -659,7 +659,7 @@ ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, cons
   const size_t bA = al256((size_t)s * mpad * lpad), bB = al256((size_t)s * npad * lpad);
   const size_t bD = al256((size_t)s * mpad * npad * 4), bE = al256((size_t)(m + n) * 4);
   void* ws = nullptr;
-  if (cudaMallocAsync(&ws, bA + bB + bD + bE, st) != cudaSuccess) {
+  if (ddg::ws_alloc(&ws, bA + bB + bD + bE, st) != cudaSuccess) {
     cudaGetLastError();
     return set_error(DDG_ENOMEM, "ozaki: workspace allocation failed");
   }
@@ -703,7 +703,7 @@ ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, cons
     launched();
     e = cudaGetLastError();
   }
-  cudaFreeAsync(ws, st);
+  ddg::ws_free(ws, st);
   if (e != cudaSuccess) return set_error(DDG_ECUDA, std::string("ozaki: ") + cudaGetErrorString(e));
   return DDG_OK;
 }
@@ -722,7 +722,7 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
   const size_t bA = al256((size_t)N * mpad * lpad), bB = al256((size_t)N * npad * lpad);
   const size_t bR = al256((size_t)N * mpad * npad), bE = al256((size_t)(m + n) * 4);
   void* ws = nullptr;
-  if (cudaMallocAsync(&ws, bA + bB + bR + bE, st) != cudaSuccess) {
+  if (ddg::ws_alloc(&ws, bA + bB + bR + bE, st) != cudaSuccess) {
     cudaGetLastError();
     return set_error(DDG_ENOMEM, "ozaki2: workspace allocation failed");
   }
@@ -758,7 +758,7 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
     launched();
     e = cudaGetLastError();
   }
-  cudaFreeAsync(ws, st);
+  ddg::ws_free(ws, st);
   if (e != cudaSuccess) return set_error(DDG_ECUDA, std::string("ozaki2: ") + cudaGetErrorString(e));
   return DDG_OK;
 }

@@ -1,5 +1,7 @@
 // Throughput probe for the roofline denominators: FP64 DFMA / DADD, FP32 FFMA,
-// INT32 IMAD / IADD, INT8 mma.sync (m16n8k32) and FP64 mma.sync (m8n8k4).
+// INT32 IMAD / IADD, 64-bit mad.wide, mad.hi, the three-instruction
+// multiword multiply-add step, INT8 mma.sync (m16n8k32) and FP64 mma.sync
+// (m8n8k4).
 // Each kernel runs independent dependency chains in every thread of a grid of
 // 1..8 blocks per SM; best of 5 timed launches. Prints one JSON line.
 #include <cstdio>
@@ -50,6 +52,91 @@ __global__ void k_imad(unsigned* out, int iters, unsigned a, unsigned b){
     for(int i=0;i<ILP;i++) x[i]=x[i]*a+b;
   }
   unsigned s=0; for(int i=0;i<ILP;i++) s^=x[i];
+  out[blockIdx.x*blockDim.x+threadIdx.x]=s;
+}
+// 64-bit multiply-add of 32-bit operands: x64 += lo32(x64) * a (mad.wide)
+template<int ILP, bool SIGNED>
+__global__ void k_imadwide(unsigned long long* out, int iters, unsigned a){
+  unsigned long long x[ILP];
+  for(int i=0;i<ILP;i++) x[i]=threadIdx.x+i;
+  for(int it=0; it<iters; it++){
+    #pragma unroll
+    for(int i=0;i<ILP;i++){
+      if(SIGNED) asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(x[i]) : "r"((unsigned)x[i]), "r"(a));
+      else asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(x[i]) : "r"((unsigned)x[i]), "r"(a));
+    }
+  }
+  unsigned long long s=0; for(int i=0;i<ILP;i++) s^=x[i];
+  out[blockIdx.x*blockDim.x+threadIdx.x]=s;
+}
+// high word of a 32 x 32-bit product plus an addend (mad.hi)
+template<int ILP>
+__global__ void k_imadhi(unsigned* out, int iters, unsigned a, unsigned b){
+  unsigned x[ILP];
+  for(int i=0;i<ILP;i++) x[i]=threadIdx.x+i;
+  for(int it=0; it<iters; it++){
+    #pragma unroll
+    for(int i=0;i<ILP;i++) asm("mad.hi.u32 %0, %0, %1, %2;" : "+r"(x[i]) : "r"(a), "r"(b));
+  }
+  unsigned s=0; for(int i=0;i<ILP;i++) s^=x[i];
+  out[blockIdx.x*blockDim.x+threadIdx.x]=s;
+}
+// one partial product into a three-word running sum with carries
+// (mad.lo.cc, madc.hi.cc, madc.lo): counted as one step of three instructions
+template<int ILP>
+__global__ void k_comba(unsigned* out, int iters, unsigned a, unsigned b){
+  unsigned c0[ILP], c1[ILP], c2[ILP];
+  for(int i=0;i<ILP;i++){c0[i]=threadIdx.x+i; c1[i]=i; c2[i]=0;}
+  for(int it=0; it<iters; it++){
+    #pragma unroll
+    for(int i=0;i<ILP;i++)
+      asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\tmadc.hi.cc.u32 %1, %3, %4, %1;\n\tmadc.lo.u32 %2, %2, 1, 0;"
+          : "+r"(c0[i]), "+r"(c1[i]), "+r"(c2[i]) : "r"(a ^ c2[i]), "r"(b));
+  }
+  unsigned s=0; for(int i=0;i<ILP;i++) s^=c0[i]^c1[i]^c2[i];
+  out[blockIdx.x*blockDim.x+threadIdx.x]=s;
+}
+// the same step with the carry captured by addc instead of madc.lo
+template<int ILP>
+__global__ void k_comba_addc(unsigned* out, int iters, unsigned a, unsigned b){
+  unsigned c0[ILP], c1[ILP], c2[ILP];
+  for(int i=0;i<ILP;i++){c0[i]=threadIdx.x+i; c1[i]=i; c2[i]=0;}
+  for(int it=0; it<iters; it++){
+    #pragma unroll
+    for(int i=0;i<ILP;i++)
+      asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\tmadc.hi.cc.u32 %1, %3, %4, %1;\n\taddc.u32 %2, %2, 0;"
+          : "+r"(c0[i]), "+r"(c1[i]), "+r"(c2[i]) : "r"(a ^ c2[i]), "r"(b));
+  }
+  unsigned s=0; for(int i=0;i<ILP;i++) s^=c0[i]^c1[i]^c2[i];
+  out[blockIdx.x*blockDim.x+threadIdx.x]=s;
+}
+// high half only into a two-word sum (mad.hi.cc, addc)
+template<int ILP>
+__global__ void k_hi_addc(unsigned* out, int iters, unsigned a, unsigned b){
+  unsigned c1[ILP], c2[ILP];
+  for(int i=0;i<ILP;i++){c1[i]=threadIdx.x+i; c2[i]=0;}
+  for(int it=0; it<iters; it++){
+    #pragma unroll
+    for(int i=0;i<ILP;i++)
+      asm("mad.hi.cc.u32 %0, %2, %3, %0;\n\taddc.u32 %1, %1, 0;"
+          : "+r"(c1[i]), "+r"(c2[i]) : "r"(a ^ c2[i]), "r"(b));
+  }
+  unsigned s=0; for(int i=0;i<ILP;i++) s^=c1[i]^c2[i];
+  out[blockIdx.x*blockDim.x+threadIdx.x]=s;
+}
+// two-word add with carry written as multiply-by-one (madc.lo x, y, 1, x) or as addc
+template<int ILP, bool MADC>
+__global__ void k_addcarry(unsigned* out, int iters, unsigned a, unsigned b){
+  unsigned x0[ILP], x1[ILP];
+  for(int i=0;i<ILP;i++){x0[i]=threadIdx.x+i; x1[i]=i;}
+  for(int it=0; it<iters; it++){
+    #pragma unroll
+    for(int i=0;i<ILP;i++){
+      if(MADC) asm("add.cc.u32 %0, %0, %2;\n\tmadc.lo.u32 %1, %3, 1, %1;" : "+r"(x0[i]), "+r"(x1[i]) : "r"(a), "r"(b ^ x0[i]));
+      else asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;" : "+r"(x0[i]), "+r"(x1[i]) : "r"(a), "r"(b ^ x0[i]));
+    }
+  }
+  unsigned s=0; for(int i=0;i<ILP;i++) s^=x0[i]^x1[i];
   out[blockIdx.x*blockDim.x+threadIdx.x]=s;
 }
 template<int ILP>
@@ -115,6 +202,14 @@ int main(){
   timeit([&]{k_ffma<8><<<blocks,th>>>((float*)buf,it,1.0000001f,1e-9f);}, (double)blocks*th*it*8, "ffma_per_s");
   timeit([&]{k_imad<8><<<blocks,th>>>((unsigned*)buf,it,12345u,678u);}, (double)blocks*th*it*8, "imad_per_s");
   timeit([&]{k_iadd<8><<<blocks,th>>>((unsigned*)buf,it,12345u,678u);}, (double)blocks*th*it*16, "iaddxor_per_s");
+  timeit([&]{k_imadwide<8,false><<<blocks,th>>>((unsigned long long*)buf,it,12345u);}, (double)blocks*th*it*8, "imad_wide_u32_per_s");
+  timeit([&]{k_imadwide<8,true><<<blocks,th>>>((unsigned long long*)buf,it,12345u);}, (double)blocks*th*it*8, "imad_wide_s32_per_s");
+  timeit([&]{k_imadhi<8><<<blocks,th>>>((unsigned*)buf,it,12345u,678u);}, (double)blocks*th*it*8, "imad_hi_per_s");
+  timeit([&]{k_comba<8><<<blocks,th>>>((unsigned*)buf,it,12345u,678u);}, (double)blocks*th*it*8, "comba_step_per_s");
+  timeit([&]{k_comba_addc<8><<<blocks,th>>>((unsigned*)buf,it,12345u,678u);}, (double)blocks*th*it*8, "comba_step_addc_per_s");
+  timeit([&]{k_hi_addc<8><<<blocks,th>>>((unsigned*)buf,it,12345u,678u);}, (double)blocks*th*it*8, "hi_addc_step_per_s");
+  timeit([&]{k_addcarry<8,true><<<blocks,th>>>((unsigned*)buf,it,12345u,678u);}, (double)blocks*th*it*8, "add2_madc1_per_s");
+  timeit([&]{k_addcarry<8,false><<<blocks,th>>>((unsigned*)buf,it,12345u,678u);}, (double)blocks*th*it*8, "add2_addc_per_s");
   }
   for(int bpsm: {1,4}){
     int blocks=sms*bpsm, th=256, it=2000; char nm[64];

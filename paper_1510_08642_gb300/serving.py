@@ -18,7 +18,9 @@ requests that arrive over time:
 * continuous: requests that arrive while others run are admitted as slots
   and memory free up, so their work overlaps on the device;
 * completion: a CUDA event per unit of work; latency = completion time on
-  the device clock (relative to a reference event) minus arrival time.
+  the device clock (relative to a reference event) minus arrival time;
+* workspace: the library's temporaries come from its pool, reserved at
+  start-up (ddg_workspace_reserve) so that no request maps memory.
 
 Every arithmetic step runs in the CUDA library; this module only schedules.
 Operands are generated on the device from a seed per request (uniform
@@ -117,7 +119,8 @@ class Server:
     def __init__(self, device=None, slots: int = 4, hbm_budget: int = 64 << 30, max_batch: int = 32,
                  lu_slots: int | None = None,
                  gemm_algo: str = "winograd", gemm_cutoff: int = 256, lu_K: int = 256,
-                 lu_algo: str = "winograd", lu_cutoff: int = 512, keep_results: bool = False):
+                 lu_algo: str = "winograd", lu_cutoff: int = 512, keep_results: bool = False,
+                 workspace_reserve: int = 8 << 30):
         import torch
         self.torch = torch
         self.device = device or torch.device("cuda", torch.cuda.current_device())
@@ -134,6 +137,19 @@ class Server:
         self.gemm_algo, self.gemm_cutoff = gemm_algo, gemm_cutoff
         self.lu_K, self.lu_algo, self.lu_cutoff = lu_K, lu_algo, lu_cutoff
         self.keep_results = keep_results
+        # keep the library's temporaries mapped between requests (the solves
+        # synchronise the host, which would otherwise hand the pool back)
+        self.dev_index = self.device.index if self.device.index is not None else torch.cuda.current_device()
+        self.workspace_reserve = workspace_reserve
+        if workspace_reserve:
+            capi.ddg_workspace_reserve(self.dev_index, workspace_reserve)
+
+    def close(self):
+        """Return the reserved workspace to the device."""
+        if self.workspace_reserve:
+            self.torch.cuda.synchronize(self.device)
+            capi.ddg_workspace_release(self.dev_index)
+            self.workspace_reserve = 0
 
     # -- dispatch -----------------------------------------------------------
     def _start_gemms(self, reqs, slot):

@@ -93,3 +93,14 @@ def test_qd_validation():
     q.ld = 2
     st = capi.qd_gemm(4, 4, 4, q, q, q, 0, None, 0)  # ld too small
     assert st == capi.DDG_EINVAL
+
+
+def test_workspace_device_checked():
+    # negative or too large device indices fail before any CUDA call
+    lib = capi.load()
+    info = capi.ddg_workspace_info()
+    assert lib.ddg_workspace_reserve(-1, 1) == capi.DDG_EINVAL
+    assert lib.ddg_workspace_release(64) == capi.DDG_EINVAL
+    assert lib.ddg_workspace_stats(-3, ctypes.byref(info)) == capi.DDG_EINVAL
+    assert lib.ddg_workspace_stats(0, None) == capi.DDG_EINVAL
+    assert "workspace" in capi.last_error()

@@ -193,3 +193,60 @@ def test_paper_matrices_table1_shapes():
                 assert abs(got - want) <= abs(want) * Fraction(1, 1 << 80)
             err = O.gemm_error(A, B, C, rows=rows, cols=cols)
             assert np.all(np.abs(err) <= normwise_bound(n, 2, algo) * absprod(A, B, rows, cols))
+
+
+# ------------------------------------- narrow products (n <= 8 columns) ----
+NARROW = [(300, 1000, 1), (37, 5000, 3), (130, 33, 8), (1, 1, 1), (64, 7, 5), (17, 100, 2)]
+
+
+@pytest.mark.parametrize("limbs", [2, 4])
+@pytest.mark.parametrize("shape", NARROW)
+def test_narrow_same_bits_as_block_tile(limbs, shape):
+    """n <= 8 runs one warp per output; its window is the exact sum of the
+    same truncated products the Block tile accumulates, so the result equals
+    the first n columns of a product wide enough for the tile kernel."""
+    m, l, n = shape
+    A = I.uniform(m, l, limbs, seed=40)
+    B = I.wide(l, n, limbs, seed=41)
+    Bw = np.concatenate([B, I.uniform(l, 40 - n, limbs, seed=42)], axis=2)
+    C = run(A, B, algo="block")
+    Cw = run(A, Bw, algo="block")
+    assert np.array_equal(C, Cw[:, :, :n])
+    check_bounds(A, B, C, "block")
+
+
+@pytest.mark.parametrize("limbs", [2, 4])
+@pytest.mark.parametrize("mode", ["add", "sub"])
+def test_narrow_update_modes(limbs, mode):
+    A = I.wide(200, 700, limbs, seed=43)
+    B = I.uniform(700, 4, limbs, seed=44)
+    C0 = I.uniform(200, 4, limbs, seed=45)
+    C = run(A, B, C0, algo="winograd", cutoff=16, mode=mode)  # n <= cutoff: the base case
+    check_bounds(A, B, C, "block", C0=C0, mode=mode)
+
+
+@pytest.mark.parametrize("limbs", [2, 4])
+def test_narrow_special_values(limbs):
+    """Zero row / column, tiny and huge magnitudes, exact cancellation."""
+    m, l, n = 40, 70, 6
+    A = I.uniform(m, l, limbs, seed=46)
+    B = I.uniform(l, n, limbs, seed=47)
+    A[:, 3, :] = 0.0
+    B[:, :, 5] = 0.0
+    A[:, 7, :] *= 2.0 ** -600
+    B[:, :, 2] *= 2.0 ** 500
+    A[:, 11, 35:] = A[:, 11, :35]
+    B[:, 35:, 1] = -B[:, :35, 1]  # row 11 x column 1 cancels exactly
+    C = run(A, B, algo="block")
+    err = O.gemm_error(A, B, C)
+    u2 = U2 if limbs == 2 else 8 * Q2
+    assert np.all(np.abs(err) <= (2 * l + 4) * u2 * absprod(A, B) + 1e-300)
+    assert not C[:, 3, :].any() and not C[:, :, 5].any()
+    assert not C[:, 11, 1].any()
+
+
+def test_narrow_integer_exact():
+    A = I.integer(90, 3000, 2, seed=48, bits=20)
+    B = I.integer(3000, 3, 2, seed=49, bits=20)
+    C = run(A, B, algo="block")
+    assert not O.gemm_error(A, B, C).any()

@@ -34,6 +34,7 @@ def test_results_same_alone_and_in_mix():
         assert r.info == 0
         if r.kind == "lu":  # solution of A x = A 1
             assert np.abs(a[0] - 1.0 + a[1]).max() < 1e-20
+    srv.close()
 
 
 def test_small_budget_serialises_but_completes():
@@ -43,3 +44,4 @@ def test_small_budget_serialises_but_completes():
     st = srv.run(reqs)
     assert st["all"]["count"] == 12
     assert all(np.isfinite(r.done) and r.done >= r.arrival for r in reqs)
+    srv.close()
