@@ -113,10 +113,14 @@ typedef struct {
                       `stream`; 7 (default, also for 0) = on 7 concurrent
                       streams (the paper's 7 OpenMP sections, Figs. 1-2) */
   int32_t accum;   /* Block multiply-add: 0 (default) = exact fixed-point
-                      window accumulation of the leading products on the
-                      integer pipe, cross terms by FMA (2 FP64 instructions
-                      per DD multiply-add, 4 per QD); 1 = TwoSum accumulation
-                      on the FP64 pipe (12 per DD, 113 per QD) */
+                      window accumulation on the integer pipe (operands as
+                      multiword integers, no FP64 in the inner loop); larger
+                      Block products first convert each operand once into
+                      library workspace (about 20 B per DD element, 36 per
+                      QD, of A and of B); 2 = the same arithmetic and bits,
+                      every tile converted as it is staged (no operand
+                      workspace); 1 = TwoSum accumulation on the FP64 pipe
+                      (12 FP64 instructions per DD multiply-add, 113 per QD) */
   int32_t slices;  /* DDG_OZAKI: number of INT8 slices s, DD in [2, 18]
                       (0 = 16, about 2^-110 of the row / column maxima), QD
                       in [2, 32] (0 = 32, about 2^-222); DDG_OZAKI2: number
@@ -265,7 +269,7 @@ ddg_status ddg_batch_destroy(ddg_batch b, void* stream);
 ddg_status dd_gemm_batched(int32_t count, const ddg_problem* probs, void* stream);
 
 /* FP64 instructions per DD (limbs = 2) or QD (limbs = 4) multiply-add in
- * the Block kernel's inner loop for accumulation scheme `accum` (0 or 1, as
+ * the Block kernel's inner loop for accumulation scheme `accum` (0, 1 or 2, as
  * in ddg_opts), counted from its source (for rooflines): 0 for the
  * fixed-point scheme, whose inner loop runs on the integer pipe; -1 if
  * invalid. */
@@ -282,7 +286,7 @@ int32_t ddg_ozaki2_precision(int32_t moduli, int64_t l);
  * stream. ddg_profile_end() waits for those events and fills out[k] for
  * kernel kinds k = 0 (Simple), 1 (Block), 2 (quadrant passes), 3 (INT8
  * products), 4 (Block products with at most 8 columns, one warp per
- * output), k < nkinds:
+ * output), 5 (operand conversions of the Block products), k < nkinds:
  * launches, sum of launch durations, busy time (union of the launch
  * intervals), and the algorithmic work and bytes of those launches.
  * For measurement only: it adds two event records per launch. */
@@ -291,8 +295,9 @@ typedef struct {
   double sum_ms;
   double busy_ms;
   double ops;   /* FP64 instructions (kind 0), multiply-adds (kinds 1 and 4),
-                   DD / QD sums (kind 2) or INT8 operations, 2 per
-                   multiply-add (kind 3, the INT8 products) */
+                   DD / QD sums (kind 2), INT8 operations, 2 per
+                   multiply-add (kind 3, the INT8 products) or converted
+                   elements (kind 5) */
   double bytes;
 } ddg_kernel_prof;
 ddg_status ddg_profile_begin(void);

@@ -37,8 +37,9 @@ def gemm(A, B, C=None, algo: str = "winograd", cutoff: int = 512, mode: str = "s
     """C (mode) A B through dd_gemm / qd_gemm on the current CUDA stream.
 
     A: (limbs, m, l), B: (limbs, l, n), C: (limbs, m, n) or None (allocated).
-    limbs = 2 (DD) or 4 (QD). accum: "fx" (fixed-point window, default) or
-    "twosum" for the Block base case. Returns C.
+    limbs = 2 (DD) or 4 (QD). accum: "fx" (fixed-point window, default),
+    "fx_tile" (the same bits, tiles converted as they are staged, no operand
+    workspace) or "twosum" for the Block base case. Returns C.
     """
     import torch
 

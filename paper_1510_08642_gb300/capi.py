@@ -45,7 +45,7 @@ class ddg_kernel_prof(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
-PROF_KINDS = ("simple", "block", "pass", "ozaki", "gemv")
+PROF_KINDS = ("simple", "block", "pass", "ozaki", "gemv", "convert")
 
 
 class ddg_problem(ctypes.Structure):
@@ -129,7 +129,7 @@ def check(status: int) -> None:
         raise DDGError(status, last_error())
 
 
-ACCUMS = {"fx": 0, "twosum": 1}
+ACCUMS = {"fx": 0, "twosum": 1, "fx_tile": 2}
 
 
 def opts(algo="winograd", cutoff: int = 512, pad: bool = False, streams: int = 7,

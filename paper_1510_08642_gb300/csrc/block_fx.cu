@@ -14,6 +14,13 @@
 //     NW words per output entry (fx::place_shr) whose scale is fixed before
 //     the k loop from the largest exponent of row i of A and column j of B;
 //   * epilogue: the window rounded to DD / QD once.
+// Conversion once per operand: a tile of A is staged by every CTA of its row
+// of tiles (n / BN of them) and a tile of B by m / BM CTAs, so converting on
+// the fly repeats to_fixed for each element that often. For products with
+// many tiles the conversion runs once per element in its own elementwise
+// kernel (fx_convert_kernel, into scratch the caller provides) and the Block
+// kernel stages the converted words by plain copies (block_fxc_kernel); the
+// words, shifts and therefore the results are the same bits either way.
 // Error per term: the dropped partial products, < 2^-123 (DD) / 2^-219
 // (QD) of |a_ik b_kj|, and the truncation below the window, 2^-159 (DD) /
 // 2^-255 (QD) of the largest product of row i and column j; the sum in the
@@ -74,12 +81,26 @@ __device__ __forceinline__ void stage(const double (&x)[L], int fmax, uint4* w, 
   *e = make_int2(zero ? 0 : fmax - (es & 0xFFFF), (es >> 16) ? -1 : 0);
 }
 
+// The same staging from a converted operand: copy the words and derive the
+// shift and sign mask from f exactly as stage() does from to_fixed.
+template <int L>
+__device__ __forceinline__ void stage_pre(bool ok, const fxop& X, int64_t e, int fmax, uint4* w, int stride,
+                                          int2* ex) {
+  constexpr int WV = fx_smem<L>::WV;
+#pragma unroll
+  for (int v = 0; v < WV; ++v) w[v * stride] = ok ? X.w[e * WV + v] : make_uint4(0u, 0u, 0u, 0u);
+  const int f = ok ? X.f[e] : FX_ZERO;
+  *ex = make_int2(f < 0 ? 0 : fmax - (f & 0xFFFF), ((f >> 16) & 1) ? -1 : 0);
+}
+
 }  // namespace
 
 // One BM x BN tile of C at (i0, j0): C (mode) A B restricted to the tile.
-template <int L>
+// PRE: the operands come converted in Ax, Bx (A and B are then not read).
+template <int L, bool PRE>
 __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
-                                        const mat& C, int mode, int64_t i0, int64_t j0, fx_smem<L>& sm) {
+                                        const mat& C, int mode, int64_t i0, int64_t j0, fx_smem<L>& sm,
+                                        const fxop& Ax, const fxop& Bx) {
   using P = fxcfg<L>;
   constexpr int BM = P::BM, BN = P::BN, BK = P::BK, TM = P::TM, TN = P::TN, NW = P::NW;
   constexpr int W = P::W, D = P::D, K = P::K, WV = fx_smem<L>::WV;
@@ -96,8 +117,13 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
   for (int r = warp; r < BM; r += NT / 32) {
     int f = 1;
     const int64_t gi = i0 + r;
-    if (gi < m)
-      for (int64_t k = lane; k < l; k += 32) f = max(f, fx::expfield(A.p[0][gi * A.ld + k]));
+    if (gi < m) {
+      if constexpr (PRE) {
+        for (int64_t k = lane; k < l; k += 32) f = max(f, Ax.f[gi * Ax.ld + k] & 0xFFFF);
+      } else {
+        for (int64_t k = lane; k < l; k += 32) f = max(f, fx::expfield(A.p[0][gi * A.ld + k]));
+      }
+    }
     f = __reduce_max_sync(0xffffffffu, f);
     if (lane == 0) row_f[r] = f;
   }
@@ -106,8 +132,13 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
     const int c = tid % BN;
     const int64_t gj = j0 + c;
     int f = 1;
-    if (gj < n)
-      for (int64_t k = tid / BN; k < l; k += NT / BN) f = max(f, fx::expfield(B.p[0][k * B.ld + gj]));
+    if (gj < n) {
+      if constexpr (PRE) {
+        for (int64_t k = tid / BN; k < l; k += NT / BN) f = max(f, Bx.f[k * Bx.ld + gj] & 0xFFFF);
+      } else {
+        for (int64_t k = tid / BN; k < l; k += NT / BN) f = max(f, fx::expfield(B.p[0][k * B.ld + gj]));
+      }
+    }
     atomicMax(&col_f[c], f);
   }
   __syncthreads();
@@ -126,20 +157,28 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
       const int r = idx / BK, c = idx % BK;
       const int64_t gi = i0 + r, gk = k0 + c;
       const bool ok = gi < m && gk < l;
-      double x[L];
+      if constexpr (PRE) {
+        stage_pre<L>(ok, Ax, gi * Ax.ld + gk, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
+      } else {
+        double x[L];
 #pragma unroll
-      for (int q = 0; q < L; ++q) x[q] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
-      stage<L>(x, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
+        for (int q = 0; q < L; ++q) x[q] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
+        stage<L>(x, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
+      }
     }
 #pragma unroll
     for (int idx = tid; idx < BK * BN; idx += NT) {
       const int r = idx / BN, c = idx % BN;
       const int64_t gk = k0 + r, gj = j0 + c;
       const bool ok = gk < l && gj < n;
-      double x[L];
+      if constexpr (PRE) {
+        stage_pre<L>(ok, Bx, gk * Bx.ld + gj, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
+      } else {
+        double x[L];
 #pragma unroll
-      for (int q = 0; q < L; ++q) x[q] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
-      stage<L>(x, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
+        for (int q = 0; q < L; ++q) x[q] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
+        stage<L>(x, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
+      }
     }
     __syncthreads();
 #pragma unroll 1
@@ -198,8 +237,46 @@ template <int L>
 __global__ void __launch_bounds__(128, fxcfg<L>::MINB) block_fx_kernel(int64_t m, int64_t l, int64_t n, mat A, mat B,
                                                        mat C, int mode) {
   __shared__ fx_smem<L> sm;
-  fx_tile<L>(m, l, n, A, B, C, mode, (int64_t)blockIdx.y * fxcfg<L>::BM,
-             (int64_t)blockIdx.x * fxcfg<L>::BN, sm);
+  fx_tile<L, false>(m, l, n, A, B, C, mode, (int64_t)blockIdx.y * fxcfg<L>::BM,
+                    (int64_t)blockIdx.x * fxcfg<L>::BN, sm, fxop{}, fxop{});
+}
+
+// The Block kernel on converted operands (A, B given only by Ax, Bx).
+template <int L>
+__global__ void __launch_bounds__(128, fxcfg<L>::MINB) block_fxc_kernel(int64_t m, int64_t l, int64_t n, fxop Ax,
+                                                                        fxop Bx, mat C, int mode) {
+  __shared__ fx_smem<L> sm;
+  fx_tile<L, true>(m, l, n, mat{}, mat{}, C, mode, (int64_t)blockIdx.y * fxcfg<L>::BM,
+                   (int64_t)blockIdx.x * fxcfg<L>::BN, sm, Ax, Bx);
+}
+
+// Every element of up to FX_CONV_MAX operands converted once (to_fixed),
+// each into the dense layout of fxop (ld = cols): blockIdx.z = operand,
+// thread = column, CTA row = matrix row.
+template <int L>
+__global__ void __launch_bounds__(256) fx_convert_kernel(fx_conv_jobs J) {
+  constexpr int W = fxcfg<L>::W, WV = fx_smem<L>::WV;
+  const fx_conv_job& jb = J.job[blockIdx.z];
+  const int64_t rows = jb.rows, cols = jb.cols;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  uint4* __restrict__ w = jb.w;
+  int* __restrict__ f = jb.f;
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+    double x[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) x[q] = jb.X.p[q][r * jb.X.ld + c];
+    uint32_t M[4 * WV];
+    uint32_t(&Mw)[W] = *reinterpret_cast<uint32_t(*)[W]>(M);
+    const int es = fx::to_fixed<L, W>(x, Mw);
+#pragma unroll
+    for (int t = W; t < 4 * WV; ++t) M[t] = 0u;
+    const bool zero = (fx::dbits(x[0]) << 1) == 0u;
+    const int64_t e = r * cols + c;
+#pragma unroll
+    for (int v = 0; v < WV; ++v) w[e * WV + v] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
+    f[e] = zero ? FX_ZERO : es;
+  }
 }
 
 // Grouped persistent launch: every CTA takes the next tile of the task list
@@ -225,7 +302,8 @@ __global__ void __launch_bounds__(128, fxcfg<L>::MINB - 1) grouped_fx_kernel(con
     const gtask g = tasks[lo];
     const int64_t local = t - g.tile0;
     const int64_t bi = local / g.tiles_n, bj = local % g.tiles_n;
-    fx_tile<L>(g.m, g.l, g.n, g.A, g.B, g.C, g.mode, bi * fxcfg<L>::BM, bj * fxcfg<L>::BN, sm);
+    fx_tile<L, false>(g.m, g.l, g.n, g.A, g.B, g.C, g.mode, bi * fxcfg<L>::BM, bj * fxcfg<L>::BN, sm, fxop{},
+                      fxop{});
     __syncthreads();
   }
 }
@@ -279,6 +357,90 @@ cudaError_t launch_block_fx(int limbs, int64_t m, int64_t l, int64_t n, mat A, m
     prof_end_launch(s, ev, PROF_BLOCK, macs, bytes);
   }
   return e;
+}
+
+namespace {
+inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+inline size_t wv_of(int limbs) { return limbs == 2 ? fx_smem<2>::WV : fx_smem<4>::WV; }
+}  // namespace
+
+size_t fxop_bytes(int limbs, int64_t rows, int64_t cols) {
+  const size_t elems = (size_t)rows * (size_t)cols;
+  return al256(elems * 16 * wv_of(limbs)) + al256(elems * 4);
+}
+
+cudaError_t launch_fx_convert(int limbs, int count, const int64_t* rows, const int64_t* cols, const mat* X,
+                              char* const* buf, fxop* out, cudaStream_t s) {
+  if (count < 1 || count > FX_CONV_MAX) return cudaErrorInvalidValue;
+  fx_conv_jobs J{};
+  J.count = count;
+  int64_t max_rows = 0, max_cols = 0;
+  double elems = 0.0;
+  for (int t = 0; t < count; ++t) {
+    uint4* w = reinterpret_cast<uint4*>(buf[t]);
+    int* f = reinterpret_cast<int*>(buf[t] + al256((size_t)rows[t] * (size_t)cols[t] * 16 * wv_of(limbs)));
+    J.job[t] = fx_conv_job{rows[t], cols[t], X[t], w, f};
+    out[t] = fxop{w, f, cols[t]};
+    max_rows = std::max(max_rows, rows[t]);
+    max_cols = std::max(max_cols, cols[t]);
+    elems += (double)rows[t] * (double)cols[t];
+  }
+  if (max_rows == 0 || max_cols == 0) return cudaSuccess;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaEvent_t ev = nullptr;
+  prof_begin_launch(s, &ev);
+  const dim3 grid((unsigned)((max_cols + 255) / 256), (unsigned)std::min<int64_t>(max_rows, 65535), (unsigned)count);
+  if (limbs == 2) fx_convert_kernel<2><<<grid, 256, 0, s>>>(J);
+  else fx_convert_kernel<4><<<grid, 256, 0, s>>>(J);
+  cudaError_t e = cudaGetLastError();
+  if (ev) prof_end_launch(s, ev, PROF_CONVERT, elems, elems * (8.0 * limbs + 16.0 * wv_of(limbs) + 4.0));
+  return e;
+}
+
+bool block_fx_converts(int limbs, int64_t m, int64_t l, int64_t n) {
+  (void)limbs;
+  // each operand element is otherwise converted once per CTA row / column
+  // of tiles: worth a separate pass once the grid is a few tiles each way
+  return l >= 32 && m >= 64 && n >= 64;
+}
+
+size_t block_fx_scratch_bytes(int limbs, int64_t m, int64_t l, int64_t n) {
+  return fxop_bytes(limbs, m, l) + fxop_bytes(limbs, l, n);
+}
+
+cudaError_t launch_block_fxc(int limbs, int64_t m, int64_t l, int64_t n, const fxop& Ax, const fxop& Bx, mat C,
+                             int mode, cudaStream_t s) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaEvent_t ev = nullptr;
+  prof_begin_launch(s, &ev);
+  if (limbs == 2) {
+    dim3 grid((unsigned)((n + fxcfg<2>::BN - 1) / fxcfg<2>::BN), (unsigned)((m + fxcfg<2>::BM - 1) / fxcfg<2>::BM));
+    block_fxc_kernel<2><<<grid, 128, 0, s>>>(m, l, n, Ax, Bx, C, mode);
+  } else {
+    dim3 grid((unsigned)((n + fxcfg<4>::BN - 1) / fxcfg<4>::BN), (unsigned)((m + fxcfg<4>::BM - 1) / fxcfg<4>::BM));
+    block_fxc_kernel<4><<<grid, 128, 0, s>>>(m, l, n, Ax, Bx, C, mode);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (ev) {
+    const double macs = (double)m * (double)l * (double)n;
+    const double bytes = 8.0 * limbs * ((double)m * l + (double)l * n + (double)m * n * (mode == MODE_SET ? 1 : 2));
+    prof_end_launch(s, ev, PROF_BLOCK, macs, bytes);
+  }
+  return e;
+}
+
+cudaError_t launch_block_fx_converted(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C, int mode,
+                                      void* scratch, cudaStream_t s) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  if (l == 0) return launch_block_fx(limbs, m, l, n, A, B, C, mode, s);
+  char* buf[2] = {static_cast<char*>(scratch), static_cast<char*>(scratch) + fxop_bytes(limbs, m, l)};
+  const int64_t rows[2] = {m, l}, cols[2] = {l, n};
+  const mat X[2] = {A, B};
+  fxop op[2];
+  cudaError_t e = launch_fx_convert(limbs, 2, rows, cols, X, buf, op, s);
+  if (e != cudaSuccess) return e;
+  return launch_block_fxc(limbs, m, l, n, op[0], op[1], C, mode, s);
 }
 
 int block_fx_fp64_ops_per_mac(int limbs) { return limbs == 2 || limbs == 4 ? 0 : -1; }

@@ -22,7 +22,9 @@
 // block is taken from the stream-ordered allocator. Each fork branch has a
 // stack of its own: nodes below the top level run in stream order, so a
 // node's temporaries are reused by its next sibling. Total for a square n:
-// about 15 (n/2)^2 (1 + 7/3) DD/QD entries.
+// about 15 (n/2)^2 (1 + 7/3) DD/QD entries. Each stack also has one area for
+// the converted operands of its Block base cases (they run in stream order
+// too), sized by its largest base case.
 #include <algorithm>
 #include <cstddef>
 #include <cstring>
@@ -93,6 +95,11 @@ struct Ctx {
   char* base = nullptr;
   size_t region_off[8] = {0};
   size_t peak[8] = {0};
+  // Block base cases with operands converted once (accum 0): their scratch
+  // area per region (offset, size); off for accum 2 and the fixed scratch
+  bool convert = true;
+  size_t leaf_off[8] = {0};
+  size_t leaf_peak[8] = {0};
   cudaStream_t* pool = nullptr;
 };
 
@@ -121,11 +128,24 @@ static ddg_status copy_mat(const Ctx& c, const mat& dst, const mat& src, int64_t
   return DDG_OK;
 }
 
-static cudaError_t base_case(const Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
-                             const mat& C, int mode, cudaStream_t s) {
-  if (c.accum != 0) return launch_block(c.L, m, l, n, A, B, C, mode, s);
-  return n <= GEMV_MAX_N ? launch_gemv_fx(c.L, m, l, n, A, B, C, mode, s)
-                         : launch_block_fx(c.L, m, l, n, A, B, C, mode, s);
+// Is the base case m x l x n a Block product on operands converted once?
+static bool converts(const Ctx& c, int64_t m, int64_t l, int64_t n) {
+  return c.accum == 0 && c.convert && n > GEMV_MAX_N && block_fx_converts(c.L, m, l, n);
+}
+
+// The base case on stack `region`; a dry run only sizes its scratch.
+static cudaError_t base_case(Ctx& c, int region, int64_t m, int64_t l, int64_t n, const mat& A,
+                             const mat& B, const mat& C, int mode, cudaStream_t s) {
+  if (c.accum == 1) return c.dry ? cudaSuccess : launch_block(c.L, m, l, n, A, B, C, mode, s);
+  if (n <= GEMV_MAX_N) return c.dry ? cudaSuccess : launch_gemv_fx(c.L, m, l, n, A, B, C, mode, s);
+  if (converts(c, m, l, n)) {
+    if (c.dry) {
+      c.leaf_peak[region] = std::max(c.leaf_peak[region], block_fx_scratch_bytes(c.L, m, l, n));
+      return cudaSuccess;
+    }
+    return launch_block_fx_converted(c.L, m, l, n, A, B, C, mode, c.base + c.leaf_off[region], s);
+  }
+  return c.dry ? cudaSuccess : launch_block_fx(c.L, m, l, n, A, B, C, mode, s);
 }
 
 static bool splits(const Ctx& c, int64_t m, int64_t l, int64_t n) {
@@ -168,6 +188,34 @@ static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, c
     const mat R_[7] = {SR[0], B11, SR[1], SR[2], B22, SR[3], SR[4]};
     for (int i = 0; i < 7; ++i) { lhs[i] = L_[i]; rhs[i] = R_[i]; }
   }
+  // Children that are Block base cases on converted operands: their 14
+  // operands are converted in one launch on s (into the stack's leaf area)
+  // before the products, rather than 2 by 2 before each product, which keeps
+  // each stream's queue short.
+  const bool leaves = !splits(c, h, k, w) && converts(c, h, k, w);
+  fxop opl[7], opr[7];
+  if (leaves) {
+    const size_t bl = fxop_bytes(c.L, h, k), br = fxop_bytes(c.L, k, w);
+    c.leaf_peak[region] = std::max(c.leaf_peak[region], 7 * (bl + br));
+    if (!c.dry) {
+      char* area = c.base + c.leaf_off[region];
+      int64_t rows[14], cols[14];
+      mat X[14];
+      char* buf[14];
+      fxop op[14];
+      for (int i = 0; i < 7; ++i) {
+        rows[i] = h, cols[i] = k, X[i] = lhs[i], buf[i] = area + i * bl;
+        rows[7 + i] = k, cols[7 + i] = w, X[7 + i] = rhs[i], buf[7 + i] = area + 7 * bl + i * br;
+      }
+      DDG_CUDA(launch_fx_convert(c.L, 14, rows, cols, X, buf, op, s));
+      for (int i = 0; i < 7; ++i) opl[i] = op[i], opr[i] = op[7 + i];
+    }
+  }
+  auto child = [&](int i, cudaStream_t cs, int reg, size_t rsp) -> ddg_status {
+    if (!leaves) return rec(c, h, k, w, lhs[i], rhs[i], P[i], MODE_SET, cs, reg, rsp, depth + 1);
+    if (!c.dry) DDG_CUDA(launch_block_fxc(c.L, h, k, w, opl[i], opr[i], P[i], MODE_SET, cs));
+    return DDG_OK;
+  };
   const bool fork = depth == 0 && c.nstreams == 7;
   if (fork) {
     cudaEvent_t ev_fork = nullptr, ev_join[7] = {nullptr};
@@ -178,7 +226,7 @@ static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, c
     for (int i = 0; i < 7; ++i) {
       cudaStream_t cs = c.dry ? s : c.pool[i];
       if (!c.dry) DDG_CUDA(cudaStreamWaitEvent(cs, ev_fork, 0));
-      DDG_TRY(rec(c, h, k, w, lhs[i], rhs[i], P[i], MODE_SET, cs, 1 + i, 0, depth + 1));
+      DDG_TRY(child(i, cs, 1 + i, 0));
       if (!c.dry) {
         DDG_CUDA(cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming));
         DDG_CUDA(cudaEventRecord(ev_join[i], cs));
@@ -190,8 +238,7 @@ static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, c
       for (int i = 0; i < 7; ++i) DDG_CUDA(cudaEventDestroy(ev_join[i]));
     }
   } else {
-    for (int i = 0; i < 7; ++i)
-      DDG_TRY(rec(c, h, k, w, lhs[i], rhs[i], P[i], MODE_SET, s, region, sp, depth + 1));
+    for (int i = 0; i < 7; ++i) DDG_TRY(child(i, s, region, sp));
   }
   if (!c.dry) {
     const mat qc[4] = {C11, C12, C21, C22};
@@ -205,20 +252,18 @@ static ddg_status rec(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, con
   if (m == 0 || n == 0) return DDG_OK;
   if (l == 0) return (mode == MODE_SET && !c.dry) ? zero_mat(c, C, m, n, s) : DDG_OK;
   if (!splits(c, m, l, n)) {
-    if (!c.dry) DDG_CUDA(base_case(c, m, l, n, A, B, C, mode, s));
+    DDG_CUDA(base_case(c, region, m, l, n, A, B, C, mode, s));
     return DDG_OK;
   }
   const int64_t m2 = m & ~int64_t(1), l2 = l & ~int64_t(1), n2 = n & ~int64_t(1);
   DDG_TRY(level(c, m2, l2, n2, A, B, C, mode, s, region, sp, depth));
-  if (!c.dry) {
-    if (l2 != l)  // C[:m2, :n2] (+/-)= A[:m2, l2] B[l2, :n2]
-      DDG_CUDA(base_case(c, m2, 1, n2, view(A, 0, l2), view(B, l2, 0), C,
-                            mode == MODE_SUB ? MODE_SUB : MODE_ADD, s));
-    if (n2 != n)
-      DDG_CUDA(base_case(c, m2, l, 1, A, view(B, 0, n2), view(C, 0, n2), mode, s));
-    if (m2 != m)
-      DDG_CUDA(base_case(c, 1, l, n, view(A, m2, 0), B, view(C, m2, 0), mode, s));
-  }
+  if (l2 != l)  // C[:m2, :n2] (+/-)= A[:m2, l2] B[l2, :n2]
+    DDG_CUDA(base_case(c, region, m2, 1, n2, view(A, 0, l2), view(B, l2, 0), C,
+                       mode == MODE_SUB ? MODE_SUB : MODE_ADD, s));
+  if (n2 != n)
+    DDG_CUDA(base_case(c, region, m2, l, 1, A, view(B, 0, n2), view(C, 0, n2), mode, s));
+  if (m2 != m)
+    DDG_CUDA(base_case(c, region, 1, l, n, view(A, m2, 0), B, view(C, m2, 0), mode, s));
   return DDG_OK;
 }
 
@@ -313,7 +358,7 @@ static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& 
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
   if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
   if (o.streams != 0 && o.streams != 1 && o.streams != 7) return fail(DDG_EINVAL, "streams must be 0, 1 or 7");
-  if (o.accum != 0 && o.accum != 1) return fail(DDG_EINVAL, "accum must be 0 or 1");
+  if (o.accum < 0 || o.accum > 2) return fail(DDG_EINVAL, "accum must be 0, 1 or 2");
   for (int i = 0; i < 2; ++i)
     if (o.reserved[i] != 0) return fail(DDG_EINVAL, "reserved option fields must be zero");
   std::string why;
@@ -358,22 +403,18 @@ ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const 
   c.algo = o.algo;
   c.cutoff = o.cutoff;
   c.nstreams = o.streams == 1 ? 1 : 7;
-  if (!splits(c, m, l, n)) {
-    if (l == 0) {
-      if (mode == MODE_SET) return zero_mat(c, C, m, n, s);
-      return DDG_OK;
-    }
-    DDG_CUDA(base_case(c, m, l, n, A, B, C, mode, s));
-    return DDG_OK;
-  }
-  if (c.nstreams == 7) DDG_TRY(stream_pool(&c.pool));
-  // plan
+  if (splits(c, m, l, n) && c.nstreams == 7) DDG_TRY(stream_pool(&c.pool));
+  // plan (a Block product alone plans its converted operands only)
   c.dry = true;
   DDG_TRY(top(c, m, l, n, A, B, C, mode, o.pad == 1, s));
   size_t total = 0;
   for (int r = 0; r < 8; ++r) {
     c.region_off[r] = total;
     total += (c.peak[r] + 255) & ~(size_t)255;
+  }
+  for (int r = 0; r < 8; ++r) {
+    c.leaf_off[r] = total;
+    total += (c.leaf_peak[r] + 255) & ~(size_t)255;
   }
   // run
   c.dry = false;
@@ -425,8 +466,8 @@ ddg_status qd_gemm(int64_t m, int64_t l, int64_t n, qd_mat A, qd_mat B, qd_mat C
 }
 
 int32_t ddg_block_fp64_ops_per_mac(int32_t limbs, int32_t accum) {
-  if ((limbs != 2 && limbs != 4) || (accum != 0 && accum != 1)) return -1;
-  return accum == 0 ? ddg::block_fx_fp64_ops_per_mac(limbs) : ddg::block_fp64_ops_per_mac(limbs);
+  if ((limbs != 2 && limbs != 4) || accum < 0 || accum > 2) return -1;
+  return accum != 1 ? ddg::block_fx_fp64_ops_per_mac(limbs) : ddg::block_fp64_ops_per_mac(limbs);
 }
 
 int32_t ddg_ozaki2_precision(int32_t moduli, int64_t l) {
@@ -487,7 +528,7 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
     return fail(DDG_EINVAL, "slices must be 0 or in [2, 18] (DD) / [2, 32] (QD); moduli in [2, 40]");
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
   if (o.pad != 0 && o.pad != 1) return fail(DDG_EINVAL, "pad must be 0 or 1");
-  if (o.accum != 0 && o.accum != 1) return fail(DDG_EINVAL, "accum must be 0 or 1");
+  if (o.accum < 0 || o.accum > 2) return fail(DDG_EINVAL, "accum must be 0, 1 or 2");
   for (int i = 0; i < 2; ++i)
     if (o.reserved[i] != 0) return fail(DDG_EINVAL, "reserved option fields must be zero");
   std::string why;
@@ -509,10 +550,12 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
   c.accum = o.accum;
   c.algo = o.algo;
   c.cutoff = o.cutoff;
-  c.nstreams = 1;  // no forking: no streams or events are created
+  c.nstreams = 1;     // no forking: no streams or events are created
+  c.convert = false;  // Block base cases convert their tiles on the fly
   if (!splits(c, m, l, n)) {
     if (l == 0) return mode == MODE_SET ? zero_mat(c, C, m, n, s) : DDG_OK;
-    DDG_CUDA(base_case(c, m, l, n, A, B, C, mode, s));
+    c.dry = false;
+    DDG_CUDA(base_case(c, 0, m, l, n, A, B, C, mode, s));
     return DDG_OK;
   }
   c.dry = true;

@@ -26,7 +26,7 @@ inline mat view(const mat& M, int64_t r0, int64_t c0) {
 extern std::atomic<uint64_t> g_launches;
 
 // Launch profiling hooks (profile.cu); no-ops unless ddg_profile_begin ran.
-enum ProfKind { PROF_SIMPLE = 0, PROF_BLOCK = 1, PROF_PASS = 2, PROF_OZAKI = 3, PROF_GEMV = 4 };
+enum ProfKind { PROF_SIMPLE = 0, PROF_BLOCK = 1, PROF_PASS = 2, PROF_OZAKI = 3, PROF_GEMV = 4, PROF_CONVERT = 5 };
 bool prof_enabled();
 void prof_begin_launch(cudaStream_t s, cudaEvent_t* start);
 void prof_end_launch(cudaStream_t s, cudaEvent_t start, int kind, double ops, double bytes);
@@ -55,6 +55,47 @@ cudaError_t launch_simple(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat
 cudaError_t launch_block_fx(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,
                             int mode, cudaStream_t s);
 int block_fx_fp64_ops_per_mac(int limbs);
+
+// Operands converted to fixed-point words once (launch_fx_convert), for the
+// Block kernel on converted operands (launch_block_fxc): element (r, c) of a
+// rows x cols operand has its 16-byte word vectors at w[(r ld + c) WV + v]
+// (WV = 1 for DD, 2 for QD), and at f[r ld + c] its leading limb's exponent
+// field (>= 1) | sign << 16, or FX_ZERO for a zero; ld = cols.
+struct fxop {
+  const uint4* w;
+  const int* f;
+  int64_t ld;
+};
+constexpr int FX_ZERO = (int)0x80000000u;
+constexpr int FX_CONV_MAX = 14;  // operands per conversion launch
+struct fx_conv_job {
+  int64_t rows, cols;
+  mat X;
+  uint4* w;
+  int* f;
+};
+struct fx_conv_jobs {
+  fx_conv_job job[FX_CONV_MAX];
+  int count;
+};
+// Device bytes of one converted rows x cols operand (256-byte multiple).
+size_t fxop_bytes(int limbs, int64_t rows, int64_t cols);
+// Convert `count` <= FX_CONV_MAX operands X[t] (rows[t] x cols[t]) in one
+// launch into buf[t] (fxop_bytes each, 256-byte aligned); out[t] describes
+// the result.
+cudaError_t launch_fx_convert(int limbs, int count, const int64_t* rows, const int64_t* cols, const mat* X,
+                              char* const* buf, fxop* out, cudaStream_t s);
+// The Block product on converted operands: the same bits as launch_block_fx.
+cudaError_t launch_block_fxc(int limbs, int64_t m, int64_t l, int64_t n, const fxop& Ax, const fxop& Bx, mat C,
+                             int mode, cudaStream_t s);
+// Both steps for one product, scratch = block_fx_scratch_bytes (used in
+// stream order on s). block_fx_converts: whether the shape gains from it
+// (a tile of A is otherwise converted by each of the n / BN CTAs that stage
+// it, a tile of B by m / BM).
+bool block_fx_converts(int limbs, int64_t m, int64_t l, int64_t n);
+size_t block_fx_scratch_bytes(int limbs, int64_t m, int64_t l, int64_t n);
+cudaError_t launch_block_fx_converted(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C, int mode,
+                                      void* scratch, cudaStream_t s);
 
 // The same product for n <= GEMV_MAX_N columns: one warp per output, lanes
 // splitting k (gemv_fx.cu); the Block base case dispatches to it.

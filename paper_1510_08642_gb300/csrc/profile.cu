@@ -7,6 +7,7 @@
 // not double counted).
 #include <algorithm>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "ddgemm.h"
@@ -20,10 +21,39 @@ struct rec_t {
   double ops;
   double bytes;
   cudaEvent_t start, stop;
+  int dev;
 };
 std::mutex g_mu;
 bool g_on = false;
 std::vector<rec_t> g_recs;
+// Events of earlier profiles, per device, reused: creating two events per
+// launch costs more host time than the launch itself.
+std::vector<std::pair<int, cudaEvent_t>> g_free;
+
+int current_device() {
+  int d = 0;
+  return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+}
+
+cudaEvent_t take_event(int dev) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (size_t i = g_free.size(); i-- > 0;)
+      if (g_free[i].first == dev) {
+        cudaEvent_t e = g_free[i].second;
+        g_free[i] = g_free.back();
+        g_free.pop_back();
+        return e;
+      }
+  }
+  cudaEvent_t e = nullptr;
+  return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+}
+
+void give_back(const rec_t& r) {
+  g_free.push_back({r.dev, r.start});
+  g_free.push_back({r.dev, r.stop});
+}
 }  // namespace
 
 bool prof_enabled() { return g_on; }
@@ -33,17 +63,18 @@ void prof_begin_launch(cudaStream_t s, cudaEvent_t* start) {
   if (!g_on) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
-  if (cudaEventCreate(start) != cudaSuccess) { *start = nullptr; return; }
-  cudaEventRecord(*start, s);
+  *start = take_event(current_device());
+  if (*start) cudaEventRecord(*start, s);
 }
 
 void prof_end_launch(cudaStream_t s, cudaEvent_t start, int kind, double ops, double bytes) {
   if (!g_on || !start) return;
-  cudaEvent_t stop;
-  if (cudaEventCreate(&stop) != cudaSuccess) return;
+  const int dev = current_device();
+  cudaEvent_t stop = take_event(dev);
+  if (!stop) return;
   cudaEventRecord(stop, s);
   std::lock_guard<std::mutex> lk(g_mu);
-  g_recs.push_back({kind, ops, bytes, start, stop});
+  g_recs.push_back({kind, ops, bytes, start, stop, dev});
 }
 
 }  // namespace ddg
@@ -52,7 +83,7 @@ extern "C" {
 
 ddg_status ddg_profile_begin(void) {
   std::lock_guard<std::mutex> lk(ddg::g_mu);
-  for (auto& r : ddg::g_recs) { cudaEventDestroy(r.start); cudaEventDestroy(r.stop); }
+  for (auto& r : ddg::g_recs) ddg::give_back(r);
   ddg::g_recs.clear();
   ddg::g_on = true;
   return DDG_OK;
@@ -100,7 +131,8 @@ ddg_status ddg_profile_end(ddg_kernel_prof* out, int32_t nkinds) {
       if (open) busy += ce - cs;
       out[k].busy_ms = busy;
     }
-    for (auto& r : recs) { cudaEventDestroy(r.start); cudaEventDestroy(r.stop); }
+    std::lock_guard<std::mutex> lk(ddg::g_mu);
+    for (auto& r : recs) ddg::give_back(r);
   }
   return st;
 }

@@ -24,10 +24,11 @@ class Workload:
 
 
 # The headline: DD Winograd at n = 4096 (Winograd is the paper's fastest
-# algorithm, Table 1), cutoff chosen by the cutoff sweep.
-DD_WINOGRAD_4096 = Workload("dd_winograd_n4096", 2, 4096, "winograd", 512, 101, 102)
+# algorithm, Table 1), cutoff chosen by the cutoff sweep (256: four levels,
+# 2401 leaves of 256^3).
+DD_WINOGRAD_4096 = Workload("dd_winograd_n4096", 2, 4096, "winograd", 256, 101, 102)
 DD_BLOCK_4096 = Workload("dd_block_n4096", 2, 4096, "block", 512, 101, 102)
-QD_WINOGRAD_4096 = Workload("qd_winograd_n4096", 4, 4096, "winograd", 512, 103, 104)
+QD_WINOGRAD_4096 = Workload("qd_winograd_n4096", 4, 4096, "winograd", 256, 103, 104)
 QD_BLOCK_4096 = Workload("qd_block_n4096", 4, 4096, "block", 512, 103, 104)
 # The small case the oracle finishes in well under a second (Simple, n = 128).
 DD_SIMPLE_128 = Workload("dd_simple_n128", 2, 128, "simple", 512, 0, 1)
@@ -45,9 +46,10 @@ DD_OZAKI_8192_S16 = Workload("dd_ozaki_n8192_s16", 2, 8192, "ozaki", 512, 109, 1
 DD_LU_4096 = Workload("dd_lu_n4096", 2, 4096, "winograd", 512, 111, 0)
 # The same solve with the trailing updates as INT8 residue products (CRT).
 DD_LU_4096_OZ2 = Workload("dd_lu_n4096_ozaki2", 2, 4096, "ozaki2", 512, 111, 0)
-# Same 512^3 leaves as the headline at n = 2048 (two levels, 49 leaves):
-# operands 200 MB > L2, small enough for a counter capture.
-DD_WINOGRAD_2048 = Workload("dd_winograd_n2048", 2, 2048, "winograd", 512, 112, 113)
+# Same 256^3 leaves as the headline at n = 2048 (three levels, 343 leaves):
+# operands 200 MB > L2, small enough for a counter capture; likewise QD.
+DD_WINOGRAD_2048 = Workload("dd_winograd_n2048", 2, 2048, "winograd", 256, 112, 113)
+QD_WINOGRAD_2048 = Workload("qd_winograd_n2048", 4, 2048, "winograd", 256, 118, 119)
 DD_LU_1024 = Workload("dd_lu_n1024", 2, 1024, "winograd", 512, 114, 0)
 # The CRT (Ozaki scheme II) DD product with 32 moduli (P = 113 at l = 4096).
 DD_OZAKI2_4096_N32 = Workload("dd_ozaki2_n4096_n32", 2, 4096, "ozaki2", 512, 101, 102, 32)

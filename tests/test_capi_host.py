@@ -80,10 +80,13 @@ def test_reserved_and_accum_checked():
     o.reserved[0] = 1
     st = capi.dd_gemm(4, 4, 4, dd(4), dd(4, FAKE + (1 << 33)), dd(4, FAKE + (1 << 34)), 0, o, 0)
     assert st == capi.DDG_EINVAL
-    o = capi.opts()
-    o.accum = 2
-    st = capi.dd_gemm(4, 4, 4, dd(4), dd(4, FAKE + (1 << 33)), dd(4, FAKE + (1 << 34)), 0, o, 0)
-    assert st == capi.DDG_EINVAL
+    for bad in (3, -1):
+        o = capi.opts()
+        o.accum = bad
+        st = capi.dd_gemm(4, 4, 4, dd(4), dd(4, FAKE + (1 << 33)), dd(4, FAKE + (1 << 34)), 0, o, 0)
+        assert st == capi.DDG_EINVAL
+    assert capi.ddg_block_fp64_ops_per_mac(2, 2) == 0
+    assert capi.ddg_block_fp64_ops_per_mac(2, 3) == -1
 
 
 def test_qd_validation():

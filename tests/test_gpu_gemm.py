@@ -250,3 +250,105 @@ def test_narrow_integer_exact():
     B = I.integer(3000, 3, 2, seed=49, bits=20)
     C = run(A, B, algo="block")
     assert not O.gemm_error(A, B, C).any()
+
+
+# ------------------------ operands converted once vs per staged tile ------
+CONVERTED = [(100, 77, 130), (64, 32, 64), (257, 255, 263), (300, 1000, 70), (65, 33, 97)]
+
+
+def _specials(A, B):
+    """Zero and negative-zero rows of A, a zero column of B, subnormal leading
+    limbs (lower limbs zero) in a row of A."""
+    A[:, 3, :] = 0.0
+    A[:, 5, :] = -0.0
+    B[:, :, 7] = 0.0
+    A[0, 9, :] = np.ldexp(np.arange(1, A.shape[2] + 1, dtype=np.float64), -1070)
+    A[1:, 9, :] = 0.0
+
+
+@pytest.mark.parametrize("limbs", [2, 4])
+@pytest.mark.parametrize("shape", CONVERTED)
+def test_converted_operands_same_bits(limbs, shape):
+    """Block products large enough to convert each operand once into workspace
+    (accum "fx") give exactly the bits of converting every tile as it is staged
+    (accum "fx_tile"), in all three modes, on wide-range operands with zeros,
+    negative zeros and subnormals; and stay within the Block bounds."""
+    m, l, n = shape
+    A = I.wide(m, l, limbs, seed=60)
+    B = I.uniform(l, n, limbs, seed=61)
+    _specials(A, B)
+    C0 = I.uniform(m, n, limbs, seed=62)
+    for mode in ("set", "add", "sub"):
+        c0 = None if mode == "set" else C0
+        got = run(A, B, c0, algo="block", mode=mode)
+        want = run(A, B, c0, algo="block", mode=mode, accum="fx_tile")
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), mode
+        if mode == "set":
+            check_bounds(A, B, got, "block")
+            assert not got[:, 3, :].any() and not got[:, 5, :].any() and not got[:, :, 7].any()
+
+
+@pytest.mark.parametrize("limbs", [2, 4])
+@pytest.mark.parametrize("algo", ["winograd", "strassen"])
+@pytest.mark.parametrize("shape", [(301, 261, 291), (200, 150, 181)])
+def test_converted_leaves_same_bits(limbs, algo, shape):
+    """Recursion leaves on operands converted once per node (the 14 leaf
+    operands of a node in one launch): two levels with 75 x 65 x 72 leaves and
+    peeled edges, and one level whose leaves (100 x 75 x 90) run on the seven
+    forked streams; the same bits as the per-tile path, on both stream
+    schedules."""
+    m, l, n = shape
+    A = I.uniform(m, l, limbs, seed=63)
+    B = I.wide(l, n, limbs, seed=64)
+    want = run(A, B, algo=algo, cutoff=100, accum="fx_tile")
+    for streams in (7, 1):
+        got = run(A, B, algo=algo, cutoff=100, streams=streams)
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), streams
+    check_bounds(A, B, want, algo)
+
+
+def test_conversion_launches_profiled():
+    """A converted Block product is two launches: the conversion of both
+    operands (profile kind "convert") and the product."""
+    import paper_1510_08642_gb300 as P
+    from paper_1510_08642_gb300 import capi
+    dA = to_dev(I.uniform(128, 96, 2, seed=65))
+    dB = to_dev(I.uniform(96, 160, 2, seed=66))
+    for accum, conv in (("fx", 1), ("fx_tile", 0)):
+        P.gemm(dA, dB, algo="block")  # load and warm up outside the profile
+        torch.cuda.synchronize()
+        capi.ddg_profile_begin()
+        P.gemm(dA, dB, algo="block", accum=accum)
+        prof = capi.ddg_profile_end()
+        assert prof["convert"]["launches"] == conv
+        assert prof["convert"]["ops"] == (128 * 96 + 96 * 160 if conv else 0)
+        assert prof["block"]["launches"] == 1
+        assert prof["block"]["ops"] == 128 * 96 * 160
+
+
+@pytest.mark.parametrize("name", ["dd_winograd_n4096", "qd_winograd_n4096"])
+def test_benchmark_workload_sampled(name):
+    """The benchmark's DD / QD Winograd workloads at full size (n = 4096,
+    cutoff 256, seven streams, operands converted once per leaf node): sampled
+    entries against the oracle's exact error within the normwise bound scaled
+    elementwise, and every bit equal to the per-tile conversion path."""
+    import paper_1510_08642_gb300 as P
+    from paper_1510_08642_gb300 import workloads as WL
+    w = {x.name: x for x in (WL.DD_WINOGRAD_4096, WL.QD_WINOGRAD_4096)}[name]
+    A = I.uniform(w.n, w.n, w.limbs, seed=w.seed_a)
+    B = I.uniform(w.n, w.n, w.limbs, seed=w.seed_b)
+    dA, dB = to_dev(A), to_dev(B)
+    C = P.gemm(dA, dB, algo=w.algo, cutoff=w.cutoff)
+    Ct = P.gemm(dA, dB, algo=w.algo, cutoff=w.cutoff, accum="fx_tile")
+    torch.cuda.synchronize()
+    assert torch.equal(C.view(torch.int64), Ct.view(torch.int64))
+    del Ct
+    rows, cols = sample_entries(w.n, w.n, 60, seed=w.n + w.limbs)
+    Cs = C[:, rows, cols].cpu().numpy()  # (limbs, samples)
+    Cfull = np.zeros((w.limbs, w.n, w.n))
+    Cfull[:, rows, cols] = Cs
+    err = O.gemm_error(A, B, Cfull, rows=rows, cols=cols)
+    assert np.all(np.abs(err) <= normwise_bound(w.n, w.limbs, w.algo) * absprod(A, B, rows, cols))
+    # far inside the bound: a wrong quadrant formula is O(1)
+    scale = absprod(A, B, rows, cols)
+    assert np.all(np.abs(err) <= (1e-26 if w.limbs == 2 else 1e-58) * scale)
