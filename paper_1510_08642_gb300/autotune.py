@@ -7,7 +7,7 @@ split at least once -- on a small batch of that shape through the batched
 grouped launch, and keeps the fastest. The table is stored as JSON keyed by
 GPU name, so a later process reuses it; shapes without an entry fall back to
 a model: Winograd when the smallest dimension exceeds 512 (cutoff 256, or
-1/16 of the dimension above 4096), Block otherwise.
+1/32 of the dimension above 8192), Block otherwise.
 
 Timing only: choices never change results beyond the algorithms' bounds.
 """
@@ -30,12 +30,12 @@ def bucket(limbs: int, m: int, l: int, n: int) -> str:
 
 def default_choice(limbs: int, m: int, l: int, n: int):
     """Winograd once the smallest dimension exceeds 512, with leaves of 256
-    (the best of the n = 4096 cutoff sweep) or, above 4096, of 1/16 of the
-    dimension (at most four levels: deeper recursions queue thousands of
-    launches on each of the seven streams); Block otherwise."""
+    (the best of the n = 4096 and n = 8192 cutoff sweeps) or, above 8192, of
+    1/32 of the dimension (at most five levels: deeper recursions queue
+    thousands of launches on each of the seven streams); Block otherwise."""
     mn = min(m, l, n)
     if mn > 512:
-        return "winograd", max(256, (1 << (mn - 1).bit_length()) // 16)
+        return "winograd", max(256, (1 << (mn - 1).bit_length()) // 32)
     return "block", 512
 
 

@@ -241,13 +241,15 @@ __global__ void __launch_bounds__(128, fxcfg<L>::MINB) block_fx_kernel(int64_t m
                     (int64_t)blockIdx.x * fxcfg<L>::BN, sm, fxop{}, fxop{});
 }
 
-// The Block kernel on converted operands (A, B given only by Ax, Bx).
+// The Block kernel on converted operands (A, B given only by their fxop):
+// blockIdx.z picks one of G.count products of the same shape.
 template <int L>
-__global__ void __launch_bounds__(128, fxcfg<L>::MINB) block_fxc_kernel(int64_t m, int64_t l, int64_t n, fxop Ax,
-                                                                        fxop Bx, mat C, int mode) {
+__global__ void __launch_bounds__(128, fxcfg<L>::MINB) block_fxc_kernel(int64_t m, int64_t l, int64_t n,
+                                                                        fxc_group G, int mode) {
   __shared__ fx_smem<L> sm;
-  fx_tile<L, true>(m, l, n, mat{}, mat{}, C, mode, (int64_t)blockIdx.y * fxcfg<L>::BM,
-                   (int64_t)blockIdx.x * fxcfg<L>::BN, sm, Ax, Bx);
+  const int z = blockIdx.z;
+  fx_tile<L, true>(m, l, n, mat{}, mat{}, G.C[z], mode, (int64_t)blockIdx.y * fxcfg<L>::BM,
+                   (int64_t)blockIdx.x * fxcfg<L>::BN, sm, G.A[z], G.B[z]);
 }
 
 // Every element of up to FX_CONV_MAX operands converted once (to_fixed),
@@ -408,23 +410,29 @@ size_t block_fx_scratch_bytes(int limbs, int64_t m, int64_t l, int64_t n) {
   return fxop_bytes(limbs, m, l) + fxop_bytes(limbs, l, n);
 }
 
-cudaError_t launch_block_fxc(int limbs, int64_t m, int64_t l, int64_t n, const fxop& Ax, const fxop& Bx, mat C,
-                             int mode, cudaStream_t s) {
+cudaError_t launch_block_fxc(int limbs, int64_t m, int64_t l, int64_t n, const fxop* Ax, const fxop* Bx,
+                             const mat* C, int count, int mode, cudaStream_t s) {
+  if (count < 1 || count > FXC_GROUP_MAX) return cudaErrorInvalidValue;
   if (m == 0 || n == 0) return cudaSuccess;
+  fxc_group G{};
+  for (int t = 0; t < count; ++t) G.A[t] = Ax[t], G.B[t] = Bx[t], G.C[t] = C[t];
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaEvent_t ev = nullptr;
   prof_begin_launch(s, &ev);
   if (limbs == 2) {
-    dim3 grid((unsigned)((n + fxcfg<2>::BN - 1) / fxcfg<2>::BN), (unsigned)((m + fxcfg<2>::BM - 1) / fxcfg<2>::BM));
-    block_fxc_kernel<2><<<grid, 128, 0, s>>>(m, l, n, Ax, Bx, C, mode);
+    dim3 grid((unsigned)((n + fxcfg<2>::BN - 1) / fxcfg<2>::BN), (unsigned)((m + fxcfg<2>::BM - 1) / fxcfg<2>::BM),
+              (unsigned)count);
+    block_fxc_kernel<2><<<grid, 128, 0, s>>>(m, l, n, G, mode);
   } else {
-    dim3 grid((unsigned)((n + fxcfg<4>::BN - 1) / fxcfg<4>::BN), (unsigned)((m + fxcfg<4>::BM - 1) / fxcfg<4>::BM));
-    block_fxc_kernel<4><<<grid, 128, 0, s>>>(m, l, n, Ax, Bx, C, mode);
+    dim3 grid((unsigned)((n + fxcfg<4>::BN - 1) / fxcfg<4>::BN), (unsigned)((m + fxcfg<4>::BM - 1) / fxcfg<4>::BM),
+              (unsigned)count);
+    block_fxc_kernel<4><<<grid, 128, 0, s>>>(m, l, n, G, mode);
   }
   cudaError_t e = cudaGetLastError();
   if (ev) {
-    const double macs = (double)m * (double)l * (double)n;
-    const double bytes = 8.0 * limbs * ((double)m * l + (double)l * n + (double)m * n * (mode == MODE_SET ? 1 : 2));
+    const double macs = (double)count * (double)m * (double)l * (double)n;
+    const double bytes = (double)count * 8.0 * limbs *
+                         ((double)m * l + (double)l * n + (double)m * n * (mode == MODE_SET ? 1 : 2));
     prof_end_launch(s, ev, PROF_BLOCK, macs, bytes);
   }
   return e;
@@ -440,7 +448,7 @@ cudaError_t launch_block_fx_converted(int limbs, int64_t m, int64_t l, int64_t n
   fxop op[2];
   cudaError_t e = launch_fx_convert(limbs, 2, rows, cols, X, buf, op, s);
   if (e != cudaSuccess) return e;
-  return launch_block_fxc(limbs, m, l, n, op[0], op[1], C, mode, s);
+  return launch_block_fxc(limbs, m, l, n, &op[0], &op[1], &C, 1, mode, s);
 }
 
 int block_fx_fp64_ops_per_mac(int limbs) { return limbs == 2 || limbs == 4 ? 0 : -1; }

@@ -189,12 +189,11 @@ static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, c
     for (int i = 0; i < 7; ++i) { lhs[i] = L_[i]; rhs[i] = R_[i]; }
   }
   // Children that are Block base cases on converted operands: their 14
-  // operands are converted in one launch on s (into the stack's leaf area)
-  // before the products, rather than 2 by 2 before each product, which keeps
-  // each stream's queue short.
-  const bool leaves = !splits(c, h, k, w) && converts(c, h, k, w);
-  fxop opl[7], opr[7];
-  if (leaves) {
+  // operands are converted in one launch (into the stack's leaf area) and
+  // the seven products, all of one shape, run as one launch on s. This keeps
+  // each stream's queue short and fills the GPU even when one leaf product
+  // alone has few tiles.
+  if (!splits(c, h, k, w) && converts(c, h, k, w)) {
     const size_t bl = fxop_bytes(c.L, h, k), br = fxop_bytes(c.L, k, w);
     c.leaf_peak[region] = std::max(c.leaf_peak[region], 7 * (bl + br));
     if (!c.dry) {
@@ -208,13 +207,14 @@ static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, c
         rows[7 + i] = k, cols[7 + i] = w, X[7 + i] = rhs[i], buf[7 + i] = area + 7 * bl + i * br;
       }
       DDG_CUDA(launch_fx_convert(c.L, 14, rows, cols, X, buf, op, s));
-      for (int i = 0; i < 7; ++i) opl[i] = op[i], opr[i] = op[7 + i];
+      DDG_CUDA(launch_block_fxc(c.L, h, k, w, &op[0], &op[7], P, 7, MODE_SET, s));
+      const mat qc[4] = {C11, C12, C21, C22};
+      DDG_CUDA(launch_pass(c.L, win ? PASS_WINOGRAD_C : PASS_STRASSEN_C, h, w, P, 7, qc, 4, mode, s));
     }
+    return DDG_OK;
   }
   auto child = [&](int i, cudaStream_t cs, int reg, size_t rsp) -> ddg_status {
-    if (!leaves) return rec(c, h, k, w, lhs[i], rhs[i], P[i], MODE_SET, cs, reg, rsp, depth + 1);
-    if (!c.dry) DDG_CUDA(launch_block_fxc(c.L, h, k, w, opl[i], opr[i], P[i], MODE_SET, cs));
-    return DDG_OK;
+    return rec(c, h, k, w, lhs[i], rhs[i], P[i], MODE_SET, cs, reg, rsp, depth + 1);
   };
   const bool fork = depth == 0 && c.nstreams == 7;
   if (fork) {

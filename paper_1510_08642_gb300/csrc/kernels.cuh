@@ -85,9 +85,16 @@ size_t fxop_bytes(int limbs, int64_t rows, int64_t cols);
 // the result.
 cudaError_t launch_fx_convert(int limbs, int count, const int64_t* rows, const int64_t* cols, const mat* X,
                               char* const* buf, fxop* out, cudaStream_t s);
-// The Block product on converted operands: the same bits as launch_block_fx.
-cudaError_t launch_block_fxc(int limbs, int64_t m, int64_t l, int64_t n, const fxop& Ax, const fxop& Bx, mat C,
-                             int mode, cudaStream_t s);
+// The Block product on converted operands, the same bits as launch_block_fx:
+// count <= FXC_GROUP_MAX products C[t] (mode) A[t] B[t] of one shape in one
+// launch (blockIdx.z = t).
+constexpr int FXC_GROUP_MAX = 7;
+struct fxc_group {
+  fxop A[FXC_GROUP_MAX], B[FXC_GROUP_MAX];
+  mat C[FXC_GROUP_MAX];
+};
+cudaError_t launch_block_fxc(int limbs, int64_t m, int64_t l, int64_t n, const fxop* Ax, const fxop* Bx,
+                             const mat* C, int count, int mode, cudaStream_t s);
 // Both steps for one product, scratch = block_fx_scratch_bytes (used in
 // stream order on s). block_fx_converts: whether the shape gains from it
 // (a tile of A is otherwise converted by each of the n / BN CTAs that stage

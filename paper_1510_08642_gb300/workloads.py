@@ -40,7 +40,7 @@ DD_WINOGRAD_2560 = Workload("dd_winograd_n2560", 2, 2560, "winograd", 320, 105, 
 # Winograd product, n = 4096 and 8192.
 DD_OZAKI_4096_S16 = Workload("dd_ozaki_n4096_s16", 2, 4096, "ozaki", 512, 101, 102, 16)
 DD_OZAKI_4096_S13 = Workload("dd_ozaki_n4096_s13", 2, 4096, "ozaki", 512, 101, 102, 13)
-DD_WINOGRAD_8192 = Workload("dd_winograd_n8192", 2, 8192, "winograd", 512, 109, 110)
+DD_WINOGRAD_8192 = Workload("dd_winograd_n8192", 2, 8192, "winograd", 256, 109, 110)
 DD_OZAKI_8192_S16 = Workload("dd_ozaki_n8192_s16", 2, 8192, "ozaki", 512, 109, 110, 16)
 # Section 4 LU solve (random [-1, 1] matrix), block column K, Winograd update.
 DD_LU_4096 = Workload("dd_lu_n4096", 2, 4096, "winograd", 512, 111, 0)

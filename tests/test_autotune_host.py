@@ -7,7 +7,8 @@ from paper_1510_08642_gb300 import autotune
 def test_bucket_and_default():
     assert autotune.bucket(2, 1024, 1000, 33) == "2:10:10:5"
     assert autotune.default_choice(2, 4096, 4096, 4096) == ("winograd", 256)
-    assert autotune.default_choice(2, 8192, 8192, 8192) == ("winograd", 512)
+    assert autotune.default_choice(2, 8192, 8192, 8192) == ("winograd", 256)
+    assert autotune.default_choice(2, 16384, 16384, 16384) == ("winograd", 512)
     assert autotune.default_choice(4, 3000, 3000, 3000) == ("winograd", 256)
     assert autotune.default_choice(2, 600, 700, 900) == ("winograd", 256)
     assert autotune.default_choice(4, 100, 2000, 2000)[0] == "block"
