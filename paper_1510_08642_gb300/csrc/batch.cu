@@ -7,7 +7,10 @@
 //   pre[d]   fused operand passes of all nodes at depth d (top-down),
 //   leaves   every base-case Block product of every problem, plus the border
 //            products of peeled odd rows / columns (they touch disjoint parts
-//            of C), in ONE grouped launch per limb count,
+//            of C), in one grouped launch per limb count: the products with
+//            enough tiles (block_fx_converts) after one grouped launch that
+//            converts all their operands to fixed-point words, the others
+//            converting tiles as they are staged (the same bits either way),
 //   post[d]  fused combination passes at depth d (bottom-up), each followed
 //            by the rank-1 fix-ups of odd inner dimensions at that depth.
 // Passes of the same depth, kind and limb count share one grouped launch.
@@ -30,14 +33,14 @@ namespace ddg {
 namespace {
 
 struct Launch {
-  int type;  // 0 pass, 1 grouped Block
+  int type;  // 0 pass, 1 grouped Block, 2 grouped conversion, 3 grouped Block on converted operands
   int limbs;
   int kind;
   size_t task_off;  // byte offset of the task array in the plan's buffer
   int ntasks;
   int64_t total;
   size_t counter_off;
-  double ops;  // algorithmic FP64 instructions (grouped Block launches)
+  double ops;  // multiply-adds (grouped Block launches) or converted elements
 };
 
 struct Builder {
@@ -162,9 +165,15 @@ static ddg_status enqueue(ddg_batch_s* b, cudaStream_t s) {
     if (L.type == 0)
       e = launch_grouped_pass(L.limbs, L.kind, reinterpret_cast<const ptask*>(b->buf + L.task_off), L.ntasks,
                               L.total, s);
-    else
+    else if (L.type == 1)
       e = launch_grouped_fx(L.limbs, reinterpret_cast<const gtask*>(b->buf + L.task_off), L.ntasks, L.total,
                             reinterpret_cast<unsigned long long*>(b->buf + L.counter_off), L.ops, s);
+    else if (L.type == 2)
+      e = launch_grouped_convert(L.limbs, reinterpret_cast<const fx_ctask*>(b->buf + L.task_off), L.ntasks,
+                                 L.total, L.ops, s);
+    else
+      e = launch_grouped_fxc(L.limbs, reinterpret_cast<const gctask*>(b->buf + L.task_off), L.ntasks, L.total,
+                             reinterpret_cast<unsigned long long*>(b->buf + L.counter_off), L.ops, s);
     if (e != cudaSuccess) return set_error(DDG_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   }
   return DDG_OK;
@@ -218,6 +227,15 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
   Builder dry;
   build(dry);
   const size_t temps = (dry.off + 255) & ~(size_t)255;
+  // converted operands of the leaves that convert, after the temporaries
+  auto conv_bytes = [](int L, const gtask& g) {
+    return fxop_bytes(L, g.m, g.l) + fxop_bytes(L, g.l, g.n);
+  };
+  size_t convs = 0;
+  for (int L : {2, 4})
+    for (const gtask& g : dry.leaves[L])
+      if (block_fx_converts(L, g.m, g.l, g.n)) convs += conv_bytes(L, g);
+  const size_t lists = temps + convs;
   auto* b = new ddg_batch_s();
   b->use_graph = use_graph;
   if (cudaGetDevice(&b->dev) != cudaSuccess) {
@@ -232,7 +250,7 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
     const size_t at = (host.size() + 255) & ~(size_t)255;
     host.resize(at + bytes);
     std::memcpy(host.data() + at, data, bytes);
-    return temps + at;
+    return lists + at;
   };
   // temporaries, then the task lists (bounded from the dry expansion)
   std::vector<Launch> launches;
@@ -241,8 +259,13 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
     for (auto& kv : dry.pre) tb += ((kv.second.size() * sizeof(ptask) + 255) & ~(size_t)255);
     for (auto& kv : dry.post) tb += ((kv.second.size() * sizeof(ptask) + 255) & ~(size_t)255);
     for (auto& kv : dry.fix) tb += ((kv.second.size() * sizeof(gtask) + 255) & ~(size_t)255) + 256;
-    for (int L : {2, 4}) tb += ((dry.leaves[L].size() * sizeof(gtask) + 255) & ~(size_t)255) + 256;
-    b->bytes = temps + tb + 4096;
+    for (int L : {2, 4}) {
+      const size_t nl = dry.leaves[L].size();
+      tb += ((nl * sizeof(gtask) + 255) & ~(size_t)255) + 256;   // leaves converting tiles as staged
+      tb += ((nl * sizeof(gctask) + 255) & ~(size_t)255) + 256;  // leaves on converted operands
+      tb += ((2 * nl * sizeof(fx_ctask) + 255) & ~(size_t)255);  // their conversions
+    }
+    b->bytes = lists + tb + 4096;
   }
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   if (ddg::ws_alloc(reinterpret_cast<void**>(&b->buf), std::max<size_t>(b->bytes, 256), cs) != cudaSuccess) {
@@ -292,12 +315,78 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
     launches.push_back(la);
     b->stats.pass_tasks += (int64_t)v.size();
   };
+  // the leaves that convert: their operands' buffers, conversion tasks and
+  // product tasks; the others stay in the staged-conversion launch
+  size_t cursor = temps;
+  auto add_converted = [&](std::vector<gtask>& v, int L) {
+    std::vector<gtask> plain;
+    std::vector<gctask> conv;
+    std::vector<fx_ctask> jobs;
+    int64_t ctiles = 0;
+    double elems = 0.0;
+    auto job = [&](int64_t rows, int64_t cols, const mat& X, fxop* out) {
+      char* buf = b->buf + cursor;
+      cursor += fxop_bytes(L, rows, cols);
+      fx_ctask j{};
+      j.rows = rows;
+      j.cols = cols;
+      j.X = X;
+      j.w = reinterpret_cast<uint4*>(buf);
+      j.f = reinterpret_cast<int*>(buf + (((size_t)rows * cols * 16 * (L == 2 ? 1 : 2) + 255) & ~(size_t)255));
+      j.tiles_x = (cols + 255) / 256;
+      j.tile0 = ctiles;
+      ctiles += convert_tiles(rows, cols);
+      elems += (double)rows * cols;
+      jobs.push_back(j);
+      *out = fxop{j.w, j.f, cols};
+    };
+    for (const gtask& g : v) {
+      if (!block_fx_converts(L, g.m, g.l, g.n)) {
+        plain.push_back(g);
+        continue;
+      }
+      gctask c{};
+      c.m = g.m;
+      c.l = g.l;
+      c.n = g.n;
+      c.C = g.C;
+      c.mode = g.mode;
+      job(g.m, g.l, g.A, &c.A);
+      job(g.l, g.n, g.B, &c.B);
+      conv.push_back(c);
+    }
+    if (!jobs.empty()) {
+      Launch la{2, L, 0, 0, (int)jobs.size(), ctiles, 0, elems};
+      la.task_off = push_tasks(jobs.data(), jobs.size() * sizeof(fx_ctask));
+      launches.push_back(la);
+    }
+    if (!conv.empty()) {
+      int bm, bn;
+      fx_tile_shape(L, &bm, &bn);
+      std::stable_sort(conv.begin(), conv.end(), [](const gctask& x, const gctask& y) { return x.l > y.l; });
+      int64_t t0 = 0;
+      double macs = 0.0;
+      for (auto& g : conv) {
+        g.tiles_n = (int)((g.n + bn - 1) / bn);
+        g.tile0 = t0;
+        t0 += (int64_t)((g.m + bm - 1) / bm) * g.tiles_n;
+        macs += (double)g.m * g.l * g.n;
+      }
+      Launch la{3, L, 0, 0, (int)conv.size(), t0, 0, macs};
+      la.task_off = push_tasks(conv.data(), conv.size() * sizeof(gctask));
+      const uint64_t zero = 0;
+      la.counter_off = push_tasks(&zero, sizeof(zero));
+      launches.push_back(la);
+      b->stats.leaf_tiles += t0;
+    }
+    add_g(plain, L);
+  };
   for (int d = 0; d <= real.maxdepth; ++d)
     for (auto& kv : real.pre)
       if (std::get<0>(kv.first) == d) add_p(kv.second, std::get<1>(kv.first), std::get<2>(kv.first));
   for (int L : {2, 4}) {
     b->stats.leaf_tasks += (int64_t)real.leaves[L].size();
-    add_g(real.leaves[L], L);
+    add_converted(real.leaves[L], L);
   }
   for (int d = real.maxdepth; d >= 0; --d) {
     for (auto& kv : real.post)
@@ -305,14 +394,14 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
     for (auto& kv : real.fix)
       if (std::get<0>(kv.first) == d) add_g(kv.second, std::get<1>(kv.first));
   }
-  if (temps + host.size() > b->bytes) {
+  if (cursor != lists || lists + host.size() > b->bytes) {
     ddg::ws_free(b->buf, cs);
     delete b;
     return set_error(DDG_ECUDA, "ddg_batch_create: task list larger than planned");
   }
   // pageable source: the copy is staged before the call returns
   if (!host.empty() &&
-      cudaMemcpyAsync(b->buf + temps, host.data(), host.size(), cudaMemcpyHostToDevice, cs) != cudaSuccess) {
+      cudaMemcpyAsync(b->buf + lists, host.data(), host.size(), cudaMemcpyHostToDevice, cs) != cudaSuccess) {
     ddg::ws_free(b->buf, cs);
     delete b;
     return set_error(DDG_ECUDA, "ddg_batch_create: task upload");

@@ -252,32 +252,56 @@ __global__ void __launch_bounds__(128, fxcfg<L>::MINB) block_fxc_kernel(int64_t 
                    (int64_t)blockIdx.x * fxcfg<L>::BN, sm, G.A[z], G.B[z]);
 }
 
-// Every element of up to FX_CONV_MAX operands converted once (to_fixed),
-// each into the dense layout of fxop (ld = cols): blockIdx.z = operand,
-// thread = column, CTA row = matrix row.
+// Element (r, c) of X converted (to_fixed) into the dense fxop layout with
+// ld = cols: its word vectors at w[(r cols + c) WV ...], f at f[r cols + c].
+template <int L>
+__device__ __forceinline__ void convert_elem(const mat& X, int64_t r, int64_t c, int64_t cols, uint4* __restrict__ w,
+                                             int* __restrict__ f) {
+  constexpr int W = fxcfg<L>::W, WV = fx_smem<L>::WV;
+  double x[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) x[q] = X.p[q][r * X.ld + c];
+  uint32_t M[4 * WV];
+  uint32_t(&Mw)[W] = *reinterpret_cast<uint32_t(*)[W]>(M);
+  const int es = fx::to_fixed<L, W>(x, Mw);
+#pragma unroll
+  for (int t = W; t < 4 * WV; ++t) M[t] = 0u;
+  const bool zero = (fx::dbits(x[0]) << 1) == 0u;
+  const int64_t e = r * cols + c;
+#pragma unroll
+  for (int v = 0; v < WV; ++v) w[e * WV + v] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
+  f[e] = zero ? FX_ZERO : es;
+}
+
+// Every element of up to FX_CONV_MAX operands converted once, each into the
+// dense layout of fxop (ld = cols): blockIdx.z = operand, thread = column,
+// CTA row = matrix row.
 template <int L>
 __global__ void __launch_bounds__(256) fx_convert_kernel(fx_conv_jobs J) {
-  constexpr int W = fxcfg<L>::W, WV = fx_smem<L>::WV;
   const fx_conv_job& jb = J.job[blockIdx.z];
-  const int64_t rows = jb.rows, cols = jb.cols;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
-  uint4* __restrict__ w = jb.w;
-  int* __restrict__ f = jb.f;
-  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
-    double x[L];
-#pragma unroll
-    for (int q = 0; q < L; ++q) x[q] = jb.X.p[q][r * jb.X.ld + c];
-    uint32_t M[4 * WV];
-    uint32_t(&Mw)[W] = *reinterpret_cast<uint32_t(*)[W]>(M);
-    const int es = fx::to_fixed<L, W>(x, Mw);
-#pragma unroll
-    for (int t = W; t < 4 * WV; ++t) M[t] = 0u;
-    const bool zero = (fx::dbits(x[0]) << 1) == 0u;
-    const int64_t e = r * cols + c;
-#pragma unroll
-    for (int v = 0; v < WV; ++v) w[e * WV + v] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
-    f[e] = zero ? FX_ZERO : es;
+  if (c >= jb.cols) return;
+  for (int64_t r = blockIdx.y; r < jb.rows; r += gridDim.y) convert_elem<L>(jb.X, r, c, jb.cols, jb.w, jb.f);
+}
+
+// The same for a device-resident list of operands (batch plans): job t owns
+// the tiles [tile0, tile0 + rows tiles_x), each one row by 256 columns;
+// CTA b takes tiles b, b + gridDim.x, ... (no CTA waits on another).
+template <int L>
+__global__ void __launch_bounds__(256) grouped_convert_kernel(const fx_ctask* __restrict__ tasks, int ntasks,
+                                                              int64_t total) {
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tasks[mid].tile0 <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const fx_ctask& jb = tasks[lo];
+    const int64_t local = t - jb.tile0;
+    const int64_t r = local / jb.tiles_x;
+    const int64_t c = (local - r * jb.tiles_x) * 256 + threadIdx.x;
+    if (c < jb.cols) convert_elem<L>(jb.X, r, c, jb.cols, jb.w, jb.f);
   }
 }
 
@@ -306,6 +330,33 @@ __global__ void __launch_bounds__(128, fxcfg<L>::MINB - 1) grouped_fx_kernel(con
     const int64_t bi = local / g.tiles_n, bj = local % g.tiles_n;
     fx_tile<L, false>(g.m, g.l, g.n, g.A, g.B, g.C, g.mode, bi * fxcfg<L>::BM, bj * fxcfg<L>::BN, sm, fxop{},
                       fxop{});
+    __syncthreads();
+  }
+}
+
+// The grouped launch on converted operands (batch plans).
+template <int L>
+__global__ void __launch_bounds__(128, fxcfg<L>::MINB - 1) grouped_fxc_kernel(const gctask* __restrict__ tasks,
+                                                                              int ntasks, int64_t total,
+                                                                              unsigned long long* counter) {
+  __shared__ fx_smem<L> sm;
+  __shared__ int64_t st;
+  for (;;) {
+    if (threadIdx.x == 0) st = (int64_t)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const int64_t t = st;
+    __syncthreads();
+    if (t >= total) break;
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tasks[mid].tile0 <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const gctask g = tasks[lo];
+    const int64_t local = t - g.tile0;
+    const int64_t bi = local / g.tiles_n, bj = local % g.tiles_n;
+    fx_tile<L, true>(g.m, g.l, g.n, mat{}, mat{}, g.C, g.mode, bi * fxcfg<L>::BM, bj * fxcfg<L>::BN, sm, g.A, g.B);
     __syncthreads();
   }
 }
@@ -339,6 +390,51 @@ cudaError_t launch_grouped_fx(int limbs, const gtask* tasks, int ntasks, int64_t
   return e;
 }
 
+namespace {
+inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+inline size_t wv_of(int limbs) { return limbs == 2 ? fx_smem<2>::WV : fx_smem<4>::WV; }
+}  // namespace
+
+cudaError_t launch_grouped_fxc(int limbs, const gctask* tasks, int ntasks, int64_t total_tiles,
+                               unsigned long long* counter, double ops, cudaStream_t s) {
+  if (ntasks == 0 || total_tiles == 0) return cudaSuccess;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  const int per_sm = (limbs == 2 ? fxcfg<2>::MINB : fxcfg<4>::MINB) - 1;
+  const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)sms * per_sm);
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaEvent_t ev = nullptr;
+  prof_begin_launch(s, &ev);
+  if (limbs == 2) grouped_fxc_kernel<2><<<(unsigned)grid, 128, 0, s>>>(tasks, ntasks, total_tiles, counter);
+  else grouped_fxc_kernel<4><<<(unsigned)grid, 128, 0, s>>>(tasks, ntasks, total_tiles, counter);
+  e = cudaGetLastError();
+  if (ev) prof_end_launch(s, ev, PROF_BLOCK, ops, 0.0);
+  return e;
+}
+
+int64_t convert_tiles(int64_t rows, int64_t cols) { return rows * ((cols + 255) / 256); }
+
+cudaError_t launch_grouped_convert(int limbs, const fx_ctask* tasks, int ntasks, int64_t total_tiles, double elems,
+                                   cudaStream_t s) {
+  if (ntasks == 0 || total_tiles == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(total_tiles, 152 * 8);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaEvent_t ev = nullptr;
+  prof_begin_launch(s, &ev);
+  if (limbs == 2) grouped_convert_kernel<2><<<grid, 256, 0, s>>>(tasks, ntasks, total_tiles);
+  else grouped_convert_kernel<4><<<grid, 256, 0, s>>>(tasks, ntasks, total_tiles);
+  cudaError_t e = cudaGetLastError();
+  if (ev) prof_end_launch(s, ev, PROF_CONVERT, elems, elems * (8.0 * limbs + 16.0 * wv_of(limbs) + 4.0));
+  return e;
+}
+
 cudaError_t launch_block_fx(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,
                             int mode, cudaStream_t s) {
   if (m == 0 || n == 0) return cudaSuccess;
@@ -360,11 +456,6 @@ cudaError_t launch_block_fx(int limbs, int64_t m, int64_t l, int64_t n, mat A, m
   }
   return e;
 }
-
-namespace {
-inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
-inline size_t wv_of(int limbs) { return limbs == 2 ? fx_smem<2>::WV : fx_smem<4>::WV; }
-}  // namespace
 
 size_t fxop_bytes(int limbs, int64_t rows, int64_t cols) {
   const size_t elems = (size_t)rows * (size_t)cols;

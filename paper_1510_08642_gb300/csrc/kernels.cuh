@@ -120,6 +120,32 @@ struct gtask {
   int64_t tile0;
 };
 void fx_tile_shape(int limbs, int* bm, int* bn);
+
+// Grouped conversion (batch plans): operand t (rows x cols of X) into w, f
+// (fxop layout, ld = cols), owning the tiles [tile0, tile0 + rows tiles_x)
+// of one row by 256 columns (convert_tiles).
+struct fx_ctask {
+  int64_t rows, cols;
+  mat X;
+  uint4* w;
+  int* f;
+  int64_t tile0;
+  int64_t tiles_x;
+};
+int64_t convert_tiles(int64_t rows, int64_t cols);
+cudaError_t launch_grouped_convert(int limbs, const fx_ctask* tasks, int ntasks, int64_t total_tiles, double elems,
+                                   cudaStream_t s);
+// One product of a grouped launch on converted operands (tiles as gtask).
+struct gctask {
+  int64_t m, l, n;
+  fxop A, B;
+  mat C;
+  int mode;
+  int tiles_n;
+  int64_t tile0;
+};
+cudaError_t launch_grouped_fxc(int limbs, const gctask* tasks, int ntasks, int64_t total_tiles,
+                               unsigned long long* counter, double ops, cudaStream_t s);
 cudaError_t launch_grouped_fx(int limbs, const gtask* tasks, int ntasks, int64_t total_tiles,
                               unsigned long long* counter, double ops, cudaStream_t s);
 cudaError_t launch_block(int limbs, int64_t m, int64_t l, int64_t n, mat A, mat B, mat C,

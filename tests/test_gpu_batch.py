@@ -71,6 +71,35 @@ def test_batch_bit_identical_to_single_calls(use_graph):
     batch.close()
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_converted_leaves_bit_identical(use_graph):
+    """Larger problems, whose leaves convert their operands once in one
+    grouped conversion launch before a grouped product on converted
+    operands: the same bits as each product alone, and the conversion
+    launch is there (launch profile)."""
+    import paper_1510_08642_gb300 as P
+    from paper_1510_08642_gb300 import capi
+    probs = make_batch(14, 64, 420, seed=9, cutoffs=(64, 100, 200))
+    dev = []
+    for p in probs:
+        dA, dB = to_dev(p["A"]), to_dev(p["B"])
+        dev.append((dA, dB, to_dev(p["C0"]), to_dev(p["C0"])))
+    plist = [P.problem(dA, dB, dC, p["algo"], p["cutoff"], p["mode"]) for (dA, dB, dC, _), p in zip(dev, probs)]
+    batch = P.Batch(plist, use_graph=use_graph)
+    if not use_graph:
+        capi.ddg_profile_begin()
+    batch.run()
+    if not use_graph:
+        prof = capi.ddg_profile_end()
+        assert prof["convert"]["launches"] >= 1 and prof["convert"]["ops"] > 0
+    for (dA, dB, _, dC1), p in zip(dev, probs):
+        P.gemm(dA, dB, dC1, algo=p["algo"], cutoff=p["cutoff"], mode=p["mode"])
+    torch.cuda.synchronize()
+    for (dA, dB, dC, dC1), p in zip(dev, probs):
+        assert np.array_equal(to_host(dC), to_host(dC1)), (p["algo"], p["cutoff"], p["mode"], p["A"].shape)
+    batch.close()
+
+
 def test_dd_gemm_batched_one_shot():
     import paper_1510_08642_gb300 as P
     from paper_1510_08642_gb300 import capi
