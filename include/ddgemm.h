@@ -117,7 +117,9 @@ typedef struct {
                       multiword integers, no FP64 in the inner loop); larger
                       Block products first convert each operand once into
                       library workspace (about 20 B per DD element, 36 per
-                      QD, of A and of B); 2 = the same arithmetic and bits,
+                      QD, of A and of B; where that workspace cannot be
+                      allocated, tiles are converted as they are staged,
+                      as with 2); 2 = the same arithmetic and bits,
                       every tile converted as it is staged (no operand
                       workspace); 1 = TwoSum accumulation on the FP64 pipe
                       (12 FP64 instructions per DD multiply-add, 113 per QD) */

@@ -235,7 +235,10 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
   for (int L : {2, 4})
     for (const gtask& g : dry.leaves[L])
       if (block_fx_converts(L, g.m, g.l, g.n)) convs += conv_bytes(L, g);
-  const size_t lists = temps + convs;
+  // without room for the converted operands every leaf converts its tiles
+  // as they are staged (the same bits)
+  bool conv_ok = true;
+  size_t lists = temps + convs;
   auto* b = new ddg_batch_s();
   b->use_graph = use_graph;
   if (cudaGetDevice(&b->dev) != cudaSuccess) {
@@ -270,8 +273,20 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   if (ddg::ws_alloc(reinterpret_cast<void**>(&b->buf), std::max<size_t>(b->bytes, 256), cs) != cudaSuccess) {
     cudaGetLastError();
-    delete b;
-    return set_error(DDG_ENOMEM, "ddg_batch_create: workspace of " + std::to_string(b->bytes) + " bytes");
+    b->buf = nullptr;
+    if (convs) {
+      conv_ok = false;
+      b->bytes -= convs;
+      lists = temps;
+      if (ddg::ws_alloc(reinterpret_cast<void**>(&b->buf), std::max<size_t>(b->bytes, 256), cs) != cudaSuccess) {
+        cudaGetLastError();
+        b->buf = nullptr;
+      }
+    }
+    if (!b->buf) {
+      delete b;
+      return set_error(DDG_ENOMEM, "ddg_batch_create: workspace of " + std::to_string(b->bytes) + " bytes");
+    }
   }
   real.base = b->buf;
   build(real);
@@ -341,7 +356,7 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
       *out = fxop{j.w, j.f, cols};
     };
     for (const gtask& g : v) {
-      if (!block_fx_converts(L, g.m, g.l, g.n)) {
+      if (!conv_ok || !block_fx_converts(L, g.m, g.l, g.n)) {
         plain.push_back(g);
         continue;
       }

@@ -404,28 +404,37 @@ ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const 
   c.cutoff = o.cutoff;
   c.nstreams = o.streams == 1 ? 1 : 7;
   if (splits(c, m, l, n) && c.nstreams == 7) DDG_TRY(stream_pool(&c.pool));
-  // plan (a Block product alone plans its converted operands only)
-  c.dry = true;
-  DDG_TRY(top(c, m, l, n, A, B, C, mode, o.pad == 1, s));
+  // plan (a Block product alone plans its converted operands only); if the
+  // workspace with converted operands cannot be had, plan again with tiles
+  // converted as they are staged (the same bits, less workspace)
+  void* ws = nullptr;
   size_t total = 0;
-  for (int r = 0; r < 8; ++r) {
-    c.region_off[r] = total;
-    total += (c.peak[r] + 255) & ~(size_t)255;
-  }
-  for (int r = 0; r < 8; ++r) {
-    c.leaf_off[r] = total;
-    total += (c.leaf_peak[r] + 255) & ~(size_t)255;
+  for (;;) {
+    c.dry = true;
+    for (int r = 0; r < 8; ++r) c.peak[r] = c.leaf_peak[r] = 0;
+    DDG_TRY(top(c, m, l, n, A, B, C, mode, o.pad == 1, s));
+    total = 0;
+    bool converted = false;
+    for (int r = 0; r < 8; ++r) {
+      c.region_off[r] = total;
+      total += (c.peak[r] + 255) & ~(size_t)255;
+    }
+    for (int r = 0; r < 8; ++r) {
+      c.leaf_off[r] = total;
+      total += (c.leaf_peak[r] + 255) & ~(size_t)255;
+      converted = converted || c.leaf_peak[r] > 0;
+    }
+    if (!total) break;
+    cudaError_t e = ddg::ws_alloc(&ws, total, s);
+    if (e == cudaSuccess) break;
+    cudaGetLastError();
+    ws = nullptr;
+    if (!converted)
+      return fail(DDG_ENOMEM, "cudaMallocAsync of " + std::to_string(total) + " bytes: " + cudaGetErrorString(e));
+    c.convert = false;
   }
   // run
   c.dry = false;
-  void* ws = nullptr;
-  if (total) {
-    cudaError_t e = ddg::ws_alloc(&ws, total, s);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(DDG_ENOMEM, "cudaMallocAsync of " + std::to_string(total) + " bytes: " + cudaGetErrorString(e));
-    }
-  }
   c.base = static_cast<char*>(ws);
   ddg_status st = top(c, m, l, n, A, B, C, mode, o.pad == 1, s);
   if (ws) {
