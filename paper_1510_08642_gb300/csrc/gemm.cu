@@ -28,8 +28,11 @@
 #include <algorithm>
 #include <cstddef>
 #include <cstring>
+#include <functional>
+#include <memory>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "ddgemm.h"
 #include "kernels.cuh"
@@ -101,7 +104,26 @@ struct Ctx {
   size_t leaf_off[8] = {0};
   size_t leaf_peak[8] = {0};
   cudaStream_t* pool = nullptr;
+  // While a fork branch is planned, its launches are collected here and
+  // issued afterwards round-robin with the other branches' (see level()).
+  std::vector<std::function<cudaError_t()>>* q = nullptr;
 };
+
+// Where launch_fx_convert puts an operand converted into buf: the word
+// vectors first, then f, 256-byte aligned (its layout).
+static fxop fxop_at(int L, char* buf, int64_t rows, int64_t cols) {
+  const size_t words = ((size_t)rows * (size_t)cols * 16 * (L == 2 ? 1 : 2) + 255) & ~(size_t)255;
+  return fxop{reinterpret_cast<const uint4*>(buf), reinterpret_cast<const int*>(buf + words), cols};
+}
+
+// Issue a launch now, or queue it for the branch being collected.
+static cudaError_t issue(Ctx& c, std::function<cudaError_t()> fn) {
+  if (c.q) {
+    c.q->push_back(std::move(fn));
+    return cudaSuccess;
+  }
+  return fn();
+}
 
 static mat alloc_mat(Ctx& c, int region, size_t& sp, int64_t rows, int64_t cols) {
   mat M{};
@@ -136,16 +158,20 @@ static bool converts(const Ctx& c, int64_t m, int64_t l, int64_t n) {
 // The base case on stack `region`; a dry run only sizes its scratch.
 static cudaError_t base_case(Ctx& c, int region, int64_t m, int64_t l, int64_t n, const mat& A,
                              const mat& B, const mat& C, int mode, cudaStream_t s) {
-  if (c.accum == 1) return c.dry ? cudaSuccess : launch_block(c.L, m, l, n, A, B, C, mode, s);
-  if (n <= GEMV_MAX_N) return c.dry ? cudaSuccess : launch_gemv_fx(c.L, m, l, n, A, B, C, mode, s);
+  const int L = c.L;
+  if (c.accum == 1)
+    return c.dry ? cudaSuccess : issue(c, [=] { return launch_block(L, m, l, n, A, B, C, mode, s); });
+  if (n <= GEMV_MAX_N)
+    return c.dry ? cudaSuccess : issue(c, [=] { return launch_gemv_fx(L, m, l, n, A, B, C, mode, s); });
   if (converts(c, m, l, n)) {
     if (c.dry) {
       c.leaf_peak[region] = std::max(c.leaf_peak[region], block_fx_scratch_bytes(c.L, m, l, n));
       return cudaSuccess;
     }
-    return launch_block_fx_converted(c.L, m, l, n, A, B, C, mode, c.base + c.leaf_off[region], s);
+    char* scratch = c.base + c.leaf_off[region];
+    return issue(c, [=] { return launch_block_fx_converted(L, m, l, n, A, B, C, mode, scratch, s); });
   }
-  return c.dry ? cudaSuccess : launch_block_fx(c.L, m, l, n, A, B, C, mode, s);
+  return c.dry ? cudaSuccess : issue(c, [=] { return launch_block_fx(L, m, l, n, A, B, C, mode, s); });
 }
 
 static bool splits(const Ctx& c, int64_t m, int64_t l, int64_t n) {
@@ -166,16 +192,22 @@ static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, c
   const mat C11 = view(C, 0, 0), C12 = view(C, 0, w), C21 = view(C, h, 0), C22 = view(C, h, w);
   const bool win = c.algo == DDG_WINOGRAD;
   const int nl = win ? 4 : 5;  // left / right operand temporaries
-  mat SL[5], SR[5], P[7];
+  mat SL[5] = {}, SR[5] = {}, P[7] = {};
   for (int i = 0; i < nl; ++i) SL[i] = alloc_mat(c, region, sp, h, k);
   for (int i = 0; i < nl; ++i) SR[i] = alloc_mat(c, region, sp, k, w);
   for (int i = 0; i < 7; ++i) P[i] = alloc_mat(c, region, sp, h, w);
 
+  const int L = c.L;
   if (!c.dry) {
     const mat qa[4] = {A11, A12, A21, A22};
     const mat qb[4] = {B11, B12, B21, B22};
-    DDG_CUDA(launch_pass(c.L, win ? PASS_WINOGRAD_A : PASS_STRASSEN_A, h, k, qa, 4, SL, nl, MODE_SET, s));
-    DDG_CUDA(launch_pass(c.L, win ? PASS_WINOGRAD_B : PASS_STRASSEN_B, k, w, qb, 4, SR, nl, MODE_SET, s));
+    const mat sl[5] = {SL[0], SL[1], SL[2], SL[3], SL[4]}, sr[5] = {SR[0], SR[1], SR[2], SR[3], SR[4]};
+    DDG_CUDA(issue(c, [=] {
+      return launch_pass(L, win ? PASS_WINOGRAD_A : PASS_STRASSEN_A, h, k, qa, 4, sl, nl, MODE_SET, s);
+    }));
+    DDG_CUDA(issue(c, [=] {
+      return launch_pass(L, win ? PASS_WINOGRAD_B : PASS_STRASSEN_B, k, w, qb, 4, sr, nl, MODE_SET, s);
+    }));
   }
   // the seven sub-products
   mat lhs[7], rhs[7];
@@ -206,10 +238,30 @@ static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, c
         rows[i] = h, cols[i] = k, X[i] = lhs[i], buf[i] = area + i * bl;
         rows[7 + i] = k, cols[7 + i] = w, X[7 + i] = rhs[i], buf[7 + i] = area + 7 * bl + i * br;
       }
-      DDG_CUDA(launch_fx_convert(c.L, 14, rows, cols, X, buf, op, s));
-      DDG_CUDA(launch_block_fxc(c.L, h, k, w, &op[0], &op[7], P, 7, MODE_SET, s));
-      const mat qc[4] = {C11, C12, C21, C22};
-      DDG_CUDA(launch_pass(c.L, win ? PASS_WINOGRAD_C : PASS_STRASSEN_C, h, w, P, 7, qc, 4, mode, s));
+      for (int t = 0; t < 14; ++t) op[t] = fxop_at(L, buf[t], rows[t], cols[t]);
+      struct node_args {
+        int64_t rows[14], cols[14];
+        mat X[14];
+        char* buf[14];
+        fxop op[14];
+        mat P[7], qc[4];
+      };
+      auto na = std::make_shared<node_args>();
+      std::copy(rows, rows + 14, na->rows);
+      std::copy(cols, cols + 14, na->cols);
+      std::copy(X, X + 14, na->X);
+      std::copy(buf, buf + 14, na->buf);
+      std::copy(op, op + 14, na->op);
+      std::copy(P, P + 7, na->P);
+      na->qc[0] = C11, na->qc[1] = C12, na->qc[2] = C21, na->qc[3] = C22;
+      DDG_CUDA(issue(c, [=] {
+        fxop out[14];
+        return launch_fx_convert(L, 14, na->rows, na->cols, na->X, na->buf, out, s);
+      }));
+      DDG_CUDA(issue(c, [=] { return launch_block_fxc(L, h, k, w, &na->op[0], &na->op[7], na->P, 7, MODE_SET, s); }));
+      DDG_CUDA(issue(c, [=] {
+        return launch_pass(L, win ? PASS_WINOGRAD_C : PASS_STRASSEN_C, h, w, na->P, 7, na->qc, 4, mode, s);
+      }));
     }
     return DDG_OK;
   }
@@ -218,7 +270,12 @@ static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, c
   };
   const bool fork = depth == 0 && c.nstreams == 7;
   if (fork) {
+    // Each branch's launches are collected first and then issued
+    // round-robin over the seven streams: issued branch after branch, a deep
+    // recursion fills one stream's queue and blocks the host before the
+    // later branches have started.
     cudaEvent_t ev_fork = nullptr, ev_join[7] = {nullptr};
+    std::vector<std::function<cudaError_t()>> branch[7];
     if (!c.dry) {
       DDG_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
       DDG_CUDA(cudaEventRecord(ev_fork, s));
@@ -226,10 +283,22 @@ static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, c
     for (int i = 0; i < 7; ++i) {
       cudaStream_t cs = c.dry ? s : c.pool[i];
       if (!c.dry) DDG_CUDA(cudaStreamWaitEvent(cs, ev_fork, 0));
-      DDG_TRY(child(i, cs, 1 + i, 0));
+      c.q = c.dry ? nullptr : &branch[i];
+      const ddg_status st = child(i, cs, 1 + i, 0);
+      c.q = nullptr;
+      DDG_TRY(st);
+    }
+    if (!c.dry) {
+      size_t most = 0;
+      for (int i = 0; i < 7; ++i) most = std::max(most, branch[i].size());
+      for (size_t j = 0; j < most; ++j)
+        for (int i = 0; i < 7; ++i)
+          if (j < branch[i].size()) DDG_CUDA(branch[i][j]());
+    }
+    for (int i = 0; i < 7; ++i) {
       if (!c.dry) {
         DDG_CUDA(cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming));
-        DDG_CUDA(cudaEventRecord(ev_join[i], cs));
+        DDG_CUDA(cudaEventRecord(ev_join[i], c.pool[i]));
         DDG_CUDA(cudaStreamWaitEvent(s, ev_join[i], 0));
       }
     }
@@ -242,7 +311,10 @@ static ddg_status level(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, c
   }
   if (!c.dry) {
     const mat qc[4] = {C11, C12, C21, C22};
-    DDG_CUDA(launch_pass(c.L, win ? PASS_WINOGRAD_C : PASS_STRASSEN_C, h, w, P, 7, qc, 4, mode, s));
+    const mat pp[7] = {P[0], P[1], P[2], P[3], P[4], P[5], P[6]};
+    DDG_CUDA(issue(c, [=] {
+      return launch_pass(L, win ? PASS_WINOGRAD_C : PASS_STRASSEN_C, h, w, pp, 7, qc, 4, mode, s);
+    }));
   }
   return DDG_OK;
 }
