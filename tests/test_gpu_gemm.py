@@ -352,3 +352,37 @@ def test_benchmark_workload_sampled(name):
     # far inside the bound: a wrong quadrant formula is O(1)
     scale = absprod(A, B, rows, cols)
     assert np.all(np.abs(err) <= (1e-26 if w.limbs == 2 else 1e-58) * scale)
+
+
+@pytest.mark.parametrize("algo", ["strassen", "winograd"])
+def test_deep_recursion_streams_same_bits(algo):
+    """Five levels with odd sizes on the way (cutoff 8: 7^5 leaves and their
+    peeled edges, ~25,000 launches spread over the seven branches and issued
+    round-robin): the same bits as the one-stream schedule and within the
+    bound."""
+    A = I.uniform(150, 146, 2, seed=20)
+    B = I.uniform(146, 154, 2, seed=21)
+    c7 = run(A, B, algo=algo, cutoff=8, streams=7)
+    c1 = run(A, B, algo=algo, cutoff=8, streams=1)
+    assert np.array_equal(c7.view(np.uint64), c1.view(np.uint64))
+    rows, cols = sample_entries(150, 154, 40, seed=22)
+    err = O.gemm_error(A, B, c7, rows=rows, cols=cols)
+    assert np.all(np.abs(err) <= normwise_bound(146, 2, algo) * absprod(A, B, rows, cols))
+
+
+@pytest.mark.parametrize("algo", ["block", "strassen", "winograd", "ozaki", "ozaki2"])
+def test_empty_dimensions(algo):
+    """m = 0 or n = 0: nothing is touched; l = 0: C := 0 in set mode, C
+    unchanged when adding or subtracting."""
+    import paper_1510_08642_gb300 as P
+    for m, l, n in ((0, 5, 7), (5, 7, 0), (5, 0, 7)):
+        A = to_dev(np.zeros((2, m, l)))
+        B = to_dev(np.zeros((2, l, n)))
+        for mode in ("set", "add", "sub"):
+            C0 = I.uniform(m, n, 2, seed=23)
+            dC = to_dev(C0)
+            P.gemm(A, B, dC, algo=algo, cutoff=16, mode=mode)
+            torch.cuda.synchronize()
+            got = to_host(dC)
+            want = np.zeros_like(C0) if (mode == "set" and l == 0) else C0
+            assert np.array_equal(got, want), (m, l, n, mode)
