@@ -45,6 +45,13 @@ INT8_MMA_PEAK = 1.50e14           # mma.sync m16n8k32 s8 ops/s, measured by the 
 HBM_GBS = 6790.7                  # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
 ISSUE_PER_CLK_PER_SM = 4 * 32     # 4 schedulers x one warp instruction (32 lanes) per clock
 ISSUE_PEAK = SM_COUNT * ISSUE_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # thread instructions per second
+IMAD_PER_CLK_PER_SM = 64          # measured: IMAD throughput probe (profiles/fp64_int8_peaks.md)
+IMAD_PEAK = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6   # 32-bit integer multiply-adds per second
+# The Block multiply-add's irreducible integer multiplies, counted from the
+# source (fx::mul_top): the partial products a_i b_j with i + j >= D of the
+# W-word operands, each a mad.lo and a madc.hi: DD W = 4, D = 3: 10 partial
+# products, 20 IMAD; QD W = 7, D = 6: 28 partial products, 56 IMAD.
+IMAD_FLOOR_PER_MAC = {2: 20, 4: 56}
 
 
 def parse():
@@ -61,9 +68,17 @@ def parse():
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     p.add_argument("--lu-k", type=int, default=256, help="LU block column width K")
     p.add_argument("--sweep-n", type=int, default=1024, help="lu_alpha_sweep: matrix order")
-    p.add_argument("--requests", type=int, default=120, help="serving: requests per rate point")
+    p.add_argument("--requests", type=int, default=500, help="serving: requests per rate point")
+    p.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 0.9],
+                   help="the bench's serving leg: arrival rates as fractions of the saturation rate")
     p.add_argument("--rates", type=float, nargs="+", default=[0.25, 0.5, 0.75, 0.9, 1.1],
                    help="serving: arrival rates as fractions of the saturation rate")
+    p.add_argument("--record-counts", metavar="CSV", default=None,
+                   help="write the ncu counters of CSV (a --csv --print-units base capture of "
+                        "COUNT_METRICS) for --kernel into profiles/block_fx_counts.json and exit")
+    p.add_argument("--kernel", default=None, help="--record-counts: kernel, e.g. 'block_fxc_kernel<2>'")
+    p.add_argument("--leaf", type=int, default=256, help="--record-counts: leaf order (seven leaves per launch)")
+    p.add_argument("--command", default="", help="--record-counts: the command that made CSV")
     return p.parse_args()
 
 
@@ -227,18 +242,93 @@ def run_reference(args, w):
     return 0
 
 
+# ------------------------------------------------------------ ncu counts --
+# Counters captured per Block leaf-node launch (one pass each is not needed:
+# the capture runs on a small workload, three launches).
+COUNT_METRICS = ("dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum,smsp__inst_executed.sum,"
+                 "sm__inst_executed_pipe_fma.sum,sm__inst_executed_pipe_alu.sum")
+COUNT_SOURCES = ["paper_1510_08642_gb300/csrc/block_fx.cu", "paper_1510_08642_gb300/csrc/fx.cuh",
+                 "paper_1510_08642_gb300/csrc/fx_round.cuh", "paper_1510_08642_gb300/csrc/fx_rescue.cuh",
+                 "paper_1510_08642_gb300/csrc/arith.cuh", "paper_1510_08642_gb300/csrc/kernels.cuh"]
+
+
+def sources_hash(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
+
+def parse_ncu_csv(path, kernel):
+    """Per-launch metric values of the launches of `kernel` in an ncu --csv
+    log (one row per launch and metric), base units."""
+    import csv
+    scale = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "nsecond": 1.0, "ns": 1.0, "usecond": 1e3, "us": 1e3,
+             "msecond": 1e6, "second": 1e9, "inst": 1.0, "kinst": 1e3, "minst": 1e6, "ginst": 1e9, "": 1.0}
+    lines = open(path).read().splitlines()
+    start = next(i for i, ln in enumerate(lines) if ln.startswith('"ID"'))
+    launches = {}
+    for row in csv.DictReader(lines[start:]):
+        name = row["Kernel Name"].replace(" ", "")
+        if kernel.replace(" ", "") not in name:
+            continue
+        v = float(row["Metric Value"].replace(",", "")) * scale[row["Metric Unit"].strip().lower()]
+        launches.setdefault(int(row["ID"]), {})[row["Metric Name"]] = v
+    return [launches[k] for k in sorted(launches)]
+
+
+def record_counts(args):
+    """Turn an ncu capture of Block leaf-node launches into the counts record
+    the bench's roofline uses (per launch: seven leaf products of order
+    --leaf), stamped with the hash of the kernel's current sources."""
+    limbs = 2 if args.kernel.endswith("<2>") else 4
+    runs = parse_ncu_csv(args.record_counts, args.kernel.split("<")[0] + "<" + str(limbs) + ">")
+    if not runs:
+        raise SystemExit(f"no launches of {args.kernel} in {args.record_counts}")
+    macs = 7 * args.leaf ** 3
+    mean = {k: sum(r[k] for r in runs) / len(runs) for k in runs[0]}
+    rec = {
+        "what": f"one launch of the seven {args.leaf}^3 {'DD' if limbs == 2 else 'QD'} Winograd leaf products "
+                f"of a node, on converted operands, ncu",
+        "command": args.command,
+        "launches_read_write_ns_warpinst": [[r["dram__bytes_read.sum"], r["dram__bytes_write.sum"],
+                                             r["gpu__time_duration.sum"], r["smsp__inst_executed.sum"]]
+                                            for r in runs],
+        "macs_per_launch": macs,
+        "inst_per_mac": round(mean["smsp__inst_executed.sum"] * 32 / macs, 3),
+        "fma_pipe_per_mac": round(mean.get("sm__inst_executed_pipe_fma.sum", 0.0) * 32 / macs, 3),
+        "alu_pipe_per_mac": round(mean.get("sm__inst_executed_pipe_alu.sum", 0.0) * 32 / macs, 3),
+        "dram_bytes_per_launch": round(mean["dram__bytes_read.sum"] + mean["dram__bytes_write.sum"]),
+        "algorithmic_bytes_per_launch": 7 * 3 * args.leaf ** 2 * 8 * limbs,
+        "dram_note": "DRAM bytes per launch (seven leaves): the 14 converted leaf operands read once; the "
+                     "seven C leaves are still in L2 when the launch ends; algorithmic = A, B, C of the seven "
+                     "products as DD / QD",
+        "sources": COUNT_SOURCES,
+        "sources_sha256": sources_hash(COUNT_SOURCES),
+    }
+    path = os.path.join(ROOT, "profiles", "block_fx_counts.json")
+    try:
+        allrec = json.load(open(path))
+    except (OSError, ValueError):
+        allrec = {}
+    allrec[args.kernel] = rec
+    with open(path, "w") as f:
+        json.dump(allrec, f, indent=1)
+        f.write("\n")
+    print(json.dumps({args.kernel: {k: rec[k] for k in ("inst_per_mac", "fma_pipe_per_mac", "alu_pipe_per_mac",
+                                                        "dram_bytes_per_launch")}}))
+    return 0
+
+
 # ----------------------------------------------------------------- GPU leg --
 def profile_record(kernel: str):
     """The committed ncu counters of a Block leaf launch (profiles/block_fx_counts.json),
     or None when the kernel's sources changed since they were taken."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "block_fx_counts.json")
     try:
         rec = json.load(open(path))[kernel]
-        h = hashlib.sha256()
-        for f in rec["sources"]:
-            h.update(open(os.path.join(ROOT, f), "rb").read())
-        if h.hexdigest() != rec["sources_sha256"]:
+        if sources_hash(rec["sources"]) != rec["sources_sha256"]:
             return None
         return rec
     except (OSError, KeyError, ValueError):
@@ -269,21 +359,31 @@ def roofline_of(prof, limbs):
     # operands converted once per product (kind 5 launches) or per staged tile
     kernel = f"block_fxc_kernel<{limbs}>" if prof.get("convert", {}).get("launches") else f"block_fx_kernel<{limbs}>"
     rec = profile_record(kernel)
+    # algorithmic: the multiply-adds' irreducible IMAD count against the IMAD
+    # pipe (64 per clock per SM); independent of how many other instructions
+    # the kernel issues
+    floor = IMAD_FLOOR_PER_MAC[limbs]
+    achieved = macs_per_s * floor
     out = {"bound": "alu", "kernel": f"{kernel} (multiply-add on the integer pipe, no FP64)",
-           "peak": ISSUE_PEAK / 1e12, "unit": "T instr/s",
-           "peak_source": f"derived: {SM_COUNT} SMs x 4 schedulers x 32 lanes (one warp instruction "
-                          f"per scheduler per clock) x {SM_MAX_MHZ:.0f} MHz",
+           "achieved": achieved / 1e12, "peak": IMAD_PEAK / 1e12, "unit": "T IMAD/s",
+           "frac": achieved / IMAD_PEAK,
+           "peak_source": f"derived: {SM_COUNT} SMs x {IMAD_PER_CLK_PER_SM} IMAD per clock per SM (measured "
+                          f"by the IMAD throughput probe) x {SM_MAX_MHZ:.0f} MHz",
+           "algorithmic": f"{floor} IMAD per {'DD' if limbs == 2 else 'QD'} multiply-add (the partial products "
+                          f"of fx::mul_top, mad.lo + madc.hi each) x multiply-adds per busy second",
            "macs_per_s": macs_per_s, "launches": int(b["launches"]), "avg_launch_ms": avg_ms,
            "busy_ms": b["busy_ms"], "sum_launch_ms": b["sum_ms"]}
     if rec is None:
-        out.update({"achieved": None, "frac": None, "traffic": None,
-                    "note": "kernel sources changed since the committed ncu counts"})
+        out.update({"traffic": None, "note": "kernel sources changed since the committed ncu counts"})
         return out
-    achieved = macs_per_s * rec["inst_per_mac"]
-    out.update({"achieved": achieved / 1e12, "frac": achieved / ISSUE_PEAK,
-                "inst_per_mac": rec["inst_per_mac"],
-                "traffic": rec.get("dram_bytes_per_launch"),
+    issued = macs_per_s * rec["inst_per_mac"]
+    out.update({"traffic": rec.get("dram_bytes_per_launch"),
                 "traffic_note": rec.get("dram_note"),
+                "issue": {"inst_per_mac": rec["inst_per_mac"], "achieved": issued / 1e12,
+                          "peak": ISSUE_PEAK / 1e12, "unit": "T thread-instr/s", "frac": issued / ISSUE_PEAK,
+                          "note": "issue slots used (grows with extra instructions; not algorithmic)"},
+                "fma_pipe_per_mac": rec.get("fma_pipe_per_mac"),
+                "alu_pipe_per_mac": rec.get("alu_pipe_per_mac"),
                 "counts_source": "profiles/block_fx_counts.json (ncu, same sources)"})
     return out
 
@@ -321,6 +421,14 @@ def time_gpu(P, torch, w, dA, dB, dC, cutoff, steps, warmup, stream, dist=None, 
             torch.cuda.synchronize()
             prof = capi.ddg_profile_end()
         prof["steps"] = 1
+        if w.algo in ("winograd", "strassen"):
+            # the quadrant passes timed alone: one more step with the seven
+            # sub-products in order on one stream, so that no pass shares the
+            # GPU with a leaf product of another stream
+            capi.ddg_profile_begin()
+            P.gemm(dA, dB, dC, streams=1, **kw)
+            torch.cuda.synchronize()
+            prof["pass_isolated"] = capi.ddg_profile_end()["pass"]
     return ms, prof, launches
 
 
@@ -387,7 +495,7 @@ def time_lu(P, torch, w, device, stream, K):
     ones[0] = 1.0
     b0 = P.gemm(A0, ones, algo="block")
     times = []
-    for it in range(2):  # one warm-up, one timed
+    for it in range(4):  # one warm-up, three timed (median reported)
         A = A0.clone()
         b = b0.clone()
         torch.cuda.synchronize()
@@ -399,11 +507,15 @@ def time_lu(P, torch, w, device, stream, K):
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-    ms = times[-1]
+    ms = sorted(times[1:])[len(times[1:]) // 2]
     err = float((b[0] - 1.0 + b[1:].sum(dim=0)).abs().max().item())
-    return {"value": (2.0 * n ** 3 / 3.0) / (ms * 1e-3) / 1e9, "unit": "G 2mnl/s (2n^3/3 per solve)",
-            "ms": ms, "K": K, "cutoff": w.cutoff, "pivot": "partial", "steps": 1, "warmup": 1,
-            "max_abs_err_x_minus_1": err}
+    rows = sample_rows(n, 24, seed=7)
+    chk = {"name": w.name, "kind": "lu", "limbs": w.limbs, "n": n,
+           "A_rows": A0[:, rows, :].cpu().numpy(), "b_rows": b0[:, rows, :].cpu().numpy(),
+           "x": b.cpu().numpy(), "normA_inf": float(A0[0].abs().sum(dim=1).max().item())}
+    return ({"value": (2.0 * n ** 3 / 3.0) / (ms * 1e-3) / 1e9, "unit": "G 2mnl/s (2n^3/3 per solve)",
+             "ms": ms, "K": K, "cutoff": w.cutoff, "pivot": "partial", "steps": len(times) - 1, "warmup": 1,
+             "max_abs_err_x_minus_1": err}, chk)
 
 
 def time_batched(P, torch, device, stream, count=1000, reps=3):
@@ -448,6 +560,101 @@ def time_batched(P, torch, device, stream, count=1000, reps=3):
             "launches_per_run": st["launches_per_run"], "leaf_tiles": st["leaf_tiles"],
             "workspace_bytes": st["workspace_bytes"], "graph": True, "steps": reps, "warmup": 1,
             "tuning_table": os.path.exists(tuner.path)}
+
+
+def sample_rows(n, count, seed):
+    """`count` distinct sampled indices in [0, n), always with 0 and n - 1."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    idx = set(int(x) for x in rng.choice(n, size=min(n, count), replace=False))
+    idx |= {0, n - 1}
+    return np.array(sorted(idx), dtype=np.int64)
+
+
+def sample_for_check(name, hA, hB, dC, torch):
+    """Host copies of what the oracle needs to check 8 x 8 sampled entries of
+    the product C = A B: those rows of A, columns of B and entries of C."""
+    import numpy as np
+    n = hA.shape[1]
+    rows, cols = sample_rows(n, 6, seed=1), sample_rows(n, 6, seed=2)
+    r_t = torch.as_tensor(rows, device=dC.device)
+    c_t = torch.as_tensor(cols, device=dC.device)
+    C = dC.index_select(1, r_t).index_select(2, c_t).cpu().numpy()
+    return {"name": name, "kind": "gemm", "limbs": hA.shape[0], "n": n,
+            "A_rows": np.ascontiguousarray(hA[:, rows, :]), "B_cols": np.ascontiguousarray(hB[:, :, cols]),
+            "C": C, "normA": float(np.linalg.norm(hA[0])), "normB": float(np.linalg.norm(hB[0]))}
+
+
+def cpu_oracle_check(checks):
+    """The oracle's exact error of each sampled result (CPU leg, outside any
+    timed region): for products, the normwise error estimated from the
+    sampled entries (RMS error x sqrt(m n) / (||A||_F ||B||_F)) and the
+    largest elementwise error over sum_k |a_ik b_kj| in units of u^2
+    (2^-106 DD, 2^-212 QD); for LU solves, the exact residual of sampled
+    rows over ||A||_inf ||x||_inf and the bound n 2^-100 (QD: n 2^-200)."""
+    import numpy as np
+
+    import oracle as O
+    out = {}
+    for c in checks:
+        if c["kind"] == "gemm":
+            A, B, C = c["A_rows"], c["B_cols"], c["C"]
+            err = O.gemm_error(A, B, C)
+            n = c["n"]
+            nw = float(np.sqrt(np.mean(err ** 2)) * n / (c["normA"] * c["normB"]))
+            u2 = 2.0 ** -106 if c["limbs"] == 2 else 2.0 ** -212
+            scale = np.abs(A[0]) @ np.abs(B[0])
+            ew = float(np.max(np.abs(err) / (scale * u2)))
+            out[c["name"]] = {"sampled_entries": int(err.size), "normwise_est": nw,
+                              "normwise_est_log2": float(np.log2(nw)) if nw > 0 else None,
+                              "max_elementwise_over_u2": ew, "max_abs_err": float(np.abs(err).max())}
+        else:
+            A, b, x = c["A_rows"], c["b_rows"], c["x"]
+            r = O.gemm_error(A, x, b)  # A x - b for the sampled rows, exact
+            rel = float(np.abs(r).max() / (c["normA_inf"] * np.abs(x[0]).max()))
+            bound = c["n"] * (2.0 ** -100 if c["limbs"] == 2 else 2.0 ** -200)
+            out[c["name"]] = {"sampled_rows": int(A.shape[1]), "residual_rel": rel, "bound": bound,
+                              "within_bound": rel <= bound}
+    return out
+
+
+def cutoff_sweep(P, torch, device, stream, orders=(1024, 2048, 4096), cutoffs=(64, 128, 256, 512, 1024)):
+    """The Winograd cutoff sweep of the square workloads (Section 3's n_min):
+    G 2mnl/s, DD and QD, 1 warm-up + 3 timed steps per point."""
+    from paper_1510_08642_gb300 import inputs as I
+    out = {}
+    for limbs in (2, 4):
+        key = "dd" if limbs == 2 else "qd"
+        out[key] = {}
+        for n in orders:
+            XA = torch.from_numpy(I.uniform(n, n, limbs, seed=130 + n)).to(device)
+            XB = torch.from_numpy(I.uniform(n, n, limbs, seed=131 + n)).to(device)
+            XC = torch.empty((limbs, n, n), dtype=torch.float64, device=device)
+            row = {}
+            for cut in cutoffs:
+                xw = WL.Workload(f"sweep_{key}_{n}_{cut}", limbs, n, "winograd", cut, 0, 0)
+                ms, _, _ = time_gpu(P, torch, xw, XA, XB, XC, cut, 3, 1, stream, profile=False)
+                row[str(cut)] = round(2.0 * n ** 3 / (ms * 1e-3) / 1e9, 1)
+            out[key][str(n)] = row
+            del XA, XB, XC
+            torch.cuda.empty_cache()
+    out["unit"] = UNIT
+    return out
+
+
+def time_serving(args):
+    """The serving leg: saturation rate and p50 / p99 latency per request
+    type at two arrival rates (fractions of saturation), args.requests
+    requests per point (Poisson arrivals, 50% DD GEMM n log-uniform in
+    [256, 2048], 50% DD LU solves n in {1024, 2048, 4096})."""
+    from paper_1510_08642_gb300 import serving as S
+    srv = S.Server(slots=4, hbm_budget=96 << 30, max_batch=32, gemm_cutoff=512, lu_K=256, lu_cutoff=512)
+    t0 = time.perf_counter()
+    res = S.sweep(rates=tuple(args.serve_rates), count=args.requests, seed=3, server=srv)
+    srv.close()
+    res["requests_per_point"] = args.requests
+    res["wall_s"] = time.perf_counter() - t0
+    return res
 
 
 def run_ours(args, w):
@@ -503,43 +710,64 @@ def run_ours(args, w):
         "value": 2.0 * FP64_PEAK / PINNED_MAC_OPS[limbs] / 1e9,
         "frac": value / world / (2.0 * FP64_PEAK / PINNED_MAC_OPS[limbs] / 1e9),
         "note": "2 x FP64 peak / FP64 instructions of the pinned multiply-add (DD 27, QD 218)"}
-    passes = prof["pass"]
+    passes = prof.get("pass_isolated") or prof["pass"]
     if passes["launches"]:
-        line["passes"] = {"launches": int(passes["launches"]), "busy_ms": passes["busy_ms"] / prof["steps"],
-                          "GB_per_s": passes["bytes"] / (passes["busy_ms"] * 1e-3) / 1e9,
-                          "hbm_frac": passes["bytes"] / (passes["busy_ms"] * 1e-3) / 1e9 / HBM_GBS,
-                          "sums_per_s": passes["ops"] / (passes["busy_ms"] * 1e-3)}
+        line["passes"] = {"launches": int(passes["launches"]), "sum_ms": passes["sum_ms"],
+                          "GB_per_s": passes["bytes"] / (passes["sum_ms"] * 1e-3) / 1e9,
+                          "hbm_frac": passes["bytes"] / (passes["sum_ms"] * 1e-3) / 1e9 / HBM_GBS,
+                          "sums_per_s": passes["ops"] / (passes["sum_ms"] * 1e-3),
+                          "measured": "algorithmic bytes of the fused quadrant passes over the sum of their "
+                                      "launch durations, in a profiled step with the sub-products on one "
+                                      "stream (no pass overlaps another kernel)"}
     conv = prof["convert"]
     if conv["launches"]:
         line["conversions"] = {"launches": int(conv["launches"]), "busy_ms": conv["busy_ms"] / prof["steps"],
                                "GB_per_s": conv["bytes"] / (conv["busy_ms"] * 1e-3) / 1e9,
                                "hbm_frac": conv["bytes"] / (conv["busy_ms"] * 1e-3) / 1e9 / HBM_GBS,
                                "elements_per_s": conv["ops"] / (conv["busy_ms"] * 1e-3)}
-    del dA, dB, dC, hA, hB, hC
+    dC_keep = dC
+    del dA, dB, hA, hB, hC
     torch.cuda.empty_cache()
 
-    # -------- extras (rank 0 of a single-GPU run only; 1 warm-up, 1 timed)
+    # -------- extras (single-GPU run only; 1 warm-up, 3 timed steps each)
+    checks = []
     if args.extras == "all" and world == 1 and w.name == WL.DD_WINOGRAD_4096.name:
         extras = {}
-        for xw in (WL.DD_BLOCK_4096, WL.QD_WINOGRAD_4096, WL.QD_BLOCK_4096, WL.DD_OZAKI_4096_S16,
-                   WL.DD_OZAKI_4096_S13, WL.DD_WINOGRAD_8192, WL.DD_OZAKI_8192_S16,
-                   WL.QD_OZAKI_4096_S32, WL.DD_OZAKI2_4096_N32, WL.DD_OZAKI2_8192_N32):
-            XA = torch.from_numpy(I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_a)).to(device)
-            XB = torch.from_numpy(I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_b)).to(device)
+        for xw in (WL.DD_BLOCK_4096, WL.QD_WINOGRAD_4096, WL.QD_BLOCK_4096, WL.DD_WINOGRAD_3000,
+                   WL.QD_WINOGRAD_3000, WL.DD_OZAKI_4096_S16, WL.DD_OZAKI_4096_S13, WL.DD_WINOGRAD_8192,
+                   WL.DD_OZAKI_8192_S16, WL.QD_OZAKI_4096_S32, WL.DD_OZAKI2_4096_N32, WL.DD_OZAKI2_8192_N32):
+            hXA = I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_a)
+            hXB = I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_b)
+            XA, XB = torch.from_numpy(hXA).to(device), torch.from_numpy(hXB).to(device)
             XC = torch.empty((xw.limbs, xw.n, xw.n), dtype=torch.float64, device=device)
-            xms, xprof, _ = time_gpu(P, torch, xw, XA, XB, XC, xw.cutoff, 1, 1, stream)
+            xms, xprof, _ = time_gpu(P, torch, xw, XA, XB, XC, xw.cutoff, 3, 1, stream)
             extras[xw.name] = {"value": 2.0 * xw.macs / (xms * 1e-3) / 1e9, "unit": UNIT, "ms": xms,
-                               "roofline": roofline_of(xprof, xw.limbs), "steps": 1, "warmup": 1}
-            del XA, XB, XC
+                               "roofline": roofline_of(xprof, xw.limbs), "steps": 3, "warmup": 1}
+            checks.append(sample_for_check(xw.name, hXA, hXB, XC, torch))
+            del XA, XB, XC, hXA, hXB
             torch.cuda.empty_cache()
-        extras[WL.DD_LU_4096.name] = time_lu(P, torch, WL.DD_LU_4096, device, stream, K=256)
-        extras[WL.DD_LU_4096_OZ2.name] = time_lu(P, torch, WL.DD_LU_4096_OZ2, device, stream, K=256)
-        extras[WL.QD_LU_2048.name] = time_lu(P, torch, WL.QD_LU_2048, device, stream, K=256)
+        extras["cutoff_sweep"] = cutoff_sweep(P, torch, device, stream)
+        for lw in (WL.DD_LU_4096, WL.DD_LU_4096_OZ2, WL.QD_LU_2048):
+            extras[lw.name], chk = time_lu(P, torch, lw, device, stream, K=256)
+            checks.append(chk)
         extras["batched_1000_mixed"] = time_batched(P, torch, device, stream)
+        extras["serving"] = time_serving(args)
         line["extras"] = extras
+    if checks:
+        checks.insert(0, sample_for_check(w.name, A, B, dC_keep, torch))
 
+    del dC_keep
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        # the CPU leg: the oracle timed on host cores (DD, and QD on the QD
+        # workload), then the oracle's exact error of every sampled result
         line["cpu_baseline"] = cpu_oracle_rate(w, args.cpu_seconds)
+        line["cpu_baseline"]["qd"] = cpu_oracle_rate(WL.QD_WINOGRAD_4096, args.cpu_seconds / 2)
+        if checks:
+            errs = cpu_oracle_check(checks)
+            line["error_vs_oracle"] = errs[w.name]
+            for name, e in errs.items():
+                if name in line.get("extras", {}):
+                    line["extras"][name]["error_vs_oracle"] = e
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -572,7 +800,7 @@ def run_lu_only(args, w):
     from paper_1510_08642_gb300 import capi
     capi.load()
     stream = torch.cuda.current_stream(device)
-    r = time_lu(P, torch, w, device, stream, K=args.lu_k)
+    r, _ = time_lu(P, torch, w, device, stream, K=args.lu_k)
     print(json.dumps({"workload": w.name, **r}), flush=True)
     return 0
 
@@ -623,6 +851,8 @@ def run_lu_alpha_sweep(args):
 
 def main():
     args = parse()
+    if args.record_counts:
+        return record_counts(args)
     if args.workload == "lu_alpha_sweep":
         return run_lu_alpha_sweep(args)
     w = workload_by_name(args.workload)

@@ -36,6 +36,10 @@
  *     zeros for mode DDG_SET). Negative sizes, ld smaller than the column
  *     count, null planes of a non-empty matrix and C overlapping A or B are
  *     DDG_EINVAL.
+ *   - The library keeps per-device state for the life of the process (its
+ *     forked streams, its workspace pool, the address of the fixed array of
+ *     dd_gemm_noalloc), made in the device's primary context: do not call
+ *     it again in a process after cudaDeviceReset.
  */
 #ifndef DDGEMM_H
 #define DDGEMM_H
@@ -138,13 +142,20 @@ void ddg_opts_default(ddg_opts* opts);
  * dd_gemm: C (mode) A B in double-double, A m x l, B l x n, C m x n.
  * opts NULL = defaults. Accuracy: DDG_SIMPLE follows the pinned sequence
  * exactly; DDG_BLOCK stays within |C - C^| <= (2 l + 4) 2^-106 |A||B|
- * elementwise; Strassen/Winograd within the normwise bound
- * 8 l^log2(12) 2^-104 ||A|| ||B||.
+ * elementwise for every input, like the DD arithmetic of Section 2's Block
+ * (each output's fixed-point window is set from the largest exponents of
+ * its row of A and column of B; an output whose window sum keeps fewer
+ * than 106 significant bits, as when those maxima sit at different k far
+ * apart, is recomputed with the window at its own largest term);
+ * Strassen/Winograd within the normwise bound 8 l^log2(12) 2^-104
+ * ||A|| ||B|| (these recursions are only normwise stable).
  */
 ddg_status dd_gemm(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, dd_mat C, int32_t mode,
                    const ddg_opts* opts, void* stream);
 
-/* qd_gemm: as dd_gemm for quad-double (2^-208 in place of 2^-104). */
+/* qd_gemm: as dd_gemm for quad-double: Block within (2 l + 4) 2^-209 |A||B|
+ * elementwise (outputs keeping fewer than 212 window bits recomputed),
+ * Strassen / Winograd within 8 l^log2(12) 2^-208 ||A|| ||B||. */
 ddg_status qd_gemm(int64_t m, int64_t l, int64_t n, qd_mat A, qd_mat B, qd_mat C, int32_t mode,
                    const ddg_opts* opts, void* stream);
 

@@ -24,11 +24,15 @@
 // Error per term: the dropped partial products, < 2^-123 (DD) / 2^-219
 // (QD) of |a_ik b_kj|, and the truncation below the window, 2^-159 (DD) /
 // 2^-255 (QD) of the largest product of row i and column j; the sum in the
-// window is exact for l < 2^31. One final rounding to DD / QD.
+// window is exact for l < 2^31. An output whose window sum keeps fewer than
+// 53 L significant bits is recomputed with the window at its own largest
+// term (fx_rescue.cuh), so every output is accurate relative to its own
+// sum_k |a_ik b_kj|. One final rounding to DD / QD.
 #include <algorithm>
 
 #include "arith.cuh"
 #include "fx.cuh"
+#include "fx_rescue.cuh"
 #include "fx_round.cuh"
 #include "kernels.cuh"
 
@@ -217,20 +221,37 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
   }
 
   using N = num<L>;
+  auto finish = [&](int64_t gi, int64_t gj, uint32_t(&w)[NW], int lsb) {
+    typename N::T v = window_round<L, NW>(w, lsb);
+    const int64_t off = gi * C.ld + gj;
+    if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
+    else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));
+    N::store(C.p, off, v);
+  };
+  uint32_t rescue = 0u;  // outputs left for the rescue, bit r TN + c
 #pragma unroll
   for (int r = 0; r < TM; ++r)
 #pragma unroll
     for (int c = 0; c < TN; ++c) {
       const int64_t gi = i0 + ty + r * NY, gj = j0 + tx + c * NX;
       if (gi < m && gj < n) {
-        const int lsb = row_f[ty + r * NY] + col_f[tx + c * NX] + P::LSB0;
-        typename N::T v = window_round<L, NW>(acc[r][c], lsb);
-        const int64_t off = gi * C.ld + gj;
-        if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
-        else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));
-        N::store(C.p, off, v);
+        if (fx::acc_mag_below<NW>(acc[r][c], fxkeep<L>::bits)) {
+          rescue |= 1u << (r * TN + c);
+          continue;
+        }
+        finish(gi, gj, acc[r][c], row_f[ty + r * NY] + col_f[tx + c * NX] + P::LSB0);
       }
     }
+  // Outputs whose row / column window kept fewer than 53 L significant bits,
+  // recomputed with the window at their own largest term (fx_rescue.cuh);
+  // rare, and run when no accumulator is live any more.
+#pragma unroll 1
+  for (int b = 0; b < TM * TN; ++b) {
+    if (!((rescue >> b) & 1u)) continue;
+    const int64_t gi = i0 + ty + (b / TN) * NY, gj = j0 + tx + (b % TN) * NX;
+    fxacc<L> x = fx_rescue<L, PRE>(l, A, B, Ax, Bx, gi, gj);
+    finish(gi, gj, x.w, x.lsb);
+  }
 }
 
 template <int L>

@@ -228,6 +228,25 @@ __host__ __device__ __forceinline__ uint32_t acc_abs(uint32_t (&A)[NW]) {
   return neg;
 }
 
+// Whether the two's-complement NW-word A has magnitude below 2^bits
+// (0 < bits < 32 NW); A is not changed.
+template <int NW>
+__host__ __device__ __forceinline__ bool acc_mag_below(const uint32_t (&A)[NW], int bits) {
+  const uint32_t m = 0u - (A[NW - 1] >> 31);
+  uint64_t c = m & 1u;
+  bool below = true;
+  const int w = bits >> 5, r = bits & 31;
+#pragma unroll
+  for (int t = 0; t < NW; ++t) {
+    const uint64_t v = (uint64_t)(A[t] ^ m) + c;
+    const uint32_t x = (uint32_t)v;
+    c = v >> 32;
+    if (t > w && x != 0u) below = false;
+    if (t == w && (x >> r) != 0u) below = false;
+  }
+  return below;
+}
+
 // B = A shifted up by whole words so that A's highest nonzero word lands in
 // B[NW - 1]; returns the index of that word in A, or -1 if A = 0. A barrel
 // shifter (conditional shifts by 8, 4, 2, 1 words with fixed indices): no

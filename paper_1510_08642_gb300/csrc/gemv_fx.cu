@@ -14,9 +14,13 @@
 //     multiword two's-complement additions; the window has 32 bits of
 //     headroom, enough for l < 2^31 terms in any order);
 //   * lane 0 rounds the window once (window_round) and applies the mode.
+//   * an output whose window sum keeps fewer than 53 L significant bits is
+//     recomputed by the warp with the window at its own largest term
+//     (fx_rescue.cuh), as in the Block kernel.
 // The result is the one the Block kernel's arithmetic defines: every term
 // carries the same truncations, and the window sum is exact, so the order
 // of the terms does not matter.
+#include "fx_rescue.cuh"
 #include "fx_round.cuh"
 #include "kernels.cuh"
 
@@ -76,9 +80,32 @@ __global__ void __launch_bounds__(32 * GV_WARPS) gemv_fx_kernel(int64_t m, int64
     for (int w = 0; w < NW; ++w) o[w] = __shfl_xor_sync(0xffffffffu, acc[w], off);
     fx::acc_add_mask<NW>(acc, o, 0u);
   }
+  // every lane holds the total: a warp-uniform test, and the rescue of
+  // fx_rescue.cuh with the lanes splitting k
+  int lsb = fa + fb + F::LSB0;
+  if (fx::acc_mag_below<NW>(acc, fxkeep<L>::bits)) {
+    int E = -1;
+    for (int64_t k = lane; k < l; k += 32)
+      E = max(E, fx_pair_field<L, false>(A, B, fxop{}, fxop{}, arow + k, k * B.ld + j));
+    E = __reduce_max_sync(0xffffffffu, E);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) acc[w] = 0u;
+    if (E >= 0) {
+      for (int64_t k = lane; k < l; k += 32)
+        fx_pair_place<L, false>(A, B, fxop{}, fxop{}, arow + k, k * B.ld + j, E, acc);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        uint32_t o[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) o[w] = __shfl_xor_sync(0xffffffffu, acc[w], off);
+        fx::acc_add_mask<NW>(acc, o, 0u);
+      }
+      lsb = E + F::LSB0;
+    }
+  }
   if (lane == 0) {
     using N = num<L>;
-    typename N::T v = window_round<L, NW>(acc, fa + fb + F::LSB0);
+    typename N::T v = window_round<L, NW>(acc, lsb);
     const int64_t off = i * C.ld + j;
     if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
     else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));

@@ -35,12 +35,14 @@
 // P = 113 at l = 4096 with 32 INT8 products, where slicing needs 136 for
 // the same precision.
 #include <algorithm>
+#include <cuda_bf16.h>
 #include <cmath>
 #include <cstring>
 #include <string>
 
 #include "arith.cuh"
 #include "fx.cuh"
+#include "crt.cuh"
 #include "kernels.cuh"
 
 namespace ddg {
@@ -51,7 +53,6 @@ constexpr int OBM = 128, OBN = 128, OBK = 64, OST = 3, OROW = OBK + 16;
 constexpr int STAGE_BYTES = (OBM + OBN) * OROW;
 constexpr int OZ_SMEM = OST * STAGE_BYTES;
 constexpr int OZ_MAXS = 40;  // most slices (QD: 32; DD: 18) or CRT moduli (40)
-constexpr int CRT_MAXN = 40;
 constexpr int CRT_NW = 10;   // 320-bit CRT reconstruction word
 constexpr int CRT_PMAX = 120;
 
@@ -165,32 +166,19 @@ __device__ __forceinline__ void oz_digits(const double (&x)[L], int field, int s
   out[0] = (int8_t)(int)(long long)X[0];  // remaining top digit in [-64, 64]
 }
 
-// The CRT moduli: the 40 largest pairwise-coprime integers <= 256, taken
-// greedily from 256 downward.
-__host__ __device__ constexpr int crt_mod(int t) {
-  constexpr int tab[CRT_MAXN] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199,
-                                 197, 193, 191, 181, 179, 173, 167, 163, 157, 151, 149, 139, 137, 131,
-                                 127, 113, 109, 107, 103, 101, 97,  89,  83,  79,  73,  71};
-  return tab[t];
-}
-
-constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
-constexpr bool crt_mods_ok() {
-  for (int a = 0; a < CRT_MAXN; ++a) {
-    if (crt_mod(a) < 2 || crt_mod(a) > 256 || (a > 0 && crt_mod(a) >= crt_mod(a - 1))) return false;
-    for (int b = 0; b < a; ++b)
-      if (gcd_c(crt_mod(a), crt_mod(b)) != 1) return false;
-  }
-  return true;
-}
-static_assert(crt_mods_ok(), "CRT moduli must be pairwise coprime, decreasing, <= 256");
 
 // Residues of the integer round(x 2^(P - e)) modulo m_0 .. m_(N-1), each as
 // an int8 representative (r or r - m_t). |X| < 2^121 is taken as four 32-bit
 // words w_k; X mod m = sum_k (w_k mod m) (2^(32 k) mod m) mod m, with every
 // modulus a compile-time constant (the loop is unrolled), so each reduction
 // is a multiply-high sequence on the integer pipe.
-__device__ __forceinline__ void oz_residues(const double (&x)[2], int field, int N, int P, int8_t* out,
+// A residue or digit stored as an int8 (mma.sync operands) or as a bf16
+// (tcgen05 operands; every integer of magnitude <= 256 is exact in bf16).
+__device__ __forceinline__ void oz_put(int8_t* p, int v) { *p = (int8_t)v; }
+__device__ __forceinline__ void oz_put(__nv_bfloat16* p, int v) { *p = __int2bfloat16_rn(v); }
+
+template <typename T>
+__device__ __forceinline__ void oz_residues(const double (&x)[2], int field, int N, int P, T* out,
                                             int64_t stride) {
   unsigned long long X[2];
   oz_integer<2>(x, field, P, X);
@@ -209,7 +197,7 @@ __device__ __forceinline__ void oz_residues(const double (&x)[2], int field, int
       const uint32_t p64 = (p32 * p32) % m, p96 = (p64 * p32) % m;
       uint32_t r = (w0 % m + (w1 % m) * p32 + (w2 % m) * p64 + (w3 % m) * p96) % m;
       if (neg && r != 0u) r = m - r;
-      out[(int64_t)t * stride] = (int8_t)(r < 128u ? (int)r : (int)r - (int)m);
+      oz_put(out + (int64_t)t * stride, r < 128u ? (int)r : (int)r - (int)m);
     }
   }
 }
@@ -217,14 +205,14 @@ __device__ __forceinline__ void oz_residues(const double (&x)[2], int field, int
 // Slices of A (per row) into As[s][mpad][lpad], of B (per column, stored
 // transposed) into Bs[s][npad][lpad]; padding is zero. With CRT, the N
 // residue planes instead (s = N, T = P).
-template <int L, bool CRT>
+template <int L, bool CRT, typename T = int8_t>
 __global__ void oz_split_a_kernel(int64_t m, int64_t l, mat A, const int* ex, int s, int P, int64_t mpad,
-                                  int64_t lpad, int8_t* As) {
+                                  int64_t lpad, T* As) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = blockIdx.y;
   if (k >= lpad) return;
   const int64_t stride = mpad * lpad;
-  int8_t* out = As + i * lpad + k;
+  T* out = As + i * lpad + k;
   if (i < m && k < l) {
     double x[L];
 #pragma unroll
@@ -232,13 +220,13 @@ __global__ void oz_split_a_kernel(int64_t m, int64_t l, mat A, const int* ex, in
     if constexpr (CRT) oz_residues(x, ex[i], s, P, out, stride);
     else oz_digits<L>(x, ex[i], s, out, stride);
   } else {
-    for (int p = 0; p < s; ++p) out[(int64_t)p * stride] = 0;
+    for (int p = 0; p < s; ++p) oz_put(out + (int64_t)p * stride, 0);
   }
 }
 
-template <int L, bool CRT>
+template <int L, bool CRT, typename T = int8_t>
 __global__ void oz_split_b_kernel(int64_t l, int64_t n, mat B, const int* ex, int s, int P, int64_t npad,
-                                  int64_t lpad, int8_t* Bs) {
+                                  int64_t lpad, T* Bs) {
   // tile: 32 k x 32 j; digits staged in shared memory and written k-contiguous
   __shared__ int8_t t[OZ_MAXS][32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -262,28 +250,10 @@ __global__ void oz_split_b_kernel(int64_t l, int64_t n, mat B, const int* ex, in
   for (int jj = ty; jj < 32; jj += 8) {
     const int64_t j = j0 + jj, k = k0 + tx;
     if (j < npad && k < lpad)
-      for (int p = 0; p < s; ++p) Bs[(int64_t)p * stride + j * lpad + k] = t[p][jj][tx];
+      for (int p = 0; p < s; ++p) oz_put(Bs + (int64_t)p * stride + j * lpad + k, t[p][jj][tx]);
   }
 }
 
-// Reduction constants of each CRT modulus for the GEMM epilogue: for
-// |v| <= 2^30, u = v + bias (bias = m ceil(2^30 / m)) lies in [0, 2^32) and
-// u mod m = u - m q with q = umulhi(u, floor(2^32 / m)) or q + 1. Fixed at
-// compile time (constant memory, no per-call state).
-struct crt_red {
-  uint32_t m[CRT_MAXN], magic[CRT_MAXN], bias[CRT_MAXN];
-};
-constexpr crt_red make_crt_red() {
-  crt_red r{};
-  for (int t = 0; t < CRT_MAXN; ++t) {
-    const uint32_t m = (uint32_t)crt_mod(t);
-    r.m[t] = m;
-    r.magic[t] = (uint32_t)((1ull << 32) / m);
-    r.bias[t] = m * (((1u << 30) + m - 1u) / m);
-  }
-  return r;
-}
-__constant__ crt_red c_crt_red = make_crt_red();
 
 // Slices: D[r - 2] = sum_{p + q = r} alpha^(p) beta^(q) for the diagonal of
 // blockIdx.z (z = 0 is the longest diagonal, r = s + 1, scheduled first).

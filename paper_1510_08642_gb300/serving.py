@@ -20,7 +20,13 @@ requests that arrive over time:
 * completion: a CUDA event per unit of work; latency = completion time on
   the device clock (relative to a reference event) minus arrival time;
 * workspace: the library's temporaries come from its pool, reserved at
-  start-up (ddg_workspace_reserve) so that no request maps memory.
+  start-up (ddg_workspace_reserve) so that no request maps memory;
+* refusal and deadlines: a malformed request (unknown kind, order < 1 or
+  above the server's limit) or one whose footprint can never fit the budget
+  is refused at arrival; a request still queued past its admission deadline
+  (seconds after arrival) is cancelled before anything of it is launched.
+  Work already on the GPU always runs to completion (kernels are not
+  interrupted), so a deadline bounds the wait for admission, not the run.
 
 Every arithmetic step runs in the CUDA library; this module only schedules.
 Operands are generated on the device from a seed per request (uniform
@@ -45,10 +51,14 @@ class Request:
     n: int
     arrival: float       # seconds after the start of the run
     seed: int
+    deadline: float = math.inf  # latest admission, seconds after arrival
     admitted: float = math.nan
     done: float = math.nan
     result: object = None   # device tensor (C, or x for an LU solve)
     info: int = 0           # LU: 0 or 1 + column of a zero pivot
+    status: str = "queued"  # queued, running, ok, refused, timeout
+    error: str = ""         # why a request was refused or cancelled
+    operands: tuple = ()    # with keep_results: (A, B) of a GEMM, (A, b) of a solve
 
     @property
     def latency(self) -> float:
@@ -66,6 +76,27 @@ def footprint(req: Request) -> int:
     if req.kind == "gemm":
         return 3 * n2 + 4 * n2          # A, B, C and Winograd temporaries (< 3.5 n^2 entries)
     return n2 + 2 * req.n * 16 + n2     # A (factored in place), b / x, temporaries of the updates
+
+
+KINDS = ("gemm", "lu")
+
+
+def check_request(req: Request, budget: int, max_n: int) -> str:
+    """Why the server refuses `req` at arrival ("" if it can be served)."""
+    if req.kind not in KINDS:
+        return f"unknown request kind {req.kind!r}"
+    if not isinstance(req.n, (int, np.integer)) or req.n < 1:
+        return f"order must be a positive integer, got {req.n!r}"
+    if req.n > max_n:
+        return f"order {req.n} above the server's limit {max_n}"
+    if footprint(req) > budget:
+        return f"footprint {footprint(req)} B above the HBM budget {budget} B"
+    return ""
+
+
+def expired(req: Request, now: float) -> bool:
+    """Whether a queued request has passed its admission deadline."""
+    return now - req.arrival > req.deadline
 
 
 def make_operands(req: Request, device):
@@ -120,7 +151,7 @@ class Server:
                  lu_slots: int | None = None,
                  gemm_algo: str = "winograd", gemm_cutoff: int = 256, lu_K: int = 256,
                  lu_algo: str = "winograd", lu_cutoff: int = 512, keep_results: bool = False,
-                 workspace_reserve: int = 8 << 30):
+                 workspace_reserve: int = 8 << 30, max_n: int = 16384):
         import torch
         self.torch = torch
         self.device = device or torch.device("cuda", torch.cuda.current_device())
@@ -137,6 +168,7 @@ class Server:
         self.gemm_algo, self.gemm_cutoff = gemm_algo, gemm_cutoff
         self.lu_K, self.lu_algo, self.lu_cutoff = lu_K, lu_algo, lu_cutoff
         self.keep_results = keep_results
+        self.max_n = max_n
         # keep the library's temporaries mapped between requests (the solves
         # synchronise the host, which would otherwise hand the pool back)
         self.dev_index = self.device.index if self.device.index is not None else torch.cuda.current_device()
@@ -164,6 +196,8 @@ class Server:
                 probs.append(problem(A, B, C, algo, self.gemm_cutoff))
                 keep += [A, B]
                 r.result = C
+                if self.keep_results:
+                    r.operands = (A, B)
             batch = Batch(probs, use_graph=False, stream=s)
             batch.run(s)
             batch.close(s)
@@ -180,6 +214,8 @@ class Server:
             ones[0] = 1.0
             from . import gemm
             b = gemm(A, ones, algo="block", stream=s)
+            if self.keep_results:  # the system as posed, before A is factored in place
+                r.operands = (A.clone(), b.clone())
             info = torch.zeros(1, dtype=torch.int64, device=self.device)
             ipiv = getrf(A, K=self.lu_K, pivot=True, algo=self.lu_algo, cutoff=self.lu_cutoff,
                          info=info, stream=s)
@@ -191,9 +227,13 @@ class Server:
 
     # -- loop ---------------------------------------------------------------
     def run(self, requests, poll_s: float = 2e-4):
-        """Serve `requests` (arrival times relative to the start); returns stats."""
+        """Serve `requests` (arrival times relative to the start); returns stats.
+        Refused and cancelled requests end with status "refused" / "timeout"
+        and their reason in `error`; the others with status "ok"."""
         torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival)
+        for r in requests:
+            r.status, r.error = "queued", ""
         queue, inflight = [], []
         free_lu = list(range(self.lu_slots))
         free_gemm = list(range(self.lu_slots, len(self.streams)))
@@ -210,8 +250,19 @@ class Server:
         while done < len(requests):
             now = time.perf_counter() - t0
             while ip < len(pending) and pending[ip].arrival <= now:
-                queue.append(pending[ip])
+                r = pending[ip]
                 ip += 1
+                why = check_request(r, self.budget, self.max_n)
+                if why:
+                    r.status, r.error, r.done = "refused", why, now
+                    done += 1
+                else:
+                    queue.append(r)
+            for r in [r for r in queue if expired(r, now)]:
+                queue.remove(r)
+                r.status, r.done = "timeout", now
+                r.error = f"not admitted within {r.deadline} s of arrival"
+                done += 1
             # completions
             still = []
             for u in inflight:
@@ -219,6 +270,7 @@ class Server:
                     t_dev = ref.elapsed_time(u.event) * 1e-3
                     for r in u.reqs:
                         r.done = t_dev
+                        r.status = "ok"
                         if u.kind == "lu":
                             r.info = int(u.keep[2].item())
                         if not self.keep_results:
@@ -245,6 +297,7 @@ class Server:
                 for r in take:
                     queue.remove(r)
                     r.admitted = time.perf_counter() - t0
+                    r.status = "running"
                 u = self._start_gemms(take, free_gemm.pop(0))
                 inflight.append(u)
                 used += u.bytes
@@ -256,6 +309,7 @@ class Server:
                     break
                 queue.remove(lu)
                 lu.admitted = time.perf_counter() - t0
+                lu.status = "running"
                 u = self._start_lu(lu, free_lu.pop(0))
                 inflight.append(u)
                 used += u.bytes
@@ -268,9 +322,11 @@ class Server:
 
 
 def stats(requests) -> dict:
+    """p50 / p99 latency and throughput of the served requests per kind, and
+    the counts of refused and cancelled ones."""
     out = {}
     for kind in ("gemm", "lu", "all"):
-        rs = [r for r in requests if kind == "all" or r.kind == kind]
+        rs = [r for r in requests if (kind == "all" or r.kind == kind) and r.status not in ("refused", "timeout")]
         if not rs:
             continue
         lat = np.array([r.latency for r in rs]) * 1e3
@@ -279,6 +335,8 @@ def stats(requests) -> dict:
                      "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                      "throughput_rps": len(rs) / span if span > 0 else float("inf"),
                      "work_G2mnl_per_s": sum(r.work for r in rs) / span / 1e9 if span > 0 else float("inf")}
+    out["refused"] = sum(r.status == "refused" for r in requests)
+    out["timeout"] = sum(r.status == "timeout" for r in requests)
     return out
 
 

@@ -58,3 +58,6 @@ DD_OZAKI2_8192_N32 = Workload("dd_ozaki2_n8192_n32", 2, 8192, "ozaki2", 512, 109
 QD_LU_2048 = Workload("qd_lu_n2048", 4, 2048, "winograd", 256, 115, 0)
 QD_LU_1024 = Workload("qd_lu_n1024", 4, 1024, "winograd", 256, 117, 0)
 QD_OZAKI_4096_S32 = Workload("qd_ozaki_n4096_s32", 4, 4096, "ozaki", 512, 103, 104, 32)
+# Odd order of the square sweep (odd dimensions peeled at every level).
+DD_WINOGRAD_3000 = Workload("dd_winograd_n3000", 2, 3000, "winograd", 256, 120, 121)
+QD_WINOGRAD_3000 = Workload("qd_winograd_n3000", 4, 3000, "winograd", 256, 122, 123)

@@ -11,6 +11,7 @@
 //   F L x(L) l(L) y(L)         -> window: x - l y, rounded to L limbs (hex)
 //   A L emax top n (sign x0 .. x(L-1)) x n -> add_at into V (NW = 5 / 9),
 //                              then from_fixed: V[0..NW-1] ; limbs (hex)
+//   B NW bits A[0..NW-1]       -> acc_mag_below: 0 / 1          (NW = 6 / 9)
 // Doubles are read as 16 hex digits of their bit pattern.
 #include <cinttypes>
 #include <cstdio>
@@ -135,6 +136,15 @@ static void do_fms() {
   for (int q = 0; q < L; ++q) std::printf("%016llx%c", (unsigned long long)fx::dbits(out[q]), q + 1 < L ? ' ' : '\n');
 }
 
+template <int NW>
+static void do_below() {
+  int bits;
+  scan("%d", &bits);
+  uint32_t A[NW];
+  for (int i = 0; i < NW; ++i) scan("%u", &A[i]);
+  std::printf("%d\n", fx::acc_mag_below<NW>(A, bits) ? 1 : 0);
+}
+
 static void do_recip() {
   double b[4], out[4];
   for (int q = 0; q < 4; ++q) b[q] = rd();
@@ -177,6 +187,10 @@ int main() {
       scan("%d", &a);
       if (a == 2) do_sum<2, 5>();
       else do_sum<4, 9>();
+    } else if (cmd[0] == 'B') {
+      scan("%d", &a);
+      if (a == 6) do_below<6>();
+      else do_below<9>();
     } else if (cmd[0] == 'P') {
       scan("%d %d", &a, &b);
       if (a == 6) do_place<6, 5>();

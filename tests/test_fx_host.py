@@ -7,7 +7,9 @@ for the CPU with nvcc and compared with exact integer arithmetic:
 * mul_top: the kept words of a b lie within (D + 1) 2^32 units below
   floor(a b / 2^(32 D));
 * place_shr: the window gains exactly sign * floor(p / 2^sh) (mod 2^(32 NW)),
-  on the two fast-path offsets and the general path.
+  on the two fast-path offsets and the general path;
+* acc_mag_below: the rescue test of the Block epilogue, |A| < 2^bits for a
+  two's-complement window, at and around the threshold and for both signs.
 """
 import math
 import os
@@ -282,3 +284,18 @@ def test_window_multiply_subtract(fxbin, L):
         # W-word product (2^-123 / 2^-219 of |l y|) and the window's floor
         slack = Fraction(1, 2 ** (120 if L == 2 else 216))
         assert abs(got - exact) <= abs(exact) * Fraction(1, 2 ** (53 * L - 1)) + scale * slack, (x, l, y)
+
+
+@pytest.mark.parametrize("NW,bits", [(6, 106), (9, 212), (6, 32), (9, 31)])
+def test_acc_mag_below_threshold(fxbin, NW, bits):
+    """|A| < 2^bits exactly, for values on both sides of 2^bits, both signs,
+    zero and the window's extremes (two's complement, NW words)."""
+    rng = random.Random(NW * 1000 + bits)
+    mags = [0, 1, (1 << bits) - 1, 1 << bits, (1 << bits) + 1, (1 << (bits - 1)),
+            (1 << (32 * NW - 2)), (1 << (32 * NW - 1)) - 1]
+    mags += [rng.getrandbits(rng.randint(1, 32 * NW - 2)) for _ in range(300)]
+    vals = [v for m in mags for v in (m, -m)]
+    lines = [f"B {NW} {bits} " + " ".join(str(w) for w in words(v % (1 << (32 * NW)), NW)) for v in vals]
+    out = run(fxbin, lines)
+    for v, o in zip(vals, out):
+        assert int(o) == (1 if abs(v) < (1 << bits) else 0), (v, bits)

@@ -39,3 +39,31 @@ def test_stats_percentiles():
     st = S.stats(rs)
     assert abs(st["gemm"]["p50_ms"] - 50.5) < 1e-6
     assert st["gemm"]["p99_ms"] > 99.0
+
+
+def test_check_request_refusals():
+    ok = S.Request(0, "gemm", 512, 0.0, 1)
+    assert S.check_request(ok, 1 << 40, 16384) == ""
+    assert "kind" in S.check_request(S.Request(1, "qr", 512, 0.0, 1), 1 << 40, 16384)
+    assert "positive" in S.check_request(S.Request(2, "lu", 0, 0.0, 1), 1 << 40, 16384)
+    assert "positive" in S.check_request(S.Request(3, "lu", 2.5, 0.0, 1), 1 << 40, 16384)
+    assert "limit" in S.check_request(S.Request(4, "lu", 20000, 0.0, 1), 1 << 40, 16384)
+    big = S.Request(5, "gemm", 4096, 0.0, 1)
+    assert "budget" in S.check_request(big, S.footprint(big) - 1, 16384)
+    assert S.check_request(big, S.footprint(big), 16384) == ""
+
+
+def test_admission_deadline():
+    r = S.Request(0, "gemm", 256, 1.0, 1, deadline=0.5)
+    assert not S.expired(r, 1.2) and not S.expired(r, 1.5)
+    assert S.expired(r, 1.5001)
+    assert not S.expired(S.Request(1, "lu", 1024, 0.0, 1), 1e9)  # no deadline
+
+
+def test_stats_count_refusals_apart():
+    rs = [S.Request(i, "gemm", 256, 0.0, i) for i in range(10)]
+    for i, r in enumerate(rs):
+        r.done, r.status = (i + 1) * 1e-3, "ok"
+    rs[0].status, rs[1].status = "refused", "timeout"
+    st = S.stats(rs)
+    assert st["gemm"]["count"] == 8 and st["refused"] == 1 and st["timeout"] == 1
