@@ -89,7 +89,17 @@ typedef enum {
                        rounded to DD. Error <= l 2^-P max|a_i.| max|b_.j| per
                        entry plus the DD rounding, P from
                        ddg_ozaki2_precision (N = 32, l = 4096: P = 113);
-                       l <= 65536, m <= 65535; QD gives DDG_ENOTSUP */
+                       l <= 65536, m <= 65535; QD gives DDG_ENOTSUP */,
+  DDG_OZAKI2_TC = 6 /* DDG_OZAKI2 with its residue products on the
+                       fifth-generation tensor cores (not in the paper):
+                       residues as BF16 (exact for |r| <= 128), tcgen05.mma
+                       with FP32 accumulation in tensor memory, drained into
+                       integers every 256 terms (exact: partial sums stay
+                       integers below 2^22), operands staged by TMA. The
+                       residues of the product, hence C, are the same bits
+                       as DDG_OZAKI2; same limits (DD only, l <= 65536,
+                       m <= 65535). The residue planes take 2 bytes per
+                       element per modulus (twice DDG_OZAKI2's). */
 } ddg_algo;
 
 /* How C is written: C := A B, C := C + A B or C := C - A B. */
@@ -345,6 +355,14 @@ ddg_status ddg_workspace_stats(int32_t device, ddg_workspace_info* out);
 /* Number of CUDA kernels this library has launched in this process, all
  * threads and devices together (monotonic; for launch accounting). */
 uint64_t ddg_kernel_launches(void);
+
+/* Bounded device waits that ran out on the current device since the last
+ * reset: the tensor-core kernel of DDG_OZAKI2_TC waits on shared-memory
+ * barriers with an iteration limit; a CTA whose wait runs out counts here,
+ * finishes its copies and MMAs in flight, frees its tensor memory and
+ * returns (its part of C is then wrong). Synchronous: waits for the device.
+ * reset != 0 sets the count back to 0. -1 if it cannot be read. */
+int32_t ddg_device_timeouts(int32_t reset);
 
 /* Message describing the last failure on this host thread ("" if none). */
 const char* ddg_last_error(void);

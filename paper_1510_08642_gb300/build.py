@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libddgemm.so")
-SOURCES = ["simple.cu", "block.cu", "block_fx.cu", "passes.cu", "gemm.cu", "profile.cu", "lu.cu", "ozaki.cu", "batch.cu", "pool.cu", "gemv_fx.cu"]
+SOURCES = ["simple.cu", "block.cu", "block_fx.cu", "passes.cu", "gemm.cu", "profile.cu", "lu.cu", "ozaki.cu", "batch.cu", "pool.cu", "gemv_fx.cu", "ozaki_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")

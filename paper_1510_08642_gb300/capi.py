@@ -19,9 +19,9 @@ c_i32, c_i64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
 DDG_OK, DDG_EINVAL, DDG_ENOMEM, DDG_ECUDA, DDG_ESINGULAR, DDG_ETIMEOUT, DDG_ENOTSUP = range(7)
 STATUS_NAMES = ["DDG_OK", "DDG_EINVAL", "DDG_ENOMEM", "DDG_ECUDA", "DDG_ESINGULAR",
                 "DDG_ETIMEOUT", "DDG_ENOTSUP"]
-DDG_SIMPLE, DDG_BLOCK, DDG_STRASSEN, DDG_WINOGRAD, DDG_OZAKI, DDG_OZAKI2 = range(6)
+DDG_SIMPLE, DDG_BLOCK, DDG_STRASSEN, DDG_WINOGRAD, DDG_OZAKI, DDG_OZAKI2, DDG_OZAKI2_TC = range(7)
 ALGOS = {"simple": DDG_SIMPLE, "block": DDG_BLOCK, "strassen": DDG_STRASSEN,
-         "winograd": DDG_WINOGRAD, "ozaki": DDG_OZAKI, "ozaki2": DDG_OZAKI2}
+         "winograd": DDG_WINOGRAD, "ozaki": DDG_OZAKI, "ozaki2": DDG_OZAKI2, "ozaki2_tc": DDG_OZAKI2_TC}
 DDG_SET, DDG_ADD, DDG_SUB = range(3)
 MODES = {"set": DDG_SET, "add": DDG_ADD, "sub": DDG_SUB}
 
@@ -97,6 +97,7 @@ SIGNATURES = {
     "ddg_workspace_stats": (c_i32, [c_i32, ctypes.POINTER(ddg_workspace_info)]),
     "ddg_last_error": (ctypes.c_char_p, []),
     "ddg_kernel_launches": (ctypes.c_uint64, []),
+    "ddg_device_timeouts": (c_i32, [c_i32]),
     "ddg_profile_begin": (c_i32, []),
     "ddg_profile_end": (c_i32, [ctypes.POINTER(ddg_kernel_prof), c_i32]),
 }
@@ -174,6 +175,10 @@ def ddg_ozaki2_precision(moduli: int, l: int) -> int:
 
 def ddg_kernel_launches() -> int:
     return load().ddg_kernel_launches()
+
+
+def ddg_device_timeouts(reset: bool = False) -> int:
+    return load().ddg_device_timeouts(1 if reset else 0)
 
 
 def ddg_profile_begin() -> None:

@@ -423,8 +423,8 @@ static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& 
   if (opts) o = *opts;
   if (m < 0 || l < 0 || n < 0) return fail(DDG_EINVAL, "negative size");
   if (mode < DDG_SET || mode > DDG_SUB) return fail(DDG_EINVAL, "mode must be DDG_SET, DDG_ADD or DDG_SUB");
-  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI2) return fail(DDG_EINVAL, "unknown algo");
-  if (o.algo == DDG_OZAKI2 ? (o.slices != 0 && (o.slices < 2 || o.slices > 40))
+  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI2_TC) return fail(DDG_EINVAL, "unknown algo");
+  if (o.algo == DDG_OZAKI2 || o.algo == DDG_OZAKI2_TC ? (o.slices != 0 && (o.slices < 2 || o.slices > 40))
                            : (o.slices != 0 && (o.slices < 2 || o.slices > (L == 2 ? 18 : 32))))
     return fail(DDG_EINVAL, "slices must be 0 or in [2, 18] (DD) / [2, 32] (QD); moduli in [2, 40]");
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
@@ -459,7 +459,7 @@ ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const 
     }
     return ozaki_gemm(L, m, l, n, A, B, C, mode, o.slices ? o.slices : (L == 2 ? 16 : 32), s);
   }
-  if (o.algo == DDG_OZAKI2) {
+  if (o.algo == DDG_OZAKI2 || o.algo == DDG_OZAKI2_TC) {
     if (L != 2) return fail(DDG_ENOTSUP, "DDG_OZAKI2: DD only (the moduli <= 256 give at most ~2^369)");
     if (m > 65535) return fail(DDG_EINVAL, "DDG_OZAKI2: m must be <= 65535");
     if (l == 0) {
@@ -467,7 +467,7 @@ ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const 
       z.L = L;
       return mode == MODE_SET ? zero_mat(z, C, m, n, s) : DDG_OK;
     }
-    return ozaki_crt_gemm(m, l, n, A, B, C, mode, o.slices ? o.slices : 32, s);
+    return ozaki_crt_gemm(m, l, n, A, B, C, mode, o.slices ? o.slices : 32, o.algo == DDG_OZAKI2_TC, s);
   }
   Ctx c;
   c.L = L;
@@ -561,6 +561,11 @@ const char* ddg_last_error(void) { return ddg::g_err.c_str(); }
 
 uint64_t ddg_kernel_launches(void) { return ddg::g_launches.load(std::memory_order_relaxed); }
 
+int32_t ddg_device_timeouts(int32_t reset) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+  return ddg::crt_tc_timeouts(reset != 0);
+}
+
 }  // extern "C"
 
 // ------------------------------------------------ allocation-free variant --
@@ -603,8 +608,8 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
   if (opts) o = *opts;
   if (m < 0 || l < 0 || n < 0) return fail(DDG_EINVAL, "negative size");
   if (mode < DDG_SET || mode > DDG_SUB) return fail(DDG_EINVAL, "mode must be DDG_SET, DDG_ADD or DDG_SUB");
-  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI2) return fail(DDG_EINVAL, "unknown algo");
-  if (o.algo == DDG_OZAKI2 ? (o.slices != 0 && (o.slices < 2 || o.slices > 40))
+  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI2_TC) return fail(DDG_EINVAL, "unknown algo");
+  if (o.algo == DDG_OZAKI2 || o.algo == DDG_OZAKI2_TC ? (o.slices != 0 && (o.slices < 2 || o.slices > 40))
                            : (o.slices != 0 && (o.slices < 2 || o.slices > (L == 2 ? 18 : 32))))
     return fail(DDG_EINVAL, "slices must be 0 or in [2, 18] (DD) / [2, 32] (QD); moduli in [2, 40]");
   if (o.cutoff < 1) return fail(DDG_EINVAL, "cutoff must be >= 1");
@@ -618,8 +623,8 @@ static ddg_status gemm_noalloc_entry(int64_t m, int64_t l, int64_t n, const mat&
   if (overlaps(L, C, m, n, A, m, l) || overlaps(L, C, m, n, B, l, n))
     return fail(DDG_EINVAL, "C overlaps A or B");
   if (m > (int64_t)65535 * 8 || n > ((int64_t)1 << 36)) return fail(DDG_EINVAL, "matrix too large");
-  if (o.algo == DDG_OZAKI || o.algo == DDG_OZAKI2)
-    return fail(DDG_EINVAL, "dd_gemm_noalloc: the INT8 products need a workspace; use dd_gemm");
+  if (o.algo == DDG_OZAKI || o.algo == DDG_OZAKI2 || o.algo == DDG_OZAKI2_TC)
+    return fail(DDG_EINVAL, "dd_gemm_noalloc: the INT8 / BF16 residue products need a workspace; use dd_gemm");
   if (m == 0 || n == 0) return DDG_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (o.algo == DDG_SIMPLE) {

@@ -195,10 +195,21 @@ cudaError_t ws_free(void* p, cudaStream_t s);
 ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
                     int mode, const ddg_opts& o, cudaStream_t s);
 
-// DD product by INT8 residues and the Chinese remainder theorem (Ozaki
-// scheme II), N moduli (ozaki.cu); the integer scaling precision it uses.
+// DD product by residues and the Chinese remainder theorem (Ozaki scheme
+// II), N moduli (ozaki.cu); the residue products on the INT8 mma.sync path
+// (tc = false) or as BF16 on the tcgen05 tensor cores (tc = true, the same
+// bits); the integer scaling precision it uses.
 ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C, int mode,
-                          int N, cudaStream_t st);
+                          int N, bool tc, cudaStream_t st);
+
+// The tcgen05 residue products (ozaki_tc.cu): N BF16 residue planes of A
+// (mpad x lpad, k contiguous) and of B (npad x lpad, B transposed) in, N
+// byte planes of the product's residues (mpad x npad) out; mpad, npad
+// multiples of 128, lpad a multiple of 64 and <= 65536. crt_tc_timeouts:
+// how many CTAs of that kernel gave up a bounded wait (reset: set to 0).
+cudaError_t launch_crt_tc(int N, int64_t mpad, int64_t npad, int64_t lpad, const void* As, const void* Bs,
+                          uint8_t* R, cudaStream_t st);
+int crt_tc_timeouts(bool reset);
 int ozaki_crt_precision(int N, int64_t l);
 
 // DD / QD product by INT8 slices (Ozaki scheme), s slices (ozaki.cu).

@@ -640,7 +640,7 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
   ddg_opts o;
   ddg_opts_default(&o);
   if (opts) o = *opts;
-  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI2 || o.cutoff < 1 || o.accum < 0 || o.accum > 2 ||
+  if (o.algo < DDG_SIMPLE || o.algo > DDG_OZAKI2_TC || o.cutoff < 1 || o.accum < 0 || o.accum > 2 ||
       (o.pad != 0 && o.pad != 1) || (o.streams != 0 && o.streams != 1 && o.streams != 7))
     return set_error(DDG_EINVAL, nm + ": invalid options");
   if (n == 0) return DDG_OK;

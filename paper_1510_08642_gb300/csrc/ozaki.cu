@@ -679,7 +679,7 @@ ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, cons
 }
 
 ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C, int mode,
-                          int N, cudaStream_t st) {
+                          int N, bool tc, cudaStream_t st) {
   if (m == 0 || n == 0) return DDG_OK;
   if (N < 2 || N > CRT_MAXN)
     return set_error(DDG_EINVAL, "ozaki2: moduli must be in [2, " + std::to_string(CRT_MAXN) + "]");
@@ -689,7 +689,8 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
   crt_consts cc;
   const int P = crt_precision(N, l, &cc);
   if (P < 1) return set_error(DDG_EINVAL, "ozaki2: too few moduli for this l");
-  const size_t bA = al256((size_t)N * mpad * lpad), bB = al256((size_t)N * npad * lpad);
+  const size_t esz = tc ? 2 : 1;  // residues as bf16 (tensor cores) or int8 (mma.sync)
+  const size_t bA = al256((size_t)N * mpad * lpad * esz), bB = al256((size_t)N * npad * lpad * esz);
   const size_t bR = al256((size_t)N * mpad * npad), bE = al256((size_t)(m + n) * 4);
   void* ws = nullptr;
   if (ddg::ws_alloc(&ws, bA + bB + bR + bE, st) != cudaSuccess) {
@@ -697,8 +698,6 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
     return set_error(DDG_ENOMEM, "ozaki2: workspace allocation failed");
   }
   char* base = static_cast<char*>(ws);
-  int8_t* As = reinterpret_cast<int8_t*>(base);
-  int8_t* Bs = reinterpret_cast<int8_t*>(base + bA);
   uint8_t* R = reinterpret_cast<uint8_t*>(base + bA + bB);
   int* exa = reinterpret_cast<int*>(base + bA + bB + bR);
   int* exb = exa + m;
@@ -710,18 +709,32 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
   oz_exp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(l, n, B, 0, exb);
   launched();
   const dim3 ga((unsigned)((lpad + 255) / 256), (unsigned)mpad), gb((unsigned)(npad / 32), (unsigned)(lpad / 32));
-  oz_split_a_kernel<2, true><<<ga, 256, 0, st>>>(m, l, A, exa, N, P, mpad, lpad, As);
-  launched();
-  oz_split_b_kernel<2, true><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, N, P, npad, lpad, Bs);
-  launched();
-  prof_begin_launch(st, &ev);
-  oz_gemm_kernel<true><<<dim3((unsigned)(npad / OBN), (unsigned)(mpad / OBM), (unsigned)N), 256, OZ_SMEM, st>>>(
-      mpad, npad, lpad, N, As, Bs, nullptr, R);
-  launched();
-  cudaError_t e = cudaGetLastError();
-  if (ev)
-    prof_end_launch(st, ev, PROF_OZAKI, 2.0 * N * (double)mpad * (double)npad * (double)lpad,
-                    (double)N * (mpad + npad) * lpad + (double)N * mpad * npad);
+  cudaError_t e = cudaSuccess;
+  if (tc) {
+    __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(base + bA);
+    oz_split_a_kernel<2, true, __nv_bfloat16><<<ga, 256, 0, st>>>(m, l, A, exa, N, P, mpad, lpad, As);
+    launched();
+    oz_split_b_kernel<2, true, __nv_bfloat16><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, N, P, npad, lpad, Bs);
+    launched();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_crt_tc(N, mpad, npad, lpad, As, Bs, R, st);
+  } else {
+    int8_t* As = reinterpret_cast<int8_t*>(base);
+    int8_t* Bs = reinterpret_cast<int8_t*>(base + bA);
+    oz_split_a_kernel<2, true><<<ga, 256, 0, st>>>(m, l, A, exa, N, P, mpad, lpad, As);
+    launched();
+    oz_split_b_kernel<2, true><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, N, P, npad, lpad, Bs);
+    launched();
+    prof_begin_launch(st, &ev);
+    oz_gemm_kernel<true><<<dim3((unsigned)(npad / OBN), (unsigned)(mpad / OBM), (unsigned)N), 256, OZ_SMEM, st>>>(
+        mpad, npad, lpad, N, As, Bs, nullptr, R);
+    launched();
+    e = cudaGetLastError();
+    if (ev)
+      prof_end_launch(st, ev, PROF_OZAKI, 2.0 * N * (double)mpad * (double)npad * (double)lpad,
+                      (double)N * (mpad + npad) * lpad + (double)N * mpad * npad);
+  }
   if (e == cudaSuccess) {
     const dim3 gr((unsigned)((n + 255) / 256), (unsigned)m);
     oz_crt_recombine_kernel<<<gr, 256, 0, st>>>(m, n, N, P, mpad, npad, R, exa, exb, C, mode, cc);
