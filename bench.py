@@ -42,7 +42,21 @@ SM_MAX_MHZ = 2070.0               # profiling recipe / MEASURED_PEAKS.json
 FP64_PEAK = SM_COUNT * FP64_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # FP64 instructions per second
 PINNED_MAC_OPS = {2: 27, 4: 218}  # DD / QD multiply then add of the Simple kernel
 INT8_MMA_PEAK = 1.50e14           # mma.sync m16n8k32 s8 ops/s, measured by the same probe
-HBM_GBS = 6790.7                  # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+_PEAKS = _measured_peaks()
+# copy bandwidth and cuBLAS bf16 GEMM rate measured on the GB300s;
+# without the file, the profiling recipe's fallback figures
+HBM_GBS = float(_PEAKS.get("hbm_gbs", 6800.0))
+BF16_PEAK = float(_PEAKS.get("bf16_tflops", 1900.0)) * 1e12
+PEAK_NOTE = "of measured (MEASURED_PEAKS.json)" if _PEAKS else "of fallback (6.8 TB/s, 1.9 PFLOP/s bf16)"
 ISSUE_PER_CLK_PER_SM = 4 * 32     # 4 schedulers x one warp instruction (32 lanes) per clock
 ISSUE_PEAK = SM_COUNT * ISSUE_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # thread instructions per second
 IMAD_PER_CLK_PER_SM = 64          # measured: IMAD throughput probe (profiles/fp64_int8_peaks.md)
@@ -336,11 +350,22 @@ def profile_record(kernel: str):
 
 
 def roofline_of(prof, limbs):
-    """Dominant kernel: the Block base case (thread instructions issued per
-    busy second, from its multiply-adds and the committed ncu count of
-    instructions per multiply-add, against the SM issue rate) or, for the
-    INT8 products, the INT8 GEMM (INT8 ops against the measured mma.sync
-    peak)."""
+    """Dominant kernel: the tcgen05 residue products (BF16 operations against
+    the measured bf16 GEMM rate), the INT8 GEMM (INT8 operations against the
+    measured mma.sync peak) or the Block base case (its irreducible IMAD
+    count per multiply-add against the IMAD pipe, plus the issue-slot use
+    from the committed ncu counts)."""
+    tc = prof.get("tensor")
+    if tc and tc["launches"]:
+        achieved = tc["ops"] / (tc["busy_ms"] * 1e-3)
+        return {"bound": "tensor", "kernel": "crt_tc_kernel (tcgen05.mma kind::f16, BF16 residues, FP32 in "
+                                             "tensor memory, TMA operands)",
+                "achieved": achieved / 1e12, "peak": BF16_PEAK / 1e12, "unit": "T BF16-op/s",
+                "frac": achieved / BF16_PEAK, "traffic": None,
+                "peak_source": f"bf16_tflops {PEAK_NOTE}: cuBLAS bf16 GEMM, burst (the kernel is timed alone)",
+                "algorithmic": "2 x N moduli x m l n (padded to 128 x 64 x 128) BF16 multiply-adds per product",
+                "launches": int(tc["launches"]), "avg_launch_ms": tc["sum_ms"] / tc["launches"],
+                "busy_ms": tc["busy_ms"]}
     oz = prof.get("ozaki")
     if oz and oz["launches"]:
         achieved = oz["ops"] / (oz["busy_ms"] * 1e-3)
@@ -735,7 +760,8 @@ def run_ours(args, w):
         extras = {}
         for xw in (WL.DD_BLOCK_4096, WL.QD_WINOGRAD_4096, WL.QD_BLOCK_4096, WL.DD_WINOGRAD_3000,
                    WL.QD_WINOGRAD_3000, WL.DD_OZAKI_4096_S16, WL.DD_OZAKI_4096_S13, WL.DD_WINOGRAD_8192,
-                   WL.DD_OZAKI_8192_S16, WL.QD_OZAKI_4096_S32, WL.DD_OZAKI2_4096_N32, WL.DD_OZAKI2_8192_N32):
+                   WL.DD_OZAKI_8192_S16, WL.QD_OZAKI_4096_S32, WL.DD_OZAKI2_4096_N32, WL.DD_OZAKI2_8192_N32,
+                   WL.DD_OZAKI2TC_4096_N32, WL.DD_OZAKI2TC_8192_N32):
             hXA = I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_a)
             hXB = I.uniform(xw.n, xw.n, xw.limbs, seed=xw.seed_b)
             XA, XB = torch.from_numpy(hXA).to(device), torch.from_numpy(hXB).to(device)
@@ -747,7 +773,7 @@ def run_ours(args, w):
             del XA, XB, XC, hXA, hXB
             torch.cuda.empty_cache()
         extras["cutoff_sweep"] = cutoff_sweep(P, torch, device, stream)
-        for lw in (WL.DD_LU_4096, WL.DD_LU_4096_OZ2, WL.QD_LU_2048):
+        for lw in (WL.DD_LU_4096, WL.DD_LU_4096_OZ2, WL.DD_LU_4096_OZ2TC, WL.QD_LU_2048):
             extras[lw.name], chk = time_lu(P, torch, lw, device, stream, K=256)
             checks.append(chk)
         extras["batched_1000_mixed"] = time_batched(P, torch, device, stream)

@@ -309,7 +309,8 @@ int32_t ddg_ozaki2_precision(int32_t moduli, int64_t l);
  * stream. ddg_profile_end() waits for those events and fills out[k] for
  * kernel kinds k = 0 (Simple), 1 (Block), 2 (quadrant passes), 3 (INT8
  * products), 4 (Block products with at most 8 columns, one warp per
- * output), 5 (operand conversions of the Block products), k < nkinds:
+ * output), 5 (operand conversions of the Block products), 6 (tcgen05
+ * residue products of DDG_OZAKI2_TC), k < nkinds:
  * launches, sum of launch durations, busy time (union of the launch
  * intervals), and the algorithmic work and bytes of those launches.
  * For measurement only: it adds two event records per launch. */
@@ -319,7 +320,8 @@ typedef struct {
   double busy_ms;
   double ops;   /* FP64 instructions (kind 0), multiply-adds (kinds 1 and 4),
                    DD / QD sums (kind 2), INT8 operations, 2 per
-                   multiply-add (kind 3, the INT8 products) or converted
+                   multiply-add (kind 3, the INT8 products), BF16
+                   operations, 2 per multiply-add (kind 6) or converted
                    elements (kind 5) */
   double bytes;
 } ddg_kernel_prof;

@@ -45,7 +45,7 @@ class ddg_kernel_prof(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
-PROF_KINDS = ("simple", "block", "pass", "ozaki", "gemv", "convert")
+PROF_KINDS = ("simple", "block", "pass", "ozaki", "gemv", "convert", "tensor")
 
 
 class ddg_problem(ctypes.Structure):

@@ -26,7 +26,10 @@ inline mat view(const mat& M, int64_t r0, int64_t c0) {
 extern std::atomic<uint64_t> g_launches;
 
 // Launch profiling hooks (profile.cu); no-ops unless ddg_profile_begin ran.
-enum ProfKind { PROF_SIMPLE = 0, PROF_BLOCK = 1, PROF_PASS = 2, PROF_OZAKI = 3, PROF_GEMV = 4, PROF_CONVERT = 5 };
+enum ProfKind {
+  PROF_SIMPLE = 0, PROF_BLOCK = 1, PROF_PASS = 2, PROF_OZAKI = 3, PROF_GEMV = 4, PROF_CONVERT = 5,
+  PROF_TENSOR = 6  // tcgen05 residue products
+};
 bool prof_enabled();
 void prof_begin_launch(cudaStream_t s, cudaEvent_t* start);
 void prof_end_launch(cudaStream_t s, cudaEvent_t start, int kind, double ops, double bytes);

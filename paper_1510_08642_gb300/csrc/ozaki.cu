@@ -92,11 +92,21 @@ __global__ void oz_exp_kernel(int64_t rows, int64_t cols, mat X, int byrow, int*
     f = __reduce_max_sync(0xffffffffu, f);
     if (lane == 0) ex[r] = f;
   } else {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
+    // 32 columns per CTA, its 8 warps splitting the rows (coalesced rows of
+    // 32 doubles), then a shared-memory reduction over the warps
+    __shared__ int part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * 32 + lane;
     int f = 1;
-    for (int64_t k = 0; k < rows; ++k) f = max(f, fx::expfield(X.p[0][k * X.ld + c]));
-    ex[c] = f;
+    if (c < cols)
+      for (int64_t k = w; k < rows; k += 8) f = max(f, fx::expfield(X.p[0][k * X.ld + c]));
+    part[w][lane] = f;
+    __syncthreads();
+    if (w == 0 && c < cols) {
+#pragma unroll
+      for (int t = 1; t < 8; ++t) f = max(f, part[t][lane]);
+      ex[c] = f;
+    }
   }
 }
 
@@ -644,7 +654,7 @@ ddg_status ozaki_gemm(int L, int64_t m, int64_t l, int64_t n, const mat& A, cons
   auto launched = [&]() { g_launches.fetch_add(1, std::memory_order_relaxed); };
   oz_exp_kernel<<<(unsigned)((m + 7) / 8), 256, 0, st>>>(m, l, A, 1, exa);
   launched();
-  oz_exp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(l, n, B, 0, exb);
+  oz_exp_kernel<<<(unsigned)((n + 31) / 32), 256, 0, st>>>(l, n, B, 0, exb);
   launched();
   const dim3 ga((unsigned)((lpad + 255) / 256), (unsigned)mpad), gb((unsigned)(npad / 32), (unsigned)(lpad / 32));
   if (L == 2) {
@@ -683,7 +693,8 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
   if (m == 0 || n == 0) return DDG_OK;
   if (N < 2 || N > CRT_MAXN)
     return set_error(DDG_EINVAL, "ozaki2: moduli must be in [2, " + std::to_string(CRT_MAXN) + "]");
-  const int64_t mpad = (m + OBM - 1) / OBM * OBM, npad = (n + OBN - 1) / OBN * OBN;
+  const int64_t nb = tc ? 2 * OBN : OBN;  // the tensor-core tiles are 256 columns wide
+  const int64_t mpad = (m + OBM - 1) / OBM * OBM, npad = (n + nb - 1) / nb * nb;
   const int64_t lpad = std::max<int64_t>(OBK, (l + OBK - 1) / OBK * OBK);
   if (lpad > 65536) return set_error(DDG_EINVAL, "ozaki2: l must be <= 65536 (exact INT32 residue products)");
   crt_consts cc;
@@ -706,7 +717,7 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
   auto launched = [&]() { g_launches.fetch_add(1, std::memory_order_relaxed); };
   oz_exp_kernel<<<(unsigned)((m + 7) / 8), 256, 0, st>>>(m, l, A, 1, exa);
   launched();
-  oz_exp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(l, n, B, 0, exb);
+  oz_exp_kernel<<<(unsigned)((n + 31) / 32), 256, 0, st>>>(l, n, B, 0, exb);
   launched();
   const dim3 ga((unsigned)((lpad + 255) / 256), (unsigned)mpad), gb((unsigned)(npad / 32), (unsigned)(lpad / 32));
   cudaError_t e = cudaSuccess;

@@ -17,20 +17,23 @@
 // same residues the INT8 mma.sync kernel writes; the CRT reconstruction
 // that follows is shared.
 //
-// Kernel layout (one persistent CTA per SM, 192 threads):
-//   warp 0: TMA producer (one lane): 128 x 64 BF16 boxes of A and B
-//           (128-byte rows, 128-byte swizzle) into a ring of 6 stages;
-//   warp 1: allocates 256 tensor-memory columns (two 128 x 128 FP32
-//           accumulators) and issues the MMAs (one lane): per 64-wide k
-//           block four 128 x 128 x 16 MMAs, per 256-term chunk one
-//           accumulator, alternating, so that the drain of one chunk
-//           overlaps the MMAs of the next;
-//   warps 2-5: drain: warp w reads lanes 32 (w mod 4) .. + 31 of the
+// Kernel layout (one persistent CTA per SM, 320 threads; tiles of 128 rows
+// of A by 256 columns of B, so that a 48 KB stage feeds twice the MMA work
+// of a 128 x 128 tile for 1.5 times the bytes):
+//   warp 0: TMA producer (one lane): 64-wide k blocks of A (128 rows) and B
+//           (256 rows of the transposed B) as 128 x 64 BF16 boxes
+//           (128-byte rows, 128-byte swizzle) into a ring of 4 stages;
+//   warp 1: allocates all 512 tensor-memory columns (two 128 x 256 FP32
+//           accumulators) and issues the MMAs (one lane): per k block four
+//           128 x 256 x 16 MMAs, per 256-term chunk one accumulator,
+//           alternating, so that the drain of one chunk overlaps the MMAs
+//           of the next;
+//   warps 2-9: drain: warp w reads lanes 32 (w mod 4) .. + 31 of the
 //           accumulator (one row of the tile per thread, tcgen05.ld
-//           32x32b), adds the chunk into 128 integer sums, releases the
-//           accumulator; at the end of a tile reduces mod m_t and writes
-//           the row's 128 residues.
-// Tiles (modulus t, 128-row block, 128-column block) are taken in that
+//           32x32b), columns 128 ((w - 2) / 4) .. + 127, adds the chunk
+//           into 128 integer sums, releases the accumulator; at the end of
+//           a tile reduces mod m_t and writes its 128 residues of the row.
+// Tiles (modulus t, 128-row block, 256-column block) are taken in that
 // order, CTA b taking tiles b, b + gridDim.x, ... (no CTA waits on another):
 // consecutive tiles share a modulus, so the 152 resident tiles read one
 // modulus's residue planes (2 x 32 MB at n = 4096) through the L2.
@@ -51,14 +54,16 @@ namespace ddg {
 
 namespace {
 
-constexpr int TBM = 128, TBN = 128, TBK = 64;  // tile; a k block is one 128-byte BF16 row
-constexpr int TST = 6;                          // shared-memory stages
+constexpr int TBM = 128, TBN = 256, TBK = 64;  // tile; a k block is one 128-byte BF16 row
+constexpr int TST = 4;                          // shared-memory stages (48 KB each)
+constexpr int DRAIN_WARPS = 8;                  // two per tensor-memory lane quarter
+constexpr int DCOLS = TBN / 2;                  // accumulator columns per draining warp
 constexpr int TCHUNK = 256;                     // terms per exact FP32 accumulation
 constexpr int KB_PER_CHUNK = TCHUNK / TBK;
 constexpr int A_BYTES = TBM * TBK * 2, B_BYTES = TBN * TBK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 2 * TBN;
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 32 * (2 + DRAIN_WARPS);
 // barriers: full[TST], empty[TST], acc_full[2], acc_empty[2], drained; then
 // the tensor-memory address and the abort flag
 constexpr int BAR_BYTES = 8 * (2 * TST + 5) + 8;
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full(b), 1);
-      mbar_init(acc_empty(b), 4);  // one arrival per draining warp
+      mbar_init(acc_empty(b), DRAIN_WARPS);  // one arrival per draining warp
     }
     mbar_init(drained, 1);
     *abort = 0;
@@ -243,6 +248,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           mbar_expect_tx(full(stage), STAGE_BYTES);
           tma_load_2d(sa, &tmA, kb * TBK, ya, full(stage));
           tma_load_2d(sa + A_BYTES, &tmB, kb * TBK, yb, full(stage));
+          tma_load_2d(sa + A_BYTES + B_BYTES / 2, &tmB, kb * TBK, yb + TBN / 2, full(stage));
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
           if (++stage == TST) {
@@ -298,14 +304,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else {
     // --------------------------------------------------------------- drain
-    const int q = warp & 3;  // lanes 32 q .. 32 q + 31 of tensor memory
-    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    const int q = warp & 3;                 // lanes 32 q .. 32 q + 31 of tensor memory
+    const int h = (warp - 2) >> 2;          // columns h DCOLS .. h DCOLS + DCOLS - 1
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * DCOLS);
     uint32_t accn = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
-      int sum[TBN];
+      int sum[DCOLS];
 #pragma unroll
-      for (int j = 0; j < TBN; ++j) sum[j] = 0;
+      for (int j = 0; j < DCOLS; ++j) sum[j] = 0;
       for (int c = 0; c < nchunks; ++c, ++accn) {
         const uint32_t b = accn & 1u, use = accn >> 1;
         // a warp-uniform outcome: the loads below are .sync.aligned
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_after();
 #pragma unroll
-        for (int piece = 0; piece < TBN / 32; ++piece) {
+        for (int piece = 0; piece < DCOLS / 32; ++piece) {
           uint32_t v[32];
           tc_ld32(lane_base + b * TBN + piece * 32, v);
 #pragma unroll
@@ -328,11 +335,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       if (!ok) break;
       const int64_t t = tile / per_mod, rem = tile % per_mod;
-      const int64_t row = (rem / g.nt) * TBM + q * 32 + lane, col0 = (rem % g.nt) * TBN;
+      const int64_t row = (rem / g.nt) * TBM + q * 32 + lane, col0 = (rem % g.nt) * TBN + h * DCOLS;
       const uint32_t m = c_crt_red.m[t], magic = c_crt_red.magic[t], bias = c_crt_red.bias[t];
       uint4* out = reinterpret_cast<uint4*>(g.R + (t * g.mpad + row) * g.npad + col0);
 #pragma unroll
-      for (int v16 = 0; v16 < TBN / 16; ++v16) {
+      for (int v16 = 0; v16 < DCOLS / 16; ++v16) {
         uint32_t w[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -430,7 +437,7 @@ cudaError_t launch_crt_tc(int N, int64_t mpad, int64_t npad, int64_t lpad, const
   crt_tc_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, a);
   e = cudaGetLastError();
   if (ev)
-    prof_end_launch(st, ev, PROF_OZAKI, 2.0 * N * (double)mpad * (double)npad * (double)lpad,
+    prof_end_launch(st, ev, PROF_TENSOR, 2.0 * N * (double)mpad * (double)npad * (double)lpad,
                     2.0 * N * (mpad + npad) * (double)lpad + (double)N * mpad * npad);
   return e;
 }

@@ -61,3 +61,10 @@ QD_OZAKI_4096_S32 = Workload("qd_ozaki_n4096_s32", 4, 4096, "ozaki", 512, 103, 1
 # Odd order of the square sweep (odd dimensions peeled at every level).
 DD_WINOGRAD_3000 = Workload("dd_winograd_n3000", 2, 3000, "winograd", 256, 120, 121)
 QD_WINOGRAD_3000 = Workload("qd_winograd_n3000", 4, 3000, "winograd", 256, 122, 123)
+# The CRT product with its residue products on the tcgen05 tensor cores.
+DD_OZAKI2TC_4096_N32 = Workload("dd_ozaki2tc_n4096_n32", 2, 4096, "ozaki2_tc", 512, 101, 102, 32)
+DD_OZAKI2TC_8192_N32 = Workload("dd_ozaki2tc_n8192_n32", 2, 8192, "ozaki2_tc", 512, 109, 110, 32)
+# A capture size for the tensor-core kernel (operands and residue planes
+# 0.8 GB, above the L2).
+DD_OZAKI2TC_2048_N32 = Workload("dd_ozaki2tc_n2048_n32", 2, 2048, "ozaki2_tc", 512, 112, 113, 32)
+DD_LU_4096_OZ2TC = Workload("dd_lu_n4096_ozaki2tc", 2, 4096, "ozaki2_tc", 512, 111, 0)
