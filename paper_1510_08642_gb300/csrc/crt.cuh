@@ -19,6 +19,13 @@ __host__ __device__ constexpr int crt_mod(int t) {
   return tab[t];
 }
 
+// 2^e mod m (for the digit-wise residues of the split).
+__host__ __device__ constexpr uint32_t crt_pow2_mod(int e, uint32_t m) {
+  uint32_t r = 1u % m;
+  for (int i = 0; i < e; ++i) r = (r * 2u) % m;
+  return r;
+}
+
 constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
 constexpr bool crt_mods_ok() {
   for (int a = 0; a < CRT_MAXN; ++a) {

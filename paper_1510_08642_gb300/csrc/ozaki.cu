@@ -197,15 +197,25 @@ __device__ __forceinline__ void oz_residues(const double (&x)[2], int field, int
     X[0] = ~X[0] + 1ull;
     X[1] = ~X[1] + (X[0] == 0ull ? 1ull : 0ull);
   }
-  const uint32_t w0 = (uint32_t)X[0], w1 = (uint32_t)(X[0] >> 32), w2 = (uint32_t)X[1],
-                 w3 = (uint32_t)(X[1] >> 32);
+  // |X| <= 2^120 as six 21-bit digits d_k: X mod m = (sum_k d_k (2^(21 k)
+  // mod m)) mod m, the sum below 6 2^21 255 < 2^32, so one 32-bit
+  // multiply-add per digit and one reduction per modulus
+  uint32_t d[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int b = 21 * k;  // bit offset of digit k in the 128-bit |X|
+    const unsigned long long lo = b < 64 ? X[0] >> b : 0ull;
+    const unsigned long long hi = b == 0 ? 0ull : (b < 64 ? X[1] << (64 - b) : X[1] >> (b - 64));
+    d[k] = (uint32_t)(lo | hi) & 0x1FFFFFu;
+  }
 #pragma unroll
   for (int t = 0; t < CRT_MAXN; ++t) {
     if (t < N) {
       const uint32_t m = (uint32_t)crt_mod(t);
-      const uint32_t p32 = (uint32_t)((1ull << 32) % m);
-      const uint32_t p64 = (p32 * p32) % m, p96 = (p64 * p32) % m;
-      uint32_t r = (w0 % m + (w1 % m) * p32 + (w2 % m) * p64 + (w3 % m) * p96) % m;
+      uint32_t acc = 0u;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc += d[k] * crt_pow2_mod(21 * k, m);
+      uint32_t r = acc % m;
       if (neg && r != 0u) r = m - r;
       oz_put(out + (int64_t)t * stride, r < 128u ? (int)r : (int)r - (int)m);
     }
@@ -435,7 +445,7 @@ __global__ void oz_recombine_kernel(int64_t m, int64_t n, int s, int64_t mpad, i
 
 // CRT reconstruction constants for N moduli (passed by value).
 struct crt_consts {
-  uint32_t c[CRT_MAXN][CRT_NW];  // c_t = (M / m_t) ((M / m_t)^-1 mod m_t)
+  uint32_t c[CRT_MAXN][2 * CRT_NW];  // c_t = (M / m_t) ((M / m_t)^-1 mod m_t) as 16-bit digits
   uint32_t M[CRT_NW];
   uint32_t halfM[CRT_NW];        // floor(M / 2)
   double inv_scaled;             // 2^(32 (wt - 2)) / M
@@ -443,7 +453,9 @@ struct crt_consts {
 };
 
 // C (mode) Z 2^(ea_i + fb_j - 2P), Z from its residues by the CRT:
-// S = sum_t r_t c_t (lazy carries in 64-bit words), q = floor(S / M) from
+// S = sum_t r_t c_t (the constants as 16-bit digits: every digit column
+// sums below 40 2^24 < 2^30 in a 32-bit register; carries propagated once
+// at the end), q = floor(S / M) from
 // the three top words (off by at most one, corrected), Z = S - q M in
 // [0, M), then Z - M if Z > M / 2; rounded to DD as in the slice scheme.
 __global__ void oz_crt_recombine_kernel(int64_t m, int64_t n, int N, int P, int64_t mpad, int64_t npad,
@@ -454,24 +466,25 @@ __global__ void oz_crt_recombine_kernel(int64_t m, int64_t n, int N, int P, int6
   const int64_t i = blockIdx.y;
   if (j >= n || i >= m) return;
   const int64_t plane = mpad * npad;
-  unsigned long long w[CRT_NW];
+  uint32_t w[2 * CRT_NW];
 #pragma unroll
-  for (int k = 0; k < CRT_NW; ++k) w[k] = 0ull;
+  for (int k = 0; k < 2 * CRT_NW; ++k) w[k] = 0u;
 #pragma unroll
   for (int t = 0; t < CRT_MAXN; ++t) {  // unrolled: static indices into the constants
     if (t < N) {
-      const unsigned long long r = R[(int64_t)t * plane + i * npad + j];
+      const uint32_t r = R[(int64_t)t * plane + i * npad + j];
 #pragma unroll
-      for (int k = 0; k < CRT_NW; ++k) w[k] += r * cc.c[t][k];  // < 40 * 2^40
+      for (int k = 0; k < 2 * CRT_NW; ++k) w[k] += r * cc.c[t][k];  // < 40 * 2^24
     }
   }
   uint32_t S[CRT_NW];
-  unsigned long long carry = 0ull;
+  uint32_t carry = 0u;
 #pragma unroll
   for (int k = 0; k < CRT_NW; ++k) {
-    const unsigned long long v = w[k] + carry;
-    S[k] = (uint32_t)v;
-    carry = v >> 32;
+    const uint32_t lo = w[2 * k] + carry;             // < 2^31
+    const uint32_t hi = w[2 * k + 1] + (lo >> 16);    // < 2^31
+    S[k] = (lo & 0xFFFFu) | (hi << 16);
+    carry = hi >> 16;
   }
   // q estimate from words wt, wt - 1, wt - 2 (selected without dynamic indexing)
   uint32_t s2 = 0u, s1 = 0u, s0 = 0u;
@@ -612,7 +625,10 @@ static int crt_precision(int N, int64_t l, crt_consts* cc) {
       for (int k = 0; k < CRT_NW; ++k) tmp[k] = Mt[k];
       const uint32_t y = inv_mod(big_div_small(tmp, mt), mt);
       big_mul_small(Mt, y);
-      for (int k = 0; k < CRT_NW; ++k) cc->c[t][k] = Mt[k];
+      for (int k = 0; k < CRT_NW; ++k) {
+        cc->c[t][2 * k] = Mt[k] & 0xFFFFu;
+        cc->c[t][2 * k + 1] = Mt[k] >> 16;
+      }
     }
     for (int k = 0; k < CRT_NW; ++k)
       cc->halfM[k] = (M[k] >> 1) | (k + 1 < CRT_NW ? (M[k + 1] << 31) : 0u);
