@@ -24,6 +24,7 @@
 // The loop runs while columns remain; the last block has min(K, remaining)
 // columns (the paper's garbled loop end, read as "until no columns remain").
 #include <algorithm>
+#include <cstdlib>
 #include <functional>
 #include <string>
 
@@ -368,6 +369,276 @@ __global__ void __launch_bounds__(256) lu_col_kernel(int64_t n, mat A, int64_t c
   if (last_block(cs)) finish_pivot<L>(n, A, j + 1, c0, pe, gridDim.x, part, ipiv, info, pivot, cs);
 }
 
+// ---------------------------------------------------------------------------
+// One launch per narrow panel (the Section 4 step 1 panel factorisation of
+// PANEL_BASE columns, all its column steps in one cooperative kernel).
+//
+// The rows [c0, n) are split into G contiguous chunks of R rows, one per
+// CTA; each CTA keeps its rows of the panel in shared memory for the whole
+// panel. Per column j one grid barrier: before it, every CTA publishes its
+// best pivot candidate together with that row's panel values, and the
+// owner of row j publishes row j (double-buffered slots, so that a CTA one
+// column ahead never overwrites what a slower CTA still reads); after it,
+// every CTA picks the same pivot from the G candidates, takes the pivot row
+// from the winner's slot, performs its part of the row interchange, forms
+// 1 / pivot, its quotients and its rank-1 updates with the same arithmetic
+// as the per-column kernels. All CTAs are co-resident (cooperative launch);
+// the barrier's wait is bounded and a CTA that gives up records -1 in
+// *info and returns.
+constexpr int PR_MAX = 64;  // rows per CTA kept in shared memory
+
+struct pub_t {
+  partial_t c;
+  double row[PANEL_BASE * 4];  // the candidate's panel row, L doubles per entry
+};
+
+struct panel_sync {
+  unsigned int count;  // arrivals at the current barrier
+  unsigned int gen;    // completed barriers
+};
+
+constexpr unsigned int PANEL_WAIT_TRIES = 1u << 22;
+
+// Barrier of the G co-resident CTAs; false if the wait ran out (then *info
+// = -1) or another CTA gave up before.
+__device__ __forceinline__ bool panel_barrier(panel_sync* ps, unsigned int& gen, unsigned int G, int64_t* info) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned int g = gen;
+    __threadfence();
+    if (atomicAdd(&ps->count, 1u) == G - 1u) {
+      atomicExch(&ps->count, 0u);
+      __threadfence();
+      atomicExch(&ps->gen, g + 1u);
+    } else {
+      unsigned int i = 0;
+      while (*reinterpret_cast<volatile unsigned int*>(&ps->gen) == g) {
+        if (++i > PANEL_WAIT_TRIES || *reinterpret_cast<volatile int64_t*>(info) < 0) {
+          ok = 0;
+          atomicExch(reinterpret_cast<unsigned long long*>(info), (unsigned long long)(int64_t)-1);
+          break;
+        }
+        if (i > 32) __nanosleep(64);
+      }
+    }
+    __threadfence();
+    gen = g + 1u;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int L>
+__device__ __forceinline__ void put_row(double* dst, const typename num<L>::T* src, int w) {
+  for (int c = threadIdx.x; c < w; c += blockDim.x) {
+    const double* x = reinterpret_cast<const double*>(&src[c]);
+#pragma unroll
+    for (int q = 0; q < L; ++q) dst[c * L + q] = x[q];
+  }
+}
+
+// Reads of what other CTAs published bypass L1 (__ldcg): the slots are
+// reused every other column and L1 is not coherent across SMs.
+template <int L>
+__device__ __forceinline__ void get_row(typename num<L>::T* dst, const double* src, int w) {
+  for (int c = threadIdx.x; c < w; c += blockDim.x) {
+    double* x = reinterpret_cast<double*>(&dst[c]);
+#pragma unroll
+    for (int q = 0; q < L; ++q) x[q] = __ldcg(src + c * L + q);
+  }
+}
+
+__device__ __forceinline__ partial_t get_cand(const partial_t* p) {
+  return partial_t{__ldcg(&p->kh), __ldcg(&p->kl), (int64_t)__ldcg(reinterpret_cast<const long long*>(&p->idx))};
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t c0, int64_t pe, int64_t R,
+                                                       int64_t* ipiv, int64_t* info, int pivot, pub_t* pub,
+                                                       double* rowj, panel_sync* ps) {
+  using N = num<L>;
+  using T = typename N::T;
+  constexpr int W = tfx<L>::W, D = tfx<L>::D, K = tfx<L>::K, NW = tfx<L>::NW;
+  constexpr int TOPW = 32 * W - 53;
+  __shared__ T rows[PR_MAX][PANEL_BASE];
+  __shared__ T prow[PANEL_BASE];  // the pivot row (row j after the interchange)
+  __shared__ T lq[PR_MAX];        // DD quotients
+  __shared__ uint32_t lw[PR_MAX][W], uw[PANEL_BASE][W];  // QD fixed-point quotients / pivot row
+  __shared__ int le[PR_MAX], ls[PR_MAX], ue[PANEL_BASE];
+  __shared__ partial_t sbest[8];
+  __shared__ T srinv;
+  const int tid = threadIdx.x, nw = blockDim.x >> 5;
+  const int w = (int)(pe - c0);
+  const unsigned int G = gridDim.x;
+  const int64_t r_lo = c0 + (int64_t)blockIdx.x * R;
+  const int64_t left = n - r_lo;
+  const int nr = left <= 0 ? 0 : (int)(left < R ? left : R);
+  unsigned int gen = *reinterpret_cast<volatile unsigned int*>(&ps->gen);
+  for (int e = tid; e < nr * w; e += blockDim.x) rows[e / w][e % w] = ldA<L>(A, r_lo + e / w, c0 + e % w);
+  __syncthreads();
+
+  for (int64_t j = c0; j < pe; ++j) {
+    const int jc = (int)(j - c0);
+    pub_t* slot = pub + (size_t)(jc & 1) * G;
+    double* rj = rowj + (size_t)(jc & 1) * PANEL_BASE * 4;
+    // ---- this CTA's best candidate (rows i >= j), published with its row
+    partial_t v = none();
+    if (pivot) {
+      for (int r = tid; r < nr; r += blockDim.x)
+        if (r_lo + r >= j) {
+          const partial_t q = cand<L>(rows[r][jc], r_lo + r);
+          if (better(q, v)) v = q;
+        }
+      warp_best(v);
+      if ((tid & 31) == 0) sbest[tid >> 5] = v;
+      __syncthreads();
+      v = sbest[0];
+      for (int k = 1; k < nw; ++k)
+        if (better(sbest[k], v)) v = sbest[k];
+      if (v.idx != INT64_MAX) put_row<L>(slot[blockIdx.x].row, rows[v.idx - r_lo], w);
+    }
+    if (tid == 0) slot[blockIdx.x].c = v;
+    if (j >= r_lo && j < r_lo + nr) put_row<L>(rj, rows[j - r_lo], w);
+    if (!panel_barrier(ps, gen, G, info)) return;
+    // ---- the pivot: the best of the G candidates (a strict order: every
+    // CTA picks the same), or row j without pivoting
+    partial_t b = none();
+    if (pivot) {
+      for (unsigned int k = tid; k < G; k += blockDim.x) {
+        const partial_t q = get_cand(&slot[k].c);
+        if (better(q, b)) b = q;
+      }
+      warp_best(b);
+      __syncthreads();
+      if ((tid & 31) == 0) sbest[tid >> 5] = b;
+      __syncthreads();
+      b = sbest[0];
+      for (int k = 1; k < nw; ++k)
+        if (better(sbest[k], b)) b = sbest[k];
+    }
+    const bool pv = pivot && b.idx >= j && b.idx < n;
+    const int64_t p = pv ? b.idx : j;
+    if (pv) get_row<L>(prow, slot[(b.idx - c0) / R].row, w);
+    else get_row<L>(prow, rj, w);
+    __syncthreads();
+    // ---- the interchange of rows j and p within the panel
+    if (j >= r_lo && j < r_lo + nr)
+      for (int c = tid; c < w; c += blockDim.x) rows[j - r_lo][c] = prow[c];
+    if (p != j && p >= r_lo && p < r_lo + nr) get_row<L>(rows[p - r_lo], rj, w);
+    if (tid == 0) {
+      const T piv = prow[jc];
+      const bool zero = is_zero<L>(piv);
+      if (blockIdx.x == 0) {
+        ipiv[j] = p;
+        if (zero && *info == 0) *info = j + 1;
+      }
+      T r = N::zero();
+      if (!zero) {
+        if constexpr (L == 4) {
+          const dd_t y = dd_recip(dd_t{piv.x[0], piv.x[1]});
+          qd_recip_refine(piv.x, y.hi, y.lo, r.x);
+        } else {
+          r = N::recip(piv);
+        }
+      }
+      srinv = r;
+    }
+    __syncthreads();
+    // ---- quotients l_ij = a_ij (1 / a_jj) and the rank-1 update of the
+    // columns (j, pe) of this CTA's rows below j
+    const T rinv = srinv;
+    const bool zero = is_zero<L>(rinv);
+    const int cols = w - jc - 1;
+    if (!zero) {
+      if constexpr (L == 2) {
+        for (int r = tid; r < nr; r += blockDim.x) {
+          T l = N::zero();
+          if (r_lo + r > j) {
+            l = N::mul(rows[r][jc], rinv);
+            rows[r][jc] = l;
+          }
+          lq[r] = l;
+        }
+        __syncthreads();
+        for (int e = tid; e < nr * cols; e += blockDim.x) {
+          const int r = e / cols, c = jc + 1 + e % cols;
+          if (r_lo + r > j) rows[r][c] = N::add(rows[r][c], N::mul(N::neg(lq[r]), prow[c]));
+        }
+      } else {
+        for (int r = tid; r < nr; r += blockDim.x) {
+          le[r] = -1;
+          const T a = rows[r][jc];
+          if (r_lo + r > j && !is_zero<L>(a)) {
+            const double* ax = reinterpret_cast<const double*>(&a);
+            const double* rx = reinterpret_cast<const double*>(&rinv);
+            double av[L], rv[L];
+#pragma unroll
+            for (int q = 0; q < L; ++q) av[q] = ax[q], rv[q] = rx[q];
+            uint32_t Ma[W], Mr[W], P[K], Ml[W];
+            const int ea = fx::to_fixed<L, W>(av, Ma), er = fx::to_fixed<L, W>(rv, Mr);
+            fx::mul_top<W, D>(Ma, Mr, P);
+            const int pp = fx::acc_normalize<K, W>(P, Ml);
+            const int el = pp + (ea & 0xFFFF) + (er & 0xFFFF) - 1075 - 2 * TOPW + 32 * D - 52;
+            const int sl = ((ea ^ er) >> 16) & 1;
+            double o[L];
+            fx::operand_to_limbs<L, W>(Ml, el, (uint32_t)sl, o);
+            T lv;
+            double* lx = reinterpret_cast<double*>(&lv);
+#pragma unroll
+            for (int q = 0; q < L; ++q) lx[q] = o[q];
+            rows[r][jc] = lv;
+#pragma unroll
+            for (int t = 0; t < W; ++t) lw[r][t] = Ml[t];
+            le[r] = el;
+            ls[r] = sl;
+          }
+        }
+        for (int c = tid; c < cols; c += blockDim.x) {
+          const double* ux = reinterpret_cast<const double*>(&prow[jc + 1 + c]);
+          double u[L];
+#pragma unroll
+          for (int q = 0; q < L; ++q) u[q] = ux[q];
+          uint32_t M[W];
+          const int es = fx::to_fixed<L, W>(u, M);
+#pragma unroll
+          for (int t = 0; t < W; ++t) uw[c][t] = M[t];
+          ue[c] = (fx::dbits(u[0]) << 1) == 0u ? -1 : es;
+        }
+        __syncthreads();
+        for (int e = tid; e < nr * cols; e += blockDim.x) {
+          const int r = e / cols, c = e % cols;
+          if (le[r] < 0 || ue[c] < 0) continue;  // l = 0 or u = 0: nothing to subtract
+          const double* ax = reinterpret_cast<const double*>(&rows[r][jc + 1 + c]);
+          double a[L];
+#pragma unroll
+          for (int q = 0; q < L; ++q) a[q] = ax[q];
+          int Aw = max(1, fx::expfield(a[0]));
+          uint32_t acc[NW];
+#pragma unroll
+          for (int t = 0; t < NW; ++t) acc[t] = 0u;
+          fx::add_at<L, NW>(acc, a, Aw, tfx<L>::TOPA, 0u);
+          uint32_t Ml[W], Mu[W];
+#pragma unroll
+          for (int t = 0; t < W; ++t) {
+            Ml[t] = lw[r][t];
+            Mu[t] = uw[c][t];
+          }
+          window_sub_product<L>(acc, Aw, Ml, le[r], (uint32_t)ls[r], Mu, ue[c] & 0xFFFF, (uint32_t)ue[c] >> 16);
+          double o[L];
+          fx::from_fixed<L, NW>(acc, Aw - 1075 - tfx<L>::TOPA, o);
+          double* dx = reinterpret_cast<double*>(&rows[r][jc + 1 + c]);
+#pragma unroll
+          for (int q = 0; q < L; ++q) dx[q] = o[q];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nr * w; e += blockDim.x) stA<L>(A, r_lo + e / w, c0 + e % w, rows[e / w][e % w]);
+}
+
 // The interchanges ipiv[k0 .. k1) (in order, at most 16) applied to every
 // column outside [k0, k1). The composed permutation of the (at most 32)
 // rows involved is worked out once per CTA; then each thread reads those
@@ -646,13 +917,30 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
   if (n == 0) return DDG_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t maxparts = (n + RB - 1) / RB;
-  const size_t bytes = sizeof(partial_t) * (size_t)maxparts + 512;
+  // the fused panel kernel: one CTA per SM at most, each holding up to
+  // PR_MAX rows; the per-column kernels otherwise (or when asked for by
+  // DDG_LU_COLUMN_STEPS=1, which tests use to cover both forms)
+  int dev = 0, nsm = 0, coop = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<L>, 256, 0);
+  cudaGetLastError();
+  const char* env = std::getenv("DDG_LU_COLUMN_STEPS");
+  const bool fused_ok = coop && per_sm >= 1 && nsm > 0 && !(env && env[0] == '1');
+  const int64_t gmax = std::max(1, nsm);
+  const size_t pub_bytes = 2 * sizeof(pub_t) * (size_t)gmax;
+  const size_t bytes = sizeof(partial_t) * (size_t)maxparts + 512 + pub_bytes + 2 * PANEL_BASE * 4 * 8 + 256;
   void* ws = nullptr;
   if (ddg::ws_alloc(&ws, bytes, s) != cudaSuccess) {
     cudaGetLastError();
     return set_error(DDG_ENOMEM, nm + ": scratch allocation failed");
   }
   partial_t* part = reinterpret_cast<partial_t*>(static_cast<char*>(ws) + 512);
+  char* after = static_cast<char*>(ws) + 512 + sizeof(partial_t) * (size_t)maxparts;
+  pub_t* pub = reinterpret_cast<pub_t*>(after);
+  double* rowj = reinterpret_cast<double*>(after + pub_bytes);
+  panel_sync* psync = reinterpret_cast<panel_sync*>(after + pub_bytes + 2 * PANEL_BASE * 4 * 8);
   int64_t* dinfo = info ? info : reinterpret_cast<int64_t*>(ws);
   col_state* cs = reinterpret_cast<col_state*>(static_cast<char*>(ws) + 256);
   ddg_status st = DDG_OK;
@@ -661,7 +949,8 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
     if (e != cudaSuccess && st == DDG_OK) st = set_error(DDG_ECUDA, nm + ": " + cudaGetErrorString(e));
   };
   if (cudaMemsetAsync(dinfo, 0, sizeof(int64_t), s) != cudaSuccess ||
-      cudaMemsetAsync(cs, 0, sizeof(col_state), s) != cudaSuccess)
+      cudaMemsetAsync(cs, 0, sizeof(col_state), s) != cudaSuccess ||
+      cudaMemsetAsync(psync, 0, sizeof(panel_sync), s) != cudaSuccess)
     st = set_error(DDG_ECUDA, nm + ": memset");
   // Panel of columns [c0, c0 + w), rows [c0, n): per-column kernels for
   // narrow panels; wider ones split in halves (left half, its triangular
@@ -672,6 +961,22 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
     if (st != DDG_OK || w <= 0) return;
     if (w <= PANEL_BASE) {
       const int64_t pe = c0 + w;
+      const int64_t prow = n - c0;
+      const int64_t R = std::max<int64_t>(8, (prow + gmax - 1) / gmax);
+      if (fused_ok && R <= PR_MAX) {
+        const unsigned G = (unsigned)((prow + R - 1) / R);
+        int64_t nn = n, cc0 = c0, ppe = pe, RR = R;
+        int piv = pivot;
+        mat MM = M;
+        int64_t* ip = ipiv;
+        void* args[] = {&nn, &MM, &cc0, &ppe, &RR, &ip, &dinfo, &piv, &pub, &rowj, &psync};
+        cu(cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<L>, dim3(G), dim3(256), args, 0, s));
+        if (pivot && st == DDG_OK) {
+          lu_laswp_kernel<L><<<dim3((unsigned)((n + 127) / 128), L), 128, 0, s>>>(n, M, c0, pe, ipiv);
+          cu(cudaGetLastError());
+        }
+        return;
+      }
       const int64_t nstart = pivot ? (n - c0 + RB - 1) / RB : 1;
       lu_start_kernel<L><<<(unsigned)nstart, 256, 0, s>>>(n, M, c0, pe, part, ipiv, dinfo, pivot, cs);
       cu(cudaGetLastError());
@@ -715,6 +1020,8 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
       st = set_error(DDG_ECUDA, nm + ": reading the pivot status");
   }
   ddg::ws_free(ws, s);
+  if (st == DDG_OK && hinfo < 0)
+    return set_error(DDG_ETIMEOUT, nm + ": a bounded device wait of the panel kernel ran out");
   if (st == DDG_OK && hinfo != 0)
     return set_error(DDG_ESINGULAR, nm + ": exactly zero pivot in column " + std::to_string(hinfo - 1));
   return st;

@@ -207,3 +207,75 @@ def test_int8_trailing_updates(algo):
     assert rel_residual(A, Xh, Bv) <= n * 2.0 ** -100
     _, piv_o, info = O.dd_getrf(A, pivot=True)
     assert np.array_equal(ipiv, piv_o)
+
+
+# ------------------------------------- fused panel kernel (one launch per panel)
+def _factor(A, K, cutoff, algo="winograd", pivot=True, column_steps=False):
+    """getrf through the C ABI; column_steps forces the per-column kernels
+    (DDG_LU_COLUMN_STEPS=1) instead of the fused panel kernel."""
+    import os
+    import paper_1510_08642_gb300 as P
+    old = os.environ.get("DDG_LU_COLUMN_STEPS")
+    os.environ["DDG_LU_COLUMN_STEPS"] = "1" if column_steps else "0"
+    try:
+        dA = to_dev(A)
+        ipiv = P.getrf(dA, K=K, pivot=pivot, algo=algo, cutoff=cutoff)
+        torch.cuda.synchronize()
+    finally:
+        if old is None:
+            del os.environ["DDG_LU_COLUMN_STEPS"]
+        else:
+            os.environ["DDG_LU_COLUMN_STEPS"] = old
+    return to_host(dA), ipiv.cpu().numpy()
+
+
+@pytest.mark.parametrize("limbs", [2, 4])
+@pytest.mark.parametrize("n,K,pivot", [(1, 1, True), (37, 16, True), (300, 64, True), (1000, 256, True),
+                                       (150, 32, False)])
+def test_fused_panel_same_bits_as_column_steps(limbs, n, K, pivot):
+    """The panel kernel runs each column step with the per-column kernels'
+    arithmetic (same quotients, same updates, same pivot rule), so the
+    factors and pivots are the same bits."""
+    A = I.uniform(n, n, limbs, seed=70 + n)
+    if not pivot:
+        A[0] += np.eye(n) * n
+    LUf, pf = _factor(A, K, 16, pivot=pivot)
+    LUc, pc = _factor(A, K, 16, pivot=pivot, column_steps=True)
+    assert np.array_equal(pf, pc)
+    assert np.array_equal(LUf.view(np.uint64), LUc.view(np.uint64))
+
+
+def _sampled_rel_residual(A, Xh, Bv, rows):
+    r = O.gemm_error(np.ascontiguousarray(A[:, rows, :]), Xh, np.ascontiguousarray(Bv[:, rows, :]))
+    return np.abs(r).max() / (np.abs(A[0]).sum(axis=1).max() * np.abs(Xh[0]).max())
+
+
+@pytest.mark.parametrize("limbs,n,cutoff", [(2, 4096, 512), (4, 2048, 256)])
+def test_bench_configs_sampled_residual_and_paths(limbs, n, cutoff):
+    """The bench's LU solves (DD n = 4096, QD n = 2048, K = 256, partial
+    pivoting, Winograd trailing updates): the exact residual of sampled rows
+    against the oracle within n 2^-100 (DD) / n 2^-200 (QD), and the fused
+    panels give the per-column kernels' factors and pivots bit for bit."""
+    import paper_1510_08642_gb300 as P
+    A = I.uniform(n, n, limbs, seed=71)
+    X = np.zeros((limbs, n, 1))
+    X[0] = 1.0
+    rows = np.array(sorted({0, n - 1, *np.random.default_rng(3).choice(n, 30, replace=False)}))
+    LUf, pf = _factor(A, 256, cutoff)
+    LUc, pc = _factor(A, 256, cutoff, column_steps=True)
+    assert np.array_equal(pf, pc)
+    assert np.array_equal(LUf.view(np.uint64), LUc.view(np.uint64))
+    assert np.all(pf >= np.arange(n)) and np.all(pf < n)
+    # solve b = A 1 with the factors (b from the GPU Block product, exact
+    # residual of the computed x against that b)
+    dA = to_dev(A)
+    ones = torch.zeros((limbs, n, 1), dtype=torch.float64, device="cuda")
+    ones[0] = 1.0
+    b = P.gemm(dA, ones, algo="block")
+    Bv = to_host(b)
+    dLU = to_dev(LUf)
+    P.getrs(dLU, torch.from_numpy(pf).cuda(), b)
+    torch.cuda.synchronize()
+    Xh = to_host(b)
+    bound = n * (2.0 ** -100 if limbs == 2 else 2.0 ** -200)
+    assert _sampled_rel_residual(A, Xh, Bv, rows) <= bound
