@@ -526,6 +526,7 @@ cudaError_t launch_block_fxc(int limbs, int64_t m, int64_t l, int64_t n, const f
                              const mat* C, int count, int mode, cudaStream_t s) {
   if (count < 1 || count > FXC_GROUP_MAX) return cudaErrorInvalidValue;
   if (m == 0 || n == 0) return cudaSuccess;
+  nvtx_range nv("ddg.leaf x%d %lldx%lldx%lld", count, (long long)m, (long long)l, (long long)n);
   fxc_group G{};
   for (int t = 0; t < count; ++t) G.A[t] = Ax[t], G.B[t] = Bx[t], G.C[t] = C[t];
   g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -328,7 +328,11 @@ static ddg_status rec(Ctx& c, int64_t m, int64_t l, int64_t n, const mat& A, con
     return DDG_OK;
   }
   const int64_t m2 = m & ~int64_t(1), l2 = l & ~int64_t(1), n2 = n & ~int64_t(1);
-  DDG_TRY(level(c, m2, l2, n2, A, B, C, mode, s, region, sp, depth));
+  if (!c.dry) nvtxRangePushA(depth == 0 ? "ddg.level 0" : depth == 1 ? "ddg.level 1" : depth == 2 ? "ddg.level 2"
+                                                        : depth == 3 ? "ddg.level 3" : "ddg.level 4+");
+  const ddg_status lst = level(c, m2, l2, n2, A, B, C, mode, s, region, sp, depth);
+  if (!c.dry) nvtxRangePop();
+  DDG_TRY(lst);
   if (l2 != l)  // C[:m2, :n2] (+/-)= A[:m2, l2] B[l2, :n2]
     DDG_CUDA(base_case(c, region, m2, 1, n2, view(A, 0, l2), view(B, l2, 0), C,
                        mode == MODE_SUB ? MODE_SUB : MODE_ADD, s));
@@ -445,6 +449,7 @@ static ddg_status gemm_entry(int L, int64_t m, int64_t l, int64_t n, const mat& 
 ddg_status gemm_run(int L, int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
                     int mode, const ddg_opts& o, cudaStream_t s) {
   if (m == 0 || n == 0) return DDG_OK;
+  nvtx_range nv("ddg.gemm L%d algo %d %lldx%lldx%lld", L, o.algo, (long long)m, (long long)l, (long long)n);
 
   if (o.algo == DDG_SIMPLE) {
     DDG_CUDA(launch_simple(L, m, l, n, A, B, C, mode, s));

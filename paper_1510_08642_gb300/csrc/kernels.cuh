@@ -3,10 +3,28 @@
 
 #include <atomic>
 #include <cstdint>
+#include <cstdio>
 #include <string>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace ddg {
+
+// NVTX range over a scope of host code that issues work (a product, a
+// recursion level, a fused pass, a CRT stage, an LU phase); a no-op unless
+// a profiler that records NVTX is attached.
+struct nvtx_range {
+  explicit nvtx_range(const char* name) { nvtxRangePushA(name); }
+  template <class... Args>
+  nvtx_range(const char* fmt, Args... args) {
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), fmt, args...);
+    nvtxRangePushA(buf);
+  }
+  ~nvtx_range() { nvtxRangePop(); }
+  nvtx_range(const nvtx_range&) = delete;
+  nvtx_range& operator=(const nvtx_range&) = delete;
+};
 
 // A matrix of L limb planes (L = 2 for DD, 4 for QD), each row-major with
 // leading dimension ld (in doubles). Unused plane pointers are null.

@@ -960,6 +960,7 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
   std::function<void(int64_t, int64_t)> panel = [&](int64_t c0, int64_t w) {
     if (st != DDG_OK || w <= 0) return;
     if (w <= PANEL_BASE) {
+      nvtx_range nv("ddg.getrf panel %lld", (long long)c0);
       const int64_t pe = c0 + w;
       const int64_t prow = n - c0;
       const int64_t R = std::max<int64_t>(8, (prow + gmax - 1) / gmax);
@@ -1011,6 +1012,7 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
     st = trsm_lower_unit<L>(kb, rest, view(M, j0, j0), view(M, j0, pe), s);
     if (st != DDG_OK) break;
     // Section 4 step 3: A22 := A22 - L21 U12
+    nvtx_range nv("ddg.getrf trailing update %lld", (long long)pe);
     st = gemm_run(L, rest, kb, rest, view(M, pe, j0), view(M, j0, pe), view(M, pe, pe), MODE_SUB, o, s);
   }
   int64_t hinfo = 0;

@@ -731,6 +731,7 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
   set_gemm_attrs();
   cudaEvent_t ev = nullptr;
   auto launched = [&]() { g_launches.fetch_add(1, std::memory_order_relaxed); };
+  nvtxRangePushA(tc ? "ddg.crt split (bf16)" : "ddg.crt split (int8)");
   oz_exp_kernel<<<(unsigned)((m + 7) / 8), 256, 0, st>>>(m, l, A, 1, exa);
   launched();
   oz_exp_kernel<<<(unsigned)((n + 31) / 32), 256, 0, st>>>(l, n, B, 0, exb);
@@ -745,6 +746,8 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
     oz_split_b_kernel<2, true, __nv_bfloat16><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, N, P, npad, lpad, Bs);
     launched();
     e = cudaGetLastError();
+    nvtxRangePop();
+    nvtx_range nv("ddg.crt residue products (tcgen05) N %d", N);
     if (e == cudaSuccess) e = launch_crt_tc(N, mpad, npad, lpad, As, Bs, R, st);
   } else {
     int8_t* As = reinterpret_cast<int8_t*>(base);
@@ -753,6 +756,8 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
     launched();
     oz_split_b_kernel<2, true><<<gb, dim3(32, 8), 0, st>>>(l, n, B, exb, N, P, npad, lpad, Bs);
     launched();
+    nvtxRangePop();
+    nvtx_range nv("ddg.crt residue products (int8) N %d", N);
     prof_begin_launch(st, &ev);
     oz_gemm_kernel<true><<<dim3((unsigned)(npad / OBN), (unsigned)(mpad / OBM), (unsigned)N), 256, OZ_SMEM, st>>>(
         mpad, npad, lpad, N, As, Bs, nullptr, R);
@@ -763,6 +768,7 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
                       (double)N * (mpad + npad) * lpad + (double)N * mpad * npad);
   }
   if (e == cudaSuccess) {
+    nvtx_range nv2("ddg.crt reconstruction");
     const dim3 gr((unsigned)((n + 255) / 256), (unsigned)m);
     oz_crt_recombine_kernel<<<gr, 256, 0, st>>>(m, n, N, P, mpad, npad, R, exa, exb, C, mode, cc);
     launched();

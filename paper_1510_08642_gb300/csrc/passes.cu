@@ -228,6 +228,7 @@ static void launch_grouped_kind(int kind, unsigned grid, cudaStream_t s, const p
 cudaError_t launch_grouped_pass(int limbs, int kind, const ptask* tasks, int ntasks, int64_t total_tiles,
                                 cudaStream_t s) {
   if (ntasks == 0 || total_tiles == 0) return cudaSuccess;
+  nvtx_range nv("ddg.grouped pass kind %d", kind);
   const unsigned grid = (unsigned)std::min<int64_t>(total_tiles, 152 * 16);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (limbs == 2) launch_grouped_kind<2>(kind, grid, s, tasks, ntasks, total_tiles);
@@ -238,6 +239,7 @@ cudaError_t launch_grouped_pass(int limbs, int kind, const ptask* tasks, int nta
 cudaError_t launch_pass(int limbs, int kind, int64_t rows, int64_t cols, const mat* in, int nin,
                         const mat* out, int nout, int mode, cudaStream_t s) {
   if (rows == 0 || cols == 0) return cudaSuccess;
+  nvtx_range nv("ddg.pass kind %d %lldx%lld", kind, (long long)rows, (long long)cols);
   pass_args a{};
   for (int q = 0; q < nin && q < 7; ++q) a.in[q] = in[q];
   for (int q = 0; q < nout && q < 5; ++q) a.out[q] = out[q];

@@ -30,3 +30,27 @@ def test_candidates_split_at_least_once():
     t = autotune.Tuner("/nonexistent/x.json")
     c = t.candidates(300, 300, 300)
     assert ("block", 512) in c and ("winograd", 256) in c and ("winograd", 512) not in c
+
+
+def test_product_candidates_and_fallback():
+    t = autotune.Tuner("/nonexistent/x.json")
+    c = t.product_candidates(2, 600, 600, 600)
+    algos = {(x["algo"], x["accum"]) for x in c}
+    assert ("block", "fx") in algos and ("block", "fx_tile") in algos and ("winograd", "fx") in algos
+    assert all(x["algo"] != "ozaki2_tc" for x in c)  # elementwise class by default
+    assert t.choose_product(2, 4096, 4096, 4096) == dict(algo="winograd", cutoff=256, accum="fx", slices=0)
+    t.table[t._pkey(2, 1024, 1024, 1024, True, 104)] = dict(algo="ozaki2_tc", cutoff=512, accum="fx",
+                                                           slices=31, seconds=1e-3)
+    assert t.choose_product(2, 1000, 1100, 1024, allow_normwise=True)["slices"] == 31
+    assert t.choose_product(2, 1000, 1100, 1024)["algo"] != "ozaki2_tc"
+
+
+def test_moduli_for_meets_the_precision():
+    """The fewest moduli whose scaling precision P >= bits + ceil(log2 l),
+    against the library's own P (the C ABI, no GPU needed)."""
+    from paper_1510_08642_gb300 import capi
+    for l, bits in ((64, 100), (1024, 104), (4096, 104), (65536, 100)):
+        N = autotune.moduli_for(l, bits)
+        need = bits + (l - 1).bit_length()
+        assert N >= 2 and capi.ddg_ozaki2_precision(N, l) >= need
+        assert capi.ddg_ozaki2_precision(N - 1, l) < need
