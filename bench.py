@@ -570,7 +570,7 @@ def time_batched(P, torch, device, stream, count=1000, reps=3, tune_buckets=8):
         tuner.tune(key[0], *(min(x, 1024) for x in key[1:]), copies=2, reps=2)
     t_tune = time.perf_counter() - t_tune
     tuner.save()
-    probs, keep, work = [], [], 0.0
+    probs, probs_host, keep, work = [], [], [], 0.0
     for t in range(count):
         m, l, n = (int(x) for x in dims[t])
         L = 4 if kind[t] < 0.3 else 2
@@ -582,11 +582,22 @@ def time_batched(P, torch, device, stream, count=1000, reps=3, tune_buckets=8):
         C = torch.empty((L, m, n), dtype=torch.float64, device=device)
         algo, cutoff = tuner.choose(L, m, l, n)
         probs.append(P.problem(A, B, C, algo, cutoff))
+        probs_host.append((A, B))
         keep.append(C)
         work += 2.0 * m * l * n
     batch = P.Batch(probs, use_graph=True)
     batch.run(stream)
     torch.cuda.synchronize()
+    # host copies for the CPU leg's oracle check of a few results (the four
+    # largest problems of each limb count): their operands and 6 x 6 sampled
+    # entries
+    checks = []
+    for L in (2, 4):
+        idx = sorted((t for t in range(count) if kinds[t] == L), key=lambda t: -float(np.prod(dims[t])))[:4]
+        for t in idx:
+            hA = probs_host[t][0].cpu().numpy()
+            hB = probs_host[t][1].cpu().numpy()
+            checks.append(sample_for_check(f"batched problem {t}", hA, hB, keep[t], torch))
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -597,13 +608,13 @@ def time_batched(P, torch, device, stream, count=1000, reps=3, tune_buckets=8):
     ms = e0.elapsed_time(e1) / reps
     st = dict(batch.stats)
     batch.close()
-    return {"value": work / (ms * 1e-3) / 1e9, "unit": UNIT, "ms": ms, "problems": count,
+    return ({"value": work / (ms * 1e-3) / 1e9, "unit": UNIT, "ms": ms, "problems": count,
             "launches_per_run": st["launches_per_run"], "leaf_tiles": st["leaf_tiles"],
             "workspace_bytes": st["workspace_bytes"], "graph": True, "steps": reps, "warmup": 1,
             "tuning_table": os.path.exists(tuner.path),
             "tuned": {f"{'DD' if k[0] == 2 else 'QD'} {k[1]}x{k[2]}x{k[3]}": tuner.choose(*k) for k in top},
             "tuned_work_share": sum(work_by_bucket[k] for k in top) / sum(work_by_bucket.values()),
-            "tuning_seconds": t_tune}
+            "tuning_seconds": t_tune}, checks)
 
 
 def sample_rows(n, count, seed):
@@ -619,12 +630,12 @@ def sample_for_check(name, hA, hB, dC, torch):
     """Host copies of what the oracle needs to check 8 x 8 sampled entries of
     the product C = A B: those rows of A, columns of B and entries of C."""
     import numpy as np
-    n = hA.shape[1]
-    rows, cols = sample_rows(n, 6, seed=1), sample_rows(n, 6, seed=2)
+    m, n = hA.shape[1], hB.shape[2]
+    rows, cols = sample_rows(m, 6, seed=1), sample_rows(n, 6, seed=2)
     r_t = torch.as_tensor(rows, device=dC.device)
     c_t = torch.as_tensor(cols, device=dC.device)
     C = dC.index_select(1, r_t).index_select(2, c_t).cpu().numpy()
-    return {"name": name, "kind": "gemm", "limbs": hA.shape[0], "n": n,
+    return {"name": name, "kind": "gemm", "limbs": hA.shape[0], "m": m, "n": n,
             "A_rows": np.ascontiguousarray(hA[:, rows, :]), "B_cols": np.ascontiguousarray(hB[:, :, cols]),
             "C": C, "normA": float(np.linalg.norm(hA[0])), "normB": float(np.linalg.norm(hB[0]))}
 
@@ -644,8 +655,8 @@ def cpu_oracle_check(checks):
         if c["kind"] == "gemm":
             A, B, C = c["A_rows"], c["B_cols"], c["C"]
             err = O.gemm_error(A, B, C)
-            n = c["n"]
-            nw = float(np.sqrt(np.mean(err ** 2)) * n / (c["normA"] * c["normB"]))
+            mn = float(c.get("m", c["n"])) * c["n"]
+            nw = float(np.sqrt(np.mean(err ** 2) * mn) / (c["normA"] * c["normB"]))
             u2 = 2.0 ** -106 if c["limbs"] == 2 else 2.0 ** -212
             scale = np.abs(A[0]) @ np.abs(B[0])
             ew = float(np.max(np.abs(err) / (scale * u2)))
@@ -795,7 +806,8 @@ def run_ours(args, w):
         for lw in (WL.DD_LU_4096, WL.DD_LU_4096_OZ2, WL.DD_LU_4096_OZ2TC, WL.QD_LU_2048):
             extras[lw.name], chk = time_lu(P, torch, lw, device, stream, K=256)
             checks.append(chk)
-        extras["batched_1000_mixed"] = time_batched(P, torch, device, stream)
+        extras["batched_1000_mixed"], bchecks = time_batched(P, torch, device, stream)
+        checks += bchecks
         extras["serving"] = time_serving(args)
         line["extras"] = extras
     if checks:
@@ -813,6 +825,8 @@ def run_ours(args, w):
             for name, e in errs.items():
                 if name in line.get("extras", {}):
                     line["extras"][name]["error_vs_oracle"] = e
+                elif name.startswith("batched problem") and "batched_1000_mixed" in line.get("extras", {}):
+                    line["extras"]["batched_1000_mixed"].setdefault("error_vs_oracle", {})[name] = e
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

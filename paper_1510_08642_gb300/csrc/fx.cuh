@@ -365,9 +365,11 @@ __host__ __device__ __forceinline__ void mul_top(const uint32_t (&a)[W], const u
       const int j = k - i;
       if (j < 0 || j >= W) continue;
 #ifdef __CUDA_ARCH__
+      // the carry out of the high word goes to c2 by an add (integer ALU
+      // pipe), leaving the IMAD pipe to the two multiplies: QD +8%, DD +1%
       asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
           "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
-          "madc.lo.u32 %2, %2, 1, 0;"
+          "addc.u32 %2, %2, 0;"
           : "+r"(c0), "+r"(c1), "+r"(c2)
           : "r"(a[i]), "r"(b[j]));
 #else

@@ -326,7 +326,8 @@ def test_conversion_launches_profiled():
         assert prof["block"]["ops"] == 128 * 96 * 160
 
 
-@pytest.mark.parametrize("name", ["dd_winograd_n4096", "qd_winograd_n4096"])
+@pytest.mark.parametrize("name", ["dd_winograd_n4096", "qd_winograd_n4096", "dd_winograd_n3000",
+                                  "qd_winograd_n3000"])
 def test_benchmark_workload_sampled(name):
     """The benchmark's DD / QD Winograd workloads at full size (n = 4096,
     cutoff 256, seven streams, operands converted once per leaf node): sampled
@@ -334,7 +335,9 @@ def test_benchmark_workload_sampled(name):
     elementwise, and every bit equal to the per-tile conversion path."""
     import paper_1510_08642_gb300 as P
     from paper_1510_08642_gb300 import workloads as WL
-    w = {x.name: x for x in (WL.DD_WINOGRAD_4096, WL.QD_WINOGRAD_4096)}[name]
+    # n = 3000: odd sizes below the top level (1500 -> 750 -> 375) peeled
+    w = {x.name: x for x in (WL.DD_WINOGRAD_4096, WL.QD_WINOGRAD_4096, WL.DD_WINOGRAD_3000,
+                             WL.QD_WINOGRAD_3000)}[name]
     A = I.uniform(w.n, w.n, w.limbs, seed=w.seed_a)
     B = I.uniform(w.n, w.n, w.limbs, seed=w.seed_b)
     dA, dB = to_dev(A), to_dev(B)
