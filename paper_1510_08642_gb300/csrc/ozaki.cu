@@ -449,6 +449,7 @@ struct crt_consts {
   uint32_t M[CRT_NW];
   uint32_t halfM[CRT_NW];        // floor(M / 2)
   double inv_scaled;             // 2^(32 (wt - 2)) / M
+  float inv_scaled_f;            // the same in FP32 (the quotient estimate)
   int wt;                        // highest word of sum_t r_t c_t that can be nonzero (>= 2)
 };
 
@@ -494,8 +495,12 @@ __global__ void oz_crt_recombine_kernel(int64_t m, int64_t n, int N, int P, int6
     s1 = k == cc.wt - 1 ? S[k] : s1;
     s0 = k == cc.wt - 2 ? S[k] : s0;
   }
-  const double sd = __fma_rn((double)s2, 18446744073709551616.0, __fma_rn((double)s1, 4294967296.0, (double)s0));
-  const uint32_t q = (uint32_t)floor(__dmul_rn(sd, cc.inv_scaled));
+  // q < N 2^8 <= 2^14: in FP32 (relative error a few 2^-24, so q is off by
+  // less than 2^-8 before the floor, i.e. at most one either way, which the
+  // correction below absorbs; all three words count when M is small)
+  const float sf = __fmaf_rn(__fmaf_rn(__uint2float_rn(s2), 4294967296.0f, __uint2float_rn(s1)), 4294967296.0f,
+                             __uint2float_rn(s0));
+  const uint32_t q = (uint32_t)floorf(__fmul_rn(sf, cc.inv_scaled_f));
   // Z = S - q M
   uint32_t Z[CRT_NW];
   unsigned long long pc = 0ull;
@@ -540,17 +545,32 @@ __global__ void oz_crt_recombine_kernel(int64_t m, int64_t n, int N, int P, int6
   const uint32_t neg = fx::acc_abs<CRT_NW>(Z);
   uint64_t ch[2];
   int ex[2];
-  double x[2] = {0.0, 0.0};
+  dd_t v{0.0, 0.0};
   if (fx::acc_chunks<CRT_NW, 2>(Z, ch, ex)) {
+    const int e0 = lsb + ex[0];  // chunk 0 in [2^52, 2^53) at 2^e0, chunk 1 at 2^(e0 - 53)
+    if (e0 >= -1000 && e0 <= 960) {
+      // two_sum(chunk 0, chunk 1) on the integer pipe: the head rounded to
+      // nearest (ties to even) at 2^e0, the remainder exact; the same bits
+      uint64_t h = ch[0];
+      int64_t lo = (int64_t)ch[1];
+      const uint64_t half = 1ull << 52;
+      if (ch[1] > half || (ch[1] == half && (h & 1ull))) {
+        h += 1ull;
+        lo -= (int64_t)1 << 53;
+      }
+      v.hi = fx::make_double(h, e0, neg);
+      v.lo = lo == 0 ? 0.0 : fx::make_double((uint64_t)(lo < 0 ? -lo : lo), e0 - 53, neg ^ (lo < 0 ? 1u : 0u));
+    } else {
+      double x[2];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int e = lsb + ex[k];
-      double v = (ch[k] == 0 || e < -2044) ? 0.0 : fx::pow2_product(__ull2double_rn(ch[k]), e > 2046 ? 2046 : e);
-      x[k] = neg ? -v : v;
+      for (int k = 0; k < 2; ++k) {
+        const int e = lsb + ex[k];
+        double w = (ch[k] == 0 || e < -2044) ? 0.0 : fx::pow2_product(__ull2double_rn(ch[k]), e > 2046 ? 2046 : e);
+        x[k] = neg ? -w : w;
+      }
+      two_sum(x[0], x[1], v.hi, v.lo);
     }
   }
-  dd_t v;
-  two_sum(x[0], x[1], v.hi, v.lo);
   const int64_t off = i * C.ld + j;
   if (mode == MODE_ADD) v = Nm::add(Nm::load(C.p, off), v);
   else if (mode == MODE_SUB) v = Nm::add(Nm::load(C.p, off), Nm::neg(v));
@@ -636,6 +656,7 @@ static int crt_precision(int N, int64_t l, crt_consts* cc) {
     double md = 0.0;
     for (int k = CRT_NW - 1; k >= 0; --k) md = md * 4294967296.0 + (double)M[k];
     cc->inv_scaled = std::ldexp(1.0 / md, 32 * (cc->wt - 2));
+    cc->inv_scaled_f = (float)cc->inv_scaled;
   }
   return P;
 }
