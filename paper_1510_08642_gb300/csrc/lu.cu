@@ -42,6 +42,12 @@ constexpr int RB = 8;        // rows per CTA in the column kernels (many CTAs: t
 constexpr int TB = 32;       // triangle size of the substitution base case (one warp)
 constexpr int KMAX = 512;    // widest block column
 constexpr int PANEL_BASE = 16;  // widest panel factored column by column
+// DD column steps (quotients and rank-1 updates of a panel): the exact
+// fixed-point form on the integer pipe, as for QD (false), or the DD
+// sequences on the FP64 pipe (true). The FP64 pipe retires 2 instructions
+// per clock per SM, so with the panel's rows spread over all SMs in one
+// launch the integer form is the faster one.
+constexpr bool kDDColumnFP64 = false;
 
 // Pivot candidates compare by integer keys of |x| (leading limb magnitude,
 // then the second limb with the leading limb's sign): no FP64 compare
@@ -272,9 +278,8 @@ __global__ void __launch_bounds__(256) lu_col_kernel(int64_t n, mat A, int64_t c
   const int64_t r0 = j + 1 + (int64_t)blockIdx.x * RB;
   const int rows = (int)(n - r0 < RB ? n - r0 : RB);
   const int cols = (int)(pe - j - 1);
-  if constexpr (L == 2) {
-    // DD: the FP64 sequences are short (7 + 20 instructions per update)
-    // and beat the fixed-point form here
+  if constexpr (L == 2 && kDDColumnFP64) {
+    // DD on the FP64 pipe (7 + 20 instructions per update)
     using T = typename N::T;
     __shared__ T u[PANEL_BASE];
     __shared__ T lq[RB];
@@ -552,7 +557,7 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t
     const bool zero = is_zero<L>(rinv);
     const int cols = w - jc - 1;
     if (!zero) {
-      if constexpr (L == 2) {
+      if constexpr (L == 2 && kDDColumnFP64) {
         for (int r = tid; r < nr; r += blockDim.x) {
           T l = N::zero();
           if (r_lo + r > j) {
