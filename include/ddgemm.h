@@ -366,6 +366,21 @@ uint64_t ddg_kernel_launches(void);
  * reset != 0 sets the count back to 0. -1 if it cannot be read. */
 int32_t ddg_device_timeouts(int32_t reset);
 
+/* Test support (no counterpart in the paper): run one of the library's
+ * bounded device waits on a barrier that nothing completes, so that a test
+ * can check that the wait gives up, the kernel returns and the host reads
+ * the status, with no GPU fault, trap or hang. Synchronous (waits for the
+ * device; about a second).
+ *   which = 0: one CTA of the DDG_OZAKI2_TC tensor-core kernel with its TMA
+ *              producer idle: the MMA thread's wait on the first stage runs
+ *              out; ddg_device_timeouts() then counts it.
+ *   which = 1: one LU panel launch whose grid barrier expects one arrival
+ *              more than there are CTAs: every CTA's wait runs out and the
+ *              factorisation status (info) becomes -1.
+ * Returns DDG_ETIMEOUT when the wait ran out as intended, DDG_OK if it did
+ * not, DDG_EINVAL for another `which`, DDG_ECUDA / DDG_ENOMEM on errors. */
+ddg_status ddg_test_bounded_wait(int32_t which);
+
 /* Message describing the last failure on this host thread ("" if none). */
 const char* ddg_last_error(void);
 

@@ -98,6 +98,7 @@ SIGNATURES = {
     "ddg_last_error": (ctypes.c_char_p, []),
     "ddg_kernel_launches": (ctypes.c_uint64, []),
     "ddg_device_timeouts": (c_i32, [c_i32]),
+    "ddg_test_bounded_wait": (c_i32, [c_i32]),
     "ddg_profile_begin": (c_i32, []),
     "ddg_profile_end": (c_i32, [ctypes.POINTER(ddg_kernel_prof), c_i32]),
 }
@@ -179,6 +180,10 @@ def ddg_kernel_launches() -> int:
 
 def ddg_device_timeouts(reset: bool = False) -> int:
     return load().ddg_device_timeouts(1 if reset else 0)
+
+
+def ddg_test_bounded_wait(which: int) -> int:
+    return load().ddg_test_bounded_wait(which)
 
 
 def ddg_profile_begin() -> None:

@@ -566,6 +566,18 @@ const char* ddg_last_error(void) { return ddg::g_err.c_str(); }
 
 uint64_t ddg_kernel_launches(void) { return ddg::g_launches.load(std::memory_order_relaxed); }
 
+ddg_status ddg_test_bounded_wait(int32_t which) {
+  ddg::clear_error();
+  if (which == 0) {
+    const cudaError_t e = ddg::crt_tc_wait_test();
+    if (e != cudaSuccess) return ddg::set_error(DDG_ECUDA, std::string("wait test: ") + cudaGetErrorString(e));
+    return ddg::crt_tc_timeouts(false) > 0 ? ddg::set_error(DDG_ETIMEOUT, "tensor-core wait ran out (as intended)")
+                                           : DDG_OK;
+  }
+  if (which == 1) return ddg::lu_panel_wait_test();
+  return ddg::set_error(DDG_EINVAL, "ddg_test_bounded_wait: which must be 0 or 1");
+}
+
 int32_t ddg_device_timeouts(int32_t reset) {
   if (cudaDeviceSynchronize() != cudaSuccess) return -1;
   return ddg::crt_tc_timeouts(reset != 0);

@@ -231,6 +231,8 @@ ddg_status ozaki_crt_gemm(int64_t m, int64_t l, int64_t n, const mat& A, const m
 cudaError_t launch_crt_tc(int N, int64_t mpad, int64_t npad, int64_t lpad, const void* As, const void* Bs,
                           uint8_t* R, cudaStream_t st);
 int crt_tc_timeouts(bool reset);
+cudaError_t crt_tc_wait_test();     // test support (ozaki_tc.cu)
+ddg_status lu_panel_wait_test();    // test support (lu.cu)
 int ozaki_crt_precision(int N, int64_t l);
 
 // DD / QD product by INT8 slices (Ozaki scheme), s slices (ozaki.cu).

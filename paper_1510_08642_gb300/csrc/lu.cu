@@ -462,7 +462,7 @@ __device__ __forceinline__ partial_t get_cand(const partial_t* p) {
 template <int L>
 __global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t c0, int64_t pe, int64_t R,
                                                        int64_t* ipiv, int64_t* info, int pivot, pub_t* pub,
-                                                       double* rowj, panel_sync* ps) {
+                                                       double* rowj, panel_sync* ps, int extra) {
   using N = num<L>;
   using T = typename N::T;
   constexpr int W = tfx<L>::W, D = tfx<L>::D, K = tfx<L>::K, NW = tfx<L>::NW;
@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t
   const int tid = threadIdx.x, nw = blockDim.x >> 5;
   const int w = (int)(pe - c0);
   const unsigned int G = gridDim.x;
+  const unsigned int arrivals = G + (unsigned int)extra;  // extra > 0 only in the wait test
   const int64_t r_lo = c0 + (int64_t)blockIdx.x * R;
   const int64_t left = n - r_lo;
   const int nr = left <= 0 ? 0 : (int)(left < R ? left : R);
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t
     }
     if (tid == 0) slot[blockIdx.x].c = v;
     if (j >= r_lo && j < r_lo + nr) put_row<L>(rj, rows[j - r_lo], w);
-    if (!panel_barrier(ps, gen, G, info)) return;
+    if (!panel_barrier(ps, gen, arrivals, info)) return;
     // ---- the pivot: the best of the G candidates (a strict order: every
     // CTA picks the same), or row j without pivoting
     partial_t b = none();
@@ -972,10 +973,10 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
       if (fused_ok && R <= PR_MAX) {
         const unsigned G = (unsigned)((prow + R - 1) / R);
         int64_t nn = n, cc0 = c0, ppe = pe, RR = R;
-        int piv = pivot;
+        int piv = pivot, extra = 0;
         mat MM = M;
         int64_t* ip = ipiv;
-        void* args[] = {&nn, &MM, &cc0, &ppe, &RR, &ip, &dinfo, &piv, &pub, &rowj, &psync};
+        void* args[] = {&nn, &MM, &cc0, &ppe, &RR, &ip, &dinfo, &piv, &pub, &rowj, &psync, &extra};
         cu(cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<L>, dim3(G), dim3(256), args, 0, s));
         if (pivot && st == DDG_OK) {
           lu_laswp_kernel<L><<<dim3((unsigned)((n + 127) / 128), L), 128, 0, s>>>(n, M, c0, pe, ipiv);
@@ -1032,6 +1033,38 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
   if (st == DDG_OK && hinfo != 0)
     return set_error(DDG_ESINGULAR, nm + ": exactly zero pivot in column " + std::to_string(hinfo - 1));
   return st;
+}
+
+// Test support: one panel of a 64 x 64 DD matrix in 8 CTAs whose grid
+// barrier expects one arrival more than there are CTAs, so that every CTA's
+// bounded wait runs out; synchronous. DDG_ETIMEOUT when info came back -1.
+ddg_status lu_panel_wait_test() {
+  const int64_t n = 64;
+  char* buf = nullptr;
+  const size_t mat_bytes = 2 * n * n * sizeof(double);
+  const size_t bytes = mat_bytes + n * sizeof(int64_t) + 64 + 2 * 8 * sizeof(pub_t) + 2 * PANEL_BASE * 4 * 8 + 64;
+  if (cudaMalloc(&buf, bytes) != cudaSuccess) return set_error(DDG_ENOMEM, "wait test: allocation failed");
+  cudaMemset(buf, 0, bytes);
+  mat M{};
+  M.p[0] = reinterpret_cast<double*>(buf);
+  M.p[1] = M.p[0] + n * n;
+  M.ld = n;
+  int64_t* ipiv = reinterpret_cast<int64_t*>(buf + mat_bytes);
+  int64_t* info = ipiv + n;
+  pub_t* pub = reinterpret_cast<pub_t*>(buf + mat_bytes + n * sizeof(int64_t) + 64);
+  double* rowj = reinterpret_cast<double*>(reinterpret_cast<char*>(pub) + 2 * 8 * sizeof(pub_t));
+  panel_sync* ps = reinterpret_cast<panel_sync*>(rowj + 2 * PANEL_BASE * 4);
+  int64_t nn = n, c0 = 0, pe = PANEL_BASE, R = 8;
+  int piv = 1, extra = 1;
+  void* args[] = {&nn, &M, &c0, &pe, &R, &ipiv, &info, &piv, &pub, &rowj, &ps, &extra};
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<2>, dim3(8), dim3(256), args, 0, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int64_t h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, info, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return set_error(DDG_ECUDA, std::string("wait test: ") + cudaGetErrorString(e));
+  return h < 0 ? set_error(DDG_ETIMEOUT, "panel barrier wait ran out (as intended)") : DDG_OK;
 }
 
 template <int L>

@@ -179,6 +179,7 @@ struct tc_args {
   int N;               // moduli
   uint8_t* R;          // residues of the product: N planes of mpad x npad bytes
   int* timeouts;       // incremented by a CTA whose wait ran out
+  int idle_producer;   // test support: 1 = the TMA producer issues nothing
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (warp == 0) {
     // ---------------------------------------------------------- producer
-    if (lane == 0) {
+    if (lane == 0 && !g.idle_producer) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
       int stage = 0;
@@ -428,7 +429,7 @@ cudaError_t launch_crt_tc(int N, int64_t mpad, int64_t npad, int64_t lpad, const
   int* timeouts = nullptr;
   cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&timeouts), g_tc_timeouts);
   if (e != cudaSuccess) return e;
-  tc_args a{mpad / TBM, npad / TBN, mpad, npad, (int)(lpad / TBK), N, R, timeouts};
+  tc_args a{mpad / TBM, npad / TBN, mpad, npad, (int)(lpad / TBK), N, R, timeouts, 0};
   const int64_t tiles = a.mt * a.nt * N;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms);
   g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -439,6 +440,36 @@ cudaError_t launch_crt_tc(int N, int64_t mpad, int64_t npad, int64_t lpad, const
   if (ev)
     prof_end_launch(st, ev, PROF_TENSOR, 2.0 * N * (double)mpad * (double)npad * (double)lpad,
                     2.0 * N * (mpad + npad) * (double)lpad + (double)N * mpad * npad);
+  return e;
+}
+
+// Test support: one CTA of the kernel on a 128 x 64 x 256 problem with its
+// TMA producer idle, so that the MMA thread's wait on the first stage runs
+// out; synchronous. Returns the CUDA status of the launch and the wait.
+cudaError_t crt_tc_wait_test() {
+  __nv_bfloat16 *a = nullptr, *b = nullptr;
+  uint8_t* r = nullptr;
+  cudaError_t e = cudaMalloc(&a, 128 * 64 * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&b, TBN * 64 * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&r, 128 * TBN);
+  if (e == cudaSuccess) e = cudaMemset(a, 0, 128 * 64 * 2);
+  if (e == cudaSuccess) e = cudaMemset(b, 0, TBN * 64 * 2);
+  CUtensorMap ma, mb;
+  if (e == cudaSuccess && (!make_map(&ma, a, 128, 64) || !make_map(&mb, b, TBN, 64))) e = cudaErrorInvalidValue;
+  int* timeouts = nullptr;
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(reinterpret_cast<void**>(&timeouts), g_tc_timeouts);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  if (e == cudaSuccess) {
+    tc_args t{1, 1, 128, TBN, 1, 1, r, timeouts, 1};
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    crt_tc_kernel<<<1, TC_THREADS, TC_SMEM>>>(ma, mb, t);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  cudaFree(a);
+  cudaFree(b);
+  cudaFree(r);
   return e;
 }
 
