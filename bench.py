@@ -908,10 +908,25 @@ def run_lu_alpha_sweep(args):
     return 0
 
 
+def run_batched_only(args):
+    """The batched workload alone (tuning, one plan, timed replays)."""
+    import torch
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    import paper_1510_08642_gb300 as P
+    from paper_1510_08642_gb300 import capi
+    capi.load()
+    r, _ = time_batched(P, torch, device, torch.cuda.current_stream(device), reps=args.steps)
+    print(json.dumps({"workload": "batched_1000_mixed", **r}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.record_counts:
         return record_counts(args)
+    if args.workload == "batched_1000_mixed":
+        return run_batched_only(args)
     if args.workload == "lu_alpha_sweep":
         return run_lu_alpha_sweep(args)
     w = workload_by_name(args.workload)
