@@ -26,7 +26,11 @@
 #include <algorithm>
 #include <cstdlib>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <string>
+
+#include <cooperative_groups.h>
 
 #include "arith.cuh"
 #include "fx.cuh"
@@ -34,6 +38,8 @@
 #include "kernels.cuh"
 
 namespace ddg {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -459,14 +465,129 @@ __device__ __forceinline__ partial_t get_cand(const partial_t* p) {
   return partial_t{__ldcg(&p->kh), __ldcg(&p->kl), (int64_t)__ldcg(reinterpret_cast<const long long*>(&p->idx))};
 }
 
+// One column step of a panel held in shared memory: the quotients
+// l_ij = a_ij (1 / a_jj) of this CTA's rows below j and the rank-1 update of
+// their columns (j, w), with the per-column kernels' arithmetic (exact
+// fixed-point form on the integer pipe). rows: nr rows starting at global row
+// r_lo; prow: the pivot row; scratch in shared memory.
+template <int L>
+struct panel_scratch {
+  typename num<L>::T* lq;
+  uint32_t (*lw)[tfx<L>::W];
+  int* le;
+  int* ls;
+  uint32_t (*uw)[tfx<L>::W];
+  int* ue;
+};
+
+template <int L>
+__device__ __forceinline__ void panel_column_step(typename num<L>::T (*rows)[PANEL_BASE], int nr, int64_t r_lo,
+                                                  int64_t j, int jc, int w, const typename num<L>::T* prow,
+                                                  const typename num<L>::T rinv, const panel_scratch<L>& sc) {
+  using N = num<L>;
+  using T = typename N::T;
+  constexpr int W = tfx<L>::W, D = tfx<L>::D, K = tfx<L>::K, NW = tfx<L>::NW;
+  constexpr int TOPW = 32 * W - 53;
+  const int tid = threadIdx.x;
+  T* lq = sc.lq;
+  uint32_t (*lw)[W] = sc.lw;
+  uint32_t (*uw)[W] = sc.uw;
+  int *le = sc.le, *ls = sc.ls, *ue = sc.ue;
+  (void)lq;
+  const bool zero = is_zero<L>(rinv);
+  const int cols = w - jc - 1;
+  if (!zero) {
+    if constexpr (L == 2 && kDDColumnFP64) {
+      for (int r = tid; r < nr; r += blockDim.x) {
+        T l = N::zero();
+        if (r_lo + r > j) {
+          l = N::mul(rows[r][jc], rinv);
+          rows[r][jc] = l;
+        }
+        lq[r] = l;
+      }
+      __syncthreads();
+      for (int e = tid; e < nr * cols; e += blockDim.x) {
+        const int r = e / cols, c = jc + 1 + e % cols;
+        if (r_lo + r > j) rows[r][c] = N::add(rows[r][c], N::mul(N::neg(lq[r]), prow[c]));
+      }
+    } else {
+      for (int r = tid; r < nr; r += blockDim.x) {
+        le[r] = -1;
+        const T a = rows[r][jc];
+        if (r_lo + r > j && !is_zero<L>(a)) {
+          const double* ax = reinterpret_cast<const double*>(&a);
+          const double* rx = reinterpret_cast<const double*>(&rinv);
+          double av[L], rv[L];
+#pragma unroll
+          for (int q = 0; q < L; ++q) av[q] = ax[q], rv[q] = rx[q];
+          uint32_t Ma[W], Mr[W], P[K], Ml[W];
+          const int ea = fx::to_fixed<L, W>(av, Ma), er = fx::to_fixed<L, W>(rv, Mr);
+          fx::mul_top<W, D>(Ma, Mr, P);
+          const int pp = fx::acc_normalize<K, W>(P, Ml);
+          const int el = pp + (ea & 0xFFFF) + (er & 0xFFFF) - 1075 - 2 * TOPW + 32 * D - 52;
+          const int sl = ((ea ^ er) >> 16) & 1;
+          double o[L];
+          fx::operand_to_limbs<L, W>(Ml, el, (uint32_t)sl, o);
+          T lv;
+          double* lx = reinterpret_cast<double*>(&lv);
+#pragma unroll
+          for (int q = 0; q < L; ++q) lx[q] = o[q];
+          rows[r][jc] = lv;
+#pragma unroll
+          for (int t = 0; t < W; ++t) lw[r][t] = Ml[t];
+          le[r] = el;
+          ls[r] = sl;
+        }
+      }
+      for (int c = tid; c < cols; c += blockDim.x) {
+        const double* ux = reinterpret_cast<const double*>(&prow[jc + 1 + c]);
+        double u[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) u[q] = ux[q];
+        uint32_t M[W];
+        const int es = fx::to_fixed<L, W>(u, M);
+#pragma unroll
+        for (int t = 0; t < W; ++t) uw[c][t] = M[t];
+        ue[c] = (fx::dbits(u[0]) << 1) == 0u ? -1 : es;
+      }
+      __syncthreads();
+      for (int e = tid; e < nr * cols; e += blockDim.x) {
+        const int r = e / cols, c = e % cols;
+        if (le[r] < 0 || ue[c] < 0) continue;  // l = 0 or u = 0: nothing to subtract
+        const double* ax = reinterpret_cast<const double*>(&rows[r][jc + 1 + c]);
+        double a[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) a[q] = ax[q];
+        int Aw = max(1, fx::expfield(a[0]));
+        uint32_t acc[NW];
+#pragma unroll
+        for (int t = 0; t < NW; ++t) acc[t] = 0u;
+        fx::add_at<L, NW>(acc, a, Aw, tfx<L>::TOPA, 0u);
+        uint32_t Ml[W], Mu[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+          Ml[t] = lw[r][t];
+          Mu[t] = uw[c][t];
+        }
+        window_sub_product<L>(acc, Aw, Ml, le[r], (uint32_t)ls[r], Mu, ue[c] & 0xFFFF, (uint32_t)ue[c] >> 16);
+        double o[L];
+        fx::from_fixed<L, NW>(acc, Aw - 1075 - tfx<L>::TOPA, o);
+        double* dx = reinterpret_cast<double*>(&rows[r][jc + 1 + c]);
+#pragma unroll
+        for (int q = 0; q < L; ++q) dx[q] = o[q];
+      }
+    }
+  }
+}
+
 template <int L>
 __global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t c0, int64_t pe, int64_t R,
                                                        int64_t* ipiv, int64_t* info, int pivot, pub_t* pub,
                                                        double* rowj, panel_sync* ps, int extra) {
   using N = num<L>;
   using T = typename N::T;
-  constexpr int W = tfx<L>::W, D = tfx<L>::D, K = tfx<L>::K, NW = tfx<L>::NW;
-  constexpr int TOPW = 32 * W - 53;
+  constexpr int W = tfx<L>::W;
   __shared__ T rows[PR_MAX][PANEL_BASE];
   __shared__ T prow[PANEL_BASE];  // the pivot row (row j after the interchange)
   __shared__ T lq[PR_MAX];        // DD quotients
@@ -555,94 +676,122 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t
     // ---- quotients l_ij = a_ij (1 / a_jj) and the rank-1 update of the
     // columns (j, pe) of this CTA's rows below j
     const T rinv = srinv;
-    const bool zero = is_zero<L>(rinv);
-    const int cols = w - jc - 1;
-    if (!zero) {
-      if constexpr (L == 2 && kDDColumnFP64) {
-        for (int r = tid; r < nr; r += blockDim.x) {
-          T l = N::zero();
-          if (r_lo + r > j) {
-            l = N::mul(rows[r][jc], rinv);
-            rows[r][jc] = l;
-          }
-          lq[r] = l;
-        }
-        __syncthreads();
-        for (int e = tid; e < nr * cols; e += blockDim.x) {
-          const int r = e / cols, c = jc + 1 + e % cols;
-          if (r_lo + r > j) rows[r][c] = N::add(rows[r][c], N::mul(N::neg(lq[r]), prow[c]));
-        }
-      } else {
-        for (int r = tid; r < nr; r += blockDim.x) {
-          le[r] = -1;
-          const T a = rows[r][jc];
-          if (r_lo + r > j && !is_zero<L>(a)) {
-            const double* ax = reinterpret_cast<const double*>(&a);
-            const double* rx = reinterpret_cast<const double*>(&rinv);
-            double av[L], rv[L];
-#pragma unroll
-            for (int q = 0; q < L; ++q) av[q] = ax[q], rv[q] = rx[q];
-            uint32_t Ma[W], Mr[W], P[K], Ml[W];
-            const int ea = fx::to_fixed<L, W>(av, Ma), er = fx::to_fixed<L, W>(rv, Mr);
-            fx::mul_top<W, D>(Ma, Mr, P);
-            const int pp = fx::acc_normalize<K, W>(P, Ml);
-            const int el = pp + (ea & 0xFFFF) + (er & 0xFFFF) - 1075 - 2 * TOPW + 32 * D - 52;
-            const int sl = ((ea ^ er) >> 16) & 1;
-            double o[L];
-            fx::operand_to_limbs<L, W>(Ml, el, (uint32_t)sl, o);
-            T lv;
-            double* lx = reinterpret_cast<double*>(&lv);
-#pragma unroll
-            for (int q = 0; q < L; ++q) lx[q] = o[q];
-            rows[r][jc] = lv;
-#pragma unroll
-            for (int t = 0; t < W; ++t) lw[r][t] = Ml[t];
-            le[r] = el;
-            ls[r] = sl;
-          }
-        }
-        for (int c = tid; c < cols; c += blockDim.x) {
-          const double* ux = reinterpret_cast<const double*>(&prow[jc + 1 + c]);
-          double u[L];
-#pragma unroll
-          for (int q = 0; q < L; ++q) u[q] = ux[q];
-          uint32_t M[W];
-          const int es = fx::to_fixed<L, W>(u, M);
-#pragma unroll
-          for (int t = 0; t < W; ++t) uw[c][t] = M[t];
-          ue[c] = (fx::dbits(u[0]) << 1) == 0u ? -1 : es;
-        }
-        __syncthreads();
-        for (int e = tid; e < nr * cols; e += blockDim.x) {
-          const int r = e / cols, c = e % cols;
-          if (le[r] < 0 || ue[c] < 0) continue;  // l = 0 or u = 0: nothing to subtract
-          const double* ax = reinterpret_cast<const double*>(&rows[r][jc + 1 + c]);
-          double a[L];
-#pragma unroll
-          for (int q = 0; q < L; ++q) a[q] = ax[q];
-          int Aw = max(1, fx::expfield(a[0]));
-          uint32_t acc[NW];
-#pragma unroll
-          for (int t = 0; t < NW; ++t) acc[t] = 0u;
-          fx::add_at<L, NW>(acc, a, Aw, tfx<L>::TOPA, 0u);
-          uint32_t Ml[W], Mu[W];
-#pragma unroll
-          for (int t = 0; t < W; ++t) {
-            Ml[t] = lw[r][t];
-            Mu[t] = uw[c][t];
-          }
-          window_sub_product<L>(acc, Aw, Ml, le[r], (uint32_t)ls[r], Mu, ue[c] & 0xFFFF, (uint32_t)ue[c] >> 16);
-          double o[L];
-          fx::from_fixed<L, NW>(acc, Aw - 1075 - tfx<L>::TOPA, o);
-          double* dx = reinterpret_cast<double*>(&rows[r][jc + 1 + c]);
-#pragma unroll
-          for (int q = 0; q < L; ++q) dx[q] = o[q];
-        }
-      }
-    }
+    panel_column_step<L>(rows, nr, r_lo, j, jc, w, prow, rinv,
+                         panel_scratch<L>{lq, lw, le, ls, uw, ue});
     __syncthreads();
   }
   for (int e = tid; e < nr * w; e += blockDim.x) stA<L>(A, r_lo + e / w, c0 + e % w, rows[e / w][e % w]);
+}
+
+// ---------------------------------------------------------------------------
+// The same panel factorisation by one thread-block cluster (up to 16 CTAs;
+// distributed shared memory): each CTA holds up to RCL_MAX rows of the
+// panel in shared memory; per column, after a cluster barrier every CTA
+// reads the CTAs' candidates and the pivot row and row j straight from the
+// owners' shared memory, a second cluster barrier lets the owners
+// interchange the rows, and the column step follows. The barriers are the
+// hardware's (every CTA passes every one of them; no spin-wait), and the
+// arithmetic is panel_column_step's, so the factors are the same bits as the
+// grid form's and the per-column kernels'.
+constexpr int RCL_MAX = 256;  // rows per CTA of the cluster form
+
+template <int L>
+struct cl_smem {
+  typename num<L>::T rows[RCL_MAX][PANEL_BASE];
+  typename num<L>::T prow[PANEL_BASE], oldj[PANEL_BASE];
+  typename num<L>::T lq[RCL_MAX];
+  uint32_t lw[RCL_MAX][tfx<L>::W], uw[PANEL_BASE][tfx<L>::W];
+  int le[RCL_MAX], ls[RCL_MAX], ue[PANEL_BASE];
+  partial_t cand, sbest[8];
+  typename num<L>::T rinv;
+};
+
+template <int L>
+__global__ void __launch_bounds__(256) lu_panel_cluster_kernel(int64_t n, mat A, int64_t c0, int64_t pe, int64_t R,
+                                                               int64_t* ipiv, int64_t* info, int pivot) {
+  using N = num<L>;
+  using T = typename N::T;
+  extern __shared__ __align__(16) unsigned char cl_raw[];
+  cl_smem<L>& sm = *reinterpret_cast<cl_smem<L>*>(cl_raw);
+  cg::cluster_group cluster = cg::this_cluster();
+  const unsigned int rank = cluster.block_rank(), CS = cluster.num_blocks();
+  const int tid = threadIdx.x, nw = blockDim.x >> 5;
+  const int w = (int)(pe - c0);
+  const int64_t r_lo = c0 + (int64_t)rank * R;
+  const int64_t left = n - r_lo;
+  const int nr = left <= 0 ? 0 : (int)(left < R ? left : R);
+  for (int e = tid; e < nr * w; e += blockDim.x) sm.rows[e / w][e % w] = ldA<L>(A, r_lo + e / w, c0 + e % w);
+  __syncthreads();
+
+  for (int64_t j = c0; j < pe; ++j) {
+    const int jc = (int)(j - c0);
+    // ---- this CTA's best candidate (rows i >= j)
+    partial_t v = none();
+    if (pivot) {
+      for (int r = tid; r < nr; r += blockDim.x)
+        if (r_lo + r >= j) {
+          const partial_t q = cand<L>(sm.rows[r][jc], r_lo + r);
+          if (better(q, v)) v = q;
+        }
+      warp_best(v);
+      if ((tid & 31) == 0) sm.sbest[tid >> 5] = v;
+      __syncthreads();
+      v = sm.sbest[0];
+      for (int k = 1; k < nw; ++k)
+        if (better(sm.sbest[k], v)) v = sm.sbest[k];
+    }
+    if (tid == 0) sm.cand = v;
+    cluster.sync();  // candidates and rows visible to the whole cluster
+    // ---- the pivot (every CTA the same), the pivot row and row j from their owners
+    if (tid < 32) {
+      partial_t b = none();
+      if (pivot && (unsigned int)tid < CS) b = *cluster.map_shared_rank(&sm.cand, (unsigned int)tid);
+      warp_best(b);
+      if (tid == 0) sm.sbest[0] = b;
+    }
+    __syncthreads();
+    const partial_t b = sm.sbest[0];
+    const int64_t p = (pivot && b.idx >= j && b.idx < n) ? b.idx : j;
+    {
+      const unsigned int op = (unsigned int)((p - c0) / R), oj = (unsigned int)((j - c0) / R);
+      const T* rp = cluster.map_shared_rank(&sm.rows[0][0], op) + (p - c0 - (int64_t)op * R) * PANEL_BASE;
+      const T* rjp = cluster.map_shared_rank(&sm.rows[0][0], oj) + (j - c0 - (int64_t)oj * R) * PANEL_BASE;
+      for (int c = tid; c < w; c += blockDim.x) {
+        sm.prow[c] = rp[c];
+        sm.oldj[c] = rjp[c];
+      }
+    }
+    cluster.sync();  // every CTA has read the two rows before their owners change them
+    // ---- the interchange of rows j and p within the panel
+    if (j >= r_lo && j < r_lo + nr)
+      for (int c = tid; c < w; c += blockDim.x) sm.rows[j - r_lo][c] = sm.prow[c];
+    if (p != j && p >= r_lo && p < r_lo + nr)
+      for (int c = tid; c < w; c += blockDim.x) sm.rows[p - r_lo][c] = sm.oldj[c];
+    if (tid == 0) {
+      const T piv = sm.prow[jc];
+      const bool zero = is_zero<L>(piv);
+      if (rank == 0) {
+        ipiv[j] = p;
+        if (zero && *info == 0) *info = j + 1;
+      }
+      T r = N::zero();
+      if (!zero) {
+        if constexpr (L == 4) {
+          const dd_t y = dd_recip(dd_t{piv.x[0], piv.x[1]});
+          qd_recip_refine(piv.x, y.hi, y.lo, r.x);
+        } else {
+          r = N::recip(piv);
+        }
+      }
+      sm.rinv = r;
+    }
+    __syncthreads();
+    panel_column_step<L>(sm.rows, nr, r_lo, j, jc, w, sm.prow, sm.rinv,
+                         panel_scratch<L>{sm.lq, sm.lw, sm.le, sm.ls, sm.uw, sm.ue});
+    __syncthreads();
+  }
+  for (int e = tid; e < nr * w; e += blockDim.x) stA<L>(A, r_lo + e / w, c0 + e % w, sm.rows[e / w][e % w]);
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // The interchanges ipiv[k0 .. k1) (in order, at most 16) applied to every
@@ -904,6 +1053,47 @@ static bool bad_planes(int L, const mat& M, int64_t rows, int64_t cols) {
   return false;
 }
 
+// Cluster size of the cluster panel form on this device (16, else 8), 0 if
+// neither can be resident with the form's shared memory; per device, once.
+template <int L>
+static int cluster_panel_size() {
+  static std::mutex mu;
+  static std::map<int, int> known;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = known.find(dev);
+  if (it != known.end()) return it->second;
+  int cs = 0, cl = 0;
+  cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, dev);
+  const void* f = (const void*)lu_panel_cluster_kernel<L>;
+  if (cl && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(cl_smem<L>)) ==
+                cudaSuccess &&
+      cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    for (int c : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)c;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)c);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = sizeof(cl_smem<L>);
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, f, &cfg) == cudaSuccess && nclusters >= 1) {
+        cs = c;
+        break;
+      }
+    }
+  }
+  cudaGetLastError();
+  known[dev] = cs;
+  return cs;
+}
+
 template <int L>
 static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t* ipiv, int32_t K,
                              int32_t pivot, const ddg_opts* opts, int64_t* info, void* stream) {
@@ -923,17 +1113,27 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
   if (n == 0) return DDG_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t maxparts = (n + RB - 1) / RB;
-  // the fused panel kernel: one CTA per SM at most, each holding up to
-  // PR_MAX rows; the per-column kernels otherwise (or when asked for by
-  // DDG_LU_COLUMN_STEPS=1, which tests use to cover both forms)
+  // Panel forms, fastest first: one thread-block cluster (CS CTAs holding a
+  // few rows each, below), the cooperative grid (one CTA per SM at most, up
+  // to PR_MAX rows each), the per-column kernels. DDG_LU_PANEL = "cluster",
+  // "grid" or "columns" restricts the choice to that form and the ones after
+  // it, an explicit "cluster" taking the cluster form up to RCL_MAX rows per
+  // CTA (tests use it to cover every form; all give the same bits).
   int dev = 0, nsm = 0, coop = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<L>, 256, 0);
   cudaGetLastError();
-  const char* env = std::getenv("DDG_LU_COLUMN_STEPS");
-  const bool fused_ok = coop && per_sm >= 1 && nsm > 0 && !(env && env[0] == '1');
+  const char* env = std::getenv("DDG_LU_PANEL");
+  const std::string form = env ? env : "cluster";
+  const bool fused_ok = coop && per_sm >= 1 && nsm > 0 && form != "columns";
+  const int CS = form == "cluster" ? cluster_panel_size<L>() : 0;
+  // the cluster form only while its CTAs hold few rows: its 16 SMs are
+  // throughput-bound on the rank-1 updates of taller panels, where the grid
+  // form's 152 SMs win despite the slower grid barrier (sweep of the rows
+  // per CTA on GB300: DD best at 128, QD at 32)
+  const int64_t cl_rows = form == "cluster" && !env ? (L == 2 ? 128 : 32) : RCL_MAX;
   const int64_t gmax = std::max(1, nsm);
   const size_t pub_bytes = 2 * sizeof(pub_t) * (size_t)gmax;
   const size_t bytes = sizeof(partial_t) * (size_t)maxparts + 512 + pub_bytes + 2 * PANEL_BASE * 4 * 8 + 256;
@@ -969,6 +1169,27 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
       nvtx_range nv("ddg.getrf panel %lld", (long long)c0);
       const int64_t pe = c0 + w;
       const int64_t prow = n - c0;
+      if (CS > 0 && (prow + CS - 1) / CS <= cl_rows) {
+        const int64_t Rc = (prow + CS - 1) / CS;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)CS;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)CS);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = sizeof(cl_smem<L>);
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cu(cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<L>, n, M, c0, pe, Rc, ipiv, dinfo, (int)pivot));
+        if (pivot && st == DDG_OK) {
+          lu_laswp_kernel<L><<<dim3((unsigned)((n + 127) / 128), L), 128, 0, s>>>(n, M, c0, pe, ipiv);
+          cu(cudaGetLastError());
+        }
+        return;
+      }
       const int64_t R = std::max<int64_t>(8, (prow + gmax - 1) / gmax);
       if (fused_ok && R <= PR_MAX) {
         const unsigned G = (unsigned)((prow + R - 1) / R);

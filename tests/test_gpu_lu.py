@@ -210,22 +210,23 @@ def test_int8_trailing_updates(algo):
 
 
 # ------------------------------------- fused panel kernel (one launch per panel)
-def _factor(A, K, cutoff, algo="winograd", pivot=True, column_steps=False):
-    """getrf through the C ABI; column_steps forces the per-column kernels
-    (DDG_LU_COLUMN_STEPS=1) instead of the fused panel kernel."""
+def _factor(A, K, cutoff, algo="winograd", pivot=True, form="cluster"):
+    """getrf through the C ABI with the panel form restricted by
+    DDG_LU_PANEL: "cluster" (thread-block cluster, the default), "grid"
+    (cooperative grid) or "columns" (per-column kernels)."""
     import os
     import paper_1510_08642_gb300 as P
-    old = os.environ.get("DDG_LU_COLUMN_STEPS")
-    os.environ["DDG_LU_COLUMN_STEPS"] = "1" if column_steps else "0"
+    old = os.environ.get("DDG_LU_PANEL")
+    os.environ["DDG_LU_PANEL"] = form
     try:
         dA = to_dev(A)
         ipiv = P.getrf(dA, K=K, pivot=pivot, algo=algo, cutoff=cutoff)
         torch.cuda.synchronize()
     finally:
         if old is None:
-            del os.environ["DDG_LU_COLUMN_STEPS"]
+            del os.environ["DDG_LU_PANEL"]
         else:
-            os.environ["DDG_LU_COLUMN_STEPS"] = old
+            os.environ["DDG_LU_PANEL"] = old
     return to_host(dA), ipiv.cpu().numpy()
 
 
@@ -233,16 +234,17 @@ def _factor(A, K, cutoff, algo="winograd", pivot=True, column_steps=False):
 @pytest.mark.parametrize("n,K,pivot", [(1, 1, True), (37, 16, True), (300, 64, True), (1000, 256, True),
                                        (150, 32, False)])
 def test_fused_panel_same_bits_as_column_steps(limbs, n, K, pivot):
-    """The panel kernel runs each column step with the per-column kernels'
-    arithmetic (same quotients, same updates, same pivot rule), so the
-    factors and pivots are the same bits."""
+    """The cluster and grid panel kernels run each column step with the
+    per-column kernels' arithmetic (same quotients, same updates, same pivot
+    rule), so the factors and pivots are the same bits."""
     A = I.uniform(n, n, limbs, seed=70 + n)
     if not pivot:
         A[0] += np.eye(n) * n
-    LUf, pf = _factor(A, K, 16, pivot=pivot)
-    LUc, pc = _factor(A, K, 16, pivot=pivot, column_steps=True)
-    assert np.array_equal(pf, pc)
-    assert np.array_equal(LUf.view(np.uint64), LUc.view(np.uint64))
+    LUc, pc = _factor(A, K, 16, pivot=pivot, form="columns")
+    for form in ("cluster", "grid"):
+        LUf, pf = _factor(A, K, 16, pivot=pivot, form=form)
+        assert np.array_equal(pf, pc), form
+        assert np.array_equal(LUf.view(np.uint64), LUc.view(np.uint64)), form
 
 
 def _sampled_rel_residual(A, Xh, Bv, rows):
@@ -261,10 +263,11 @@ def test_bench_configs_sampled_residual_and_paths(limbs, n, cutoff):
     X = np.zeros((limbs, n, 1))
     X[0] = 1.0
     rows = np.array(sorted({0, n - 1, *np.random.default_rng(3).choice(n, 30, replace=False)}))
-    LUf, pf = _factor(A, 256, cutoff)
-    LUc, pc = _factor(A, 256, cutoff, column_steps=True)
-    assert np.array_equal(pf, pc)
-    assert np.array_equal(LUf.view(np.uint64), LUc.view(np.uint64))
+    LUc, pc = _factor(A, 256, cutoff, form="columns")
+    for form in ("grid", "cluster"):
+        LUf, pf = _factor(A, 256, cutoff, form=form)
+        assert np.array_equal(pf, pc), form
+        assert np.array_equal(LUf.view(np.uint64), LUc.view(np.uint64)), form
     assert np.all(pf >= np.arange(n)) and np.all(pf < n)
     # solve b = A 1 with the factors (b from the GPU Block product, exact
     # residual of the computed x against that b)
