@@ -62,10 +62,14 @@ ISSUE_PEAK = SM_COUNT * ISSUE_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # thread instru
 IMAD_PER_CLK_PER_SM = 64          # measured: IMAD throughput probe (profiles/fp64_int8_peaks.md)
 IMAD_PEAK = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6   # 32-bit integer multiply-adds per second
 # The Block multiply-add's irreducible integer multiplies, counted from the
-# source (fx::mul_top): the partial products a_i b_j with i + j >= D of the
-# W-word operands, each a mad.lo and a madc.hi: DD W = 4, D = 3: 10 partial
-# products, 20 IMAD; QD W = 7, D = 6: 28 partial products, 56 IMAD.
-IMAD_FLOOR_PER_MAC = {2: 20, 4: 56}
+# source. DD, pre-shifted form (fx_pre.cuh, mul_top_hi): the 6 partial
+# products a_i b_j with i + j >= 4 of the 4-word operands, a mad.lo and a
+# madc.hi each, and the high halves (mad.hi) of the 4 with i + j = 3: 16
+# IMAD. QD, shifted form (fx::mul_top, W = 7, D = 6): 28 partial products,
+# 56 IMAD.
+IMAD_FLOOR_PER_MAC = {2: 16, 4: 56}
+IMAD_FLOOR_SOURCE = {2: "fx_pre.cuh mul_top_hi: 6 partial products x (mad.lo + madc.hi) + 4 x mad.hi",
+                     4: "fx::mul_top: 28 partial products x (mad.lo + madc.hi)"}
 
 
 def parse():
@@ -263,6 +267,7 @@ COUNT_METRICS = ("dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.
                  "sm__inst_executed_pipe_fma.sum,sm__inst_executed_pipe_alu.sum")
 COUNT_SOURCES = ["paper_1510_08642_gb300/csrc/block_fx.cu", "paper_1510_08642_gb300/csrc/fx.cuh",
                  "paper_1510_08642_gb300/csrc/fx_round.cuh", "paper_1510_08642_gb300/csrc/fx_rescue.cuh",
+                 "paper_1510_08642_gb300/csrc/fx_pre.cuh",
                  "paper_1510_08642_gb300/csrc/arith.cuh", "paper_1510_08642_gb300/csrc/kernels.cuh"]
 
 
@@ -394,8 +399,8 @@ def roofline_of(prof, limbs):
            "frac": achieved / IMAD_PEAK,
            "peak_source": f"derived: {SM_COUNT} SMs x {IMAD_PER_CLK_PER_SM} IMAD per clock per SM (measured "
                           f"by the IMAD throughput probe) x {SM_MAX_MHZ:.0f} MHz",
-           "algorithmic": f"{floor} IMAD per {'DD' if limbs == 2 else 'QD'} multiply-add (the partial products "
-                          f"of fx::mul_top, mad.lo + madc.hi each) x multiply-adds per busy second",
+           "algorithmic": f"{floor} IMAD per {'DD' if limbs == 2 else 'QD'} multiply-add "
+                          f"({IMAD_FLOOR_SOURCE[limbs]}) x multiply-adds per busy second",
            "macs_per_s": macs_per_s, "launches": int(b["launches"]), "avg_launch_ms": avg_ms,
            "busy_ms": b["busy_ms"], "sum_launch_ms": b["sum_ms"]}
     if rec is None:

@@ -154,9 +154,12 @@ void ddg_opts_default(ddg_opts* opts);
  * exactly; DDG_BLOCK stays within |C - C^| <= (2 l + 4) 2^-106 |A||B|
  * elementwise for every input, like the DD arithmetic of Section 2's Block
  * (each output's fixed-point window is set from the largest exponents of
- * its row of A and column of B; an output whose window sum keeps fewer
+ * its row of A and column of B; operands are shifted once to that scale
+ * and an output whose window sum keeps fewer than 142 bits is recomputed
+ * with every product at its own scale, and one that still keeps fewer
  * than 106 significant bits, as when those maxima sit at different k far
- * apart, is recomputed with the window at its own largest term);
+ * apart, with the window at its own largest term); products of small
+ * integers (within 64 bits of their row / column maxima) are exact;
  * Strassen/Winograd within the normwise bound 8 l^log2(12) 2^-104
  * ||A|| ||B|| (these recursions are only normwise stable).
  */

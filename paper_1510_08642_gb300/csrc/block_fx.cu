@@ -29,9 +29,11 @@
 // term (fx_rescue.cuh), so every output is accurate relative to its own
 // sum_k |a_ik b_kj|. One final rounding to DD / QD.
 #include <algorithm>
+#include <type_traits>
 
 #include "arith.cuh"
 #include "fx.cuh"
+#include "fx_pre.cuh"
 #include "fx_rescue.cuh"
 #include "fx_round.cuh"
 #include "kernels.cuh"
@@ -49,6 +51,7 @@ template <> struct fxcfg<4> : fxwin<4> {
   static constexpr int BM = 8, BN = 32, BK = 16, TM = 1, TN = 2;
   static constexpr int MINB = 8;
 };
+
 
 }  // namespace
 
@@ -69,9 +72,28 @@ struct fx_smem {
 
 namespace {
 
-// Convert one element and store its words, shift and sign mask; a zero gets
-// shift 0 (its products are zero and stay on the fast path).
-template <int L>
+// Store one element's words and its (shift, sign mask) pair below the row /
+// column maximum fmax (SH: the shifted form; a zero gets shift 0); or, for
+// the pre-shifted form, its words shifted by that amount and shift 0.
+template <int L, bool SH>
+__device__ __forceinline__ void put_staged(uint32_t (&M)[4 * fx_smem<L>::WV], bool zero, int f, int fmax, uint4* w,
+                                           int stride, int2* e) {
+  constexpr int W = fxcfg<L>::W, WV = fx_smem<L>::WV;
+  const int sh = zero ? 0 : fmax - (f & 0xFFFF);
+  if constexpr (SH) {
+#pragma unroll
+    for (int v = 0; v < WV; ++v) w[v * stride] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
+    *e = make_int2(sh, ((f >> 16) & 1) ? -1 : 0);
+  } else {
+    shr_words<W>(*reinterpret_cast<uint32_t(*)[W]>(M), zero ? 32 * W : sh);
+#pragma unroll
+    for (int v = 0; v < WV; ++v) w[v * stride] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
+    *e = make_int2(0, ((f >> 16) & 1) && !zero ? -1 : 0);
+  }
+}
+
+// Convert one element (to_fixed) and stage it.
+template <int L, bool SH>
 __device__ __forceinline__ void stage(const double (&x)[L], int fmax, uint4* w, int stride, int2* e) {
   constexpr int W = fxcfg<L>::W, WV = (W + 3) / 4;
   uint32_t M[4 * WV];
@@ -80,43 +102,38 @@ __device__ __forceinline__ void stage(const double (&x)[L], int fmax, uint4* w, 
 #pragma unroll
   for (int t = W; t < 4 * WV; ++t) M[t] = 0u;
   const bool zero = (fx::dbits(x[0]) << 1) == 0u;
-#pragma unroll
-  for (int v = 0; v < WV; ++v) w[v * stride] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
-  *e = make_int2(zero ? 0 : fmax - (es & 0xFFFF), (es >> 16) ? -1 : 0);
+  put_staged<L, SH>(M, zero, es, fmax, w, stride, e);
 }
 
-// The same staging from a converted operand: copy the words and derive the
-// shift and sign mask from f exactly as stage() does from to_fixed.
-template <int L>
+// The same staging from a converted operand: its words and f as to_fixed
+// gave them.
+template <int L, bool SH>
 __device__ __forceinline__ void stage_pre(bool ok, const fxop& X, int64_t e, int fmax, uint4* w, int stride,
                                           int2* ex) {
   constexpr int WV = fx_smem<L>::WV;
+  uint32_t M[4 * WV];
 #pragma unroll
-  for (int v = 0; v < WV; ++v) w[v * stride] = ok ? X.w[e * WV + v] : make_uint4(0u, 0u, 0u, 0u);
+  for (int v = 0; v < WV; ++v) {
+    const uint4 q = ok ? X.w[e * WV + v] : make_uint4(0u, 0u, 0u, 0u);
+    M[4 * v] = q.x; M[4 * v + 1] = q.y; M[4 * v + 2] = q.z; M[4 * v + 3] = q.w;
+  }
   const int f = ok ? X.f[e] : FX_ZERO;
-  *ex = make_int2(f < 0 ? 0 : fmax - (f & 0xFFFF), ((f >> 16) & 1) ? -1 : 0);
+  put_staged<L, SH>(M, f == FX_ZERO, f, fmax, w, stride, ex);
 }
 
 }  // namespace
 
-// One BM x BN tile of C at (i0, j0): C (mode) A B restricted to the tile.
-// PRE: the operands come converted in Ax, Bx (A and B are then not read).
+// Largest exponent field of the leading limb per row of A and column of B
+// for the tile at (i0, j0), into sm.row_f / sm.col_f (at least 1).
 template <int L, bool PRE>
-__device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
-                                        const mat& C, int mode, int64_t i0, int64_t j0, fx_smem<L>& sm,
-                                        const fxop& Ax, const fxop& Bx) {
+__device__ __forceinline__ void fx_maxima(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, int64_t i0,
+                                          int64_t j0, fx_smem<L>& sm, const fxop& Ax, const fxop& Bx) {
   using P = fxcfg<L>;
-  constexpr int BM = P::BM, BN = P::BN, BK = P::BK, TM = P::TM, TN = P::TN, NW = P::NW;
-  constexpr int W = P::W, D = P::D, K = P::K, WV = fx_smem<L>::WV;
-  constexpr int NX = BN / TN, NY = BM / TM, NT = NX * NY;
-  static_assert(NT == 128, "block kernel assumes 128 threads");
+  constexpr int BM = P::BM, BN = P::BN, TM = P::TM, TN = P::TN;
+  constexpr int NT = (BN / TN) * (BM / TM);
   auto& row_f = sm.row_f;
   auto& col_f = sm.col_f;
-
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tx = tid % NX, ty = tid / NX;
-
-  // ---- largest exponent field of the leading limb, per row of A / column of B
   for (int c = tid; c < BN; c += NT) col_f[c] = 1;
   for (int r = warp; r < BM; r += NT / 32) {
     int f = 1;
@@ -146,78 +163,99 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
     atomicMax(&col_f[c], f);
   }
   __syncthreads();
+}
 
+// The tile's products and epilogue in the shifted form: each product placed
+// by the two operands' shifts below their row / column maxima; an output
+// that keeps fewer than 53 L window bits is rescued (fx_rescue.cuh).
+template <int L, bool PRE>
+__device__ __forceinline__ void fx_body(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
+                                        int mode, int64_t i0, int64_t j0, fx_smem<L>& sm, const fxop& Ax,
+                                        const fxop& Bx) {
+  using P = fxcfg<L>;
+  constexpr int BM = P::BM, BN = P::BN, BK = P::BK, TM = P::TM, TN = P::TN, NW = P::NW;
+  constexpr int W = P::W, D = P::D, K = P::K, WV = fx_smem<L>::WV;
+  constexpr int NX = BN / TN, NY = BM / TM, NT = NX * NY;
+  static_assert(NT == 128, "block kernel assumes 128 threads");
+  auto& row_f = sm.row_f;
+  auto& col_f = sm.col_f;
+  const int tid = threadIdx.x;
+  const int tx = tid % NX, ty = tid / NX;
+
+  // The k loop over tiles of BK: stage A and B, then per k one product per
+  // output.
   uint32_t acc[TM][TN][NW];
+  {
 #pragma unroll
-  for (int r = 0; r < TM; ++r)
+    for (int r = 0; r < TM; ++r)
 #pragma unroll
-    for (int c = 0; c < TN; ++c)
+      for (int c = 0; c < TN; ++c)
 #pragma unroll
-      for (int w = 0; w < NW; ++w) acc[r][c][w] = 0u;
-
-  for (int64_t k0 = 0; k0 < l; k0 += BK) {
+        for (int w = 0; w < NW; ++w) acc[r][c][w] = 0u;
+    for (int64_t k0 = 0; k0 < l; k0 += BK) {
 #pragma unroll
-    for (int idx = tid; idx < BM * BK; idx += NT) {
-      const int r = idx / BK, c = idx % BK;
-      const int64_t gi = i0 + r, gk = k0 + c;
-      const bool ok = gi < m && gk < l;
-      if constexpr (PRE) {
-        stage_pre<L>(ok, Ax, gi * Ax.ld + gk, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
-      } else {
-        double x[L];
+      for (int idx = tid; idx < BM * BK; idx += NT) {
+        const int r = idx / BK, c = idx % BK;
+        const int64_t gi = i0 + r, gk = k0 + c;
+        const bool ok = gi < m && gk < l;
+        if constexpr (PRE) {
+          stage_pre<L, true>(ok, Ax, gi * Ax.ld + gk, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
+        } else {
+          double x[L];
 #pragma unroll
-        for (int q = 0; q < L; ++q) x[q] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
-        stage<L>(x, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
+          for (int q = 0; q < L; ++q) x[q] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
+          stage<L, true>(x, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
+        }
       }
-    }
 #pragma unroll
-    for (int idx = tid; idx < BK * BN; idx += NT) {
-      const int r = idx / BN, c = idx % BN;
-      const int64_t gk = k0 + r, gj = j0 + c;
-      const bool ok = gk < l && gj < n;
-      if constexpr (PRE) {
-        stage_pre<L>(ok, Bx, gk * Bx.ld + gj, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
-      } else {
-        double x[L];
+      for (int idx = tid; idx < BK * BN; idx += NT) {
+        const int r = idx / BN, c = idx % BN;
+        const int64_t gk = k0 + r, gj = j0 + c;
+        const bool ok = gk < l && gj < n;
+        if constexpr (PRE) {
+          stage_pre<L, true>(ok, Bx, gk * Bx.ld + gj, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
+        } else {
+          double x[L];
 #pragma unroll
-        for (int q = 0; q < L; ++q) x[q] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
-        stage<L>(x, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
+          for (int q = 0; q < L; ++q) x[q] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
+          stage<L, true>(x, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
+        }
       }
-    }
-    __syncthreads();
+      __syncthreads();
 #pragma unroll 1
-    for (int kk = 0; kk < BK; ++kk) {
-      uint32_t a[TM][4 * WV], b[TN][4 * WV];
-      int2 ea[TM], eb[TN];
+      for (int kk = 0; kk < BK; ++kk) {
+        uint32_t a[TM][4 * WV], b[TN][4 * WV];
+        int2 ea[TM], eb[TN];
 #pragma unroll
-      for (int r = 0; r < TM; ++r) {
+        for (int r = 0; r < TM; ++r) {
 #pragma unroll
-        for (int v = 0; v < WV; ++v) {
-          const uint4 q = sm.Aw[v][kk][ty + r * NY];
-          a[r][4 * v] = q.x; a[r][4 * v + 1] = q.y; a[r][4 * v + 2] = q.z; a[r][4 * v + 3] = q.w;
+          for (int v = 0; v < WV; ++v) {
+            const uint4 q = sm.Aw[v][kk][ty + r * NY];
+            a[r][4 * v] = q.x; a[r][4 * v + 1] = q.y; a[r][4 * v + 2] = q.z; a[r][4 * v + 3] = q.w;
+          }
+          ea[r] = sm.Ae[kk][ty + r * NY];
         }
-        ea[r] = sm.Ae[kk][ty + r * NY];
-      }
-#pragma unroll
-      for (int c = 0; c < TN; ++c) {
-#pragma unroll
-        for (int v = 0; v < WV; ++v) {
-          const uint4 q = sm.Bw[v][kk][tx + c * NX];
-          b[c][4 * v] = q.x; b[c][4 * v + 1] = q.y; b[c][4 * v + 2] = q.z; b[c][4 * v + 3] = q.w;
-        }
-        eb[c] = sm.Be[kk][tx + c * NX];
-      }
-#pragma unroll
-      for (int r = 0; r < TM; ++r)
 #pragma unroll
         for (int c = 0; c < TN; ++c) {
-          uint32_t p[K];
-          fx::mul_top<W, D>(*reinterpret_cast<const uint32_t(*)[W]>(a[r]),
-                            *reinterpret_cast<const uint32_t(*)[W]>(b[c]), p);
-          fx::place_shr<NW, K>(acc[r][c], p, ea[r].x + eb[c].x, (uint32_t)(ea[r].y ^ eb[c].y));
+#pragma unroll
+          for (int v = 0; v < WV; ++v) {
+            const uint4 q = sm.Bw[v][kk][tx + c * NX];
+            b[c][4 * v] = q.x; b[c][4 * v + 1] = q.y; b[c][4 * v + 2] = q.z; b[c][4 * v + 3] = q.w;
+          }
+          eb[c] = sm.Be[kk][tx + c * NX];
         }
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+          for (int c = 0; c < TN; ++c) {
+            uint32_t p[K];
+            fx::mul_top<W, D>(*reinterpret_cast<const uint32_t(*)[W]>(a[r]),
+                              *reinterpret_cast<const uint32_t(*)[W]>(b[c]), p);
+            fx::place_shr<NW, K>(acc[r][c], p, ea[r].x + eb[c].x, (uint32_t)(ea[r].y ^ eb[c].y));
+          }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 
   using N = num<L>;
@@ -252,6 +290,133 @@ __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const m
     fxacc<L> x = fx_rescue<L, PRE>(l, A, B, Ax, Bx, gi, gj);
     finish(gi, gj, x.w, x.lsb);
   }
+}
+
+// The DD tile in the pre-shifted form (fx_pre.cuh).
+template <bool PRE>
+__device__ __forceinline__ void fx_pre(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
+                                       int mode, int64_t i0, int64_t j0, fx_smem<2>& sm, const fxop& Ax,
+                                       const fxop& Bx) {
+  using P = fxcfg<2>;
+  constexpr int BM = P::BM, BN = P::BN, BK = P::BK, TM = P::TM, TN = P::TN, NW = P::NW;
+  static_assert(P::W == 4 && NW == 6, "pre-shifted form: DD words and window");
+  constexpr int NX = BN / TN, NY = BM / TM, NT = NX * NY;
+  auto& row_f = sm.row_f;
+  auto& col_f = sm.col_f;
+  const int tid = threadIdx.x;
+  const int tx = tid % NX, ty = tid / NX;
+
+  // window words 1 .. 5 (word 0 stays 0)
+  uint32_t acc[TM][TN][5];
+#pragma unroll
+  for (int r = 0; r < TM; ++r)
+#pragma unroll
+    for (int c = 0; c < TN; ++c)
+#pragma unroll
+      for (int w = 0; w < 5; ++w) acc[r][c][w] = 0u;
+  for (int64_t k0 = 0; k0 < l; k0 += BK) {
+#pragma unroll
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      const int r = idx / BK, c = idx % BK;
+      const int64_t gi = i0 + r, gk = k0 + c;
+      const bool ok = gi < m && gk < l;
+      if constexpr (PRE) {
+        stage_pre<2, false>(ok, Ax, gi * Ax.ld + gk, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
+      } else {
+        double x[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) x[q] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
+        stage<2, false>(x, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
+      }
+    }
+#pragma unroll
+    for (int idx = tid; idx < BK * BN; idx += NT) {
+      const int r = idx / BN, c = idx % BN;
+      const int64_t gk = k0 + r, gj = j0 + c;
+      const bool ok = gk < l && gj < n;
+      if constexpr (PRE) {
+        stage_pre<2, false>(ok, Bx, gk * Bx.ld + gj, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
+      } else {
+        double x[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) x[q] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
+        stage<2, false>(x, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int kk = 0; kk < BK; ++kk) {
+      uint32_t a[TM][4], b[TN][4], sa[TM], sb[TN];
+#pragma unroll
+      for (int r = 0; r < TM; ++r) {
+        const uint4 q = sm.Aw[0][kk][ty + r * NY];
+        a[r][0] = q.x; a[r][1] = q.y; a[r][2] = q.z; a[r][3] = q.w;
+        sa[r] = (uint32_t)sm.Ae[kk][ty + r * NY].y;
+      }
+#pragma unroll
+      for (int c = 0; c < TN; ++c) {
+        const uint4 q = sm.Bw[0][kk][tx + c * NX];
+        b[c][0] = q.x; b[c][1] = q.y; b[c][2] = q.z; b[c][3] = q.w;
+        sb[c] = (uint32_t)sm.Be[kk][tx + c * NX].y;
+      }
+#pragma unroll
+      for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+          uint32_t q[4];
+          mul_top_hi<4>(a[r], b[c], q);
+          pre_add(acc[r][c], q, sa[r] ^ sb[c]);
+        }
+    }
+    __syncthreads();
+  }
+
+  using N = num<2>;
+  auto finish = [&](int64_t gi, int64_t gj, uint32_t(&w)[NW], int lsb) {
+    N::T v = window_round<2, NW>(w, lsb);
+    const int64_t off = gi * C.ld + gj;
+    if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
+    else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));
+    N::store(C.p, off, v);
+  };
+  uint32_t redo = 0u;  // outputs below fxpre<2>::keep window bits, bit r TN + c
+#pragma unroll
+  for (int r = 0; r < TM; ++r)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      const int64_t gi = i0 + ty + r * NY, gj = j0 + tx + c * NX;
+      if (gi < m && gj < n) {
+        uint32_t w[NW];
+        pre_window(acc[r][c], w);
+        if (fx::acc_mag_below<NW>(w, fxpre<2>::keep)) {
+          redo |= 1u << (r * TN + c);
+          continue;
+        }
+        finish(gi, gj, w, row_f[ty + r * NY] + col_f[tx + c * NX] + P::LSB0);
+      }
+    }
+  // rare: each such output on its own in the shifted form (then, if needed,
+  // the rescue), when no accumulator is live any more
+#pragma unroll 1
+  for (int t = 0; t < TM * TN; ++t) {
+    if (!((redo >> t) & 1u)) continue;
+    const int r = t / TN, c = t % TN;
+    const int64_t gi = i0 + ty + r * NY, gj = j0 + tx + c * NX;
+    fxacc<2> x = fx_shifted_one<2, PRE>(l, A, B, Ax, Bx, gi, gj, row_f[ty + r * NY] + col_f[tx + c * NX]);
+    finish(gi, gj, x.w, x.lsb);
+  }
+}
+
+// One BM x BN tile of C at (i0, j0): C (mode) A B restricted to the tile.
+// PRE: the operands come converted in Ax, Bx (A and B are then not read).
+// DD: the pre-shifted form (fx_pre.cuh); QD: the shifted form.
+template <int L, bool PRE>
+__device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
+                                        const mat& C, int mode, int64_t i0, int64_t j0, fx_smem<L>& sm,
+                                        const fxop& Ax, const fxop& Bx) {
+  fx_maxima<L, PRE>(m, l, n, A, B, i0, j0, sm, Ax, Bx);
+  if constexpr (fxpre<L>::on) fx_pre<PRE>(m, l, n, A, B, C, mode, i0, j0, sm, Ax, Bx);
+  else fx_body<L, PRE>(m, l, n, A, B, C, mode, i0, j0, sm, Ax, Bx);
 }
 
 template <int L>

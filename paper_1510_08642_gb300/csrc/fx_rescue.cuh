@@ -86,6 +86,19 @@ template <int L> struct fxacc {
   int lsb;
 };
 
+// The window sum of output c_ij with its window anchored at E (every term
+// placed E - f(a_ik) - f(b_kj) bits below the window top, as fx_pair_place),
+// by one thread; with E = f_a + f_b (the row / column maxima) this is the
+// window of the Block kernels' shifted form, term for term.
+template <int L, bool PRE>
+__device__ __forceinline__ void fx_window_at(int64_t l, const mat& A, const mat& B, const fxop& Ax, const fxop& Bx,
+                                             int64_t gi, int64_t gj, int E, uint32_t (&w)[fxwin<L>::NW]) {
+  const int64_t ald = PRE ? Ax.ld : A.ld, bld = PRE ? Bx.ld : B.ld;
+#pragma unroll
+  for (int t = 0; t < fxwin<L>::NW; ++t) w[t] = 0u;
+  for (int64_t k = 0; k < l; ++k) fx_pair_place<L, PRE>(A, B, Ax, Bx, gi * ald + k, k * bld + gj, E, w);
+}
+
 // One output c_ij recomputed by one thread with the window anchored at its
 // largest term (two passes over k; rare, kept out of line so that the
 // Block kernels' main loops are compiled as without it).
@@ -99,8 +112,21 @@ __device__ __noinline__ fxacc<L> fx_rescue(int64_t l, mat A, mat B, fxop Ax, fxo
   for (int w = 0; w < fxwin<L>::NW; ++w) r.w[w] = 0u;
   r.lsb = 0;
   if (E < 0) return r;  // every term is zero
-  for (int64_t k = 0; k < l; ++k) fx_pair_place<L, PRE>(A, B, Ax, Bx, gi * ald + k, k * bld + gj, E, r.w);
+  fx_window_at<L, PRE>(l, A, B, Ax, Bx, gi, gj, E, r.w);
   r.lsb = E + fxwin<L>::LSB0;
+  return r;
+}
+
+// Output c_ij in the shifted form with window anchor fab = f_a + f_b, and,
+// if that window keeps fewer than 53 L bits, the rescue: the result the
+// Block kernels' shifted form gives for it (one thread, out of line).
+template <int L, bool PRE>
+__device__ __noinline__ fxacc<L> fx_shifted_one(int64_t l, mat A, mat B, fxop Ax, fxop Bx, int64_t gi, int64_t gj,
+                                                int fab) {
+  fxacc<L> r;
+  fx_window_at<L, PRE>(l, A, B, Ax, Bx, gi, gj, fab, r.w);
+  r.lsb = fab + fxwin<L>::LSB0;
+  if (fx::acc_mag_below<fxwin<L>::NW>(r.w, fxkeep<L>::bits)) r = fx_rescue<L, PRE>(l, A, B, Ax, Bx, gi, gj);
   return r;
 }
 

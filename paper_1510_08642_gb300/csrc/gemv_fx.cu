@@ -17,9 +17,12 @@
 //   * an output whose window sum keeps fewer than 53 L significant bits is
 //     recomputed by the warp with the window at its own largest term
 //     (fx_rescue.cuh), as in the Block kernel.
-// The result is the one the Block kernel's arithmetic defines: every term
+// DD takes the pre-shifted form first (fx_pre.cuh) and the shifted form
+// only for an output below its threshold, as the Block kernel does. The
+// result is the one the Block kernel's arithmetic defines: every term
 // carries the same truncations, and the window sum is exact, so the order
 // of the terms does not matter.
+#include "fx_pre.cuh"
 #include "fx_rescue.cuh"
 #include "fx_round.cuh"
 #include "kernels.cuh"
@@ -56,6 +59,48 @@ __global__ void __launch_bounds__(32 * GV_WARPS) gemv_fx_kernel(int64_t m, int64
   fb = __reduce_max_sync(0xffffffffu, fb);
 
   uint32_t acc[NW];
+  int lsb = fa + fb + F::LSB0;
+  if constexpr (fxpre<L>::on) {
+    // DD: the pre-shifted form (fx_pre.cuh), as the tile kernel stages it;
+    // its window is kept when it reaches fxpre<L>::keep bits
+    uint32_t pa[5] = {0u, 0u, 0u, 0u, 0u};
+    for (int64_t k = lane; k < l; k += 32) {
+      double xa[L], xb[L];
+      load_limbs<L>(A, arow + k, xa);
+      load_limbs<L>(B, k * B.ld + j, xb);
+      uint32_t ma[W], mb[W];
+      const int ea = fx::to_fixed<L, W>(xa, ma);
+      const int eb = fx::to_fixed<L, W>(xb, mb);
+      const bool za = (fx::dbits(xa[0]) << 1) == 0u, zb = (fx::dbits(xb[0]) << 1) == 0u;
+      shr_words<W>(ma, za ? 32 * W : fa - (ea & 0xFFFF));
+      shr_words<W>(mb, zb ? 32 * W : fb - (eb & 0xFFFF));
+      const uint32_t sa = ((ea >> 16) & 1) && !za ? 0xFFFFFFFFu : 0u;
+      const uint32_t sb = ((eb >> 16) & 1) && !zb ? 0xFFFFFFFFu : 0u;
+      uint32_t q[W];
+      mul_top_hi<W>(ma, mb, q);
+      pre_add(pa, q, sa ^ sb);
+    }
+    pre_window(pa, acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      uint32_t o[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) o[w] = __shfl_xor_sync(0xffffffffu, acc[w], off);
+      fx::acc_add_mask<NW>(acc, o, 0u);
+    }
+    if (!fx::acc_mag_below<NW>(acc, fxpre<L>::keep)) {
+      if (lane == 0) {
+        using N = num<L>;
+        typename N::T v = window_round<L, NW>(acc, lsb);
+        const int64_t off = i * C.ld + j;
+        if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
+        else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));
+        N::store(C.p, off, v);
+      }
+      return;  // warp-uniform: every lane holds the total
+    }
+  }
+  // the shifted form (QD; DD outputs below fxpre<L>::keep bits)
 #pragma unroll
   for (int w = 0; w < NW; ++w) acc[w] = 0u;
   for (int64_t k = lane; k < l; k += 32) {
@@ -82,7 +127,6 @@ __global__ void __launch_bounds__(32 * GV_WARPS) gemv_fx_kernel(int64_t m, int64
   }
   // every lane holds the total: a warp-uniform test, and the rescue of
   // fx_rescue.cuh with the lanes splitting k
-  int lsb = fa + fb + F::LSB0;
   if (fx::acc_mag_below<NW>(acc, fxkeep<L>::bits)) {
     int E = -1;
     for (int64_t k = lane; k < l; k += 32)

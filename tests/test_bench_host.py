@@ -41,8 +41,9 @@ def test_roofline_of_block_kernel():
     macs = 2401.0 * 256 ** 3  # one DD n = 4096 step at cutoff 256: 2401 leaves, 343 launches
     r = b.roofline_of(_prof(macs, 100.0, 343), 2)
     rec = b.profile_record("block_fxc_kernel<2>")
-    # algorithmic: 20 IMAD per DD multiply-add against 152 x 64 x 2070 MHz
-    want = macs / 0.100 * 20
+    # algorithmic: 16 IMAD per DD multiply-add (the pre-shifted form's
+    # mul_top_hi: 6 x (mad.lo + madc.hi) + 4 x mad.hi) against 152 x 64 x 2070 MHz
+    want = macs / 0.100 * 16
     assert r["bound"] == "alu" and r["kernel"].startswith("block_fxc_kernel<2>")
     assert abs(r["achieved"] - want / 1e12) < 1e-9 * want
     assert abs(r["frac"] - want / (152 * 64 * 2070e6)) < 1e-12
