@@ -590,7 +590,36 @@ def time_batched(P, torch, device, stream, count=1000, reps=3, tune_buckets=8):
         probs_host.append((A, B))
         keep.append(C)
         work += 2.0 * m * l * n
-    batch = P.Batch(probs, use_graph=True)
+    # plans, each replayed as a CUDA graph: the tuned recursion with the
+    # operands of larger leaves converted once (default), the same with every
+    # leaf in one persistent grouped launch (tiles converted as staged: the
+    # same bits), and every problem as Block in that one launch (a single
+    # kernel per run); the fastest is the bench's plan
+    variants = {
+        "tuned": (probs, False),
+        "tuned_one_leaf_launch": (probs, True),
+        "block_one_launch": ([P.problem(pr_A, pr_B, keep[t], "block", 512)
+                              for t, (pr_A, pr_B) in enumerate(probs_host)], True),
+    }
+    timings = {}
+    for name, (plist, one) in variants.items():
+        b = P.Batch(plist, use_graph=True, one_launch=one)
+        b.run(stream)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            b.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_v = e0.elapsed_time(e1) / reps
+        timings[name] = {"ms": ms_v, "value": work / (ms_v * 1e-3) / 1e9,
+                         "launches_per_run": b.stats["launches_per_run"]}
+        b.close()
+    best = min(timings, key=lambda k: timings[k]["ms"])
+    plist, one = variants[best]
+    batch = P.Batch(plist, use_graph=True, one_launch=one)
     batch.run(stream)
     torch.cuda.synchronize()
     # host copies for the CPU leg's oracle check of a few results (the four
@@ -614,6 +643,7 @@ def time_batched(P, torch, device, stream, count=1000, reps=3, tune_buckets=8):
     st = dict(batch.stats)
     batch.close()
     return ({"value": work / (ms * 1e-3) / 1e9, "unit": UNIT, "ms": ms, "problems": count,
+            "plan": best, "plans": timings,
             "launches_per_run": st["launches_per_run"], "leaf_tiles": st["leaf_tiles"],
             "workspace_bytes": st["workspace_bytes"], "graph": True, "steps": reps, "warmup": 1,
             "tuning_table": os.path.exists(tuner.path),

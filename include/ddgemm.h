@@ -284,6 +284,16 @@ typedef struct ddg_batch_s* ddg_batch;
  * its first call and replays the graph afterwards. */
 ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* probs, int32_t use_graph,
                             void* stream);
+/* ddg_batch_create with plan flags: DDG_BATCH_ONE_LEAF_LAUNCH runs every
+ * base-case Block product of the batch, DD and QD together, in one
+ * persistent grouped launch with tiles converted as they are staged (the
+ * same bits as the default plan, which converts the operands of larger
+ * products once in separate launches); a batch of Block problems (or of
+ * problems no larger than their cutoff) then runs as a single kernel.
+ * Unknown flags: DDG_EINVAL. */
+#define DDG_BATCH_ONE_LEAF_LAUNCH 1
+ddg_status ddg_batch_create_ex(ddg_batch* out, int32_t count, const ddg_problem* probs, int32_t use_graph,
+                               int32_t flags, void* stream);
 /* Queue one execution of the plan on `stream` (allocation-free). Runs of
  * one plan must not overlap on the GPU (they share the temporaries). */
 ddg_status ddg_batch_run(ddg_batch b, void* stream);

@@ -103,10 +103,14 @@ def problem(A, B, C, algo: str = "block", cutoff: int = 512, mode: str = "set"):
 class Batch:
     """A batch plan (ddg_batch): grouped launches, optionally a CUDA graph."""
 
-    def __init__(self, problems, use_graph: bool = False, stream=None):
+    def __init__(self, problems, use_graph: bool = False, stream=None, one_launch: bool = False):
+        """one_launch: every base-case product (DD and QD) in one persistent
+        grouped launch, tiles converted as staged (DDG_BATCH_ONE_LEAF_LAUNCH;
+        the same bits)."""
         import torch
         self.stream = stream or torch.cuda.current_stream()
-        self.handle = capi.ddg_batch_create(problems, use_graph, self.stream.cuda_stream)
+        self.handle = capi.ddg_batch_create(problems, use_graph, self.stream.cuda_stream,
+                                            capi.DDG_BATCH_ONE_LEAF_LAUNCH if one_launch else 0)
         self.stats = capi.ddg_batch_get_stats(self.handle)
 
     def run(self, stream=None):

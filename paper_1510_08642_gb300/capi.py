@@ -84,6 +84,8 @@ SIGNATURES = {
     "ddg_block_fp64_ops_per_mac": (c_i32, [c_i32, c_i32]),
     "ddg_ozaki2_precision": (c_i32, [c_i32, c_i64]),
     "ddg_batch_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(ddg_problem), c_i32, c_vp]),
+    "ddg_batch_create_ex": (c_i32, [ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(ddg_problem), c_i32, c_i32,
+                                    c_vp]),
     "ddg_batch_run": (c_i32, [c_vp, c_vp]),
     "ddg_batch_get_stats": (c_i32, [c_vp, ctypes.POINTER(ddg_batch_stats)]),
     "ddg_batch_destroy": (c_i32, [c_vp, c_vp]),
@@ -208,11 +210,14 @@ def dd_getrs(n, nrhs, LU: dd_mat, ipiv: int, B: dd_mat, stream: int = 0) -> int:
     return load().dd_getrs(n, nrhs, LU, c_vp(ipiv), B, c_vp(stream))
 
 
-def ddg_batch_create(problems, use_graph: bool = False, stream: int = 0) -> int:
+DDG_BATCH_ONE_LEAF_LAUNCH = 1
+
+
+def ddg_batch_create(problems, use_graph: bool = False, stream: int = 0, flags: int = 0) -> int:
     arr = (ddg_problem * max(len(problems), 1))(*problems)
     h = c_vp()
-    check(load().ddg_batch_create(ctypes.byref(h), len(problems), arr, 1 if use_graph else 0,
-                                  c_vp(stream)))
+    check(load().ddg_batch_create_ex(ctypes.byref(h), len(problems), arr, 1 if use_graph else 0, flags,
+                                     c_vp(stream)))
     return h.value
 
 

@@ -33,7 +33,8 @@ namespace ddg {
 namespace {
 
 struct Launch {
-  int type;  // 0 pass, 1 grouped Block, 2 grouped conversion, 3 grouped Block on converted operands
+  int type;  // 0 pass, 1 grouped Block, 2 grouped conversion, 3 grouped Block on converted operands,
+            // 4 grouped Block of DD and QD tasks together (one leaf launch)
   int limbs;
   int kind;
   size_t task_off;  // byte offset of the task array in the plan's buffer
@@ -171,6 +172,9 @@ static ddg_status enqueue(ddg_batch_s* b, cudaStream_t s) {
     else if (L.type == 2)
       e = launch_grouped_convert(L.limbs, reinterpret_cast<const fx_ctask*>(b->buf + L.task_off), L.ntasks,
                                  L.total, L.ops, s);
+    else if (L.type == 4)
+      e = launch_grouped_mixed(reinterpret_cast<const gtask*>(b->buf + L.task_off), L.ntasks, L.total,
+                               reinterpret_cast<unsigned long long*>(b->buf + L.counter_off), L.ops, s);
     else
       e = launch_grouped_fxc(L.limbs, reinterpret_cast<const gctask*>(b->buf + L.task_off), L.ntasks, L.total,
                              reinterpret_cast<unsigned long long*>(b->buf + L.counter_off), L.ops, s);
@@ -205,12 +209,19 @@ extern "C" {
 
 ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* probs, int32_t use_graph,
                             void* stream) {
+  return ddg_batch_create_ex(out, count, probs, use_graph, 0, stream);
+}
+
+ddg_status ddg_batch_create_ex(ddg_batch* out, int32_t count, const ddg_problem* probs, int32_t use_graph,
+                               int32_t flags, void* stream) {
   using namespace ddg;
   clear_error();
   if (!out) return set_error(DDG_EINVAL, "out is null");
   *out = nullptr;
   if (count < 0 || (count > 0 && !probs)) return set_error(DDG_EINVAL, "bad problem list");
   if (use_graph != 0 && use_graph != 1) return set_error(DDG_EINVAL, "use_graph must be 0 or 1");
+  if (flags & ~DDG_BATCH_ONE_LEAF_LAUNCH) return set_error(DDG_EINVAL, "unknown batch flags");
+  const bool one_leaf = (flags & DDG_BATCH_ONE_LEAF_LAUNCH) != 0;
   for (int32_t i = 0; i < count; ++i) {
     std::string why;
     if (bad_problem(probs[i], why)) return set_error(DDG_EINVAL, "problem " + std::to_string(i) + ": " + why);
@@ -232,9 +243,10 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
     return fxop_bytes(L, g.m, g.l) + fxop_bytes(L, g.l, g.n);
   };
   size_t convs = 0;
-  for (int L : {2, 4})
-    for (const gtask& g : dry.leaves[L])
-      if (block_fx_converts(L, g.m, g.l, g.n)) convs += conv_bytes(L, g);
+  if (!one_leaf)
+    for (int L : {2, 4})
+      for (const gtask& g : dry.leaves[L])
+        if (block_fx_converts(L, g.m, g.l, g.n)) convs += conv_bytes(L, g);
   // without room for the converted operands every leaf converts its tiles
   // as they are staged (the same bits)
   bool conv_ok = true;
@@ -399,9 +411,43 @@ ddg_status ddg_batch_create(ddg_batch* out, int32_t count, const ddg_problem* pr
   for (int d = 0; d <= real.maxdepth; ++d)
     for (auto& kv : real.pre)
       if (std::get<0>(kv.first) == d) add_p(kv.second, std::get<1>(kv.first), std::get<2>(kv.first));
-  for (int L : {2, 4}) {
-    b->stats.leaf_tasks += (int64_t)real.leaves[L].size();
-    add_converted(real.leaves[L], L);
+  if (one_leaf) {
+    // every base-case product of both limb counts in one persistent launch,
+    // tiles converted as they are staged (the converted-operand bits)
+    std::vector<gtask> all;
+    for (int L : {2, 4}) {
+      b->stats.leaf_tasks += (int64_t)real.leaves[L].size();
+      for (gtask g : real.leaves[L]) {
+        g.limbs = L;
+        all.push_back(g);
+      }
+    }
+    if (!all.empty()) {
+      std::stable_sort(all.begin(), all.end(), [](const gtask& x, const gtask& y) {
+        return (double)x.l * x.limbs * x.limbs > (double)y.l * y.limbs * y.limbs;  // longest tiles first
+      });
+      int64_t t0 = 0;
+      double macs = 0.0;
+      for (auto& g : all) {
+        int bm, bn;
+        fx_tile_shape(g.limbs, &bm, &bn);
+        g.tiles_n = (int)((g.n + bn - 1) / bn);
+        g.tile0 = t0;
+        t0 += (int64_t)((g.m + bm - 1) / bm) * g.tiles_n;
+        macs += (double)g.m * g.l * g.n;
+      }
+      Launch la{4, 0, 0, 0, (int)all.size(), t0, 0, macs};
+      la.task_off = push_tasks(all.data(), all.size() * sizeof(gtask));
+      const uint64_t zero = 0;
+      la.counter_off = push_tasks(&zero, sizeof(zero));
+      launches.push_back(la);
+      b->stats.leaf_tiles += t0;
+    }
+  } else {
+    for (int L : {2, 4}) {
+      b->stats.leaf_tasks += (int64_t)real.leaves[L].size();
+      add_converted(real.leaves[L], L);
+    }
   }
   for (int d = real.maxdepth; d >= 0; --d) {
     for (auto& kv : real.post)

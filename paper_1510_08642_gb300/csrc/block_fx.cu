@@ -547,6 +547,46 @@ __global__ void __launch_bounds__(128, fxcfg<L>::MINB - 1) grouped_fxc_kernel(co
   }
 }
 
+// DD and QD tiles of one task list in one persistent launch (a batch plan
+// with one leaf launch): every CTA takes the next tile from the global
+// counter, whatever its task's limb count, and converts its tiles as they
+// are staged (the bits of the converted-operand kernels). No CTA waits on
+// another.
+union fx_smem_any {
+  fx_smem<2> d;
+  fx_smem<4> q;
+};
+
+__global__ void __launch_bounds__(128, fxcfg<2>::MINB - 1) grouped_mixed_kernel(const gtask* __restrict__ tasks,
+                                                                              int ntasks, int64_t total,
+                                                                              unsigned long long* counter) {
+  __shared__ fx_smem_any sm;
+  __shared__ int64_t st;
+  for (;;) {
+    if (threadIdx.x == 0) st = (int64_t)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const int64_t t = st;
+    __syncthreads();
+    if (t >= total) break;
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tasks[mid].tile0 <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const gtask g = tasks[lo];
+    const int64_t local = t - g.tile0;
+    const int64_t bi = local / g.tiles_n, bj = local % g.tiles_n;
+    if (g.limbs == 2)
+      fx_tile<2, false>(g.m, g.l, g.n, g.A, g.B, g.C, g.mode, bi * fxcfg<2>::BM, bj * fxcfg<2>::BN, sm.d, fxop{},
+                        fxop{});
+    else
+      fx_tile<4, false>(g.m, g.l, g.n, g.A, g.B, g.C, g.mode, bi * fxcfg<4>::BM, bj * fxcfg<4>::BN, sm.q, fxop{},
+                        fxop{});
+    __syncthreads();
+  }
+}
+
 void fx_tile_shape(int limbs, int* bm, int* bn) {
   *bm = limbs == 2 ? fxcfg<2>::BM : fxcfg<4>::BM;
   *bn = limbs == 2 ? fxcfg<2>::BN : fxcfg<4>::BN;
@@ -571,6 +611,28 @@ cudaError_t launch_grouped_fx(int limbs, const gtask* tasks, int ntasks, int64_t
   prof_begin_launch(s, &ev);
   if (limbs == 2) grouped_fx_kernel<2><<<(unsigned)grid, 128, 0, s>>>(tasks, ntasks, total_tiles, counter);
   else grouped_fx_kernel<4><<<(unsigned)grid, 128, 0, s>>>(tasks, ntasks, total_tiles, counter);
+  e = cudaGetLastError();
+  if (ev) prof_end_launch(s, ev, PROF_BLOCK, ops, 0.0);
+  return e;
+}
+
+cudaError_t launch_grouped_mixed(const gtask* tasks, int ntasks, int64_t total_tiles, unsigned long long* counter,
+                                 double ops, cudaStream_t s) {
+  if (ntasks == 0 || total_tiles == 0) return cudaSuccess;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)sms * (fxcfg<2>::MINB - 1));
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaEvent_t ev = nullptr;
+  prof_begin_launch(s, &ev);
+  grouped_mixed_kernel<<<(unsigned)grid, 128, 0, s>>>(tasks, ntasks, total_tiles, counter);
   e = cudaGetLastError();
   if (ev) prof_end_launch(s, ev, PROF_BLOCK, ops, 0.0);
   return e;

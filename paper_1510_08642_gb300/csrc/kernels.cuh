@@ -139,7 +139,13 @@ struct gtask {
   int mode;
   int tiles_n;
   int64_t tile0;
+  int limbs;  // 2 or 4; read by the mixed launch (launch_grouped_mixed) only
 };
+// DD and QD tasks of one list in one persistent launch (tiles converted as
+// they are staged; each task's tiles numbered with its own limb count's
+// tile shape, fx_tile_shape).
+cudaError_t launch_grouped_mixed(const gtask* tasks, int ntasks, int64_t total_tiles, unsigned long long* counter,
+                                 double ops, cudaStream_t s);
 void fx_tile_shape(int limbs, int* bm, int* bn);
 
 // Grouped conversion (batch plans): operand t (rows x cols of X) into w, f

@@ -100,6 +100,56 @@ def test_batch_converted_leaves_bit_identical(use_graph):
     batch.close()
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+@pytest.mark.parametrize("recursive", [False, True])
+def test_one_leaf_launch_plan_bit_identical(use_graph, recursive):
+    """DDG_BATCH_ONE_LEAF_LAUNCH: every base-case product, DD and QD, in one
+    persistent grouped launch with tiles converted as staged. The same bits
+    as the default plan (which converts larger products' operands once) and
+    as each product alone; an all-Block batch is a single kernel per run."""
+    import paper_1510_08642_gb300 as P
+    from paper_1510_08642_gb300 import capi
+    probs = make_batch(24, 3, 300, seed=11, qd_frac=0.4, cutoffs=(16, 64, 100))
+    if not recursive:
+        for p in probs:
+            p["algo"] = "block"
+    dev = []
+    for p in probs:
+        dA, dB = to_dev(p["A"]), to_dev(p["B"])
+        dev.append((dA, dB, to_dev(p["C0"]), to_dev(p["C0"])))
+    one = P.Batch([P.problem(dA, dB, dC, p["algo"], p["cutoff"], p["mode"])
+                   for (dA, dB, dC, _), p in zip(dev, probs)], use_graph=use_graph, one_launch=True)
+    ref = P.Batch([P.problem(dA, dB, dC1, p["algo"], p["cutoff"], p["mode"])
+                   for (dA, dB, _, dC1), p in zip(dev, probs)], use_graph=use_graph)
+    if not recursive:
+        assert one.stats["launches_per_run"] == 1
+    assert one.stats["leaf_tasks"] == ref.stats["leaf_tasks"]
+    if not use_graph:
+        capi.ddg_profile_begin()
+    one.run()
+    if not use_graph:
+        prof = capi.ddg_profile_end()
+        assert prof["convert"]["launches"] == 0 and prof["block"]["launches"] >= 1
+    ref.run()
+    torch.cuda.synchronize()
+    for (dA, dB, dC, dC1), p in zip(dev, probs):
+        assert np.array_equal(to_host(dC), to_host(dC1)), (p["algo"], p["cutoff"], p["mode"], p["A"].shape)
+        err = O.gemm_error(p["A"], p["B"], to_host(dC), C0=p["C0"], mode=p["mode"])
+        assert O.normwise(err, p["A"], p["B"]) <= normwise_bound(p["A"].shape[2], p["limbs"], p["algo"])
+    one.close()
+    ref.close()
+
+
+def test_batch_rejects_unknown_flags():
+    import paper_1510_08642_gb300 as P
+    from paper_1510_08642_gb300 import capi
+    A = to_dev(I.uniform(4, 4, 2, seed=1))
+    p = P.problem(A, A, to_dev(I.uniform(4, 4, 2, seed=2)), "block", 8)
+    with pytest.raises(capi.DDGError) as e:
+        capi.ddg_batch_create([p], False, torch.cuda.current_stream().cuda_stream, flags=2)
+    assert e.value.status == capi.DDG_EINVAL
+
+
 def test_dd_gemm_batched_one_shot():
     import paper_1510_08642_gb300 as P
     from paper_1510_08642_gb300 import capi
