@@ -8,11 +8,14 @@
 //     W-word fixed-point integer M (its limbs summed exactly at their own
 //     offsets below the leading limb's significand; W = 4 words for DD,
 //     7 for QD), its exponent field and sign (fx::to_fixed);
-//   * multiply-add: the K = 2 W - D leading words of M_a M_b from the
-//     partial products with i + j >= D (fx::mul_top, D = 3 / 6: 10 / 28
-//     32x32-bit multiply-adds), shifted into a two's-complement window of
-//     NW words per output entry (fx::place_shr) whose scale is fixed before
-//     the k loop from the largest exponent of row i of A and column j of B;
+//   * multiply-add, shifted form (QD; DD outputs the pre-shifted form turns
+//     down): the K = 2 W - D leading words of M_a M_b from the partial
+//     products with i + j >= D (fx::mul_top, D = 3 / 6: 10 / 28 32x32-bit
+//     multiply-adds), shifted by the operands' distances below the largest
+//     exponent of row i of A and column j of B into a two's-complement
+//     window of NW words per output (fx::place_shr);
+//   * multiply-add, pre-shifted form (DD, fx_pre.cuh): the operands shifted
+//     at staging instead, every product added unshifted;
 //   * epilogue: the window rounded to DD / QD once.
 // Conversion once per operand: a tile of A is staged by every CTA of its row
 // of tiles (n / BN of them) and a tile of B by m / BM CTAs, so converting on
@@ -21,13 +24,14 @@
 // kernel (fx_convert_kernel, into scratch the caller provides) and the Block
 // kernel stages the converted words by plain copies (block_fxc_kernel); the
 // words, shifts and therefore the results are the same bits either way.
-// Error per term: the dropped partial products, < 2^-123 (DD) / 2^-219
-// (QD) of |a_ik b_kj|, and the truncation below the window, 2^-159 (DD) /
-// 2^-255 (QD) of the largest product of row i and column j; the sum in the
-// window is exact for l < 2^31. An output whose window sum keeps fewer than
-// 53 L significant bits is recomputed with the window at its own largest
-// term (fx_rescue.cuh), so every output is accurate relative to its own
-// sum_k |a_ik b_kj|. One final rounding to DD / QD.
+// Error per term of the shifted form: the dropped partial products,
+// < 2^-123 (DD) / 2^-219 (QD) of |a_ik b_kj|, and the truncation below
+// the window, 2^-159 (DD) / 2^-255 (QD) of the largest product of row i
+// and column j; the sum in the window is exact for l < 2^31. An output
+// whose window sum keeps fewer than 53 L significant bits is recomputed
+// with the window at its own largest term (fx_rescue.cuh), so every output
+// is accurate relative to its own sum_k |a_ik b_kj|. One final rounding to
+// DD / QD.
 #include <algorithm>
 #include <type_traits>
 
@@ -364,7 +368,7 @@ __device__ __forceinline__ void fx_pre(int64_t m, int64_t l, int64_t n, const ma
 #pragma unroll
         for (int c = 0; c < TN; ++c) {
           uint32_t q[4];
-          mul_top_hi<4>(a[r], b[c], q);
+          fx::mul_top_hi<4>(a[r], b[c], q);
           pre_add(acc[r][c], q, sa[r] ^ sb[c]);
         }
     }

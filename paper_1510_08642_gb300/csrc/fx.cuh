@@ -389,6 +389,72 @@ __host__ __device__ __forceinline__ void mul_top(const uint32_t (&a)[W], const u
   p[2 * W - 1 - D] = c0;
 }
 
+// q = the W words of a b at columns W .. 2 W - 1 (column c: 2^(32 c)) from
+// the partial products a_i b_j with i + j >= W, and of those with
+// i + j = W - 1 only the high halves (their low halves, the products below
+// and all their carries are left out): q is below floor(a b / 2^(32 W)) by
+// less than 2 W. Column by column, a three-word running sum; on the device
+// 16 IMAD for W = 4 (6 products x 2 + 4 high halves). The product of the
+// pre-shifted DD Block form (fx_pre.cuh).
+template <int W>
+__host__ __device__ __forceinline__ void mul_top_hi(const uint32_t (&a)[W], const uint32_t (&b)[W],
+                                                    uint32_t (&q)[W]) {
+  constexpr int D = W - 1;
+#ifdef __CUDA_ARCH__
+  uint32_t c0 = 0u, c1 = __umulhi(a[0], b[D]), c2 = 0u;
+#pragma unroll
+  for (int i = 1; i < W; ++i)
+    asm("mad.hi.cc.u32 %0, %2, %3, %0;\n\t"
+        "addc.u32 %1, %1, 0;"
+        : "+r"(c1), "+r"(c2)
+        : "r"(a[i]), "r"(b[D - i]));
+#pragma unroll
+  for (int k = W; k <= 2 * W - 2; ++k) {
+    c0 = c1;
+    c1 = c2;
+    c2 = 0u;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      const int j = k - i;
+      if (j < 0 || j >= W) continue;
+      if (k < 2 * W - 2) {
+        asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+            "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+            "addc.u32 %2, %2, 0;"
+            : "+r"(c0), "+r"(c1), "+r"(c2)
+            : "r"(a[i]), "r"(b[j]));
+      } else {  // the top column: a b < 2^(64 W), no carry out of it
+        asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\t"
+            "madc.hi.u32 %1, %2, %3, %1;"
+            : "+r"(c0), "+r"(c1)
+            : "r"(a[i]), "r"(b[j]));
+      }
+    }
+    q[k - W] = c0;
+  }
+  q[W - 1] = c1;
+#else
+  // the same sum with 64-bit column accumulators
+  uint64_t col[2 * W + 1] = {};
+  for (int i = 0; i < W; ++i)
+    for (int j = 0; j < W; ++j) {
+      const uint64_t pr = (uint64_t)a[i] * b[j];
+      if (i + j == D) {
+        col[W] += pr >> 32;
+      } else if (i + j >= W) {
+        col[i + j] += (uint32_t)pr;
+        col[i + j + 1] += pr >> 32;
+      }
+    }
+  uint64_t carry = 0;
+  for (int k = W; k < 2 * W; ++k) {
+    const uint64_t v = col[k] + carry;
+    q[k - W] = (uint32_t)v;
+    carry = v >> 32;
+  }
+#endif
+}
+
 // (hi:lo >> r) low word, r in [0, 31]
 __host__ __device__ __forceinline__ uint32_t shr_funnel(uint32_t lo, uint32_t hi, int r) {
 #ifdef __CUDA_ARCH__

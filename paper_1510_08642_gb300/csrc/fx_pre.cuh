@@ -63,48 +63,6 @@ __device__ __forceinline__ void shr_words(uint32_t (&M)[W], int s) {
   }
 }
 
-// q = the W words of a b at columns W .. 2 W - 1 (column c: 2^(32 c)) from
-// the partial products a_i b_j with i + j >= W, and of those with
-// i + j = W - 1 only the high halves (their low halves, the products below
-// and all their carries are left out): q is below floor(a b / 2^(32 W)) by
-// less than 2 W. Column by column, a three-word running sum.
-template <int W>
-__device__ __forceinline__ void mul_top_hi(const uint32_t (&a)[W], const uint32_t (&b)[W], uint32_t (&q)[W]) {
-  constexpr int D = W - 1;
-  uint32_t c0 = 0u, c1 = __umulhi(a[0], b[D]), c2 = 0u;
-#pragma unroll
-  for (int i = 1; i < W; ++i)
-    asm("mad.hi.cc.u32 %0, %2, %3, %0;\n\t"
-        "addc.u32 %1, %1, 0;"
-        : "+r"(c1), "+r"(c2)
-        : "r"(a[i]), "r"(b[D - i]));
-#pragma unroll
-  for (int k = W; k <= 2 * W - 2; ++k) {
-    c0 = c1;
-    c1 = c2;
-    c2 = 0u;
-#pragma unroll
-    for (int i = 0; i < W; ++i) {
-      const int j = k - i;
-      if (j < 0 || j >= W) continue;
-      if (k < 2 * W - 2) {
-        asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
-            "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
-            "addc.u32 %2, %2, 0;"
-            : "+r"(c0), "+r"(c1), "+r"(c2)
-            : "r"(a[i]), "r"(b[j]));
-      } else {  // the top column: a b < 2^(64 W), no carry out of it
-        asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\t"
-            "madc.hi.u32 %1, %2, %3, %1;"
-            : "+r"(c0), "+r"(c1)
-            : "r"(a[i]), "r"(b[j]));
-      }
-    }
-    q[k - W] = c0;
-  }
-  q[W - 1] = c1;
-}
-
 // acc (window words 1 .. 5; word 0 stays 0) += the term q with sign mask s
 // (0 or ~0): (q XOR s, s) plus the carry s & 1 (two's complement; word 0 of
 // -q is 0).

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(32 * GV_WARPS) gemv_fx_kernel(int64_t m, int64
       const uint32_t sa = ((ea >> 16) & 1) && !za ? 0xFFFFFFFFu : 0u;
       const uint32_t sb = ((eb >> 16) & 1) && !zb ? 0xFFFFFFFFu : 0u;
       uint32_t q[W];
-      mul_top_hi<W>(ma, mb, q);
+      fx::mul_top_hi<W>(ma, mb, q);
       pre_add(pa, q, sa ^ sb);
     }
     pre_window(pa, acc);

@@ -3,6 +3,7 @@
 // compare them with exact integer arithmetic. Host code only (no kernels).
 //   T L x0 .. x(L-1)          -> to_fixed: es M[0] .. M[W-1]   (W = 4 / 7)
 //   M W D a[0..W-1] b[0..W-1]  -> mul_top: p[0 .. 2W-D-1]
+//   H W a[0..W-1] b[0..W-1]    -> mul_top_hi: q[0 .. W-1]           (W = 4 / 7)
 //   P NW K sh neg acc[0..NW-1] p[0..K-1] -> place_shr: acc[0 .. NW-1]
 //   N NW W A[0..NW-1]          -> acc_normalize: p M[0..W-1]   (6,4) / (9,7)
 //   R NW s A[0..NW-1]          -> acc_sar: A[0..NW-1]          (NW = 6 / 9)
@@ -52,6 +53,15 @@ static void do_mul() {
   for (int i = 0; i < W; ++i) scan("%u", &b[i]);
   fx::mul_top<W, D>(a, b, p);
   for (int i = 0; i < 2 * W - D; ++i) std::printf("%u%c", p[i], i + 1 < 2 * W - D ? ' ' : '\n');
+}
+
+template <int W>
+static void do_mul_hi() {
+  uint32_t a[W], b[W], q[W];
+  for (int i = 0; i < W; ++i) scan("%u", &a[i]);
+  for (int i = 0; i < W; ++i) scan("%u", &b[i]);
+  fx::mul_top_hi<W>(a, b, q);
+  for (int i = 0; i < W; ++i) std::printf("%u%c", q[i], i + 1 < W ? ' ' : '\n');
 }
 
 template <int NW, int K>
@@ -165,6 +175,10 @@ int main() {
       scan("%d %d", &a, &b);
       if (a == 4) do_mul<4, 3>();
       else do_mul<7, 6>();
+    } else if (cmd[0] == 'H') {
+      scan("%d", &a);
+      if (a == 4) do_mul_hi<4>();
+      else do_mul_hi<7>();
     } else if (cmd[0] == 'F') {
       scan("%d", &a);
       if (a == 2) do_fms<2>();

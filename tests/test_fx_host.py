@@ -103,6 +103,32 @@ def test_mul_top_within_dropped_columns(fxbin, W, D):
         assert 0 <= exact - p < (D + 1) * 2 ** 32
 
 
+@pytest.mark.parametrize("W", [4, 7])
+def test_mul_top_hi_is_its_definition(fxbin, W):
+    """mul_top_hi: the words at columns W .. 2W-1 of the sum of the partial
+    products a_i b_j with i + j >= W plus the high halves of those with
+    i + j = W - 1 (exact big-integer sum, written out here); below
+    floor(a b / 2^(32 W)) by less than 2 W (the dropped column W - 1)."""
+    rng = random.Random(100 + W)
+    cases = [(rng.getrandbits(32 * W), rng.getrandbits(32 * W)) for _ in range(300)]
+    cases += [(2 ** (32 * W) - 1, 2 ** (32 * W) - 1), (0, 12345), (1 << (32 * W - 1), 3), (2 ** 64 - 1, 2 ** 96 + 7)]
+    lines = [f"H {W} " + " ".join(map(str, words(a, W) + words(b, W))) for a, b in cases]
+    for (a, b), line in zip(cases, run(fxbin, lines)):
+        q = value([int(t) for t in line.split()])
+        aw, bw = words(a, W), words(b, W)
+        s = 0
+        for i in range(W):
+            for j in range(W):
+                pr = aw[i] * bw[j]
+                if i + j >= W:
+                    s += pr << (32 * (i + j))
+                elif i + j == W - 1:
+                    s += (pr >> 32) << (32 * W)
+        assert q == s >> (32 * W)
+        exact = (a * b) >> (32 * W)
+        assert 0 <= exact - q < 2 * W
+
+
 @pytest.mark.parametrize("NW,K", [(6, 5), (9, 8)])
 def test_place_shr_exact(fxbin, NW, K):
     rng = random.Random(NW)
