@@ -62,14 +62,13 @@ ISSUE_PEAK = SM_COUNT * ISSUE_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # thread instru
 IMAD_PER_CLK_PER_SM = 64          # measured: IMAD throughput probe (profiles/fp64_int8_peaks.md)
 IMAD_PEAK = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6   # 32-bit integer multiply-adds per second
 # The Block multiply-add's irreducible integer multiplies, counted from the
-# source. DD, pre-shifted form (fx_pre.cuh, mul_top_hi): the 6 partial
-# products a_i b_j with i + j >= 4 of the 4-word operands, a mad.lo and a
-# madc.hi each, and the high halves (mad.hi) of the 4 with i + j = 3: 16
-# IMAD. QD, shifted form (fx::mul_top, W = 7, D = 6): 28 partial products,
-# 56 IMAD.
-IMAD_FLOOR_PER_MAC = {2: 16, 4: 56}
-IMAD_FLOOR_SOURCE = {2: "fx_pre.cuh mul_top_hi: 6 partial products x (mad.lo + madc.hi) + 4 x mad.hi",
-                     4: "fx::mul_top: 28 partial products x (mad.lo + madc.hi)"}
+# source (the pre-shifted form, fx_pre.cuh, fx::mul_top_hi): of the W-word
+# operands the partial products a_i b_j with i + j >= W, a mad.lo and a
+# madc.hi each, and the high halves (mad.hi) of the W with i + j = W - 1:
+# DD (W = 4) 6 x 2 + 4 = 16 IMAD, QD (W = 7) 21 x 2 + 7 = 49 IMAD.
+IMAD_FLOOR_PER_MAC = {2: 16, 4: 49}
+IMAD_FLOOR_SOURCE = {2: "fx::mul_top_hi<4>: 6 partial products x (mad.lo + madc.hi) + 4 x mad.hi",
+                     4: "fx::mul_top_hi<7>: 21 partial products x (mad.lo + madc.hi) + 7 x mad.hi"}
 
 
 def parse():

@@ -167,7 +167,9 @@ ddg_status dd_gemm(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, dd_mat C
                    const ddg_opts* opts, void* stream);
 
 /* qd_gemm: as dd_gemm for quad-double: Block within (2 l + 4) 2^-209 |A||B|
- * elementwise (outputs keeping fewer than 212 window bits recomputed),
+ * elementwise (operands shifted once to their row / column maximum; an
+ * output keeping fewer than 245 window bits recomputed with every product
+ * at its own scale, and one keeping fewer than 212 at its largest term),
  * Strassen / Winograd within 8 l^log2(12) 2^-208 ||A|| ||B||. */
 ddg_status qd_gemm(int64_t m, int64_t l, int64_t n, qd_mat A, qd_mat B, qd_mat C, int32_t mode,
                    const ddg_opts* opts, void* stream);

@@ -7,16 +7,16 @@
 //   * staging: every element of the A and B tiles is converted once into a
 //     W-word fixed-point integer M (its limbs summed exactly at their own
 //     offsets below the leading limb's significand; W = 4 words for DD,
-//     7 for QD), its exponent field and sign (fx::to_fixed);
-//   * multiply-add, shifted form (QD; DD outputs the pre-shifted form turns
-//     down): the K = 2 W - D leading words of M_a M_b from the partial
-//     products with i + j >= D (fx::mul_top, D = 3 / 6: 10 / 28 32x32-bit
-//     multiply-adds), shifted by the operands' distances below the largest
-//     exponent of row i of A and column j of B into a two's-complement
-//     window of NW words per output (fx::place_shr);
-//   * multiply-add, pre-shifted form (DD, fx_pre.cuh): the operands shifted
-//     at staging instead, every product added unshifted;
-//   * epilogue: the window rounded to DD / QD once.
+//     7 for QD; fx::to_fixed) and shifted to the largest exponent of its
+//     row of A / column of B; its sign kept as a mask (fx_pre.cuh);
+//   * multiply-add: the upper W words of M_a M_b (fx::mul_top_hi: the
+//     partial products with i + j >= W and the high halves of those with
+//     i + j = W - 1; 16 IMAD for DD, 49 for QD), added unshifted into a
+//     two's-complement window of NW = W + 2 words per output whose scale
+//     is fixed before the k loop from those maxima;
+//   * epilogue: the window rounded to DD / QD once; an output that keeps
+//     too few window bits is recomputed by its warp in the shifted form and
+//     rescued if needed (fx_rescue.cuh).
 // Conversion once per operand: a tile of A is staged by every CTA of its row
 // of tiles (n / BN of them) and a tile of B by m / BM CTAs, so converting on
 // the fly repeats to_fixed for each element that often. For products with
@@ -24,14 +24,8 @@
 // kernel (fx_convert_kernel, into scratch the caller provides) and the Block
 // kernel stages the converted words by plain copies (block_fxc_kernel); the
 // words, shifts and therefore the results are the same bits either way.
-// Error per term of the shifted form: the dropped partial products,
-// < 2^-123 (DD) / 2^-219 (QD) of |a_ik b_kj|, and the truncation below
-// the window, 2^-159 (DD) / 2^-255 (QD) of the largest product of row i
-// and column j; the sum in the window is exact for l < 2^31. An output
-// whose window sum keeps fewer than 53 L significant bits is recomputed
-// with the window at its own largest term (fx_rescue.cuh), so every output
-// is accurate relative to its own sum_k |a_ik b_kj|. One final rounding to
-// DD / QD.
+// Error per term and the acceptance test: fx_pre.cuh; the sum in the window
+// is exact for l < 2^31; one final rounding to DD / QD.
 #include <algorithm>
 #include <type_traits>
 
@@ -49,7 +43,7 @@ namespace {
 template <int L> struct fxcfg;
 template <> struct fxcfg<2> : fxwin<2> {
   static constexpr int BM = 16, BN = 32, BK = 16, TM = 2, TN = 2;
-  static constexpr int MINB = 7;  // resident CTAs per SM (register cap 72; 8 CTAs at 64 measured 0.9% slower)
+  static constexpr int MINB = 8;  // resident CTAs per SM (register cap 64; 7 at 72 measured 3% slower)
 };
 template <> struct fxcfg<4> : fxwin<4> {
   static constexpr int BM = 8, BN = 32, BK = 16, TM = 1, TN = 2;
@@ -69,36 +63,28 @@ struct fx_smem {
   static constexpr int WV = (fxcfg<L>::W + 3) / 4;
   uint4 Aw[WV][fxcfg<L>::BK][fxcfg<L>::BM + 1];
   uint4 Bw[WV][fxcfg<L>::BK][fxcfg<L>::BN];
-  int2 Ae[fxcfg<L>::BK][fxcfg<L>::BM + 1];
-  int2 Be[fxcfg<L>::BK][fxcfg<L>::BN];
+  int As[fxcfg<L>::BK][fxcfg<L>::BM + 1];  // sign masks (0 or -1)
+  int Bs[fxcfg<L>::BK][fxcfg<L>::BN];
   int row_f[fxcfg<L>::BM], col_f[fxcfg<L>::BN];
 };
 
 namespace {
 
-// Store one element's words and its (shift, sign mask) pair below the row /
-// column maximum fmax (SH: the shifted form; a zero gets shift 0); or, for
-// the pre-shifted form, its words shifted by that amount and shift 0.
-template <int L, bool SH>
+// Store one element's words shifted to its row / column maximum fmax
+// (fx_pre.cuh; a zero stores 0) and its sign mask.
+template <int L>
 __device__ __forceinline__ void put_staged(uint32_t (&M)[4 * fx_smem<L>::WV], bool zero, int f, int fmax, uint4* w,
-                                           int stride, int2* e) {
+                                           int stride, int* sgn) {
   constexpr int W = fxcfg<L>::W, WV = fx_smem<L>::WV;
-  const int sh = zero ? 0 : fmax - (f & 0xFFFF);
-  if constexpr (SH) {
+  shr_words<W>(*reinterpret_cast<uint32_t(*)[W]>(M), zero ? 32 * W : fmax - (f & 0xFFFF));
 #pragma unroll
-    for (int v = 0; v < WV; ++v) w[v * stride] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
-    *e = make_int2(sh, ((f >> 16) & 1) ? -1 : 0);
-  } else {
-    shr_words<W>(*reinterpret_cast<uint32_t(*)[W]>(M), zero ? 32 * W : sh);
-#pragma unroll
-    for (int v = 0; v < WV; ++v) w[v * stride] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
-    *e = make_int2(0, ((f >> 16) & 1) && !zero ? -1 : 0);
-  }
+  for (int v = 0; v < WV; ++v) w[v * stride] = make_uint4(M[4 * v], M[4 * v + 1], M[4 * v + 2], M[4 * v + 3]);
+  *sgn = ((f >> 16) & 1) && !zero ? -1 : 0;
 }
 
 // Convert one element (to_fixed) and stage it.
-template <int L, bool SH>
-__device__ __forceinline__ void stage(const double (&x)[L], int fmax, uint4* w, int stride, int2* e) {
+template <int L>
+__device__ __forceinline__ void stage(const double (&x)[L], int fmax, uint4* w, int stride, int* sgn) {
   constexpr int W = fxcfg<L>::W, WV = (W + 3) / 4;
   uint32_t M[4 * WV];
   uint32_t(&Mw)[W] = *reinterpret_cast<uint32_t(*)[W]>(M);
@@ -106,14 +92,14 @@ __device__ __forceinline__ void stage(const double (&x)[L], int fmax, uint4* w, 
 #pragma unroll
   for (int t = W; t < 4 * WV; ++t) M[t] = 0u;
   const bool zero = (fx::dbits(x[0]) << 1) == 0u;
-  put_staged<L, SH>(M, zero, es, fmax, w, stride, e);
+  put_staged<L>(M, zero, es, fmax, w, stride, sgn);
 }
 
 // The same staging from a converted operand: its words and f as to_fixed
 // gave them.
-template <int L, bool SH>
+template <int L>
 __device__ __forceinline__ void stage_pre(bool ok, const fxop& X, int64_t e, int fmax, uint4* w, int stride,
-                                          int2* ex) {
+                                          int* sgn) {
   constexpr int WV = fx_smem<L>::WV;
   uint32_t M[4 * WV];
 #pragma unroll
@@ -122,7 +108,7 @@ __device__ __forceinline__ void stage_pre(bool ok, const fxop& X, int64_t e, int
     M[4 * v] = q.x; M[4 * v + 1] = q.y; M[4 * v + 2] = q.z; M[4 * v + 3] = q.w;
   }
   const int f = ok ? X.f[e] : FX_ZERO;
-  put_staged<L, SH>(M, f == FX_ZERO, f, fmax, w, stride, ex);
+  put_staged<L>(M, f == FX_ZERO, f, fmax, w, stride, sgn);
 }
 
 }  // namespace
@@ -169,97 +155,91 @@ __device__ __forceinline__ void fx_maxima(int64_t m, int64_t l, int64_t n, const
   __syncthreads();
 }
 
-// The tile's products and epilogue in the shifted form: each product placed
-// by the two operands' shifts below their row / column maxima; an output
-// that keeps fewer than 53 L window bits is rescued (fx_rescue.cuh).
+// The tile in the pre-shifted form (fx_pre.cuh).
 template <int L, bool PRE>
-__device__ __forceinline__ void fx_body(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
-                                        int mode, int64_t i0, int64_t j0, fx_smem<L>& sm, const fxop& Ax,
-                                        const fxop& Bx) {
+__device__ __forceinline__ void fx_pre(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
+                                       int mode, int64_t i0, int64_t j0, fx_smem<L>& sm, const fxop& Ax,
+                                       const fxop& Bx) {
   using P = fxcfg<L>;
-  constexpr int BM = P::BM, BN = P::BN, BK = P::BK, TM = P::TM, TN = P::TN, NW = P::NW;
-  constexpr int W = P::W, D = P::D, K = P::K, WV = fx_smem<L>::WV;
+  constexpr int BM = P::BM, BN = P::BN, BK = P::BK, TM = P::TM, TN = P::TN, NW = P::NW, W = P::W;
+  constexpr int WV = fx_smem<L>::WV, NP = NW - 1;
+  static_assert(NW == W + 2, "pre-shifted form: window of W + 2 words");
   constexpr int NX = BN / TN, NY = BM / TM, NT = NX * NY;
-  static_assert(NT == 128, "block kernel assumes 128 threads");
   auto& row_f = sm.row_f;
   auto& col_f = sm.col_f;
   const int tid = threadIdx.x;
   const int tx = tid % NX, ty = tid / NX;
 
-  // The k loop over tiles of BK: stage A and B, then per k one product per
-  // output.
-  uint32_t acc[TM][TN][NW];
-  {
+  // window words 1 .. NW - 1 (word 0 stays 0)
+  uint32_t acc[TM][TN][NP];
 #pragma unroll
-    for (int r = 0; r < TM; ++r)
+  for (int r = 0; r < TM; ++r)
 #pragma unroll
-      for (int c = 0; c < TN; ++c)
+    for (int c = 0; c < TN; ++c)
 #pragma unroll
-        for (int w = 0; w < NW; ++w) acc[r][c][w] = 0u;
-    for (int64_t k0 = 0; k0 < l; k0 += BK) {
+      for (int w = 0; w < NP; ++w) acc[r][c][w] = 0u;
+  for (int64_t k0 = 0; k0 < l; k0 += BK) {
 #pragma unroll
-      for (int idx = tid; idx < BM * BK; idx += NT) {
-        const int r = idx / BK, c = idx % BK;
-        const int64_t gi = i0 + r, gk = k0 + c;
-        const bool ok = gi < m && gk < l;
-        if constexpr (PRE) {
-          stage_pre<L, true>(ok, Ax, gi * Ax.ld + gk, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
-        } else {
-          double x[L];
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      const int r = idx / BK, c = idx % BK;
+      const int64_t gi = i0 + r, gk = k0 + c;
+      const bool ok = gi < m && gk < l;
+      if constexpr (PRE) {
+        stage_pre<L>(ok, Ax, gi * Ax.ld + gk, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.As[c][r]);
+      } else {
+        double x[L];
 #pragma unroll
-          for (int q = 0; q < L; ++q) x[q] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
-          stage<L, true>(x, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
-        }
+        for (int q = 0; q < L; ++q) x[q] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
+        stage<L>(x, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.As[c][r]);
       }
+    }
 #pragma unroll
-      for (int idx = tid; idx < BK * BN; idx += NT) {
-        const int r = idx / BN, c = idx % BN;
-        const int64_t gk = k0 + r, gj = j0 + c;
-        const bool ok = gk < l && gj < n;
-        if constexpr (PRE) {
-          stage_pre<L, true>(ok, Bx, gk * Bx.ld + gj, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
-        } else {
-          double x[L];
+    for (int idx = tid; idx < BK * BN; idx += NT) {
+      const int r = idx / BN, c = idx % BN;
+      const int64_t gk = k0 + r, gj = j0 + c;
+      const bool ok = gk < l && gj < n;
+      if constexpr (PRE) {
+        stage_pre<L>(ok, Bx, gk * Bx.ld + gj, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Bs[r][c]);
+      } else {
+        double x[L];
 #pragma unroll
-          for (int q = 0; q < L; ++q) x[q] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
-          stage<L, true>(x, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
-        }
+        for (int q = 0; q < L; ++q) x[q] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
+        stage<L>(x, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Bs[r][c]);
       }
-      __syncthreads();
+    }
+    __syncthreads();
 #pragma unroll 1
-      for (int kk = 0; kk < BK; ++kk) {
-        uint32_t a[TM][4 * WV], b[TN][4 * WV];
-        int2 ea[TM], eb[TN];
+    for (int kk = 0; kk < BK; ++kk) {
+      uint32_t a[TM][4 * WV], b[TN][4 * WV], sa[TM], sb[TN];
 #pragma unroll
-        for (int r = 0; r < TM; ++r) {
+      for (int r = 0; r < TM; ++r) {
 #pragma unroll
-          for (int v = 0; v < WV; ++v) {
-            const uint4 q = sm.Aw[v][kk][ty + r * NY];
-            a[r][4 * v] = q.x; a[r][4 * v + 1] = q.y; a[r][4 * v + 2] = q.z; a[r][4 * v + 3] = q.w;
-          }
-          ea[r] = sm.Ae[kk][ty + r * NY];
+        for (int v = 0; v < WV; ++v) {
+          const uint4 q = sm.Aw[v][kk][ty + r * NY];
+          a[r][4 * v] = q.x; a[r][4 * v + 1] = q.y; a[r][4 * v + 2] = q.z; a[r][4 * v + 3] = q.w;
         }
+        sa[r] = (uint32_t)sm.As[kk][ty + r * NY];
+      }
+#pragma unroll
+      for (int c = 0; c < TN; ++c) {
+#pragma unroll
+        for (int v = 0; v < WV; ++v) {
+          const uint4 q = sm.Bw[v][kk][tx + c * NX];
+          b[c][4 * v] = q.x; b[c][4 * v + 1] = q.y; b[c][4 * v + 2] = q.z; b[c][4 * v + 3] = q.w;
+        }
+        sb[c] = (uint32_t)sm.Bs[kk][tx + c * NX];
+      }
+#pragma unroll
+      for (int r = 0; r < TM; ++r)
 #pragma unroll
         for (int c = 0; c < TN; ++c) {
-#pragma unroll
-          for (int v = 0; v < WV; ++v) {
-            const uint4 q = sm.Bw[v][kk][tx + c * NX];
-            b[c][4 * v] = q.x; b[c][4 * v + 1] = q.y; b[c][4 * v + 2] = q.z; b[c][4 * v + 3] = q.w;
-          }
-          eb[c] = sm.Be[kk][tx + c * NX];
+          uint32_t q[W];
+          fx::mul_top_hi<W>(*reinterpret_cast<const uint32_t(*)[W]>(a[r]),
+                            *reinterpret_cast<const uint32_t(*)[W]>(b[c]), q);
+          pre_add(acc[r][c], q, sa[r] ^ sb[c]);
         }
-#pragma unroll
-        for (int r = 0; r < TM; ++r)
-#pragma unroll
-          for (int c = 0; c < TN; ++c) {
-            uint32_t p[K];
-            fx::mul_top<W, D>(*reinterpret_cast<const uint32_t(*)[W]>(a[r]),
-                              *reinterpret_cast<const uint32_t(*)[W]>(b[c]), p);
-            fx::place_shr<NW, K>(acc[r][c], p, ea[r].x + eb[c].x, (uint32_t)(ea[r].y ^ eb[c].y));
-          }
-      }
-      __syncthreads();
     }
+    __syncthreads();
   }
 
   using N = num<L>;
@@ -270,120 +250,7 @@ __device__ __forceinline__ void fx_body(int64_t m, int64_t l, int64_t n, const m
     else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));
     N::store(C.p, off, v);
   };
-  uint32_t rescue = 0u;  // outputs left for the rescue, bit r TN + c
-#pragma unroll
-  for (int r = 0; r < TM; ++r)
-#pragma unroll
-    for (int c = 0; c < TN; ++c) {
-      const int64_t gi = i0 + ty + r * NY, gj = j0 + tx + c * NX;
-      if (gi < m && gj < n) {
-        if (fx::acc_mag_below<NW>(acc[r][c], fxkeep<L>::bits)) {
-          rescue |= 1u << (r * TN + c);
-          continue;
-        }
-        finish(gi, gj, acc[r][c], row_f[ty + r * NY] + col_f[tx + c * NX] + P::LSB0);
-      }
-    }
-  // Outputs whose row / column window kept fewer than 53 L significant bits,
-  // recomputed with the window at their own largest term (fx_rescue.cuh);
-  // rare, and run when no accumulator is live any more.
-#pragma unroll 1
-  for (int b = 0; b < TM * TN; ++b) {
-    if (!((rescue >> b) & 1u)) continue;
-    const int64_t gi = i0 + ty + (b / TN) * NY, gj = j0 + tx + (b % TN) * NX;
-    fxacc<L> x = fx_rescue<L, PRE>(l, A, B, Ax, Bx, gi, gj);
-    finish(gi, gj, x.w, x.lsb);
-  }
-}
-
-// The DD tile in the pre-shifted form (fx_pre.cuh).
-template <bool PRE>
-__device__ __forceinline__ void fx_pre(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B, const mat& C,
-                                       int mode, int64_t i0, int64_t j0, fx_smem<2>& sm, const fxop& Ax,
-                                       const fxop& Bx) {
-  using P = fxcfg<2>;
-  constexpr int BM = P::BM, BN = P::BN, BK = P::BK, TM = P::TM, TN = P::TN, NW = P::NW;
-  static_assert(P::W == 4 && NW == 6, "pre-shifted form: DD words and window");
-  constexpr int NX = BN / TN, NY = BM / TM, NT = NX * NY;
-  auto& row_f = sm.row_f;
-  auto& col_f = sm.col_f;
-  const int tid = threadIdx.x;
-  const int tx = tid % NX, ty = tid / NX;
-
-  // window words 1 .. 5 (word 0 stays 0)
-  uint32_t acc[TM][TN][5];
-#pragma unroll
-  for (int r = 0; r < TM; ++r)
-#pragma unroll
-    for (int c = 0; c < TN; ++c)
-#pragma unroll
-      for (int w = 0; w < 5; ++w) acc[r][c][w] = 0u;
-  for (int64_t k0 = 0; k0 < l; k0 += BK) {
-#pragma unroll
-    for (int idx = tid; idx < BM * BK; idx += NT) {
-      const int r = idx / BK, c = idx % BK;
-      const int64_t gi = i0 + r, gk = k0 + c;
-      const bool ok = gi < m && gk < l;
-      if constexpr (PRE) {
-        stage_pre<2, false>(ok, Ax, gi * Ax.ld + gk, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
-      } else {
-        double x[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) x[q] = ok ? A.p[q][gi * A.ld + gk] : 0.0;
-        stage<2, false>(x, row_f[r], &sm.Aw[0][c][r], BK * (BM + 1), &sm.Ae[c][r]);
-      }
-    }
-#pragma unroll
-    for (int idx = tid; idx < BK * BN; idx += NT) {
-      const int r = idx / BN, c = idx % BN;
-      const int64_t gk = k0 + r, gj = j0 + c;
-      const bool ok = gk < l && gj < n;
-      if constexpr (PRE) {
-        stage_pre<2, false>(ok, Bx, gk * Bx.ld + gj, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
-      } else {
-        double x[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) x[q] = ok ? B.p[q][gk * B.ld + gj] : 0.0;
-        stage<2, false>(x, col_f[c], &sm.Bw[0][r][c], BK * BN, &sm.Be[r][c]);
-      }
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int kk = 0; kk < BK; ++kk) {
-      uint32_t a[TM][4], b[TN][4], sa[TM], sb[TN];
-#pragma unroll
-      for (int r = 0; r < TM; ++r) {
-        const uint4 q = sm.Aw[0][kk][ty + r * NY];
-        a[r][0] = q.x; a[r][1] = q.y; a[r][2] = q.z; a[r][3] = q.w;
-        sa[r] = (uint32_t)sm.Ae[kk][ty + r * NY].y;
-      }
-#pragma unroll
-      for (int c = 0; c < TN; ++c) {
-        const uint4 q = sm.Bw[0][kk][tx + c * NX];
-        b[c][0] = q.x; b[c][1] = q.y; b[c][2] = q.z; b[c][3] = q.w;
-        sb[c] = (uint32_t)sm.Be[kk][tx + c * NX].y;
-      }
-#pragma unroll
-      for (int r = 0; r < TM; ++r)
-#pragma unroll
-        for (int c = 0; c < TN; ++c) {
-          uint32_t q[4];
-          fx::mul_top_hi<4>(a[r], b[c], q);
-          pre_add(acc[r][c], q, sa[r] ^ sb[c]);
-        }
-    }
-    __syncthreads();
-  }
-
-  using N = num<2>;
-  auto finish = [&](int64_t gi, int64_t gj, uint32_t(&w)[NW], int lsb) {
-    N::T v = window_round<2, NW>(w, lsb);
-    const int64_t off = gi * C.ld + gj;
-    if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
-    else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));
-    N::store(C.p, off, v);
-  };
-  uint32_t redo = 0u;  // outputs below fxpre<2>::keep window bits, bit r TN + c
+  uint32_t redo = 0u;  // outputs below fxpre<L>::keep window bits, bit r TN + c
 #pragma unroll
   for (int r = 0; r < TM; ++r)
 #pragma unroll
@@ -391,36 +258,44 @@ __device__ __forceinline__ void fx_pre(int64_t m, int64_t l, int64_t n, const ma
       const int64_t gi = i0 + ty + r * NY, gj = j0 + tx + c * NX;
       if (gi < m && gj < n) {
         uint32_t w[NW];
-        pre_window(acc[r][c], w);
-        if (fx::acc_mag_below<NW>(w, fxpre<2>::keep)) {
+        pre_window<NW>(acc[r][c], w);
+        if (fx::acc_mag_below<NW>(w, fxpre<L>::keep)) {
           redo |= 1u << (r * TN + c);
           continue;
         }
         finish(gi, gj, w, row_f[ty + r * NY] + col_f[tx + c * NX] + P::LSB0);
       }
     }
-  // rare: each such output on its own in the shifted form (then, if needed,
-  // the rescue), when no accumulator is live any more
-#pragma unroll 1
-  for (int t = 0; t < TM * TN; ++t) {
-    if (!((redo >> t) & 1u)) continue;
+  // Such outputs one at a time in the shifted form, each by the whole warp
+  // (the lanes split k; a warp-uniform loop), when no accumulator is live
+  // any more; the owning lane stores the result.
+  const int lane = tid & 31;
+  unsigned pend = __ballot_sync(0xffffffffu, redo != 0u);
+  while (pend) {
+    const int src = __ffs((int)pend) - 1;
+    const uint32_t msrc = __shfl_sync(0xffffffffu, redo, src);
+    const int t = __ffs((int)msrc) - 1;
+    const int ts = (tid & ~31) + src, txs = ts % NX, tys = ts / NX;
     const int r = t / TN, c = t % TN;
-    const int64_t gi = i0 + ty + r * NY, gj = j0 + tx + c * NX;
-    fxacc<2> x = fx_shifted_one<2, PRE>(l, A, B, Ax, Bx, gi, gj, row_f[ty + r * NY] + col_f[tx + c * NX]);
-    finish(gi, gj, x.w, x.lsb);
+    const int64_t gi = i0 + tys + r * NY, gj = j0 + txs + c * NX;
+    fxacc<L> x = warp_shifted_one<L, PRE>(l, A, B, Ax, Bx, gi, gj, row_f[tys + r * NY] + col_f[txs + c * NX]);
+    if (lane == src) {
+      finish(gi, gj, x.w, x.lsb);
+      redo &= ~(1u << t);
+    }
+    pend = __ballot_sync(0xffffffffu, redo != 0u);
   }
 }
 
-// One BM x BN tile of C at (i0, j0): C (mode) A B restricted to the tile.
-// PRE: the operands come converted in Ax, Bx (A and B are then not read).
-// DD: the pre-shifted form (fx_pre.cuh); QD: the shifted form.
+// One BM x BN tile of C at (i0, j0): C (mode) A B restricted to the tile,
+// in the pre-shifted form (fx_pre.cuh). PRE: the operands come converted in
+// Ax, Bx (A and B are then not read).
 template <int L, bool PRE>
 __device__ __forceinline__ void fx_tile(int64_t m, int64_t l, int64_t n, const mat& A, const mat& B,
                                         const mat& C, int mode, int64_t i0, int64_t j0, fx_smem<L>& sm,
                                         const fxop& Ax, const fxop& Bx) {
   fx_maxima<L, PRE>(m, l, n, A, B, i0, j0, sm, Ax, Bx);
-  if constexpr (fxpre<L>::on) fx_pre<PRE>(m, l, n, A, B, C, mode, i0, j0, sm, Ax, Bx);
-  else fx_body<L, PRE>(m, l, n, A, B, C, mode, i0, j0, sm, Ax, Bx);
+  fx_pre<L, PRE>(m, l, n, A, B, C, mode, i0, j0, sm, Ax, Bx);
 }
 
 template <int L>

@@ -1,25 +1,25 @@
 // Elementwise accuracy of the integer-pipe Block product (Kouya 2015,
 // Section 2, Block with DD / QD arithmetic: every c_ij is accurate relative
-// to its own sum_k |a_ik b_kj|).
+// to its own sum_k |a_ik b_kj|): the per-output paths behind the
+// pre-shifted form (fx_pre.cuh).
 //
-// The Block kernels fix the window of an output c_ij from the largest
-// exponent field of row i of A (f_a) and of column j of B (f_b): the window
-// keeps 2^-159 (DD) / 2^-255 (QD) of 2^(f_a + f_b) and truncates below. When
-// the two maxima sit at different k and every actual product a_ik b_kj is
-// far below 2^(f_a + f_b) (row [2^200, 2^-200] times column [2^-200,
-// 2^200]: both products are 1, the window sees nothing), the truncation is
-// not small relative to sum_k |a_ik b_kj|.
+// Shifted form: each term a_ik b_kj of an output is formed at its own scale
+// (fx::mul_top of the operands' full words) and placed E - f(a_ik) - f(b_kj)
+// bits below the top of a window anchored at E; with E = f_a + f_b (the
+// largest exponent fields of row i of A and column j of B) the window keeps
+// 2^-159 (DD) / 2^-255 (QD) of 2^(f_a + f_b) and truncates below. When the
+// two maxima sit at different k and every actual product a_ik b_kj is far
+// below 2^(f_a + f_b) (row [2^200, 2^-200] times column [2^-200, 2^200]:
+// both products are 1, the window sees nothing), that truncation is not
+// small relative to sum_k |a_ik b_kj|.
 //
 // Test and rescue: the window sum S (in window units, error < l units) is
 // accepted when |S| >= 2^(53 L); then sum_k |a_ik b_kj| >= |c_ij| >= 2^(53 L
 // - 1) units and the truncation, l units, is within 2 l 2^-(53 L) of it.
 // Otherwise the output is recomputed with its window anchored at its own
-// largest term: E = max_k (f(a_ik) + f(b_kj)) over the nonzero pairs, each
-// term shifted by E - f(a_ik) - f(b_kj), window LSB at 2^(E + LSB0). The
-// truncation per term is then below 2^-158 (DD) / 2^-254 (QD) of
-// max_k |a_ik b_kj| <= sum_k |a_ik b_kj|. Ordinary inputs (no cancellation
-// beyond 2^-53 of max|a_i.| max|b_.j|) never take the rescue, and their bits
-// are those of the plain window.
+// largest term: E = max_k (f(a_ik) + f(b_kj)) over the nonzero pairs, window
+// LSB at 2^(E + LSB0). The truncation per term is then below 2^-158 (DD) /
+// 2^-254 (QD) of max_k |a_ik b_kj| <= sum_k |a_ik b_kj|.
 #pragma once
 
 #include "fx_round.cuh"
@@ -86,47 +86,49 @@ template <int L> struct fxacc {
   int lsb;
 };
 
-// The window sum of output c_ij with its window anchored at E (every term
-// placed E - f(a_ik) - f(b_kj) bits below the window top, as fx_pair_place),
-// by one thread; with E = f_a + f_b (the row / column maxima) this is the
-// window of the Block kernels' shifted form, term for term.
-template <int L, bool PRE>
-__device__ __forceinline__ void fx_window_at(int64_t l, const mat& A, const mat& B, const fxop& Ax, const fxop& Bx,
-                                             int64_t gi, int64_t gj, int E, uint32_t (&w)[fxwin<L>::NW]) {
-  const int64_t ald = PRE ? Ax.ld : A.ld, bld = PRE ? Bx.ld : B.ld;
+// The exact sum of the 32 lanes' windows, in every lane (a butterfly of
+// multiword two's-complement additions; the order does not matter).
+template <int NW>
+__device__ __forceinline__ void warp_window_sum(uint32_t (&w)[NW]) {
 #pragma unroll
-  for (int t = 0; t < fxwin<L>::NW; ++t) w[t] = 0u;
-  for (int64_t k = 0; k < l; ++k) fx_pair_place<L, PRE>(A, B, Ax, Bx, gi * ald + k, k * bld + gj, E, w);
+  for (int off = 16; off > 0; off >>= 1) {
+    uint32_t o[NW];
+#pragma unroll
+    for (int t = 0; t < NW; ++t) o[t] = __shfl_xor_sync(0xffffffffu, w[t], off);
+    fx::acc_add_mask<NW>(w, o, 0u);
+  }
 }
 
-// One output c_ij recomputed by one thread with the window anchored at its
-// largest term (two passes over k; rare, kept out of line so that the
-// Block kernels' main loops are compiled as without it).
+// Output c_ij in the shifted form by one whole warp (warp-uniform
+// arguments; the lanes split k): the window at anchor fab = f_a + f_b, and,
+// if it keeps fewer than 53 L bits, the window at the largest term. The
+// same terms and exact sums whatever the order; the result in every lane.
 template <int L, bool PRE>
-__device__ __noinline__ fxacc<L> fx_rescue(int64_t l, mat A, mat B, fxop Ax, fxop Bx, int64_t gi, int64_t gj) {
+__device__ __forceinline__ fxacc<L> warp_shifted_one(int64_t l, const mat& A, const mat& B, const fxop& Ax,
+                                                     const fxop& Bx, int64_t gi, int64_t gj, int fab) {
+  constexpr int NW = fxwin<L>::NW;
+  const int lane = threadIdx.x & 31;
   const int64_t ald = PRE ? Ax.ld : A.ld, bld = PRE ? Bx.ld : B.ld;
-  int E = -1;
-  for (int64_t k = 0; k < l; ++k) E = max(E, fx_pair_field<L, PRE>(A, B, Ax, Bx, gi * ald + k, k * bld + gj));
   fxacc<L> r;
 #pragma unroll
-  for (int w = 0; w < fxwin<L>::NW; ++w) r.w[w] = 0u;
-  r.lsb = 0;
-  if (E < 0) return r;  // every term is zero
-  fx_window_at<L, PRE>(l, A, B, Ax, Bx, gi, gj, E, r.w);
-  r.lsb = E + fxwin<L>::LSB0;
-  return r;
-}
-
-// Output c_ij in the shifted form with window anchor fab = f_a + f_b, and,
-// if that window keeps fewer than 53 L bits, the rescue: the result the
-// Block kernels' shifted form gives for it (one thread, out of line).
-template <int L, bool PRE>
-__device__ __noinline__ fxacc<L> fx_shifted_one(int64_t l, mat A, mat B, fxop Ax, fxop Bx, int64_t gi, int64_t gj,
-                                                int fab) {
-  fxacc<L> r;
-  fx_window_at<L, PRE>(l, A, B, Ax, Bx, gi, gj, fab, r.w);
+  for (int t = 0; t < NW; ++t) r.w[t] = 0u;
+  for (int64_t k = lane; k < l; k += 32) fx_pair_place<L, PRE>(A, B, Ax, Bx, gi * ald + k, k * bld + gj, fab, r.w);
+  warp_window_sum<NW>(r.w);
   r.lsb = fab + fxwin<L>::LSB0;
-  if (fx::acc_mag_below<fxwin<L>::NW>(r.w, fxkeep<L>::bits)) r = fx_rescue<L, PRE>(l, A, B, Ax, Bx, gi, gj);
+  if (fx::acc_mag_below<NW>(r.w, fxkeep<L>::bits)) {
+    int E = -1;
+    for (int64_t k = lane; k < l; k += 32) E = max(E, fx_pair_field<L, PRE>(A, B, Ax, Bx, gi * ald + k, k * bld + gj));
+    E = __reduce_max_sync(0xffffffffu, E);
+#pragma unroll
+    for (int t = 0; t < NW; ++t) r.w[t] = 0u;
+    r.lsb = 0;
+    if (E >= 0) {
+      for (int64_t k = lane; k < l; k += 32)
+        fx_pair_place<L, PRE>(A, B, Ax, Bx, gi * ald + k, k * bld + gj, E, r.w);
+      warp_window_sum<NW>(r.w);
+      r.lsb = E + fxwin<L>::LSB0;
+    }
+  }
   return r;
 }
 

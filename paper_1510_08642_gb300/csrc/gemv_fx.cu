@@ -9,17 +9,16 @@
 //   * the largest exponent fields of row i of A and column j of B (a warp
 //     max reduction) fix the window scale, exactly as in the Block kernel;
 //   * lane t accumulates the terms k = t, t + 32, ... into its own window
-//     (fx::to_fixed, fx::mul_top, fx::place_shr);
+//     in the pre-shifted form (fx::to_fixed, shr_words, fx::mul_top_hi);
 //   * the 32 windows are summed exactly across the warp (butterfly of
 //     multiword two's-complement additions; the window has 32 bits of
 //     headroom, enough for l < 2^31 terms in any order);
 //   * lane 0 rounds the window once (window_round) and applies the mode.
-//   * an output whose window sum keeps fewer than 53 L significant bits is
-//     recomputed by the warp with the window at its own largest term
-//     (fx_rescue.cuh), as in the Block kernel.
-// DD takes the pre-shifted form first (fx_pre.cuh) and the shifted form
-// only for an output below its threshold, as the Block kernel does. The
-// result is the one the Block kernel's arithmetic defines: every term
+//   * an output whose window keeps fewer than fxpre<L>::keep bits is
+//     recomputed by the warp in the shifted form, and then, if it keeps
+//     fewer than 53 L significant bits, with the window at its own largest
+//     term (warp_shifted_one, fx_rescue.cuh), as in the Block kernel.
+// The result is the one the Block kernel's arithmetic defines: every term
 // carries the same truncations, and the window sum is exact, so the order
 // of the terms does not matter.
 #include "fx_pre.cuh"
@@ -43,7 +42,7 @@ template <int L>
 __global__ void __launch_bounds__(32 * GV_WARPS) gemv_fx_kernel(int64_t m, int64_t l, int64_t n, mat A, mat B,
                                                                 mat C, int mode) {
   using F = fxwin<L>;
-  constexpr int W = F::W, D = F::D, K = F::K, NW = F::NW;
+  constexpr int W = F::W, NW = F::NW;
   const int lane = threadIdx.x & 31;
   const int64_t e = (int64_t)blockIdx.x * GV_WARPS + (threadIdx.x >> 5);
   if (e >= m * n) return;  // warp-uniform
@@ -58,12 +57,20 @@ __global__ void __launch_bounds__(32 * GV_WARPS) gemv_fx_kernel(int64_t m, int64
   fa = __reduce_max_sync(0xffffffffu, fa);
   fb = __reduce_max_sync(0xffffffffu, fb);
 
-  uint32_t acc[NW];
-  int lsb = fa + fb + F::LSB0;
-  if constexpr (fxpre<L>::on) {
-    // DD: the pre-shifted form (fx_pre.cuh), as the tile kernel stages it;
-    // its window is kept when it reaches fxpre<L>::keep bits
-    uint32_t pa[5] = {0u, 0u, 0u, 0u, 0u};
+  using N = num<L>;
+  auto finish = [&](uint32_t(&w)[NW], int lsb) {
+    typename N::T v = window_round<L, NW>(w, lsb);
+    const int64_t off = i * C.ld + j;
+    if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
+    else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));
+    N::store(C.p, off, v);
+  };
+  {
+    // the pre-shifted form (fx_pre.cuh), as the tile kernel stages it; its
+    // window is kept when it reaches fxpre<L>::keep bits
+    uint32_t pa[NW - 1];
+#pragma unroll
+    for (int t = 0; t < NW - 1; ++t) pa[t] = 0u;
     for (int64_t k = lane; k < l; k += 32) {
       double xa[L], xb[L];
       load_limbs<L>(A, arow + k, xa);
@@ -80,81 +87,18 @@ __global__ void __launch_bounds__(32 * GV_WARPS) gemv_fx_kernel(int64_t m, int64
       fx::mul_top_hi<W>(ma, mb, q);
       pre_add(pa, q, sa ^ sb);
     }
-    pre_window(pa, acc);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      uint32_t o[NW];
-#pragma unroll
-      for (int w = 0; w < NW; ++w) o[w] = __shfl_xor_sync(0xffffffffu, acc[w], off);
-      fx::acc_add_mask<NW>(acc, o, 0u);
-    }
-    if (!fx::acc_mag_below<NW>(acc, fxpre<L>::keep)) {
-      if (lane == 0) {
-        using N = num<L>;
-        typename N::T v = window_round<L, NW>(acc, lsb);
-        const int64_t off = i * C.ld + j;
-        if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
-        else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));
-        N::store(C.p, off, v);
-      }
-      return;  // warp-uniform: every lane holds the total
+    uint32_t acc[NW];
+    pre_window<NW>(pa, acc);
+    warp_window_sum<NW>(acc);
+    if (!fx::acc_mag_below<NW>(acc, fxpre<L>::keep)) {  // warp-uniform: every lane holds the total
+      if (lane == 0) finish(acc, fa + fb + F::LSB0);
+      return;
     }
   }
-  // the shifted form (QD; DD outputs below fxpre<L>::keep bits)
-#pragma unroll
-  for (int w = 0; w < NW; ++w) acc[w] = 0u;
-  for (int64_t k = lane; k < l; k += 32) {
-    double xa[L], xb[L];
-    load_limbs<L>(A, arow + k, xa);
-    load_limbs<L>(B, k * B.ld + j, xb);
-    uint32_t ma[W], mb[W];
-    const int ea = fx::to_fixed<L, W>(xa, ma);
-    const int eb = fx::to_fixed<L, W>(xb, mb);
-    // a zero operand gives a zero product: shift 0 keeps it on the fast path
-    const bool za = (fx::dbits(xa[0]) << 1) == 0u, zb = (fx::dbits(xb[0]) << 1) == 0u;
-    const int sh = (za ? 0 : fa - (ea & 0xFFFF)) + (zb ? 0 : fb - (eb & 0xFFFF));
-    const uint32_t sgn = ((ea ^ eb) >> 16) ? 0xFFFFFFFFu : 0u;
-    uint32_t p[K];
-    fx::mul_top<W, D>(ma, mb, p);
-    fx::place_shr<NW, K>(acc, p, sh, sgn);
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    uint32_t o[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) o[w] = __shfl_xor_sync(0xffffffffu, acc[w], off);
-    fx::acc_add_mask<NW>(acc, o, 0u);
-  }
-  // every lane holds the total: a warp-uniform test, and the rescue of
-  // fx_rescue.cuh with the lanes splitting k
-  if (fx::acc_mag_below<NW>(acc, fxkeep<L>::bits)) {
-    int E = -1;
-    for (int64_t k = lane; k < l; k += 32)
-      E = max(E, fx_pair_field<L, false>(A, B, fxop{}, fxop{}, arow + k, k * B.ld + j));
-    E = __reduce_max_sync(0xffffffffu, E);
-#pragma unroll
-    for (int w = 0; w < NW; ++w) acc[w] = 0u;
-    if (E >= 0) {
-      for (int64_t k = lane; k < l; k += 32)
-        fx_pair_place<L, false>(A, B, fxop{}, fxop{}, arow + k, k * B.ld + j, E, acc);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        uint32_t o[NW];
-#pragma unroll
-        for (int w = 0; w < NW; ++w) o[w] = __shfl_xor_sync(0xffffffffu, acc[w], off);
-        fx::acc_add_mask<NW>(acc, o, 0u);
-      }
-      lsb = E + F::LSB0;
-    }
-  }
-  if (lane == 0) {
-    using N = num<L>;
-    typename N::T v = window_round<L, NW>(acc, lsb);
-    const int64_t off = i * C.ld + j;
-    if (mode == MODE_ADD) v = N::add(N::load(C.p, off), v);
-    else if (mode == MODE_SUB) v = N::add(N::load(C.p, off), N::neg(v));
-    N::store(C.p, off, v);
-  }
+  // below the threshold: the shifted form by the whole warp, then, if
+  // needed, the window at the largest term (fx_rescue.cuh)
+  fxacc<L> x = warp_shifted_one<L, false>(l, A, B, fxop{}, fxop{}, i, j, fa + fb);
+  if (lane == 0) finish(x.w, x.lsb);
 }
 
 }  // namespace

@@ -51,9 +51,9 @@ def test_roofline_of_block_kernel():
     assert abs(r["issue"]["frac"] - issued / b.ISSUE_PEAK) < 1e-12
     assert r["traffic"] == rec["dram_bytes_per_launch"]
     assert abs(r["avg_launch_ms"] - 250.0 / 343) < 1e-12
-    # QD: 56 IMAD per multiply-add
+    # QD: 49 IMAD per multiply-add (mul_top_hi<7>: 21 x 2 + 7)
     rq = b.roofline_of(_prof(macs, 100.0, 343), 4)
-    assert abs(rq["frac"] - macs / 0.100 * 56 / (152 * 64 * 2070e6)) < 1e-12
+    assert abs(rq["frac"] - macs / 0.100 * 49 / (152 * 64 * 2070e6)) < 1e-12
     # tiles converted as staged: the per-tile kernel, whose counts are not committed
     r2 = b.roofline_of(_prof(macs, 100.0, 343, convert_launches=0), 2)
     assert r2["kernel"].startswith("block_fx_kernel<2>") and r2["traffic"] is None and "issue" not in r2
