@@ -581,6 +581,60 @@ __device__ __forceinline__ void panel_column_step(typename num<L>::T (*rows)[PAN
   }
 }
 
+// The interchanges of one panel (row c0 + t with row piv[t], t < w, in
+// order) applied to the columns outside [c0, pe), spread over the grid's
+// threads (all CTAs of the launch, column slices of their own: nothing
+// else touches those columns during the panel). piv: this CTA's copy of the
+// panel's pivots in shared memory. In batches of SWAP_BATCH pivots (at most
+// 2 SWAP_BATCH rows each, their composed permutation worked out once per
+// CTA): the batches in order give the interchanges in order.
+constexpr int SWAP_BATCH = 8;
+
+template <int L>
+__device__ __forceinline__ void panel_swaps(int64_t n, const mat& A, int64_t c0, int64_t pe, const int64_t* piv,
+                                           int w, unsigned int cta, unsigned int ctas) {
+  __shared__ int64_t dst[2 * SWAP_BATCH], src[2 * SWAP_BATCH];
+  __shared__ int cnt;
+  const int64_t outside = n - (pe - c0);
+  for (int t0 = 0; t0 < w; t0 += SWAP_BATCH) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int c = 0;
+      auto slot = [&](int64_t r) {
+        for (int t = 0; t < c; ++t)
+          if (dst[t] == r) return t;
+        dst[c] = r;
+        src[c] = r;
+        return c++;
+      };
+      for (int t = t0; t < w && t < t0 + SWAP_BATCH; ++t) {
+        const int64_t k = c0 + t, p = piv[t];
+        if (p == k || p < 0 || p >= n) continue;
+        const int a = slot(k), b = slot(p);
+        const int64_t x = src[a];
+        src[a] = src[b];
+        src[b] = x;
+      }
+      cnt = c;
+    }
+    __syncthreads();
+    const int nrows = cnt;
+    if (nrows == 0) continue;
+    for (int64_t e = (int64_t)cta * blockDim.x + threadIdx.x; e < outside * L; e += (int64_t)ctas * blockDim.x) {
+      const int q = (int)(e / outside);
+      int64_t col = e % outside;
+      if (col >= c0) col += pe - c0;
+      double v[2 * SWAP_BATCH];
+#pragma unroll
+      for (int t = 0; t < 2 * SWAP_BATCH; ++t)
+        if (t < nrows) v[t] = A.p[q][src[t] * A.ld + col];
+#pragma unroll
+      for (int t = 0; t < 2 * SWAP_BATCH; ++t)
+        if (t < nrows) A.p[q][dst[t] * A.ld + col] = v[t];
+    }
+  }
+}
+
 template <int L>
 __global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t c0, int64_t pe, int64_t R,
                                                        int64_t* ipiv, int64_t* info, int pivot, pub_t* pub,
@@ -595,6 +649,7 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t
   __shared__ int le[PR_MAX], ls[PR_MAX], ue[PANEL_BASE];
   __shared__ partial_t sbest[8];
   __shared__ T srinv;
+  __shared__ int64_t piv_s[PANEL_BASE];  // the panel's pivots, for panel_swaps
   const int tid = threadIdx.x, nw = blockDim.x >> 5;
   const int w = (int)(pe - c0);
   const unsigned int G = gridDim.x;
@@ -647,6 +702,7 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t
     }
     const bool pv = pivot && b.idx >= j && b.idx < n;
     const int64_t p = pv ? b.idx : j;
+    if (tid == 0) piv_s[jc] = p;
     if (pv) get_row<L>(prow, slot[(b.idx - c0) / R].row, w);
     else get_row<L>(prow, rj, w);
     __syncthreads();
@@ -681,6 +737,7 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(int64_t n, mat A, int64_t
     __syncthreads();
   }
   for (int e = tid; e < nr * w; e += blockDim.x) stA<L>(A, r_lo + e / w, c0 + e % w, rows[e / w][e % w]);
+  if (pivot) panel_swaps<L>(n, A, c0, pe, piv_s, w, blockIdx.x, G);
 }
 
 // ---------------------------------------------------------------------------
@@ -704,6 +761,7 @@ struct cl_smem {
   int le[RCL_MAX], ls[RCL_MAX], ue[PANEL_BASE];
   partial_t cand, sbest[8];
   typename num<L>::T rinv;
+  int64_t piv[PANEL_BASE];  // the panel's pivots, for panel_swaps
 };
 
 template <int L>
@@ -752,6 +810,7 @@ __global__ void __launch_bounds__(256) lu_panel_cluster_kernel(int64_t n, mat A,
     __syncthreads();
     const partial_t b = sm.sbest[0];
     const int64_t p = (pivot && b.idx >= j && b.idx < n) ? b.idx : j;
+    if (tid == 0) sm.piv[jc] = p;
     {
       const unsigned int op = (unsigned int)((p - c0) / R), oj = (unsigned int)((j - c0) / R);
       const T* rp = cluster.map_shared_rank(&sm.rows[0][0], op) + (p - c0 - (int64_t)op * R) * PANEL_BASE;
@@ -791,6 +850,7 @@ __global__ void __launch_bounds__(256) lu_panel_cluster_kernel(int64_t n, mat A,
     __syncthreads();
   }
   for (int e = tid; e < nr * w; e += blockDim.x) stA<L>(A, r_lo + e / w, c0 + e % w, sm.rows[e / w][e % w]);
+  if (pivot) panel_swaps<L>(n, A, c0, pe, sm.piv, w, rank, CS);
   cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
@@ -1184,11 +1244,7 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
         cfg.attrs = at;
         cfg.numAttrs = 1;
         cu(cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<L>, n, M, c0, pe, Rc, ipiv, dinfo, (int)pivot));
-        if (pivot && st == DDG_OK) {
-          lu_laswp_kernel<L><<<dim3((unsigned)((n + 127) / 128), L), 128, 0, s>>>(n, M, c0, pe, ipiv);
-          cu(cudaGetLastError());
-        }
-        return;
+        return;  // the kernel applies the panel's interchanges outside it too
       }
       const int64_t R = std::max<int64_t>(8, (prow + gmax - 1) / gmax);
       if (fused_ok && R <= PR_MAX) {
@@ -1199,11 +1255,7 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
         int64_t* ip = ipiv;
         void* args[] = {&nn, &MM, &cc0, &ppe, &RR, &ip, &dinfo, &piv, &pub, &rowj, &psync, &extra};
         cu(cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<L>, dim3(G), dim3(256), args, 0, s));
-        if (pivot && st == DDG_OK) {
-          lu_laswp_kernel<L><<<dim3((unsigned)((n + 127) / 128), L), 128, 0, s>>>(n, M, c0, pe, ipiv);
-          cu(cudaGetLastError());
-        }
-        return;
+        return;  // the kernel applies the panel's interchanges outside it too
       }
       const int64_t nstart = pivot ? (n - c0 + RB - 1) / RB : 1;
       lu_start_kernel<L><<<(unsigned)nstart, 256, 0, s>>>(n, M, c0, pe, part, ipiv, dinfo, pivot, cs);
