@@ -854,45 +854,15 @@ __global__ void __launch_bounds__(256) lu_panel_cluster_kernel(int64_t n, mat A,
   cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
-// The interchanges ipiv[k0 .. k1) (in order, at most 16) applied to every
-// column outside [k0, k1). The composed permutation of the (at most 32)
-// rows involved is worked out once per CTA; then each thread reads those
-// rows of its column (independent loads) and writes them back permuted.
+// The interchanges ipiv[k0 .. k1) (in order, at most PANEL_BASE) applied to
+// every column outside [k0, k1) (the per-column kernels' panels; the fused
+// panel kernels do this themselves): panel_swaps over the grid.
 template <int L>
 __global__ void lu_laswp_kernel(int64_t n, mat A, int64_t k0, int64_t k1, const int64_t* ipiv) {
-  __shared__ int64_t dst[2 * PANEL_BASE], src[2 * PANEL_BASE];
-  __shared__ int cnt;
-  if (threadIdx.x == 0) {
-    int c = 0;
-    auto slot = [&](int64_t r) {
-      for (int t = 0; t < c; ++t)
-        if (dst[t] == r) return t;
-      dst[c] = r;
-      src[c] = r;
-      return c++;
-    };
-    for (int64_t k = k0; k < k1; ++k) {
-      const int64_t p = ipiv[k];
-      if (p == k || p < 0 || p >= n) continue;
-      const int a = slot(k), b = slot(p);
-      const int64_t t = src[a];
-      src[a] = src[b];
-      src[b] = t;
-    }
-    cnt = c;
-  }
-  __syncthreads();
-  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int nrows = cnt;
-  if (col >= n || (col >= k0 && col < k1) || nrows == 0) return;
-  const int q = blockIdx.y;  // limb plane
-  double v[2 * PANEL_BASE];
-#pragma unroll
-  for (int t = 0; t < 2 * PANEL_BASE; ++t)
-    if (t < nrows) v[t] = A.p[q][src[t] * A.ld + col];
-#pragma unroll
-  for (int t = 0; t < 2 * PANEL_BASE; ++t)
-    if (t < nrows) A.p[q][dst[t] * A.ld + col] = v[t];
+  __shared__ int64_t piv[PANEL_BASE];
+  const int w = (int)(k1 - k0);
+  for (int t = threadIdx.x; t < w; t += blockDim.x) piv[t] = ipiv[k0 + t];
+  panel_swaps<L>(n, A, k0, k1, piv, w, blockIdx.x, gridDim.x);
 }
 
 template <int L>
@@ -1266,7 +1236,7 @@ static ddg_status getrf_impl(const char* name, int64_t n, const mat& M, int64_t*
         cu(cudaGetLastError());
       }
       if (pivot && st == DDG_OK) {
-        lu_laswp_kernel<L><<<dim3((unsigned)((n + 127) / 128), L), 128, 0, s>>>(n, M, c0, pe, ipiv);
+        lu_laswp_kernel<L><<<(unsigned)((n * L + 127) / 128), 128, 0, s>>>(n, M, c0, pe, ipiv);
         cu(cudaGetLastError());
       }
       return;
