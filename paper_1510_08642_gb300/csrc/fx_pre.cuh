@@ -43,7 +43,7 @@ template <> struct fxpre<4> { static constexpr int keep = 245; };
 // M >> s for a W-word M (bits shifted out dropped; 0 for s >= 32 W): a
 // funnel shift per word, then whole-word steps of 2 and 1 at fixed indices.
 template <int W>
-__device__ __forceinline__ void shr_words(uint32_t (&M)[W], int s) {
+__host__ __device__ __forceinline__ void shr_words(uint32_t (&M)[W], int s) {
   if (s <= 0) return;
   if (s >= 32 * W) {
 #pragma unroll
@@ -70,6 +70,7 @@ __device__ __forceinline__ void shr_words(uint32_t (&M)[W], int s) {
 // acc (window words 1 .. NW - 1; word 0 stays 0) += the term q (W = NW - 2
 // words) with sign mask s (0 or ~0): (q XOR s, s) plus the carry s & 1
 // (two's complement; word 0 of -q is 0).
+#ifdef __CUDACC__
 __device__ __forceinline__ void pre_add(uint32_t (&acc)[5], const uint32_t (&q)[4], uint32_t s) {
   asm("{\n\t.reg .u32 t;\n\t"
       "add.cc.u32 t, %9, %9;\n\t"
@@ -99,9 +100,11 @@ __device__ __forceinline__ void pre_add(uint32_t (&acc)[8], const uint32_t (&q)[
         "r"(s));
 }
 
+#endif
+
 // The NW-word window (word 0 = 0) of the pre-shifted accumulator.
 template <int NW>
-__device__ __forceinline__ void pre_window(const uint32_t (&acc)[NW - 1], uint32_t (&w)[NW]) {
+__host__ __device__ __forceinline__ void pre_window(const uint32_t (&acc)[NW - 1], uint32_t (&w)[NW]) {
   w[0] = 0u;
 #pragma unroll
   for (int t = 0; t < NW - 1; ++t) w[t + 1] = acc[t];

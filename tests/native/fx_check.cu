@@ -4,6 +4,8 @@
 //   T L x0 .. x(L-1)          -> to_fixed: es M[0] .. M[W-1]   (W = 4 / 7)
 //   M W D a[0..W-1] b[0..W-1]  -> mul_top: p[0 .. 2W-D-1]
 //   H W a[0..W-1] b[0..W-1]    -> mul_top_hi: q[0 .. W-1]           (W = 4 / 7)
+//   S L fa fb xa(L) xb(L)      -> the pre-shifted term a b at the window of the
+//                                 fields fa, fb: window words 0 .. NW-1 (L = 2 / 4)
 //   P NW K sh neg acc[0..NW-1] p[0..K-1] -> place_shr: acc[0 .. NW-1]
 //   N NW W A[0..NW-1]          -> acc_normalize: p M[0..W-1]   (6,4) / (9,7)
 //   R NW s A[0..NW-1]          -> acc_sar: A[0..NW-1]          (NW = 6 / 9)
@@ -20,6 +22,7 @@
 #include <cstring>
 
 #include "fx.cuh"
+#include "fx_pre.cuh"
 #include "fxscalar.cuh"
 
 using namespace ddg;
@@ -62,6 +65,39 @@ static void do_mul_hi() {
   for (int i = 0; i < W; ++i) scan("%u", &b[i]);
   fx::mul_top_hi<W>(a, b, q);
   for (int i = 0; i < W; ++i) std::printf("%u%c", q[i], i + 1 < W ? ' ' : '\n');
+}
+
+// The pre-shifted form's term (fx_pre.cuh) on the host: the operands
+// shifted to the fields fa, fb, the product's upper words (mul_top_hi) and
+// the sign, as the window words 1 .. NW-1 (word 0 = 0) of that one term.
+template <int L, int W, int NW>
+static void do_pre_term() {
+  int fa, fb;
+  scan("%d %d", &fa, &fb);
+  double xa[L], xb[L];
+  for (int q = 0; q < L; ++q) xa[q] = rd();
+  for (int q = 0; q < L; ++q) xb[q] = rd();
+  uint32_t ma[W], mb[W];
+  const int ea = fx::to_fixed<L, W>(xa, ma), eb = fx::to_fixed<L, W>(xb, mb);
+  const bool za = (fx::dbits(xa[0]) << 1) == 0u, zb = (fx::dbits(xb[0]) << 1) == 0u;
+  shr_words<W>(ma, za ? 32 * W : fa - (ea & 0xFFFF));
+  shr_words<W>(mb, zb ? 32 * W : fb - (eb & 0xFFFF));
+  const bool neg = ((((ea >> 16) & 1) != 0) && !za) != ((((eb >> 16) & 1) != 0) && !zb);
+  uint32_t q[W];
+  fx::mul_top_hi<W>(ma, mb, q);
+  uint32_t acc[NW - 1] = {};
+  for (int t = 0; t < W; ++t) acc[t] = q[t];
+  if (neg) {  // two's complement of (q, 0)
+    uint64_t c = 1;
+    for (int t = 0; t < NW - 1; ++t) {
+      const uint64_t v = (uint64_t)(acc[t] ^ 0xFFFFFFFFu) + c;
+      acc[t] = (uint32_t)v;
+      c = v >> 32;
+    }
+  }
+  uint32_t w[NW];
+  pre_window<NW>(acc, w);
+  for (int i = 0; i < NW; ++i) std::printf("%u%c", w[i], i + 1 < NW ? ' ' : '\n');
 }
 
 template <int NW, int K>
@@ -175,6 +211,10 @@ int main() {
       scan("%d %d", &a, &b);
       if (a == 4) do_mul<4, 3>();
       else do_mul<7, 6>();
+    } else if (cmd[0] == 'S') {
+      scan("%d", &a);
+      if (a == 2) do_pre_term<2, 4, 6>();
+      else do_pre_term<4, 7, 9>();
     } else if (cmd[0] == 'H') {
       scan("%d", &a);
       if (a == 4) do_mul_hi<4>();

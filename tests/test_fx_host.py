@@ -129,6 +129,40 @@ def test_mul_top_hi_is_its_definition(fxbin, W):
         assert 0 <= exact - q < 2 * W
 
 
+@pytest.mark.parametrize("L", [2, 4])
+def test_pre_shifted_term_within_its_bound(fxbin, L):
+    """The pre-shifted form's term (fx_pre.cuh: operands shifted to the
+    row / column fields fa, fb, fx::mul_top_hi, the sign) against the exact
+    product, in window units 2^(fa + fb + LSB0): below 2^35.33 (DD) / 2^36
+    (QD) units, the bound the acceptance test at 2^142 / 2^245 units turns
+    into the elementwise bound; zero for small integers within 64 bits of
+    their maxima (both errors vanish there)."""
+    rng = random.Random(200 + L)
+    NW, lsb0, bound = (6, -2204, 2.0 ** 35.33) if L == 2 else (9, -2300, 2.0 ** 36)
+    field = lambda x: max(1, (struct.unpack("<Q", struct.pack("<d", x[0]))[0] >> 52) & 0x7FF)  # noqa: E731
+    cases, lines = [], []
+    for t in range(600):
+        xa, xb = expansion(rng, L, sparse=t % 3 == 0), expansion(rng, L, sparse=t % 5 == 0)
+        fa = field(xa) + rng.choice([0, 0, 1, 3, 17, 40, 90, 130, 300])
+        fb = field(xb) + rng.choice([0, 0, 2, 5, 31, 64, 100, 230])
+        cases.append((xa, xb, fa, fb))
+    for t in range(100):  # small integers within 64 bits of their maxima: exact
+        a, b = rng.randint(-2 ** 20, 2 ** 20) or 1, rng.randint(-2 ** 20, 2 ** 20) or 1
+        xa, xb = [float(a)] + [0.0] * (L - 1), [float(b)] + [0.0] * (L - 1)
+        cases.append((xa, xb, field(xa) + rng.randint(0, 40), field(xb) + rng.randint(0, 20)))
+    for xa, xb, fa, fb in cases:
+        lines.append(f"S {L} {fa} {fb} " + " ".join(hexd(v) for v in xa + xb))
+    for k, ((xa, xb, fa, fb), line) in enumerate(zip(cases, run(fxbin, lines))):
+        w = value([int(v) for v in line.split()])
+        if w >= 1 << (32 * NW - 1):
+            w -= 1 << (32 * NW)
+        exact = sum(Fraction(v) for v in xa) * sum(Fraction(v) for v in xb) / Fraction(2) ** (fa + fb + lsb0)
+        err = abs(Fraction(w) - exact)
+        assert err < bound, (k, float(err))
+        if k >= 600:
+            assert err == 0, (k, xa[0], xb[0], fa, fb)
+
+
 @pytest.mark.parametrize("NW,K", [(6, 5), (9, 8)])
 def test_place_shr_exact(fxbin, NW, K):
     rng = random.Random(NW)
