@@ -474,13 +474,10 @@ void fx_tile_shape(int limbs, int* bm, int* bn) {
 cudaError_t launch_grouped_fx(int limbs, const gtask* tasks, int ntasks, int64_t total_tiles,
                               unsigned long long* counter, double ops, cudaStream_t s) {
   if (ntasks == 0 || total_tiles == 0) return cudaSuccess;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
+  int dev = 0, sms = 0;  // the current device's (a cheap runtime query; no shared cache)
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 152;
   const int per_sm = (limbs == 2 ? fxcfg<2>::MINB : fxcfg<4>::MINB) - 1;  // resident CTAs per SM
   const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)sms * per_sm);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
@@ -498,13 +495,10 @@ cudaError_t launch_grouped_fx(int limbs, const gtask* tasks, int ntasks, int64_t
 cudaError_t launch_grouped_mixed(const gtask* tasks, int ntasks, int64_t total_tiles, unsigned long long* counter,
                                  double ops, cudaStream_t s) {
   if (ntasks == 0 || total_tiles == 0) return cudaSuccess;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
+  int dev = 0, sms = 0;  // the current device's (a cheap runtime query; no shared cache)
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 152;
   const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)sms * (fxcfg<2>::MINB - 1));
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
@@ -525,13 +519,10 @@ inline size_t wv_of(int limbs) { return limbs == 2 ? fx_smem<2>::WV : fx_smem<4>
 cudaError_t launch_grouped_fxc(int limbs, const gctask* tasks, int ntasks, int64_t total_tiles,
                                unsigned long long* counter, double ops, cudaStream_t s) {
   if (ntasks == 0 || total_tiles == 0) return cudaSuccess;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
+  int dev = 0, sms = 0;  // the current device's (a cheap runtime query; no shared cache)
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 152;
   const int per_sm = (limbs == 2 ? fxcfg<2>::MINB : fxcfg<4>::MINB) - 1;
   const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)sms * per_sm);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);

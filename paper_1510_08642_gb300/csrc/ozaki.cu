@@ -35,6 +35,8 @@
 // P = 113 at l = 4096 with 32 INT8 products, where slicing needs 136 for
 // the same precision.
 #include <algorithm>
+#include <mutex>
+#include <set>
 #include <cuda_bf16.h>
 #include <cmath>
 #include <cstring>
@@ -580,13 +582,17 @@ __global__ void oz_crt_recombine_kernel(int64_t m, int64_t n, int N, int P, int6
 // ------------------------------------------------------------------ host --
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// The INT8 kernels' shared-memory attribute, once per device (thread-safe).
 static void set_gemm_attrs() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
-    cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
-    done = true;
-  }
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(dev)) return;
+  cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+  cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+  done.insert(dev);
 }
 
 // Multiword helpers for the CRT constants (little-endian 32-bit words).

@@ -14,7 +14,8 @@ requests that arrive over time:
   (grouped persistent launches of the library); each LU solve takes a slot
   of its own (dd_getrf with Winograd trailing updates, then dd_getrs);
   slots are split between GEMM batches and LU solves so that short products
-  do not wait behind long solves;
+  do not wait behind long solves; a solve's launches are queued by a worker
+  thread of its slot, so that the loop keeps admitting GEMMs meanwhile;
 * continuous: requests that arrive while others run are admitted as slots
   and memory free up, so their work overlaps on the device;
 * completion: a CUDA event per unit of work; latency = completion time on
@@ -144,6 +145,7 @@ class Unit:
     bytes: int
     keep: list = field(default_factory=list)
     batch: object = None
+    future: object = None  # an LU solve still being queued by its worker thread
 
 
 class Server:
@@ -175,9 +177,15 @@ class Server:
         self.workspace_reserve = workspace_reserve
         if workspace_reserve:
             capi.ddg_workspace_reserve(self.dev_index, workspace_reserve)
+        # an LU solve queues thousands of launches; a worker thread per LU
+        # slot queues them (the library's calls release the GIL) while this
+        # loop keeps admitting and launching GEMM batches
+        from concurrent.futures import ThreadPoolExecutor
+        self.workers = ThreadPoolExecutor(max_workers=max(1, self.lu_slots))
 
     def close(self):
-        """Return the reserved workspace to the device."""
+        """Stop the worker threads; return the reserved workspace to the device."""
+        self.workers.shutdown(wait=True)
         if self.workspace_reserve:
             self.torch.cuda.synchronize(self.device)
             capi.ddg_workspace_release(self.dev_index)
@@ -206,7 +214,14 @@ class Server:
         return Unit("gemm", reqs, slot, ev, sum(footprint(r) for r in reqs), keep)
 
     def _start_lu(self, r, slot):
+        fut = self.workers.submit(self._queue_lu, r, slot)
+        return Unit("lu", [r], slot, None, footprint(r), [], future=fut)
+
+    def _queue_lu(self, r, slot):
+        """Worker thread: queue one solve on its slot's stream; returns the
+        completion event and the tensors to keep until then."""
         torch = self.torch
+        torch.cuda.set_device(self.device)
         s = self.streams[slot]
         with torch.cuda.stream(s):
             (A,) = make_operands(r, self.device)
@@ -223,7 +238,7 @@ class Server:
             r.result = b
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
-        return Unit("lu", [r], slot, ev, footprint(r), [A, ipiv, info, ones])
+        return ev, [A, ipiv, info, ones]
 
     # -- loop ---------------------------------------------------------------
     def run(self, requests, poll_s: float = 2e-4):
@@ -266,6 +281,12 @@ class Server:
             # completions
             still = []
             for u in inflight:
+                if u.future is not None:
+                    if not u.future.done():
+                        still.append(u)
+                        continue
+                    u.event, u.keep = u.future.result()  # raises the worker's error, if any
+                    u.future = None
                 if u.event.query():
                     t_dev = ref.elapsed_time(u.event) * 1e-3
                     for r in u.reqs:
