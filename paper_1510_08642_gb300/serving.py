@@ -27,7 +27,11 @@ requests that arrive over time:
   is refused at arrival; a request still queued past its admission deadline
   (seconds after arrival) is cancelled before anything of it is launched.
   Work already on the GPU always runs to completion (kernels are not
-  interrupted), so a deadline bounds the wait for admission, not the run.
+  interrupted), so a deadline bounds the wait for admission, not the run;
+* failures: a unit of work whose library call or device allocation raises
+  (a refused plan, a failed launch, device memory exhausted) ends its
+  requests with status "error" and the reason; its slot is handed back once
+  whatever it had queued has finished, and the loop serves the others.
 
 Every arithmetic step runs in the CUDA library; this module only schedules.
 Operands are generated on the device from a seed per request (uniform
@@ -57,8 +61,8 @@ class Request:
     done: float = math.nan
     result: object = None   # device tensor (C, or x for an LU solve)
     info: int = 0           # LU: 0 or 1 + column of a zero pivot
-    status: str = "queued"  # queued, running, ok, refused, timeout
-    error: str = ""         # why a request was refused or cancelled
+    status: str = "queued"  # queued, running, ok, refused, timeout, error
+    error: str = ""         # why a request was refused, cancelled or failed
     operands: tuple = ()    # with keep_results: (A, B) of a GEMM, (A, b) of a solve
 
     @property
@@ -144,8 +148,9 @@ class Unit:
     event: object
     bytes: int
     keep: list = field(default_factory=list)
-    batch: object = None
     future: object = None  # an LU solve still being queued by its worker thread
+    info: object = None    # an LU solve's device info tensor
+    error: str = ""        # set if queueing the unit's work raised
 
 
 class Server:
@@ -195,23 +200,30 @@ class Server:
     def _start_gemms(self, reqs, slot):
         torch = self.torch
         s = self.streams[slot]
-        keep, probs = [], []
+        keep, probs, error = [], [], ""
         with torch.cuda.stream(s):
-            for r in reqs:
-                A, B = make_operands(r, self.device)
-                C = torch.empty((2, r.n, r.n), dtype=torch.float64, device=self.device)
-                algo = self.gemm_algo if r.n > self.gemm_cutoff else "block"
-                probs.append(problem(A, B, C, algo, self.gemm_cutoff))
-                keep += [A, B]
-                r.result = C
-                if self.keep_results:
-                    r.operands = (A, B)
-            batch = Batch(probs, use_graph=False, stream=s)
-            batch.run(s)
-            batch.close(s)
+            try:
+                for r in reqs:
+                    A, B = make_operands(r, self.device)
+                    C = torch.empty((2, r.n, r.n), dtype=torch.float64, device=self.device)
+                    keep += [A, B, C]
+                    algo = self.gemm_algo if r.n > self.gemm_cutoff else "block"
+                    probs.append(problem(A, B, C, algo, self.gemm_cutoff))
+                    r.result = C
+                    if self.keep_results:
+                        r.operands = (A, B)
+                batch = Batch(probs, use_graph=False, stream=s)
+                try:
+                    batch.run(s)
+                finally:
+                    batch.close(s)
+            except RuntimeError as e:  # the library's refusals, CUDA and allocation errors
+                error = f"{type(e).__name__}: {e}"
+            # recorded in every case: the slot is free again once whatever
+            # was queued on it has run
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
-        return Unit("gemm", reqs, slot, ev, sum(footprint(r) for r in reqs), keep)
+        return Unit("gemm", reqs, slot, ev, sum(footprint(r) for r in reqs), keep, error=error)
 
     def _start_lu(self, r, slot):
         fut = self.workers.submit(self._queue_lu, r, slot)
@@ -219,32 +231,55 @@ class Server:
 
     def _queue_lu(self, r, slot):
         """Worker thread: queue one solve on its slot's stream; returns the
-        completion event and the tensors to keep until then."""
+        completion event, the tensors to keep until then, the device info
+        tensor and the error text ("" if everything was queued)."""
         torch = self.torch
         torch.cuda.set_device(self.device)
         s = self.streams[slot]
+        keep, info, error = [], None, ""
         with torch.cuda.stream(s):
-            (A,) = make_operands(r, self.device)
-            ones = torch.zeros((2, r.n, 1), dtype=torch.float64, device=self.device)
-            ones[0] = 1.0
-            from . import gemm
-            b = gemm(A, ones, algo="block", stream=s)
-            if self.keep_results:  # the system as posed, before A is factored in place
-                r.operands = (A.clone(), b.clone())
-            info = torch.zeros(1, dtype=torch.int64, device=self.device)
-            ipiv = getrf(A, K=self.lu_K, pivot=True, algo=self.lu_algo, cutoff=self.lu_cutoff,
-                         info=info, stream=s)
-            getrs(A, ipiv, b, stream=s)
-            r.result = b
+            try:
+                (A,) = make_operands(r, self.device)
+                ones = torch.zeros((2, r.n, 1), dtype=torch.float64, device=self.device)
+                keep += [A, ones]
+                ones[0] = 1.0
+                from . import gemm
+                b = gemm(A, ones, algo="block", stream=s)
+                keep.append(b)
+                if self.keep_results:  # the system as posed, before A is factored in place
+                    r.operands = (A.clone(), b.clone())
+                info = torch.zeros(1, dtype=torch.int64, device=self.device)
+                keep.append(info)
+                ipiv = getrf(A, K=self.lu_K, pivot=True, algo=self.lu_algo, cutoff=self.lu_cutoff,
+                             info=info, stream=s)
+                keep.append(ipiv)
+                getrs(A, ipiv, b, stream=s)
+                r.result = b
+            except RuntimeError as e:  # the library's refusals, CUDA and allocation errors
+                error = f"{type(e).__name__}: {e}"
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
-        return ev, [A, ipiv, info, ones]
+        return ev, keep, info, error
+
+    # -- device clock -------------------------------------------------------
+    def _clock_start(self):
+        """Drain the device and record the run's time origin on it."""
+        torch = self.torch
+        torch.cuda.synchronize(self.device)
+        self._ref = torch.cuda.Event(enable_timing=True)
+        self._ref.record(torch.cuda.current_stream(self.device))
+        torch.cuda.synchronize(self.device)
+
+    def _device_seconds(self, event) -> float:
+        """Seconds from the run's time origin to a completed event."""
+        return self._ref.elapsed_time(event) * 1e-3
 
     # -- loop ---------------------------------------------------------------
     def run(self, requests, poll_s: float = 2e-4):
         """Serve `requests` (arrival times relative to the start); returns stats.
-        Refused and cancelled requests end with status "refused" / "timeout"
-        and their reason in `error`; the others with status "ok"."""
+        Refused, cancelled and failed requests end with status "refused" /
+        "timeout" / "error" and their reason in `error`; the others with
+        status "ok"."""
         torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival)
         for r in requests:
@@ -255,10 +290,7 @@ class Server:
         if not free_gemm:
             free_gemm = free_lu  # one shared pool
         used = 0
-        torch.cuda.synchronize(self.device)
-        ref = torch.cuda.Event(enable_timing=True)
-        ref.record(torch.cuda.current_stream(self.device))
-        torch.cuda.synchronize(self.device)
+        self._clock_start()
         t0 = time.perf_counter()
         done = 0
         ip = 0
@@ -285,15 +317,19 @@ class Server:
                     if not u.future.done():
                         still.append(u)
                         continue
-                    u.event, u.keep = u.future.result()  # raises the worker's error, if any
+                    # raises only what the worker did not catch (a bug)
+                    u.event, u.keep, u.info, u.error = u.future.result()
                     u.future = None
                 if u.event.query():
-                    t_dev = ref.elapsed_time(u.event) * 1e-3
+                    t_dev = self._device_seconds(u.event)
                     for r in u.reqs:
                         r.done = t_dev
+                        if u.error:
+                            r.status, r.error, r.result = "error", u.error, None
+                            continue
                         r.status = "ok"
-                        if u.kind == "lu":
-                            r.info = int(u.keep[2].item())
+                        if u.info is not None:
+                            r.info = int(u.info.item())
                         if not self.keep_results:
                             r.result = None
                     used -= u.bytes
@@ -344,10 +380,11 @@ class Server:
 
 def stats(requests) -> dict:
     """p50 / p99 latency and throughput of the served requests per kind, and
-    the counts of refused and cancelled ones."""
+    the counts of refused, cancelled and failed ones."""
     out = {}
     for kind in ("gemm", "lu", "all"):
-        rs = [r for r in requests if (kind == "all" or r.kind == kind) and r.status not in ("refused", "timeout")]
+        rs = [r for r in requests
+              if (kind == "all" or r.kind == kind) and r.status not in ("refused", "timeout", "error")]
         if not rs:
             continue
         lat = np.array([r.latency for r in rs]) * 1e3
@@ -358,6 +395,7 @@ def stats(requests) -> dict:
                      "work_G2mnl_per_s": sum(r.work for r in rs) / span / 1e9 if span > 0 else float("inf")}
     out["refused"] = sum(r.status == "refused" for r in requests)
     out["timeout"] = sum(r.status == "timeout" for r in requests)
+    out["error"] = sum(r.status == "error" for r in requests)
     return out
 
 
