@@ -248,7 +248,9 @@ ddg_status dd_gemm_noalloc(int64_t m, int64_t l, int64_t n, dd_mat A, dd_mat B, 
  * Winograd recursion is expanded breadth-first, the fused passes of one
  * depth share a launch, and every base-case Block product of the batch
  * shares one launch per limb count (tiles taken from a global counter).
- * Problems must write disjoint C; A and B may be shared.
+ * Problems must write disjoint C; A and B may be shared. A problem whose C
+ * overlaps its own A or B is DDG_EINVAL; C overlapping another problem's
+ * matrices is not checked (undefined results).
  */
 typedef struct {
   int32_t limbs;   /* 2 (DD) or 4 (QD) */

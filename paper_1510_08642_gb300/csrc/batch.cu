@@ -200,7 +200,17 @@ static bool bad_problem(const ddg_problem& p, std::string& why) {
       if (!x[q]) { why = std::string(nm) + ": null plane"; return true; }
     return false;
   };
-  return bad(p.A, p.lda, p.m, p.l, "A") || bad(p.B, p.ldb, p.l, p.n, "B") || bad(p.C, p.ldc, p.m, p.n, "C");
+  if (bad(p.A, p.lda, p.m, p.l, "A") || bad(p.B, p.ldb, p.l, p.n, "B") || bad(p.C, p.ldc, p.m, p.n, "C"))
+    return true;
+  auto planes = [&](double* const* x, int64_t ld) {
+    return mat{{x[0], x[1], L == 4 ? x[2] : nullptr, L == 4 ? x[3] : nullptr}, ld};
+  };
+  const mat A = planes(p.A, p.lda), B = planes(p.B, p.ldb), C = planes(p.C, p.ldc);
+  if (overlaps(L, C, p.m, p.n, A, p.m, p.l) || overlaps(L, C, p.m, p.n, B, p.l, p.n)) {
+    why = "C overlaps A or B";
+    return true;
+  }
+  return false;
 }
 
 }  // namespace ddg

@@ -408,7 +408,7 @@ static bool region_overlap(const double* x, int64_t xr, int64_t xc, int64_t xld,
   return false;
 }
 
-static bool overlaps(int L, const mat& X, int64_t xr, int64_t xc, const mat& Y, int64_t yr, int64_t yc) {
+bool overlaps(int L, const mat& X, int64_t xr, int64_t xc, const mat& Y, int64_t yr, int64_t yc) {
   if (xr == 0 || xc == 0 || yr == 0 || yc == 0) return false;
   for (int p = 0; p < L; ++p)
     for (int q = 0; q < L; ++q)

@@ -203,3 +203,39 @@ def test_lu_arguments_checked():
     q.x[3] = 0
     assert lib.qd_getrf(8, q, piv, 4, 1, None, None, None) == E and "null plane" in capi.last_error()
     assert lib.qd_getrs(8, 1, q, piv, q, None) == E and capi.last_error().startswith("qd_getrs")
+
+
+@no_device
+def test_batch_problem_overlap_checked():
+    """A batch problem whose C overlaps its own A or B is refused, like
+    dd_gemm; views of one matrix that share no element are accepted."""
+    lib = capi.load()
+    h = ctypes.c_void_p()
+    M = FAKE  # one made-up 16 x 16 DD matrix (planes 1 GiB apart), ld 16
+
+    def prob(a_col, c_col, m=8, l=4, n=4):
+        p = capi.ddg_problem()
+        p.limbs, p.mode, p.m, p.l, p.n = 2, 0, m, l, n
+        p.algo, p.cutoff = capi.DDG_BLOCK, 64
+        for q in range(2):
+            p.A[q] = M + q * (1 << 30) + 8 * a_col
+            p.B[q] = FAKE + (1 << 33) + q * (1 << 30)
+            p.C[q] = M + q * (1 << 30) + 8 * c_col
+        p.lda = p.ldc = 16
+        p.ldb = n
+        return p
+
+    # C in columns 2..5 overlaps A in columns 0..3 of the same rows
+    probs = (capi.ddg_problem * 1)(prob(0, 2))
+    assert lib.ddg_batch_create_ex(ctypes.byref(h), 1, probs, 0, 0, None) == capi.DDG_EINVAL
+    assert "problem 0: C overlaps A or B" in capi.last_error()
+    # C in columns 4..7 and A in columns 0..3: interleaved rows, no shared element
+    probs = (capi.ddg_problem * 1)(prob(0, 4))
+    lib.ddg_batch_create_ex(ctypes.byref(h), 1, probs, 0, 0, None)
+    assert not capi.last_error().startswith("problem"), capi.last_error()
+    # C's lo plane on A's hi plane
+    p = prob(0, 4)
+    p.C[1] = p.A[0]
+    probs = (capi.ddg_problem * 1)(p)
+    assert lib.ddg_batch_create_ex(ctypes.byref(h), 1, probs, 0, 0, None) == capi.DDG_EINVAL
+    assert "C overlaps A or B" in capi.last_error()
