@@ -183,6 +183,10 @@ static ddg_status enqueue(ddg_batch_s* b, cudaStream_t s) {
   return DDG_OK;
 }
 
+// Do the limb planes of X (xr x xc) and Y (yr x yc) share an element?
+// (gemm.cu: exact for views with one leading dimension, else conservative.)
+bool overlaps(int L, const mat& X, int64_t xr, int64_t xc, const mat& Y, int64_t yr, int64_t yc);
+
 static bool bad_problem(const ddg_problem& p, std::string& why) {
   const int L = p.limbs;
   if (L != 2 && L != 4) { why = "limbs must be 2 or 4"; return true; }

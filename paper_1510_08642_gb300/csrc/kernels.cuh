@@ -214,10 +214,6 @@ ddg_status set_error(ddg_status st, const std::string& msg);
 
 // Temporaries of a call: the library's workspace pool of the current device
 // (pool.cu), stream-ordered like cudaMallocAsync / cudaFreeAsync.
-// Do the limb planes of X (xr x xc) and Y (yr x yc) share an element?
-// Exact for views with one leading dimension, conservative otherwise.
-bool overlaps(int L, const mat& X, int64_t xr, int64_t xc, const mat& Y, int64_t yr, int64_t yc);
-
 cudaError_t ws_alloc(void** p, size_t bytes, cudaStream_t s);
 cudaError_t ws_free(void* p, cudaStream_t s);
 
