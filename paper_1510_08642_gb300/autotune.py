@@ -61,17 +61,22 @@ def default_choice(limbs: int, m: int, l: int, n: int):
     return "block", 512
 
 
+def _read_table(path: str) -> dict:
+    """The stored tables by GPU name ({} if the file is absent or unreadable)."""
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    return data if isinstance(data, dict) else {}
+
+
 class Tuner:
     def __init__(self, path: str | None = None):
         from . import build
         self.path = path or os.environ.get("DDG_TUNE_TABLE") or os.path.join(build.OUT_DIR, "tune.json")
         self.gpu = self._gpu_name()
-        self.table = {}
-        if os.path.exists(self.path):
-            try:
-                self.table = json.load(open(self.path)).get(self.gpu, {})
-            except (OSError, ValueError):
-                self.table = {}
+        self.table = _read_table(self.path).get(self.gpu, {})
 
     @staticmethod
     def _gpu_name() -> str:
@@ -190,12 +195,7 @@ class Tuner:
         return dict(algo=algo, cutoff=cutoff, accum="fx", slices=0)
 
     def save(self):
-        data = {}
-        if os.path.exists(self.path):
-            try:
-                data = json.load(open(self.path))
-            except (OSError, ValueError):
-                data = {}
+        data = _read_table(self.path)
         data[self.gpu] = self.table
         os.makedirs(os.path.dirname(self.path) or ".", exist_ok=True)
         tmp = self.path + f".tmp{os.getpid()}"

@@ -54,3 +54,14 @@ def test_moduli_for_meets_the_precision():
         need = bits + (l - 1).bit_length()
         assert N >= 2 and capi.ddg_ozaki2_precision(N, l) >= need
         assert capi.ddg_ozaki2_precision(N - 1, l) < need
+
+
+def test_unreadable_table_starts_empty(tmp_path):
+    bad = tmp_path / "tune.json"
+    for text in ("{not json", "[1, 2]"):
+        bad.write_text(text)
+        t = autotune.Tuner(str(bad))
+        assert t.table == {} and t.choose(2, 4096, 4096, 4096) == ("winograd", 256)
+    t.table["2:9:9:9"] = {"algo": "block", "cutoff": 512, "seconds": 1e-3}
+    t.save()  # replaces the unreadable file
+    assert autotune.Tuner(str(bad)).choose(2, 512, 512, 512) == ("block", 512)
