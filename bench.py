@@ -457,8 +457,33 @@ def time_gpu(P, torch, w, dA, dB, dC, cutoff, steps, warmup, stream, dist=None, 
             capi.ddg_profile_begin()
             P.gemm(dA, dB, dC, streams=1, **kw)
             torch.cuda.synchronize()
-            prof["pass_isolated"] = capi.ddg_profile_end()["pass"]
+            iso = capi.ddg_profile_end()
+            prof["pass_isolated"] = iso["pass"]
+            prof["convert_isolated"] = iso["convert"]
     return ms, prof, launches
+
+
+def pass_and_conversion_rates(prof):
+    """The fused quadrant passes' and the operand conversions' rates:
+    algorithmic bytes (and sums / converted elements) over the sum of their
+    launch durations, from the profiled step with the sub-products in order
+    on one stream where there is one (none of their launches overlaps
+    another kernel there), else from the profiled step itself (a Block
+    product forks nothing)."""
+    out = {}
+    for kind, name, rate in (("pass", "passes", "sums_per_s"), ("convert", "conversions", "elements_per_s")):
+        iso = prof.get(kind + "_isolated")
+        k = iso if iso is not None else prof[kind]
+        if not k["launches"] or k["sum_ms"] <= 0:
+            continue
+        sec = k["sum_ms"] * 1e-3
+        out[name] = {"launches": int(k["launches"]), "sum_ms": k["sum_ms"],
+                     "GB_per_s": k["bytes"] / sec / 1e9, "hbm_frac": k["bytes"] / sec / 1e9 / HBM_GBS,
+                     rate: k["ops"] / sec,
+                     "measured": "algorithmic bytes over the sum of the launch durations, in a profiled step "
+                                 + ("with the sub-products on one stream (no launch overlaps another kernel)"
+                                    if iso is not None else "of a product that forks nothing")}
+    return out
 
 
 def run_e2e(P, torch, w, args, dist, device, stream, hA, hB, hC, dA, dB, dC, cutoff, world):
@@ -799,21 +824,7 @@ def run_ours(args, w):
         "value": 2.0 * FP64_PEAK / PINNED_MAC_OPS[limbs] / 1e9,
         "frac": value / world / (2.0 * FP64_PEAK / PINNED_MAC_OPS[limbs] / 1e9),
         "note": "2 x FP64 peak / FP64 instructions of the pinned multiply-add (DD 27, QD 218)"}
-    passes = prof.get("pass_isolated") or prof["pass"]
-    if passes["launches"]:
-        line["passes"] = {"launches": int(passes["launches"]), "sum_ms": passes["sum_ms"],
-                          "GB_per_s": passes["bytes"] / (passes["sum_ms"] * 1e-3) / 1e9,
-                          "hbm_frac": passes["bytes"] / (passes["sum_ms"] * 1e-3) / 1e9 / HBM_GBS,
-                          "sums_per_s": passes["ops"] / (passes["sum_ms"] * 1e-3),
-                          "measured": "algorithmic bytes of the fused quadrant passes over the sum of their "
-                                      "launch durations, in a profiled step with the sub-products on one "
-                                      "stream (no pass overlaps another kernel)"}
-    conv = prof["convert"]
-    if conv["launches"]:
-        line["conversions"] = {"launches": int(conv["launches"]), "busy_ms": conv["busy_ms"] / prof["steps"],
-                               "GB_per_s": conv["bytes"] / (conv["busy_ms"] * 1e-3) / 1e9,
-                               "hbm_frac": conv["bytes"] / (conv["busy_ms"] * 1e-3) / 1e9 / HBM_GBS,
-                               "elements_per_s": conv["ops"] / (conv["busy_ms"] * 1e-3)}
+    line.update(pass_and_conversion_rates(prof))
     dC_keep = dC
     del dA, dB, hA, hB, hC
     torch.cuda.empty_cache()

@@ -119,3 +119,23 @@ def test_oracle_check_of_sampled_results():
           "x": X, "normA_inf": float(np.abs(A[0]).sum(axis=1).max())}
     r = b.cpu_oracle_check([lu])["lu"]
     assert r["residual_rel"] == 0.0 and r["within_bound"]
+
+
+def test_pass_and_conversion_rates_from_the_one_stream_step():
+    b = _bench()
+    z = {"launches": 0, "sum_ms": 0.0, "busy_ms": 0.0, "ops": 0.0, "bytes": 0.0}
+    prof = {"pass": dict(z, launches=300, sum_ms=40.0, busy_ms=9.0, bytes=8e9, ops=1e9),
+            "convert": dict(z, launches=343, sum_ms=90.0, busy_ms=58.0, bytes=4e9, ops=3e8),
+            "pass_isolated": dict(z, launches=300, sum_ms=10.0, busy_ms=10.0, bytes=8e9, ops=1e9),
+            "convert_isolated": dict(z, launches=343, sum_ms=2.0, busy_ms=2.0, bytes=4e9, ops=3e8)}
+    r = b.pass_and_conversion_rates(prof)
+    # bytes over the summed durations of the one-stream step, not the overlapped seven-stream figures
+    assert abs(r["passes"]["GB_per_s"] - 800.0) < 1e-9 and abs(r["conversions"]["GB_per_s"] - 2000.0) < 1e-9
+    assert abs(r["conversions"]["elements_per_s"] - 1.5e11) < 1e-3 and r["passes"]["sums_per_s"] == 1e11
+    assert abs(r["conversions"]["hbm_frac"] - 2000.0 / b.HBM_GBS) < 1e-12
+    assert "one stream" in r["passes"]["measured"] and r["conversions"]["launches"] == 343
+    # a Block product (nothing forks, no isolated step): its own profile; no passes
+    block = {"pass": dict(z), "convert": dict(z, launches=2, sum_ms=0.5, busy_ms=0.5, bytes=1e9, ops=5e7)}
+    r = b.pass_and_conversion_rates(block)
+    assert set(r) == {"conversions"} and abs(r["conversions"]["GB_per_s"] - 2000.0) < 1e-9
+    assert "forks nothing" in r["conversions"]["measured"]
