@@ -14,12 +14,24 @@ from . import capi
 
 
 def _mat(T, limbs: int):
-    assert T.dtype.is_floating_point and T.element_size() == 8, "float64 planes expected"
-    assert T.dim() == 3 and T.shape[0] == limbs, f"expected shape ({limbs}, rows, cols)"
-    assert T.is_cuda, "device tensor expected"
-    empty = T.shape[1] == 0 or T.shape[2] == 0
-    assert empty or T.stride(2) == 1, "rows must be contiguous"
-    ld = max(T.stride(1), T.shape[2]) if not empty else max(T.shape[2], 1)
+    """The C-ABI view (planes and leading dimension) of a DD / QD tensor of
+    shape (limbs, rows, cols): float64 on a CUDA device, each row contiguous,
+    rows not overlapping. Raises TypeError / ValueError otherwise, so that
+    the library never sees a layout that would take it outside the tensor."""
+    import torch
+    if not isinstance(T, torch.Tensor) or T.dtype != torch.float64:
+        raise TypeError(f"float64 tensor expected, got {getattr(T, 'dtype', type(T))}")
+    if T.dim() != 3 or T.shape[0] != limbs:
+        raise ValueError(f"expected shape ({limbs}, rows, cols), got {tuple(T.shape)}")
+    rows, cols = T.shape[1], T.shape[2]
+    empty = rows == 0 or cols == 0
+    if not empty and cols > 1 and T.stride(2) != 1:
+        raise ValueError("each row must be contiguous (stride 1 along the last dimension)")
+    if not empty and rows > 1 and T.stride(1) < cols:
+        raise ValueError(f"rows overlap (row stride {T.stride(1)} < {cols} columns)")
+    if not T.is_cuda:
+        raise ValueError("CUDA tensor expected")
+    ld = max(T.stride(1), cols) if not empty else max(cols, 1)
     ps = T.stride(0)
     base = T.data_ptr()
     ptrs = [base + q * ps * 8 for q in range(limbs)]
@@ -43,10 +55,16 @@ def gemm(A, B, C=None, algo: str = "winograd", cutoff: int = 512, mode: str = "s
     """
     import torch
 
+    if A.dim() != 3 or B.dim() != 3 or A.shape[0] not in (2, 4):
+        raise ValueError(f"A and B must be (2 or 4, rows, cols) tensors, got {tuple(A.shape)}, {tuple(B.shape)}")
     limbs, m, l = A.shape
+    if B.shape[0] != limbs or B.shape[1] != l:
+        raise ValueError(f"B must be ({limbs}, {l}, n) for A of shape {tuple(A.shape)}, got {tuple(B.shape)}")
     n = B.shape[2]
     if C is None:
         C = torch.empty((limbs, m, n), dtype=torch.float64, device=A.device)
+    elif tuple(C.shape) != (limbs, m, n):
+        raise ValueError(f"C must be {(limbs, m, n)}, got {tuple(C.shape)}")
     o = capi.opts(algo, cutoff, pad, streams, accum, slices)
     s = (stream or torch.cuda.current_stream(A.device)).cuda_stream
     fn = capi.dd_gemm if limbs == 2 else capi.qd_gemm
@@ -60,6 +78,10 @@ def getrf(A, K: int = 64, pivot: bool = True, algo: str = "winograd", cutoff: in
     returns the device ipiv (int64, n)."""
     import torch
 
+    if A.dim() != 3 or A.shape[0] not in (2, 4) or A.shape[1] != A.shape[2]:
+        raise ValueError(f"a square (2 or 4, n, n) matrix expected, got {tuple(A.shape)}")
+    if info is not None and (info.dtype != torch.int64 or info.numel() < 1 or not info.is_cuda):
+        raise ValueError("info must be an int64 CUDA tensor of at least one element")
     limbs, n = A.shape[0], A.shape[1]
     ipiv = torch.empty(n, dtype=torch.int64, device=A.device)
     o = capi.opts(algo, cutoff, False, 7, accum)
@@ -74,7 +96,14 @@ def getrs(LU, ipiv, B, stream=None):
     """Solve with dd_getrs / qd_getrs; B (limbs, n, nrhs) is overwritten with X."""
     import torch
 
+    if LU.dim() != 3 or LU.shape[0] not in (2, 4) or LU.shape[1] != LU.shape[2]:
+        raise ValueError(f"a square (2 or 4, n, n) factor expected, got {tuple(LU.shape)}")
+    if B.dim() != 3 or B.shape[0] != LU.shape[0] or B.shape[1] != LU.shape[1]:
+        raise ValueError(f"B must be {(LU.shape[0], LU.shape[1])} x nrhs, got {tuple(B.shape)}")
     limbs, n, nrhs = B.shape
+    if (ipiv.dtype != torch.int64 or ipiv.dim() != 1 or ipiv.numel() < n or not ipiv.is_cuda
+            or not ipiv.is_contiguous()):
+        raise ValueError(f"ipiv must be a contiguous int64 CUDA tensor of {n} entries")
     s = (stream or torch.cuda.current_stream(LU.device)).cuda_stream
     fn = capi.dd_getrs if limbs == 2 else capi.qd_getrs
     capi.check(fn(n, nrhs, _mat(LU, limbs), ipiv.data_ptr(), _mat(B, limbs), s))
@@ -83,7 +112,11 @@ def getrs(LU, ipiv, B, stream=None):
 
 def problem(A, B, C, algo: str = "block", cutoff: int = 512, mode: str = "set"):
     """A ddg_problem for the batched entry points from three device tensors."""
+    if A.dim() != 3 or B.dim() != 3 or C.dim() != 3 or A.shape[0] not in (2, 4):
+        raise ValueError("A, B and C must be (2 or 4, rows, cols) tensors")
     limbs = A.shape[0]
+    if B.shape[0] != limbs or B.shape[1] != A.shape[2] or tuple(C.shape) != (limbs, A.shape[1], B.shape[2]):
+        raise ValueError(f"shapes {tuple(A.shape)} x {tuple(B.shape)} -> {tuple(C.shape)} do not agree")
     p = capi.ddg_problem()
     p.limbs = limbs
     p.mode = capi.MODES[mode]
