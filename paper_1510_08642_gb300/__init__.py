@@ -130,19 +130,24 @@ def problem(A, B, C, algo: str = "block", cutoff: int = 512, mode: str = "set"):
         setattr(p, "ld" + name.lower(), mt.ld)
     p.algo = capi.ALGOS[algo]
     p.cutoff = cutoff
+    p._tensors = (A, B, C)  # a plan made from p keeps them alive (Batch holds its problems)
     return p
 
 
 class Batch:
-    """A batch plan (ddg_batch): grouped launches, optionally a CUDA graph."""
+    """A batch plan (ddg_batch): grouped launches, optionally a CUDA graph.
+    The plan addresses the problems' matrices by pointer; it holds the
+    problems made by `problem`, and with them their tensors, so that none is
+    freed while the plan can still run."""
 
     def __init__(self, problems, use_graph: bool = False, stream=None, one_launch: bool = False):
         """one_launch: every base-case product (DD and QD) in one persistent
         grouped launch, tiles converted as staged (DDG_BATCH_ONE_LEAF_LAUNCH;
         the same bits)."""
         import torch
+        self.problems = list(problems)
         self.stream = stream or torch.cuda.current_stream()
-        self.handle = capi.ddg_batch_create(problems, use_graph, self.stream.cuda_stream,
+        self.handle = capi.ddg_batch_create(self.problems, use_graph, self.stream.cuda_stream,
                                             capi.DDG_BATCH_ONE_LEAF_LAUNCH if one_launch else 0)
         self.stats = capi.ddg_batch_get_stats(self.handle)
 

@@ -84,3 +84,29 @@ def test_batch_problem_shapes_must_agree():
         P.problem(z(2, 4, 5), z(2, 5, 3), z(4, 3))
     with pytest.raises(ValueError, match="CUDA"):  # consistent shapes reach the device check
         P.problem(z(2, 4, 5), z(2, 5, 3), z(2, 4, 3))
+
+
+def test_batch_keeps_its_tensors_alive(monkeypatch):
+    """A plan addresses its matrices by pointer: Batch holds the problems,
+    and each problem its tensors, for as long as the plan exists (the
+    device calls are replaced; only the references are checked)."""
+    import gc
+    import types
+    import weakref
+    from paper_1510_08642_gb300 import capi
+    monkeypatch.setattr(P, "_mat", lambda T, limbs: capi.dd_mat(4096, 8192, max(T.shape[2], 1)))
+    calls = []
+    monkeypatch.setattr(capi, "ddg_batch_create", lambda probs, g, s, flags=0: calls.append(len(probs)) or 1)
+    monkeypatch.setattr(capi, "ddg_batch_get_stats", lambda h: {"problems": calls[-1]})
+    monkeypatch.setattr(capi, "ddg_batch_destroy", lambda h, s: None)
+    stream = types.SimpleNamespace(cuda_stream=0)
+    A, B, C = z(2, 4, 5), z(2, 5, 3), z(2, 4, 3)
+    refs = [weakref.ref(t) for t in (A, B, C)]
+    batch = P.Batch([P.problem(A, B, C)], stream=stream)
+    del A, B, C
+    gc.collect()
+    assert all(r() is not None for r in refs) and batch.stats == {"problems": 1}
+    batch.close()
+    del batch
+    gc.collect()
+    assert all(r() is None for r in refs)
