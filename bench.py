@@ -142,6 +142,21 @@ def max_over_ranks(dist, x, device=None):
 
 
 # ------------------------------------------------------------------ clocks --
+def parse_clock_lines(lines):
+    """(SM MHz, max SM MHz, the four throttle flags) per nvidia-smi CSV line
+    of the Clocks query; malformed lines (a partial last line) are skipped."""
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+        except ValueError:
+            continue
+    return rows
+
+
 class Clocks:
     """nvidia-smi sampling every 200 ms while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -173,23 +188,23 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-            except ValueError:
-                continue
+        with open(self.path) as f:
+            rows = parse_clock_lines(f)
         os.unlink(self.path)
-        if not rows:
-            return None
-        sm = sorted(r[0] for r in rows)
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
-                "samples": len(rows), "reasons": reasons}
+        return clock_summary(rows)
+
+
+def clock_summary(rows):
+    """The bench line's clocks: median SM clock under load, the largest
+    maximum clock seen, the sample count and every throttle reason that was
+    active in any sample (None without samples)."""
+    if not rows:
+        return None
+    sm = sorted(r[0] for r in rows)
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+            "samples": len(rows), "reasons": reasons}
 
 
 # --------------------------------------------------------------- CPU leg ----

@@ -139,3 +139,19 @@ def test_pass_and_conversion_rates_from_the_one_stream_step():
     r = b.pass_and_conversion_rates(block)
     assert set(r) == {"conversions"} and abs(r["conversions"]["GB_per_s"] - 2000.0) < 1e-9
     assert "forks nothing" in r["conversions"]["measured"]
+
+
+def test_clock_samples_summarised():
+    b = _bench()
+    lines = ["0, 2070, 2070, 910.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+             "0, 1995, 2070, 1398.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+             "0, 2055, 2070, 1200.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+             "0, 2070, 20",  # a partial last line
+             "[N/A], [N/A]\n"]
+    rows = b.parse_clock_lines(lines)
+    assert len(rows) == 3
+    c = b.clock_summary(rows)
+    assert c == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"]}
+    hot = b.parse_clock_lines(["0, 1500, 2070, 900, 0x48, Active, Active, Not Active, Not Active\n"])
+    assert b.clock_summary(hot)["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    assert b.clock_summary([]) is None
