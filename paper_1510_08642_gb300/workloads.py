@@ -36,8 +36,8 @@ DD_SIMPLE_128 = Workload("dd_simple_n128", 2, 128, "simple", 512, 0, 1)
 DD_BLOCK_2560 = Workload("dd_block_n2560", 2, 2560, "block", 512, 105, 106)
 QD_BLOCK_1536 = Workload("qd_block_n1536", 4, 1536, "block", 512, 107, 108)
 DD_WINOGRAD_2560 = Workload("dd_winograd_n2560", 2, 2560, "winograd", 320, 105, 106)
-# The precision study: the INT8-slice DD product against the FP64-pipe DD
-# Winograd product, n = 4096 and 8192.
+# The precision study: the INT8-slice DD product against the DD Winograd
+# product (integer-pipe Block leaves), n = 4096 and 8192.
 DD_OZAKI_4096_S16 = Workload("dd_ozaki_n4096_s16", 2, 4096, "ozaki", 512, 101, 102, 16)
 DD_OZAKI_4096_S13 = Workload("dd_ozaki_n4096_s13", 2, 4096, "ozaki", 512, 101, 102, 13)
 DD_WINOGRAD_8192 = Workload("dd_winograd_n8192", 2, 8192, "winograd", 256, 109, 110)
