@@ -1,5 +1,5 @@
 // DD product by error-free splitting into INT8 slices (the Ozaki scheme,
-// Ozaki, Ogita, Oishi 2012), as a precision alternative to the FP64-pipe
+// Ozaki, Ogita, Oishi 2012), as a precision alternative to the integer-pipe
 // Block kernel for the DD product C := A B of Kouya 2015, Section 2, Eq. 1.
 //
 // Split (integer pipe, no FP64). Row i of A is scaled by 2^-ea_i, where
