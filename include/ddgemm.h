@@ -179,8 +179,9 @@ ddg_status qd_gemm(int64_t m, int64_t l, int64_t n, qd_mat A, qd_mat B, qd_mat C
  * (Section 4, steps 1-3): right-looking blocked LU with block columns of K
  * (1 <= K <= 512; the paper takes K = alpha n_min) whose trailing update
  * A22 := A22 - L21 U12 is the DD product of `opts` (algo, cutoff, ...;
- * NULL = defaults, Winograd; DDG_OZAKI / DDG_OZAKI2 give the INT8 products'
- * normwise accuracy for the updates) in mode DDG_SUB. On return A holds L
+ * NULL = defaults, Winograd; DDG_OZAKI / DDG_OZAKI2 / DDG_OZAKI2_TC give
+ * the residue and slice products' normwise accuracy for the updates) in
+ * mode DDG_SUB. On return A holds L
  * (unit lower, below the diagonal) and U.
  *   pivot = 1: partial pivoting, pivot of column j = the first row i >= j
  *              with the largest |a_ij| compared as DD; pivot = 0: none (the
@@ -211,7 +212,8 @@ ddg_status dd_getrs(int64_t n, int64_t nrhs, dd_mat LU, const int64_t* ipiv, dd_
 
 /* qd_getrf / qd_getrs: the same LU and solve in quad-double (the paper's
  * QD LU with Winograd updates, Section 4), same arguments with qd_mat; the
- * quotients use one QD reciprocal of each pivot (five-digit long division). */
+ * quotients use one QD reciprocal of each pivot (the DD reciprocal refined
+ * by one Newton step in QD, relative error about 2^-209). */
 ddg_status qd_getrf(int64_t n, qd_mat A, int64_t* ipiv, int32_t K, int32_t pivot, const ddg_opts* opts,
                     int64_t* info, void* stream);
 ddg_status qd_getrs(int64_t n, int64_t nrhs, qd_mat LU, const int64_t* ipiv, qd_mat B, void* stream);
