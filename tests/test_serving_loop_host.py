@@ -149,7 +149,6 @@ def test_every_request_served_slots_exclusive_and_by_kind(device):
     srv = server(slots=4, lu_slots=2, max_batch=5)
     reqs = mix(60, 2000.0, seed=3)
     st = srv.run(reqs)
-    srv.close()
     wait_done(reqs)
     assert all(r.status == "ok" for r in reqs)
     assert st["all"]["count"] == 60 and st["refused"] == st["timeout"] == st["error"] == 0
@@ -163,8 +162,13 @@ def test_every_request_served_slots_exclusive_and_by_kind(device):
         assert len(orders) <= (5 if kind == "gemm" else 1)
         # a slot takes new work only after its previous unit has completed
         assert start <= queued + 1e-9, (kind, idx, queued, start)
-    # requests that arrived together were batched
-    assert max(len(u[5]) for u in device.units if u[0] == "gemm") > 1
+    # requests that arrive together are batched, max_batch at a time
+    device.units.clear()
+    together = mix(24, 0.0, seed=9)
+    srv.run(together)
+    srv.close()
+    sizes = [len(u[5]) for u in device.units if u[0] == "gemm"]
+    assert max(sizes) == 5 and sum(sizes) == sum(r.kind == "gemm" for r in together)
 
 
 def test_work_in_flight_stays_within_the_budget(device):
